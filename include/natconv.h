@@ -1,0 +1,187 @@
+/*
+ * natconv.h — C ABI of the GB300 (sm_103a) library for the stabilised Darcy–Boussinesq
+ * natural-convection state solve, its adjoint and the design sensitivities of
+ * Pollini, Sigmund, Andreasen & Alexandersen, arXiv 1904.00182.
+ *
+ * Model (Sec. 2.2, Eq. goveq): Darcy velocity u = -kappa/mu (grad P + rho0 alpha g T)
+ * (Eq. finaldarcy) substituted into continuity, coupled to the convection-diffusion of T.
+ * Unknowns: P and T at every node of a structured grid of cubic trilinear (Q1) elements
+ * (Sec. 2.2: "the number of DOFs is reduced to only 2"), discretised with the SUPG
+ * Petrov–Galerkin weak form of App. A (Eq. weakstable, Eq. finalsyseq R(s) = M(s) s - f).
+ * The design field gamma (one value per element, 1 = solid, 0 = fluid, Sec. 2.2) is
+ * regularised by a PDE filter (Sec. 5.1) and mapped to permeability and conductivity by RAMP
+ * (Sec. 5.2, Eqs. condRAMP, permRAMP). The state solve is a damped Newton method whose
+ * damping minimises ||R|| (Sec. 5.4); the objective gradient comes from an adjoint solve
+ * (Sec. 5.1). Linear systems: flexible GMRES (Sec. 5.4, Table 4) preconditioned by a
+ * geometric multigrid V-cycle (this library's design; the paper defers the preconditioner).
+ *
+ * Set-up used by every problem (synthetic heated base plate):
+ *   box nx*h x ny*h x nz*h, gravity along -z; the bottom `heated_layers` element layers are a
+ *   solid, non-design heat source region Omega_h (Sec. 2.2) with uniform source Q; P = 0 and
+ *   T = 0 on the top face z = nz*h; every other face carries zero normal flux of fluid and
+ *   heat (natural conditions q_u = q_h = 0 of Eq. goveq's boundary conditions).
+ *
+ * Data layout (all arrays FP64, C order):
+ *   node (i,j,k), 0<=i<=nx, 0<=j<=ny, 0<=k<=nz, has index n = i + (nx+1)*(j + (ny+1)*k);
+ *   element (i,j,k), 0<=i<nx, ..., has index e = i + nx*(j + ny*k);
+ *   a "state vector" is 2*N doubles, node-interleaved pairs (P_n, T_n), N = number of nodes;
+ *   design arrays are E doubles; velocities are 3*E doubles (u_x,u_y,u_z per element).
+ *
+ * Pointers: every array argument may point to host memory (pageable or pinned) or to
+ * device memory of the problem's device: the library copies with unified addressing.
+ * Arguments are borrowed for the duration of the call only. The library owns all of its
+ * device workspace (allocated in nc_create_problem, freed in nc_destroy_problem).
+ *
+ * Streams and threads: each problem runs its work on the CUDA stream given at creation
+ * (NULL = a stream the library creates). Every call returns after its work has finished.
+ * Calls on one problem must not overlap; calls on different problems may run concurrently
+ * from different host threads and then overlap on the device.
+ *
+ * Errors: every call returns an nc_status and never aborts or traps on the device. On
+ * failure, nc_last_error() returns a message for that problem. The call order
+ * set_design -> solve_state -> solve_adjoint -> sensitivities is enforced (NC_ERR_STATE).
+ */
+#ifndef NATCONV_H
+#define NATCONV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NC_OK = 0,
+  NC_ERR_ARG = 1,      /* invalid argument (sizes, NaN or out-of-range design values ...) */
+  NC_ERR_OOM = 2,      /* device allocation failed */
+  NC_ERR_CUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+  NC_ERR_DIVERGED = 4, /* Newton found no damping factor that reduces ||R||, after source ramping */
+  NC_ERR_MAXIT = 5,    /* iteration limit reached before the tolerance */
+  NC_ERR_NAN = 6,      /* a non-finite residual or Krylov quantity appeared */
+  NC_ERR_TIMEOUT = 7,  /* the call exceeded params.timeout_s of wall-clock time */
+  NC_ERR_STATE = 8     /* call order violated (e.g. solve_state before set_design) */
+} nc_status;
+
+enum { NC_PREC_MIXED = 0, NC_PREC_FP64 = 1 };
+enum { NC_OBJ_MEAN_T_HEATED = 0 };
+
+typedef struct nc_problem nc_problem;
+
+typedef struct {
+  int nx, ny, nz; /* elements per direction, each >= 1 */
+  double h;       /* element edge length (> 0) */
+} nc_grid;
+
+/* Parameters; nc_default_params() fills the defaults shown in brackets. */
+typedef struct {
+  double alpha;         /* thermal expansion coefficient (Sec. 2.1) [1e3] */
+  double kappa_f;       /* fluid permeability; <= 0: Eq. nusselt5 with dT = tune_dT, H = 1,
+                           L = 0.5 and unit fluid properties (Sec. 3) [0] */
+  double tune_dT;       /* dT used by Eq. nusselt5 when kappa_f <= 0 [1] */
+  double kappa_ratio;   /* kappa_s / kappa_f [1e-6] */
+  double k_f, k_s;      /* fluid and solid conductivity (Sec. 6.1) [1, 100] */
+  double q_c, q_p;      /* RAMP penalties of Eqs. condRAMP / permRAMP (Sec. 6.2) [8.81, 8] */
+  double Q;             /* heat source in Omega_h; <= 0: total power 1 [0] */
+  int heated_layers;    /* element layers of Omega_h at the bottom [2] */
+  double rho0, mu, cp, g; /* reference density, viscosity, heat capacity, |g| (Sec. 6.1) [1] */
+  double filter_radius; /* PDE filter radius in element sizes (Sec. 6.3) [2.5] */
+  double newton_rtol;   /* stop when ||R_free(s)|| <= newton_rtol * ||R_free(0)|| [1e-8] */
+  int newton_maxit;     /* [50] */
+  double krylov_rtol;   /* upper bound of the FGMRES relative tolerance per Newton step [1e-2] */
+  int krylov_maxit;     /* FGMRES iterations per linear solve [300] */
+  int restart;          /* FGMRES restart length, <= 64 [30] */
+  int precision;        /* NC_PREC_MIXED (FP32 multigrid and Krylov operator, FP64 residual,
+                           orthogonalisation and coarse solve) or NC_PREC_FP64 [MIXED] */
+  int mg_levels;        /* 0: coarsen while every dimension is even [0] */
+  int nu_pre, nu_post;  /* smoothing sweeps [2, 2] */
+  double omega;         /* damping of the block-Jacobi smoother [0.6] */
+  double filter_rtol;   /* relative tolerance of the filter's conjugate gradients [1e-12] */
+  double timeout_s;     /* wall-clock limit of one call [600] */
+} nc_params;
+
+/* Per-solve statistics (any pointer argument of this type may be NULL). */
+typedef struct {
+  int newton_its;        /* Newton steps taken */
+  int krylov_its;        /* FGMRES iterations summed over the steps */
+  int residual_evals;    /* FP64 residual evaluations (including damping trials) */
+  int ramped;            /* 1 if the source ramp (Sec. 5.4) was needed */
+  double rel_residual;   /* final ||R_free|| / ||R_free(0)|| */
+  double res_hist[64];   /* relative residual after each Newton step (first 64) */
+  int krylov_hist[64];   /* FGMRES iterations of each Newton step (first 64) */
+  double t_setup_ms;     /* multigrid set-up time */
+  double t_krylov_ms;    /* FGMRES time */
+  double t_total_ms;     /* wall time of the call */
+  double alg_bytes;      /* algorithmic bytes of the operator kernels launched */
+  long long kernel_launches; /* library kernels launched by the call */
+} nc_stats;
+
+/* Fill *p with the defaults. Returns NC_ERR_ARG if p is NULL. */
+nc_status nc_default_params(nc_params* p);
+
+/* Create a problem on the current CUDA device: validates g and p, resolves kappa_f, and
+ * allocates every device buffer (state, materials, Krylov basis, multigrid hierarchy).
+ * stream: a cudaStream_t or NULL. On success *out owns the problem. */
+nc_status nc_create_problem(const nc_grid* g, const nc_params* p, void* stream, nc_problem** out);
+
+/* Release every device buffer of the problem. Accepts NULL. */
+nc_status nc_destroy_problem(nc_problem* pb);
+
+/* Device bytes nc_create_problem would allocate for (g, p) (for admission control). */
+nc_status nc_footprint_bytes(const nc_grid* g, const nc_params* p, size_t* bytes);
+
+/* Design pipeline, Sec. 5.1-5.2: rho (E values in [0,1], finite; NC_ERR_ARG otherwise) ->
+ * gamma = 1 on Omega_h -> PDE filter -> gamma~ = 1 on Omega_h -> RAMP kappa_e, k_e.
+ * Resets the state to zero unless nc_set_state is called afterwards. */
+nc_status nc_set_design(nc_problem* pb, const double* rho);
+
+/* Warm start (Sec. 5.4): P and T (N values each) become the initial Newton guess. Values on
+ * the Dirichlet top face are forced to 0. Requires a design. */
+nc_status nc_set_state(nc_problem* pb, const double* P, const double* T);
+
+/* Damped Newton state solve (Sec. 5.4) to params.newton_rtol. Requires a design.
+ * On NC_ERR_DIVERGED / NC_ERR_MAXIT the last iterate is kept and stats are filled. */
+nc_status nc_solve_state(nc_problem* pb, nc_stats* stats);
+
+/* Objective (Eq. objdiscr, read as the mean temperature over Omega_h with Galerkin weights)
+ * of the current state. Requires a solved state. */
+nc_status nc_objective(nc_problem* pb, int objective, double* f);
+
+/* Adjoint solve J(s)^T lambda = df/ds on the free DOFs (Sec. 5.1) at the solved state;
+ * writes the objective to *f_out (may be NULL). */
+nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stats* stats);
+
+/* df/drho (E values) by the chain rule through RAMP and the filter transpose; 0 on Omega_h.
+ * Requires a solved adjoint. */
+nc_status nc_sensitivities(nc_problem* pb, double* dfdrho);
+
+/* Copy the solved fields out: P, T (N values each, either may be NULL) and the centroid
+ * Darcy velocity u (3E values, Eq. finaldarcy, may be NULL). */
+nc_status nc_get_fields(const nc_problem* pb, double* P, double* T, double* u);
+
+/* Filtered design gamma~, kappa_e and k_e (E values each; any may be NULL). */
+nc_status nc_get_design_fields(const nc_problem* pb, double* gamma_tilde, double* kappa, double* k);
+
+/* Operator-level entry points: one step of the path on caller data, for parity checks.
+ * s, v, w, out are state vectors (2N doubles). Entries on the Dirichlet top face of v and w
+ * are ignored; the corresponding outputs are: R_d = s_d (residual), 0 (products). */
+
+/* R(s) (Eq. finalsyseq) and ||R_free(s)||^2 (norm2_free may be NULL). Requires a design. */
+nc_status nc_eval_residual(nc_problem* pb, const double* s, double* R, double* norm2_free);
+
+/* Exact Newton Jacobian product J(s) v, including the derivatives of tau and N*, computed in
+ * FP64 (precision = NC_PREC_FP64) or FP32 (NC_PREC_MIXED). Requires a design. */
+nc_status nc_apply_jacobian(nc_problem* pb, const double* s, const double* v, double* out,
+                            int precision);
+
+/* Transposed product J(s)^T w in FP64 (the adjoint operator). Requires a design. */
+nc_status nc_apply_jacobian_transpose(nc_problem* pb, const double* s, const double* w,
+                                      double* out);
+
+/* Message of the last failed call on pb (or of the last failed nc_create_problem if pb is
+ * NULL). Never NULL. */
+const char* nc_last_error(const nc_problem* pb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NATCONV_H */

@@ -1,0 +1,24 @@
+"""GB300 (sm_103a) library for the stabilised Darcy-Boussinesq natural-convection state solve,
+its adjoint and the design sensitivities of Pollini, Sigmund, Andreasen & Alexandersen
+(arXiv 1904.00182).
+
+All arithmetic runs in ``lib/libnatconv.so`` (CUDA kernels behind the C ABI of
+``include/natconv.h``). This module only marshals arguments through ctypes: the names mirror the
+C entry points. There is no CPU fallback: importing the package without the built library raises
+an ImportError that says how to build it (``python -m paper_1904_00182_gb300.build``).
+"""
+
+import ctypes
+import os
+
+from . import _abi
+from ._abi import (NC_OBJ_MEAN_T_HEATED, NC_PREC_FP64, NC_PREC_MIXED, NatConvError, Grid,  # noqa: F401
+                   Params, Stats, default_params, footprint_bytes, load_library)
+from .problem import Problem  # noqa: F401
+
+__all__ = ["Problem", "Grid", "Params", "Stats", "NatConvError", "default_params", "footprint_bytes",
+           "NC_PREC_MIXED", "NC_PREC_FP64", "NC_OBJ_MEAN_T_HEATED", "library_path"]
+
+
+def library_path():
+    return _abi.LIB_PATH

@@ -1,0 +1,1031 @@
+// C ABI of the natconv library: problem object, design pipeline, damped Newton state solve,
+// FGMRES with a geometric-multigrid preconditioner, adjoint and sensitivities.
+//
+// Method (paper sections): design pipeline Sec. 5.1-5.2 (PDE filter, RAMP); Newton with a
+// residual-minimising damping factor, stopping on a relative residual reduction and ramping the
+// heat source when it fails (Sec. 5.4); linear solves by flexible GMRES (Sec. 5.4, Table 4);
+// adjoint sensitivities (Sec. 5.1). The multigrid preconditioner and the precision split are this
+// library's design: in NC_PREC_MIXED the V-cycle and the Krylov operator run in FP32 while the
+// Newton residual, the Krylov orthogonalisation and the coarse solve are FP64, so the outer FP64
+// Newton (state) and refinement (adjoint) iterations recover FP64 accuracy.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "natconv.h"
+#include "nc_launch.h"
+
+using namespace nc;
+
+namespace {
+
+const double kAdjointRtol = 1e-10;
+const int kMaxRestart = 64;
+const int kMaxCoarseDofs = 2048;
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Damping of Sec. 5.4 and the Newton forcing term, shared by state solve and tests.
+double kappa_f_tuned(double alpha, double dT) {
+  // Eq. nusselt5 with H = 1, L = 0.5, beta_m = nu = g = Pr = 1.
+  const double H = 1.0, L = 0.5, Pr = 1.0;
+  return std::pow(H, 1.74) / (std::pow(alpha * dT, 0.42) * L * L) * 0.0324 *
+         std::pow(Pr * Pr / (0.2 + Pr), 0.58);
+}
+
+struct Levels {
+  std::vector<Grid> g;
+  int nf = 0;   // free DOFs of the coarsest level
+};
+
+Levels plan_levels(const Grid& g0, int max_levels) {
+  Levels L;
+  L.g.push_back(g0);
+  while (true) {
+    const Grid& c = L.g.back();
+    if (max_levels > 0 && (int)L.g.size() >= max_levels) break;
+    if (c.nx % 2 || c.ny % 2 || c.nz % 2) break;
+    L.g.push_back(make_grid(c.nx / 2, c.ny / 2, c.nz / 2, c.h * 2.0));
+  }
+  const Grid& c = L.g.back();
+  L.nf = 2 * c.NX * c.NY * c.nz;
+  return L;
+}
+
+template <typename R>
+struct MG {
+  typedef typename Vec2<R>::type R2;
+  std::vector<MGLevelDev<R>> lev;
+  double* Ainv = nullptr;
+  double* W = nullptr;
+  R* ebe0 = nullptr;   // level-0 element matrices, only when the hierarchy has one level
+  int nf = 0;
+};
+
+}  // namespace
+
+struct nc_problem {
+  int device = 0;
+  Grid g;
+  nc_params par;
+  Phys ph;
+  double Q_full = 0.0, kappa_f = 0.0, kappa_s = 0.0, vol_h = 0.0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  // state, design
+  double2 *s = nullptr, *s_try = nullptr, *lam = nullptr, *s_start = nullptr;
+  double *R = nullptr, *R_try = nullptr, *dx = nullptr, *w = nullptr, *rhs = nullptr;
+  double *rho = nullptr, *gamma_t = nullptr, *gsens = nullptr, *u = nullptr;
+  double2 *mat = nullptr, *dmat = nullptr;
+  float2 *mat32 = nullptr, *s32 = nullptr;
+  // Krylov
+  int m = 30;
+  double *V = nullptr, *Z = nullptr;
+  double *part = nullptr, *dres = nullptr, *hres = nullptr;
+  // filter PCG (node vectors)
+  double *fx = nullptr, *fb = nullptr, *fr = nullptr, *fz = nullptr, *fp = nullptr, *fq = nullptr, *fdinv = nullptr;
+  FilterConst F;
+  // multigrid
+  Levels lv;
+  MG<float> mg32;
+  MG<double> mg64;
+  int *dflag = nullptr, *hflag = nullptr;
+  // bookkeeping
+  int stage = 0;         // 0 created, 1 design set, 2 state solved, 3 adjoint solved
+  double ref_norm = 0.0; // ||R_free(0)|| with the full source
+  double t_start = 0.0;
+  Counters cnt;
+};
+
+namespace {
+
+std::string g_create_error = "no error";
+
+nc_status fail(nc_problem* pb, nc_status s, const std::string& msg) {
+  if (pb) pb->err = msg; else g_create_error = msg;
+  return s;
+}
+
+nc_status cuda_fail(nc_problem* pb, cudaError_t e, const char* what) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "CUDA error in %s: %s", what, cudaGetErrorString(e));
+  return fail(pb, e == cudaErrorMemoryAllocation ? NC_ERR_OOM : NC_ERR_CUDA, buf);
+}
+
+#define CK(x)                                                   \
+  do {                                                          \
+    cudaError_t _e = (x);                                       \
+    if (_e != cudaSuccess) return cuda_fail(pb, _e, #x);        \
+  } while (0)
+
+#define CKS(x)                                                  \
+  do {                                                          \
+    nc_status _s = (x);                                         \
+    if (_s != NC_OK) return _s;                                 \
+  } while (0)
+
+template <typename T>
+nc_status dalloc(nc_problem* pb, T** p, size_t count) {
+  size_t b = sizeof(T) * std::max<size_t>(count, 1);
+  b = (b + 255) & ~size_t(255);
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, b);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[256];
+    snprintf(buf, sizeof(buf), "cudaMalloc of %zu bytes failed: %s", b, cudaGetErrorString(e));
+    return fail(pb, NC_ERR_OOM, buf);
+  }
+  pb->allocs.push_back(q);
+  pb->bytes += b;
+  *p = (T*)q;
+  return NC_OK;
+}
+
+nc_status sync(nc_problem* pb, const char* what) {
+  cudaError_t e = cudaStreamSynchronize(pb->st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(pb, e, what);
+  return NC_OK;
+}
+
+nc_status check_timeout(nc_problem* pb) {
+  if (now_s() - pb->t_start > pb->par.timeout_s) return fail(pb, NC_ERR_TIMEOUT, "call exceeded timeout_s");
+  return NC_OK;
+}
+
+// ---------------------------------------------------------------- reductions -------
+nc_status dots(nc_problem* pb, const double* V, long long ld, int nvec, const double* w, long long n,
+               double* out) {
+  CK(launch_multidot(V, ld, nvec, w, n, pb->part, pb->dres, pb->st, &pb->cnt));
+  CK(cudaMemcpyAsync(pb->hres, pb->dres, sizeof(double) * nvec, cudaMemcpyDeviceToHost, pb->st));
+  CKS(sync(pb, "dot products"));
+  for (int i = 0; i < nvec; ++i) out[i] = pb->hres[i];
+  return NC_OK;
+}
+
+nc_status norm2_free(nc_problem* pb, const double* a, double* out) {
+  CK(launch_norm2_free(pb->g, a, pb->part, pb->dres, pb->st, &pb->cnt));
+  CK(cudaMemcpyAsync(pb->hres, pb->dres, sizeof(double), cudaMemcpyDeviceToHost, pb->st));
+  CKS(sync(pb, "norm"));
+  *out = pb->hres[0];
+  return NC_OK;
+}
+
+// ---------------------------------------------------------------- design pipeline --
+nc_status filter_solve(nc_problem* pb) {
+  // PCG (Jacobi) on (r^2 K + M) fx = fb, FP64, from fx = 0.
+  const Grid& g = pb->g;
+  const long long n = g.nn;
+  CK(cudaMemsetAsync(pb->fx, 0, sizeof(double) * n, pb->st));
+  CK(cudaMemcpyAsync(pb->fr, pb->fb, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
+  CK(launch_vmul(pb->fz, pb->fdinv, pb->fr, n, pb->st, &pb->cnt));
+  CK(cudaMemcpyAsync(pb->fp, pb->fz, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
+  double bb, rz;
+  CKS(dots(pb, pb->fb, 0, 1, pb->fb, n, &bb));
+  CKS(dots(pb, pb->fr, 0, 1, pb->fz, n, &rz));
+  if (bb == 0.0) return NC_OK;
+  const double tol2 = pb->par.filter_rtol * pb->par.filter_rtol * bb;
+  for (int it = 0; it < 2000; ++it) {
+    CK(launch_helmholtz(g, pb->F, pb->fp, pb->fq, pb->st, &pb->cnt));
+    double pq;
+    CKS(dots(pb, pb->fp, 0, 1, pb->fq, n, &pq));
+    const double a = rz / pq;
+    CK(launch_axpby(pb->fx, pb->fp, a, 1.0, n, pb->st, &pb->cnt));
+    CK(launch_axpby(pb->fr, pb->fq, -a, 1.0, n, pb->st, &pb->cnt));
+    double rr;
+    CKS(dots(pb, pb->fr, 0, 1, pb->fr, n, &rr));
+    if (!std::isfinite(rr)) return fail(pb, NC_ERR_NAN, "non-finite residual in the filter solve");
+    if (rr <= tol2) return NC_OK;
+    CK(launch_vmul(pb->fz, pb->fdinv, pb->fr, n, pb->st, &pb->cnt));
+    double rz2;
+    CKS(dots(pb, pb->fr, 0, 1, pb->fz, n, &rz2));
+    CK(launch_axpby(pb->fp, pb->fz, 1.0, rz2 / rz, n, pb->st, &pb->cnt));
+    rz = rz2;
+  }
+  return fail(pb, NC_ERR_MAXIT, "filter conjugate gradients did not converge");
+}
+
+// ---------------------------------------------------------------- operators --------
+nc_status residual(nc_problem* pb, const double2* s, double* R, double* phi) {
+  CK(launch_residual(pb->g, pb->ph, s, pb->mat, R, pb->st, &pb->cnt));
+  CKS(norm2_free(pb, R, phi));
+  if (!std::isfinite(*phi)) return fail(pb, NC_ERR_NAN, "non-finite residual");
+  return NC_OK;
+}
+
+// Outer Krylov operator: J(s) or J(s)^T, FP64 or FP32 arithmetic.
+nc_status outer_op(nc_problem* pb, bool transpose, bool fp32, const double* x, double* y) {
+  const Grid& g = pb->g;
+  if (fp32) {
+    if (transpose) CK(launch_jtv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)x, y, pb->st, &pb->cnt));
+    else CK(launch_jv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)x, y, pb->st, &pb->cnt));
+  } else {
+    if (transpose) CK(launch_jtv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, pb->st, &pb->cnt));
+    else CK(launch_jv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, pb->st, &pb->cnt));
+  }
+  return NC_OK;
+}
+
+// ---------------------------------------------------------------- multigrid --------
+template <typename R> MG<R>& mg_of(nc_problem* pb);
+template <> MG<float>& mg_of<float>(nc_problem* pb) { return pb->mg32; }
+template <> MG<double>& mg_of<double>(nc_problem* pb) { return pb->mg64; }
+
+template <typename R> const typename Vec2<R>::type* mg_state(nc_problem* pb);
+template <> const float2* mg_state<float>(nc_problem* pb) { return pb->s32; }
+template <> const double2* mg_state<double>(nc_problem* pb) { return pb->s; }
+template <typename R> const typename Vec2<R>::type* mg_mat(nc_problem* pb);
+template <> const float2* mg_mat<float>(nc_problem* pb) { return pb->mat32; }
+template <> const double2* mg_mat<double>(nc_problem* pb) { return pb->mat; }
+
+template <typename R>
+nc_status mg_alloc(nc_problem* pb) {
+  MG<R>& mg = mg_of<R>(pb);
+  const int L = (int)pb->lv.g.size();
+  mg.lev.resize(L);
+  for (int l = 0; l < L; ++l) {
+    MGLevelDev<R>& d = mg.lev[l];
+    d.g = pb->lv.g[l];
+    CKS(dalloc(pb, &d.x, d.g.nn));
+    CKS(dalloc(pb, &d.xn, d.g.nn));
+    CKS(dalloc(pb, &d.b, d.g.nn));
+    CKS(dalloc(pb, &d.y, d.g.nn));
+    if (l < L - 1) CKS(dalloc(pb, &d.dinv, 4 * d.g.nn));
+    if (l > 0) CKS(dalloc(pb, &d.ebe, 256 * d.g.ne));
+  }
+  mg.nf = pb->lv.nf;
+  if (L == 1) CKS(dalloc(pb, &mg.ebe0, 256 * pb->g.ne));
+  CKS(dalloc(pb, &mg.Ainv, (size_t)mg.nf * mg.nf));
+  CKS(dalloc(pb, &mg.W, (size_t)mg.nf * 2 * mg.nf));
+  return NC_OK;
+}
+
+// Level-0 element matrices (single-level hierarchies only): reuse the Galerkin kernel on a
+// "coarse" grid equal to the fine one is not possible, so assemble via a 1-level trick: the
+// element Jacobian columns are the Jacobian products with unit vectors.
+template <typename R>
+nc_status mg_setup(nc_problem* pb) {
+  MG<R>& mg = mg_of<R>(pb);
+  const int L = (int)mg.lev.size();
+  if (sizeof(R) == 4) CK(launch_cast_d2f((float*)pb->s32, (const double*)pb->s, 2 * pb->g.nn, pb->st, &pb->cnt));
+  for (int l = 0; l < L - 1; ++l) CK(cudaMemsetAsync(mg.lev[l].dinv, 0, sizeof(R) * 4 * mg.lev[l].g.nn, pb->st));
+  CK(cudaMemsetAsync(pb->dflag, 0, sizeof(int), pb->st));
+  if (L == 1) return fail(pb, NC_ERR_ARG, "grid dimensions must be even for the multigrid hierarchy");
+  CK(launch_galerkin_fine<R>(mg.lev[0].g, mg.lev[1].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), mg.lev[0].dinv,
+                             mg.lev[1].ebe, pb->st, &pb->cnt));
+  for (int l = 1; l < L - 1; ++l)
+    CK(launch_galerkin_coarse<R>(mg.lev[l].g, mg.lev[l + 1].g, mg.lev[l].ebe, mg.lev[l].dinv, mg.lev[l + 1].ebe,
+                                 pb->st, &pb->cnt));
+  CK(launch_dense_assemble<R>(mg.lev[L - 1].g, mg.lev[L - 1].ebe, mg.Ainv, mg.nf, pb->st, &pb->cnt));
+  CK(launch_dense_invert(mg.Ainv, mg.W, mg.nf, pb->dflag, pb->st, &pb->cnt));
+  for (int l = 0; l < L - 1; ++l) CK(launch_invert_diag<R>(mg.lev[l].g, mg.lev[l].dinv, pb->dflag, pb->st, &pb->cnt));
+  CK(cudaMemcpyAsync(pb->hflag, pb->dflag, sizeof(int), cudaMemcpyDeviceToHost, pb->st));
+  CKS(sync(pb, "multigrid set-up"));
+  if (*pb->hflag) return fail(pb, NC_ERR_NAN, "singular block in the multigrid set-up");
+  return NC_OK;
+}
+
+template <typename R>
+nc_status level_apply(nc_problem* pb, int l, bool tr, const typename Vec2<R>::type* x, typename Vec2<R>::type* y) {
+  MG<R>& mg = mg_of<R>(pb);
+  if (l == 0) CK(launch_level0_apply<R>(mg.lev[0].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), x, y, tr, pb->st, &pb->cnt));
+  else CK(launch_ebe_apply<R>(mg.lev[l].g, mg.lev[l].ebe, x, y, tr, pb->st, &pb->cnt));
+  return NC_OK;
+}
+
+// V-cycle on level l: solves approximately A_l x_l = b_l; the result is left in lev[l].x.
+template <typename R>
+nc_status vcycle(nc_problem* pb, int l, bool tr) {
+  typedef typename Vec2<R>::type R2;
+  MG<R>& mg = mg_of<R>(pb);
+  MGLevelDev<R>& d = mg.lev[l];
+  const int L = (int)mg.lev.size();
+  if (l == L - 1) {
+    CK(launch_dense_solve<R>(mg.Ainv, mg.nf, d.b, d.x, d.g.nn, tr, pb->st, &pb->cnt));
+    return NC_OK;
+  }
+  const R om = (R)pb->par.omega;
+  const int nu1 = std::max(1, pb->par.nu_pre), nu2 = std::max(0, pb->par.nu_post);
+  CK(launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.x, om, tr, true, pb->st, &pb->cnt));
+  for (int it = 1; it < nu1; ++it) {
+    CKS(level_apply<R>(pb, l, tr, d.x, d.y));
+    CK(launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.xn, om, tr, false, pb->st, &pb->cnt));
+    std::swap(d.x, d.xn);
+  }
+  CKS(level_apply<R>(pb, l, tr, d.x, d.y));
+  CK(launch_sub<R>(d.g, d.b, d.y, d.xn, pb->st, &pb->cnt));
+  MGLevelDev<R>& c = mg.lev[l + 1];
+  CK(launch_restrict<R>(d.g, c.g, d.xn, c.b, pb->st, &pb->cnt));
+  CKS(vcycle<R>(pb, l + 1, tr));
+  CK(launch_prolong_add<R>(d.g, c.g, c.x, d.x, pb->st, &pb->cnt));
+  for (int it = 0; it < nu2; ++it) {
+    CKS(level_apply<R>(pb, l, tr, d.x, d.y));
+    CK(launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.xn, om, tr, false, pb->st, &pb->cnt));
+    std::swap(d.x, d.xn);
+  }
+  return NC_OK;
+}
+
+// z = M^-1 v (one V-cycle), v and z FP64 state vectors.
+nc_status precondition(nc_problem* pb, bool tr, const double* v, double* z) {
+  if (pb->par.precision == NC_PREC_FP64) {
+    MG<double>& mg = pb->mg64;
+    CK(launch_to_mg<double>(v, mg.lev[0].b, pb->g.nn, pb->st, &pb->cnt));
+    CKS(vcycle<double>(pb, 0, tr));
+    CK(launch_from_mg<double>(mg.lev[0].x, z, pb->g.nn, pb->st, &pb->cnt));
+  } else {
+    MG<float>& mg = pb->mg32;
+    CK(launch_to_mg<float>(v, mg.lev[0].b, pb->g.nn, pb->st, &pb->cnt));
+    CKS(vcycle<float>(pb, 0, tr));
+    CK(launch_from_mg<float>(mg.lev[0].x, z, pb->g.nn, pb->st, &pb->cnt));
+  }
+  return NC_OK;
+}
+
+nc_status mg_setup_any(nc_problem* pb) {
+  if (pb->par.precision == NC_PREC_FP64) return mg_setup<double>(pb);
+  return mg_setup<float>(pb);
+}
+
+// ---------------------------------------------------------------- FGMRES ------------
+// Right-preconditioned flexible GMRES(m) with classical Gram-Schmidt applied twice. Solves
+// op(x) = b on the free DOFs from x = 0; stops when the (Arnoldi) residual is <= rtol ||b||.
+nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x, double rtol, int maxit,
+                 int* its_out, double* relres_out) {
+  const long long n = 2 * pb->g.nn;
+  const int m = pb->m;
+  double* V = pb->V;
+  double* Z = pb->Z;
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, pb->st));
+  double bb;
+  CKS(norm2_free(pb, b, &bb));
+  const double bnorm = std::sqrt(bb);
+  *its_out = 0;
+  *relres_out = 0.0;
+  if (bnorm == 0.0) return NC_OK;
+  // r = b
+  double beta = bnorm;
+  CK(launch_scale_copy(V, b, 1.0 / beta, n, pb->st, &pb->cnt));
+  CK(launch_zero_dirichlet(pb->g, V, pb->st, &pb->cnt));
+  int total = 0;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m), h(m + 2), h2(m + 2);
+  while (true) {
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int j = 0;
+    bool done = false;
+    for (; j < m && total < maxit; ++j, ++total) {
+      CKS(check_timeout(pb));
+      double* vj = V + (long long)j * n;
+      double* zj = Z + (long long)j * n;
+      double* wv = V + (long long)(j + 1) * n;
+      CKS(precondition(pb, tr, vj, zj));
+      CKS(outer_op(pb, tr, fp32, zj, wv));
+      CKS(dots(pb, V, n, j + 1, wv, n, h.data()));
+      for (int i = 0; i <= j; ++i) h2[i] = -h[i];
+      CK(launch_axpy_multi(wv, V, n, j + 1, h2.data(), n, pb->st, &pb->cnt));
+      CKS(dots(pb, V, n, j + 2, wv, n, h2.data()));   // second pass dots and ||w||^2
+      double ww = h2[j + 1];
+      double corr = 0.0;
+      for (int i = 0; i <= j; ++i) { h[i] += h2[i]; corr += h2[i] * h2[i]; h2[i] = -h2[i]; }
+      CK(launch_axpy_multi(wv, V, n, j + 1, h2.data(), n, pb->st, &pb->cnt));
+      double hn2 = ww - corr;
+      if (!std::isfinite(hn2)) return fail(pb, NC_ERR_NAN, "non-finite Krylov vector");
+      double hn = hn2 > 0.0 ? std::sqrt(hn2) : 0.0;
+      for (int i = 0; i <= j; ++i) H[i * m + j] = h[i];
+      H[(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double a = H[i * m + j], b2 = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * b2;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * b2;
+      }
+      const double a = H[j * m + j], b2 = H[(j + 1) * m + j];
+      const double r = std::hypot(a, b2);
+      cs[j] = r > 0 ? a / r : 1.0;
+      sn[j] = r > 0 ? b2 / r : 0.0;
+      H[j * m + j] = r;
+      H[(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      const double res = std::fabs(gv[j + 1]);
+      *relres_out = res / bnorm;
+      if (res <= rtol * bnorm || hn == 0.0) { ++j; ++total; done = true; break; }
+      CK(launch_scale_copy(wv, wv, 1.0 / hn, n, pb->st, &pb->cnt));
+    }
+    // x += Z y, y = H^-1 g (upper triangular j x j)
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int k = i + 1; k < j; ++k) acc -= H[i * m + k] * y[k];
+      y[i] = acc / H[i * m + i];
+    }
+    if (j > 0) CK(launch_axpy_multi(x, Z, n, j, y.data(), n, pb->st, &pb->cnt));
+    *its_out = total;
+    if (done) return NC_OK;
+    if (total >= maxit) return NC_OK;   // caller judges the reached residual
+    // restart with the true residual r = b - op(x)
+    double* r = V;
+    CKS(outer_op(pb, tr, fp32, x, pb->w));
+    CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
+    CK(launch_axpby(r, pb->w, -1.0, 1.0, n, pb->st, &pb->cnt));
+    CK(launch_zero_dirichlet(pb->g, r, pb->st, &pb->cnt));
+    double rr;
+    CKS(norm2_free(pb, r, &rr));
+    beta = std::sqrt(rr);
+    *relres_out = beta / bnorm;
+    if (beta <= rtol * bnorm) return NC_OK;
+    CK(launch_scale_copy(r, r, 1.0 / beta, n, pb->st, &pb->cnt));
+  }
+}
+
+// ---------------------------------------------------------------- Newton ------------
+struct NewtonResult {
+  bool converged = false;
+  bool failed = false;   // no damping factor decreased the residual
+};
+
+// phi(lam) = ||R_free(s + lam dx)||^2 into R_try / s_try.
+nc_status trial(nc_problem* pb, double lam, double* phi, nc_stats* stats) {
+  const long long n = 2 * pb->g.nn;
+  CK(cudaMemcpyAsync(pb->s_try, pb->s, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
+  CK(launch_axpby((double*)pb->s_try, pb->dx, lam, 1.0, n, pb->st, &pb->cnt));
+  CKS(residual(pb, pb->s_try, pb->R_try, phi));
+  if (stats) stats->residual_evals++;
+  return NC_OK;
+}
+
+nc_status accept_trial(nc_problem* pb) {
+  std::swap(pb->s, pb->s_try);
+  std::swap(pb->R, pb->R_try);
+  return NC_OK;
+}
+
+// Damping factor (Sec. 5.4: the minimiser of ||R(s + lam dx)||): full step if it reduces
+// phi = ||R||^2 by the fraction 1e-4, else the best of phi(1), phi(1/2) and the minimiser of the
+// parabola through phi(0), phi(1/2), phi(1) clamped to [0.05, 1], else halving from 1/4.
+nc_status damping(nc_problem* pb, double phi0, double* lam_out, double* phi_out, bool* ok, nc_stats* stats) {
+  *ok = false;
+  double phi1;
+  CKS(trial(pb, 1.0, &phi1, stats));
+  if (phi1 <= (1.0 - 1e-4) * phi0) { *lam_out = 1.0; *phi_out = phi1; *ok = true; return accept_trial(pb); }
+  double phih;
+  CKS(trial(pb, 0.5, &phih, stats));
+  double best_lam = 0.5, best_phi = phih;
+  if (phi1 < best_phi) { best_lam = 1.0; best_phi = phi1; }
+  const double c1 = 4.0 * phih - 3.0 * phi0 - phi1;
+  const double c2 = 2.0 * phi1 + 2.0 * phi0 - 4.0 * phih;
+  if (c2 > 0.0) {
+    const double lam = std::min(1.0, std::max(0.05, -c1 / (2.0 * c2)));
+    if (lam != 0.5 && lam != 1.0) {
+      double p;
+      CKS(trial(pb, lam, &p, stats));
+      if (p < best_phi || (p == best_phi && lam > best_lam)) { best_lam = lam; best_phi = p; }
+    }
+  }
+  if (best_phi < phi0) {
+    double p;
+    CKS(trial(pb, best_lam, &p, stats));
+    *lam_out = best_lam; *phi_out = p; *ok = true;
+    return accept_trial(pb);
+  }
+  double lam = 0.25;
+  for (int i = 0; i < 8; ++i) {
+    double p;
+    CKS(trial(pb, lam, &p, stats));
+    if (p < phi0) { *lam_out = lam; *phi_out = p; *ok = true; return accept_trial(pb); }
+    lam *= 0.5;
+  }
+  return NC_OK;
+}
+
+nc_status newton(nc_problem* pb, double rtol, double ref, nc_stats* stats, bool* failed) {
+  *failed = false;
+  double phi;
+  CKS(residual(pb, pb->s, pb->R, &phi));
+  if (stats) stats->residual_evals++;
+  const long long n = 2 * pb->g.nn;
+  const bool fp32 = pb->par.precision != NC_PREC_FP64;
+  double rel_prev = -1.0, eta_prev = pb->par.krylov_rtol;
+  for (int it = 0;; ++it) {
+    const double rel = ref > 0 ? std::sqrt(phi) / ref : 0.0;
+    if (stats) stats->rel_residual = rel;
+    if (rel <= rtol) return NC_OK;
+    if (it >= pb->par.newton_maxit) return fail(pb, NC_ERR_MAXIT, "Newton iteration limit reached");
+    CKS(check_timeout(pb));
+    // forcing term: Eisenstat-Walker (choice 2, gamma 0.9) safeguarded, and no tighter than
+    // needed to reach rtol in this step
+    double eta = pb->par.krylov_rtol;
+    if (rel_prev > 0.0) {
+      const double r = rel / rel_prev;
+      eta = 0.9 * r * r;
+      if (0.9 * eta_prev * eta_prev > 0.1) eta = std::max(eta, 0.9 * eta_prev * eta_prev);
+      eta = std::min(eta, pb->par.krylov_rtol);
+    }
+    eta = std::max(eta, 0.5 * rtol / rel);
+    eta = std::max(std::min(eta, pb->par.krylov_rtol), 1e-12);
+    double t0 = now_s();
+    CKS(mg_setup_any(pb));
+    double t1 = now_s();
+    CK(launch_scale_copy(pb->rhs, pb->R, -1.0, n, pb->st, &pb->cnt));
+    CK(launch_zero_dirichlet(pb->g, pb->rhs, pb->st, &pb->cnt));
+    int its = 0;
+    double lres = 0.0;
+    CKS(fgmres(pb, false, fp32, pb->rhs, pb->dx, eta, pb->par.krylov_maxit, &its, &lres));
+    double t2 = now_s();
+    if (stats) {
+      stats->t_setup_ms += 1e3 * (t1 - t0);
+      stats->t_krylov_ms += 1e3 * (t2 - t1);
+      stats->krylov_its += its;
+      if (stats->newton_its < 64) stats->krylov_hist[stats->newton_its] = its;
+    }
+    double lam, phi_new;
+    bool ok;
+    CKS(damping(pb, phi, &lam, &phi_new, &ok, stats));
+    if (!ok) { *failed = true; return NC_OK; }
+    phi = phi_new;
+    rel_prev = rel;
+    eta_prev = eta;
+    if (stats) {
+      const double rn = ref > 0 ? std::sqrt(phi) / ref : 0.0;
+      if (stats->newton_its < 64) stats->res_hist[stats->newton_its] = rn;
+      stats->newton_its++;
+    }
+  }
+}
+
+void set_q_scale(nc_problem* pb, double scale) { pb->ph.Q = pb->Q_full * scale; }
+
+nc_status reference_norm(nc_problem* pb) {
+  // ||R_free(0)|| with the full source: R(0) is minus the SUPG-weighted source load.
+  CK(cudaMemsetAsync(pb->s_try, 0, sizeof(double) * 2 * pb->g.nn, pb->st));
+  set_q_scale(pb, 1.0);
+  double phi;
+  CKS(residual(pb, pb->s_try, pb->R_try, &phi));
+  pb->ref_norm = std::sqrt(phi);
+  return NC_OK;
+}
+
+nc_status copy_in(nc_problem* pb, void* dst, const void* src, size_t bytes) {
+  if (!src) return fail(pb, NC_ERR_ARG, "NULL input pointer");
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, pb->st));
+  return NC_OK;
+}
+
+nc_status copy_out(nc_problem* pb, void* dst, const void* src, size_t bytes) {
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, pb->st));
+  return NC_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
+  if (!g || !p) { *why = "NULL grid or params"; return NC_ERR_ARG; }
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !(g->h > 0.0) || !std::isfinite(g->h)) {
+    *why = "grid needs nx, ny, nz >= 1 and h > 0"; return NC_ERR_ARG;
+  }
+  if ((long long)g->nx * g->ny * g->nz > (1LL << 31)) { *why = "grid too large"; return NC_ERR_ARG; }
+  if (p->heated_layers < 0 || p->heated_layers >= g->nz) { *why = "heated_layers must be in [0, nz)"; return NC_ERR_ARG; }
+  if (!(p->mu > 0) || !(p->rho0 > 0) || !(p->cp > 0) || !(p->k_f > 0) || !(p->k_s > 0) || !(p->kappa_ratio > 0)) {
+    *why = "material parameters must be positive"; return NC_ERR_ARG;
+  }
+  if (p->alpha < 0 || p->g < 0 || p->q_c < 0 || p->q_p < 0) { *why = "alpha, g, q_c, q_p must be >= 0"; return NC_ERR_ARG; }
+  if (p->restart < 1 || p->restart > kMaxRestart) { *why = "restart must be in [1, 64]"; return NC_ERR_ARG; }
+  if (p->precision != NC_PREC_MIXED && p->precision != NC_PREC_FP64) { *why = "unknown precision"; return NC_ERR_ARG; }
+  if (!(p->newton_rtol > 0) || p->newton_maxit < 0 || p->krylov_maxit < 1) { *why = "bad tolerances"; return NC_ERR_ARG; }
+  if (!(p->filter_radius >= 0) || !(p->filter_rtol > 0)) { *why = "bad filter parameters"; return NC_ERR_ARG; }
+  Grid g0 = make_grid(g->nx, g->ny, g->nz, g->h);
+  Levels lv = plan_levels(g0, p->mg_levels);
+  if (lv.g.size() < 2) { *why = "the multigrid hierarchy needs even grid dimensions"; return NC_ERR_ARG; }
+  if (lv.nf > kMaxCoarseDofs) { *why = "coarsest multigrid level too large (use more levels)"; return NC_ERR_ARG; }
+  return NC_OK;
+}
+
+size_t footprint(const nc_grid* gr, const nc_params* p) {
+  Grid g = make_grid(gr->nx, gr->ny, gr->nz, gr->h);
+  Levels lv = plan_levels(g, p->mg_levels);
+  auto al = [](size_t b) { return (std::max<size_t>(b, 1) + 255) & ~size_t(255); };
+  size_t b = 0;
+  const size_t nn = g.nn, ne = g.ne, m = p->restart;
+  b += 4 * al(16 * nn);                 // s, s_try, lam, s_start
+  b += 5 * al(16 * nn);                 // R, R_try, dx, w, rhs
+  b += 3 * al(8 * ne) + al(24 * ne);    // rho, gamma_t, gsens, u
+  b += 2 * al(16 * ne) + al(8 * ne) + al(8 * nn);   // mat, dmat, mat32, s32
+  b += al(16 * nn * (m + 1)) + al(16 * nn * m);     // V, Z
+  b += al(8 * 66 * 608) + al(8 * 66);
+  b += 7 * al(8 * nn);                  // filter vectors
+  const size_t rs = p->precision == NC_PREC_FP64 ? 8 : 4;
+  for (size_t l = 0; l < lv.g.size(); ++l) {
+    b += 4 * al(2 * rs * lv.g[l].nn);
+    if (l + 1 < lv.g.size()) b += al(4 * rs * lv.g[l].nn);
+    if (l > 0) b += al(256 * rs * lv.g[l].ne);
+  }
+  b += al(8 * (size_t)lv.nf * lv.nf) + al(16 * (size_t)lv.nf * lv.nf);
+  b += al(4);
+  return b;
+}
+
+}  // namespace
+
+// ====================================================================================
+extern "C" {
+
+nc_status nc_default_params(nc_params* p) {
+  if (!p) return NC_ERR_ARG;
+  memset(p, 0, sizeof(*p));
+  p->alpha = 1e3;
+  p->kappa_f = 0.0;
+  p->tune_dT = 1.0;
+  p->kappa_ratio = 1e-6;
+  p->k_f = 1.0;
+  p->k_s = 100.0;
+  p->q_c = 8.81;
+  p->q_p = 8.0;
+  p->Q = 0.0;
+  p->heated_layers = 2;
+  p->rho0 = p->mu = p->cp = p->g = 1.0;
+  p->filter_radius = 2.5;
+  p->newton_rtol = 1e-8;
+  p->newton_maxit = 50;
+  p->krylov_rtol = 1e-2;
+  p->krylov_maxit = 300;
+  p->restart = 30;
+  p->precision = NC_PREC_MIXED;
+  p->mg_levels = 0;
+  p->nu_pre = 2;
+  p->nu_post = 2;
+  p->omega = 0.6;
+  p->filter_rtol = 1e-12;
+  p->timeout_s = 600.0;
+  return NC_OK;
+}
+
+nc_status nc_footprint_bytes(const nc_grid* g, const nc_params* p, size_t* bytes) {
+  std::string why;
+  if (!bytes) return NC_ERR_ARG;
+  nc_status s = validate(g, p, &why);
+  if (s != NC_OK) return fail(nullptr, s, why);
+  *bytes = footprint(g, p);
+  return NC_OK;
+}
+
+nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream, nc_problem** out) {
+  if (!out) return fail(nullptr, NC_ERR_ARG, "NULL output pointer");
+  *out = nullptr;
+  std::string why;
+  nc_status vs = validate(gr, p, &why);
+  if (vs != NC_OK) return fail(nullptr, vs, why);
+  nc_problem* pb = new nc_problem();
+  cudaGetDevice(&pb->device);
+  pb->g = make_grid(gr->nx, gr->ny, gr->nz, gr->h);
+  pb->par = *p;
+  pb->m = p->restart;
+  const Grid& g = pb->g;
+  // physical constants
+  pb->kappa_f = p->kappa_f > 0 ? p->kappa_f : kappa_f_tuned(p->alpha, p->tune_dT);
+  pb->kappa_s = p->kappa_ratio * pb->kappa_f;
+  pb->vol_h = (double)g.nx * g.ny * p->heated_layers * g.h * g.h * g.h;
+  pb->Q_full = p->Q > 0 ? p->Q : (pb->vol_h > 0 ? 1.0 / pb->vol_h : 0.0);
+  pb->ph.h = g.h;
+  pb->ph.beta = p->rho0 * p->alpha * p->g;
+  pb->ph.rc = p->rho0 * p->cp;
+  pb->ph.mu = p->mu;
+  pb->ph.he = std::sqrt(3.0) * g.h;
+  pb->ph.tau3 = p->rho0 * p->cp * pb->ph.he * pb->ph.he / (4.0 * p->k_f);
+  pb->ph.Q = pb->Q_full;
+  pb->ph.heated_layers = p->heated_layers;
+  // filter element matrix r^2 K0 + M0 (Q1 cube: K0 = h/12 [4,0,-1,-1], M0 = h^3/216 [8,4,2,1] by
+  // the number of differing reference coordinates), r = R / (2 sqrt 3)
+  {
+    const double r = p->filter_radius * g.h / (2.0 * std::sqrt(3.0));
+    const double kc[4] = {4.0, 0.0, -1.0, -1.0}, mc[4] = {8.0, 4.0, 2.0, 1.0};
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b) {
+        const int d = __builtin_popcount(a ^ b);
+        pb->F.A[a * 8 + b] = r * r * g.h / 12.0 * kc[d] + g.h * g.h * g.h / 216.0 * mc[d];
+      }
+    pb->F.t0 = g.h * g.h * g.h / 8.0;
+    pb->F.diag = pb->F.A[0];
+  }
+  if (stream) pb->st = (cudaStream_t)stream;
+  else {
+    cudaError_t e = cudaStreamCreateWithFlags(&pb->st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { g_create_error = cudaGetErrorString(e); delete pb; return NC_ERR_CUDA; }
+    pb->own_stream = true;
+  }
+  pb->lv = plan_levels(g, p->mg_levels);
+  nc_status s = NC_OK;
+  const long long nn = g.nn, ne = g.ne;
+  auto A = [&](nc_status x) { if (s == NC_OK) s = x; };
+  A(dalloc(pb, &pb->s, nn)); A(dalloc(pb, &pb->s_try, nn)); A(dalloc(pb, &pb->lam, nn)); A(dalloc(pb, &pb->s_start, nn));
+  A(dalloc(pb, &pb->R, 2 * nn)); A(dalloc(pb, &pb->R_try, 2 * nn)); A(dalloc(pb, &pb->dx, 2 * nn));
+  A(dalloc(pb, &pb->w, 2 * nn)); A(dalloc(pb, &pb->rhs, 2 * nn));
+  A(dalloc(pb, &pb->rho, ne)); A(dalloc(pb, &pb->gamma_t, ne)); A(dalloc(pb, &pb->gsens, ne)); A(dalloc(pb, &pb->u, 3 * ne));
+  A(dalloc(pb, &pb->mat, ne)); A(dalloc(pb, &pb->dmat, ne)); A(dalloc(pb, &pb->mat32, ne)); A(dalloc(pb, &pb->s32, nn));
+  A(dalloc(pb, &pb->V, (size_t)2 * nn * (pb->m + 1))); A(dalloc(pb, &pb->Z, (size_t)2 * nn * pb->m));
+  A(dalloc(pb, &pb->part, 66 * 608)); A(dalloc(pb, &pb->dres, 66));
+  A(dalloc(pb, &pb->fx, nn)); A(dalloc(pb, &pb->fb, nn)); A(dalloc(pb, &pb->fr, nn)); A(dalloc(pb, &pb->fz, nn));
+  A(dalloc(pb, &pb->fp, nn)); A(dalloc(pb, &pb->fq, nn)); A(dalloc(pb, &pb->fdinv, nn));
+  A(dalloc(pb, &pb->dflag, 1));
+  if (s == NC_OK) s = p->precision == NC_PREC_FP64 ? mg_alloc<double>(pb) : mg_alloc<float>(pb);
+  if (s == NC_OK) {
+    cudaError_t e = cudaMallocHost(&pb->hres, sizeof(double) * 66);
+    if (e == cudaSuccess) e = cudaMallocHost(&pb->hflag, sizeof(int));
+    if (e != cudaSuccess) { cudaGetLastError(); s = fail(pb, NC_ERR_OOM, "pinned host allocation failed"); }
+  }
+  if (s == NC_OK) {
+    cudaError_t e = launch_helmholtz_diag(g, pb->F, pb->fdinv, pb->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pb->s, 0, sizeof(double2) * nn, pb->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pb->st);
+    if (e != cudaSuccess) s = cuda_fail(pb, e, "create");
+  }
+  if (s != NC_OK) {
+    g_create_error = pb->err;
+    nc_destroy_problem(pb);
+    return s;
+  }
+  *out = pb;
+  return NC_OK;
+}
+
+nc_status nc_destroy_problem(nc_problem* pb) {
+  if (!pb) return NC_OK;
+  DeviceGuard dg(pb->device);
+  if (pb->st) cudaStreamSynchronize(pb->st);
+  for (void* q : pb->allocs) cudaFree(q);
+  if (pb->hres) cudaFreeHost(pb->hres);
+  if (pb->hflag) cudaFreeHost(pb->hflag);
+  if (pb->own_stream && pb->st) cudaStreamDestroy(pb->st);
+  delete pb;
+  return NC_OK;
+}
+
+nc_status nc_set_design(nc_problem* pb, const double* rho) {
+  if (!pb) return NC_ERR_ARG;
+  DeviceGuard dg(pb->device);
+  pb->t_start = now_s();
+  const Grid& g = pb->g;
+  CKS(copy_in(pb, pb->rho, rho, sizeof(double) * g.ne));
+  CK(cudaMemsetAsync(pb->dflag, 0, sizeof(int), pb->st));
+  CK(launch_check_design(pb->rho, g.ne, pb->dflag, pb->st));
+  CK(cudaMemcpyAsync(pb->hflag, pb->dflag, sizeof(int), cudaMemcpyDeviceToHost, pb->st));
+  CKS(sync(pb, "design check"));
+  if (*pb->hflag) return fail(pb, NC_ERR_ARG, "design values must be finite and in [0, 1]");
+  // filter: b = T^T gamma with gamma = 1 on the heated region
+  CK(launch_filter_rhs(g, pb->rho, pb->par.heated_layers, pb->F.t0, pb->fb, pb->st, &pb->cnt));
+  CKS(filter_solve(pb));
+  CK(launch_elem_from_nodes(g, pb->fx, 0.125, pb->par.heated_layers, 1.0, pb->gamma_t, pb->st, &pb->cnt));
+  RampConst rc{pb->kappa_f, pb->kappa_s, pb->par.k_f, pb->par.k_s, pb->par.q_c, pb->par.q_p};
+  CK(launch_ramp(pb->gamma_t, g.ne, rc, pb->mat, pb->dmat, pb->mat32, pb->st, &pb->cnt));
+  CK(cudaMemsetAsync(pb->s, 0, sizeof(double2) * g.nn, pb->st));
+  CK(cudaMemsetAsync(pb->s_start, 0, sizeof(double2) * g.nn, pb->st));
+  CKS(reference_norm(pb));
+  pb->stage = 1;
+  return NC_OK;
+}
+
+nc_status nc_set_state(nc_problem* pb, const double* P, const double* T) {
+  if (!pb) return NC_ERR_ARG;
+  if (pb->stage < 1) return fail(pb, NC_ERR_STATE, "set_state needs a design");
+  if (!P || !T) return fail(pb, NC_ERR_ARG, "NULL P or T");
+  DeviceGuard dg(pb->device);
+  const long long nn = pb->g.nn;
+  CK(cudaMemcpy2DAsync((double*)pb->s_start, 16, P, 8, 8, nn, cudaMemcpyDefault, pb->st));
+  CK(cudaMemcpy2DAsync((double*)pb->s_start + 1, 16, T, 8, 8, nn, cudaMemcpyDefault, pb->st));
+  CK(launch_zero_dirichlet(pb->g, (double*)pb->s_start, pb->st, &pb->cnt));
+  CK(cudaMemcpyAsync(pb->s, pb->s_start, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, pb->st));
+  CKS(sync(pb, "set_state"));
+  pb->stage = 1;
+  return NC_OK;
+}
+
+nc_status nc_solve_state(nc_problem* pb, nc_stats* stats) {
+  if (!pb) return NC_ERR_ARG;
+  if (pb->stage < 1) return fail(pb, NC_ERR_STATE, "solve_state needs a design");
+  DeviceGuard dg(pb->device);
+  pb->t_start = now_s();
+  pb->cnt = Counters();
+  if (stats) memset(stats, 0, sizeof(*stats));
+  const long long nn = pb->g.nn;
+  CK(cudaMemcpyAsync(pb->s, pb->s_start, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, pb->st));
+  set_q_scale(pb, 1.0);
+  bool failed = false;
+  nc_status s = newton(pb, pb->par.newton_rtol, pb->ref_norm, stats, &failed);
+  if (s == NC_OK && failed) {
+    // source ramping (Sec. 5.4): 1/4, 1/2, then the full source, each from the previous state
+    if (stats) stats->ramped = 1;
+    CK(cudaMemcpyAsync(pb->s, pb->s_start, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, pb->st));
+    const double scales[3] = {0.25, 0.5, 1.0};
+    for (int i = 0; i < 3 && s == NC_OK; ++i) {
+      set_q_scale(pb, scales[i]);
+      double ref = pb->ref_norm * scales[i];
+      s = newton(pb, i < 2 ? std::max(1e-6, pb->par.newton_rtol) : pb->par.newton_rtol, ref, stats, &failed);
+      if (s == NC_OK && failed) s = fail(pb, NC_ERR_DIVERGED, "no damping factor reduces the residual");
+    }
+    set_q_scale(pb, 1.0);
+  }
+  if (stats) {
+    stats->t_total_ms = 1e3 * (now_s() - pb->t_start);
+    stats->alg_bytes = pb->cnt.bytes;
+    stats->kernel_launches = pb->cnt.launches;
+  }
+  if (s == NC_OK) pb->stage = 2;
+  return s;
+}
+
+nc_status nc_objective(nc_problem* pb, int objective, double* f) {
+  if (!pb || !f) return NC_ERR_ARG;
+  if (objective != NC_OBJ_MEAN_T_HEATED) return fail(pb, NC_ERR_ARG, "unknown objective");
+  if (pb->stage < 2) return fail(pb, NC_ERR_STATE, "objective needs a solved state");
+  DeviceGuard dg(pb->device);
+  const Grid& g = pb->g;
+  CK(launch_dfds(g, pb->par.heated_layers, g.h * g.h * g.h / 8.0 / pb->vol_h, pb->rhs, pb->st, &pb->cnt));
+  CKS(dots(pb, pb->rhs, 0, 1, (const double*)pb->s, 2 * g.nn, f));
+  return NC_OK;
+}
+
+nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stats* stats) {
+  if (!pb) return NC_ERR_ARG;
+  if (pb->stage < 2) return fail(pb, NC_ERR_STATE, "solve_adjoint needs a solved state");
+  DeviceGuard dg(pb->device);
+  pb->t_start = now_s();
+  pb->cnt = Counters();
+  if (stats) memset(stats, 0, sizeof(*stats));
+  double f;
+  CKS(nc_objective(pb, objective, &f));   // leaves df/ds in rhs
+  if (f_out) *f_out = f;
+  const Grid& g = pb->g;
+  const long long n = 2 * g.nn;
+  set_q_scale(pb, 1.0);
+  double t0 = now_s();
+  CKS(mg_setup_any(pb));
+  if (stats) stats->t_setup_ms += 1e3 * (now_s() - t0);
+  double bb;
+  CKS(norm2_free(pb, pb->rhs, &bb));
+  const double bnorm = std::sqrt(bb);
+  CK(cudaMemsetAsync(pb->lam, 0, sizeof(double) * n, pb->st));
+  if (bnorm == 0.0) { pb->stage = 3; return NC_OK; }
+  const bool fp32 = pb->par.precision != NC_PREC_FP64;
+  // refinement: r = b - J^T lam in FP64, correction from FGMRES on the (FP32 or FP64) operator
+  for (int pass = 0;; ++pass) {
+    double rr;
+    if (pass == 0) {
+      CK(cudaMemcpyAsync(pb->w, pb->rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
+      rr = bb;
+    } else {
+      CK(launch_jtv_f64(g, pb->ph, pb->s, pb->mat, pb->lam, pb->w, pb->st, &pb->cnt));
+      CK(launch_axpby(pb->w, pb->rhs, 1.0, -1.0, n, pb->st, &pb->cnt));
+      CK(launch_zero_dirichlet(g, pb->w, pb->st, &pb->cnt));
+      CKS(norm2_free(pb, pb->w, &rr));
+    }
+    const double rel = std::sqrt(rr) / bnorm;
+    if (stats) {
+      stats->rel_residual = rel;
+      if (pass < 64) stats->res_hist[pass] = rel;
+    }
+    if (!std::isfinite(rel)) return fail(pb, NC_ERR_NAN, "non-finite adjoint residual");
+    if (rel <= kAdjointRtol) break;
+    if (pass >= 30) return fail(pb, NC_ERR_MAXIT, "adjoint refinement did not converge");
+    CKS(check_timeout(pb));
+    int its;
+    double lres;
+    const double eta = fp32 ? std::max(1e-4, kAdjointRtol / rel) : std::max(0.5 * kAdjointRtol / rel, 1e-12);
+    double t1 = now_s();
+    CKS(fgmres(pb, true, fp32, pb->w, pb->dx, std::min(eta, 1e-1), pb->par.krylov_maxit, &its, &lres));
+    if (stats) {
+      stats->t_krylov_ms += 1e3 * (now_s() - t1);
+      stats->krylov_its += its;
+      if (pass < 64) stats->krylov_hist[pass] = its;
+      stats->newton_its++;
+    }
+    CK(launch_axpby((double*)pb->lam, pb->dx, 1.0, 1.0, n, pb->st, &pb->cnt));
+  }
+  CKS(sync(pb, "adjoint"));
+  if (stats) {
+    stats->t_total_ms = 1e3 * (now_s() - pb->t_start);
+    stats->alg_bytes = pb->cnt.bytes;
+    stats->kernel_launches = pb->cnt.launches;
+  }
+  pb->stage = 3;
+  return NC_OK;
+}
+
+nc_status nc_sensitivities(nc_problem* pb, double* dfdrho) {
+  if (!pb) return NC_ERR_ARG;
+  if (pb->stage < 3) return fail(pb, NC_ERR_STATE, "sensitivities need a solved adjoint");
+  if (!dfdrho) return fail(pb, NC_ERR_ARG, "NULL output");
+  DeviceGuard dg(pb->device);
+  pb->t_start = now_s();
+  const Grid& g = pb->g;
+  set_q_scale(pb, 1.0);
+  CK(launch_sens_elem(g, pb->ph, pb->s, pb->lam, pb->mat, pb->dmat, pb->gsens, pb->st, &pb->cnt));
+  // filter transpose: gamma~_e = (1/8) sum_a x_a, x = A^-1 T^T gamma  =>  df/dgamma = T A^-1 (1/8 sum)
+  CK(launch_filter_rhs(g, pb->gsens, 0, 0.125, pb->fb, pb->st, &pb->cnt));
+  CKS(filter_solve(pb));
+  CK(launch_elem_from_nodes(g, pb->fx, pb->F.t0, pb->par.heated_layers, 0.0, pb->gsens, pb->st, &pb->cnt));
+  CKS(copy_out(pb, dfdrho, pb->gsens, sizeof(double) * g.ne));
+  CKS(sync(pb, "sensitivities"));
+  return NC_OK;
+}
+
+nc_status nc_get_fields(const nc_problem* cpb, double* P, double* T, double* u) {
+  nc_problem* pb = const_cast<nc_problem*>(cpb);
+  if (!pb) return NC_ERR_ARG;
+  if (pb->stage < 1) return fail(pb, NC_ERR_STATE, "no state yet");
+  DeviceGuard dg(pb->device);
+  const long long nn = pb->g.nn;
+  if (P) CK(cudaMemcpy2DAsync(P, 8, (const double*)pb->s, 16, 8, nn, cudaMemcpyDefault, pb->st));
+  if (T) CK(cudaMemcpy2DAsync(T, 8, (const double*)pb->s + 1, 16, 8, nn, cudaMemcpyDefault, pb->st));
+  if (u) {
+    CK(launch_u_centroid(pb->g, pb->ph, pb->s, pb->mat, pb->u, pb->st, &pb->cnt));
+    CKS(copy_out(pb, u, pb->u, sizeof(double) * 3 * pb->g.ne));
+  }
+  CKS(sync(pb, "get_fields"));
+  return NC_OK;
+}
+
+nc_status nc_get_design_fields(const nc_problem* cpb, double* gamma_tilde, double* kappa, double* k) {
+  nc_problem* pb = const_cast<nc_problem*>(cpb);
+  if (!pb) return NC_ERR_ARG;
+  if (pb->stage < 1) return fail(pb, NC_ERR_STATE, "no design yet");
+  DeviceGuard dg(pb->device);
+  const long long ne = pb->g.ne;
+  if (gamma_tilde) CKS(copy_out(pb, gamma_tilde, pb->gamma_t, sizeof(double) * ne));
+  if (kappa) CK(cudaMemcpy2DAsync(kappa, 8, (const double*)pb->mat, 16, 8, ne, cudaMemcpyDefault, pb->st));
+  if (k) CK(cudaMemcpy2DAsync(k, 8, (const double*)pb->mat + 1, 16, 8, ne, cudaMemcpyDefault, pb->st));
+  CKS(sync(pb, "get_design_fields"));
+  return NC_OK;
+}
+
+nc_status nc_eval_residual(nc_problem* pb, const double* s, double* R, double* norm2_free_out) {
+  if (!pb) return NC_ERR_ARG;
+  if (pb->stage < 1) return fail(pb, NC_ERR_STATE, "residual needs a design");
+  if (!R) return fail(pb, NC_ERR_ARG, "NULL output");
+  DeviceGuard dg(pb->device);
+  const long long n = 2 * pb->g.nn;
+  set_q_scale(pb, 1.0);
+  CKS(copy_in(pb, pb->s_try, s, sizeof(double) * n));
+  double phi;
+  CKS(residual(pb, pb->s_try, pb->R_try, &phi));
+  if (norm2_free_out) *norm2_free_out = phi;
+  CKS(copy_out(pb, R, pb->R_try, sizeof(double) * n));
+  CKS(sync(pb, "eval_residual"));
+  return NC_OK;
+}
+
+static nc_status apply_generic(nc_problem* pb, const double* s, const double* v, double* out, bool tr, bool fp32) {
+  if (!pb) return NC_ERR_ARG;
+  if (pb->stage < 1) return fail(pb, NC_ERR_STATE, "operator needs a design");
+  if (!out) return fail(pb, NC_ERR_ARG, "NULL output");
+  DeviceGuard dg(pb->device);
+  const long long n = 2 * pb->g.nn;
+  set_q_scale(pb, 1.0);
+  CKS(copy_in(pb, pb->s_try, s, sizeof(double) * n));
+  CKS(copy_in(pb, pb->w, v, sizeof(double) * n));
+  const Grid& g = pb->g;
+  if (fp32) {
+    CK(launch_cast_d2f((float*)pb->s32, (const double*)pb->s_try, n, pb->st, &pb->cnt));
+    if (tr) CK(launch_jtv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
+    else CK(launch_jv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
+  } else {
+    if (tr) CK(launch_jtv_f64(g, pb->ph, pb->s_try, pb->mat, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
+    else CK(launch_jv_f64(g, pb->ph, pb->s_try, pb->mat, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
+  }
+  CKS(copy_out(pb, out, pb->R_try, sizeof(double) * n));
+  CKS(sync(pb, "operator"));
+  return NC_OK;
+}
+
+nc_status nc_apply_jacobian(nc_problem* pb, const double* s, const double* v, double* out, int precision) {
+  return apply_generic(pb, s, v, out, false, precision != NC_PREC_FP64);
+}
+
+nc_status nc_apply_jacobian_transpose(nc_problem* pb, const double* s, const double* w, double* out) {
+  return apply_generic(pb, s, w, out, true, false);
+}
+
+const char* nc_last_error(const nc_problem* pb) {
+  if (!pb) return g_create_error.c_str();
+  return pb->err.empty() ? "no error" : pb->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// Common types and index helpers of the natconv CUDA library.
+//
+// Grid: nx x ny x nz cubic Q1 elements of edge h; node (i,j,k) -> i + NX*(j + NY*k) with
+// NX = nx+1, NY = ny+1 (x fastest); element (i,j,k) -> i + nx*(j + ny*k). A state vector is
+// node-interleaved (P, T): double2 (FP64) or float2 (FP32) per node. The Dirichlet set is
+// the top node plane k = nz (P = T = 0 there).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nc {
+
+struct Grid {
+  int nx, ny, nz;   // elements
+  int NX, NY, NZ;   // nodes per direction
+  long long nn;     // nodes
+  long long ne;     // elements
+  double h;
+};
+
+inline Grid make_grid(int nx, int ny, int nz, double h) {
+  Grid g;
+  g.nx = nx; g.ny = ny; g.nz = nz;
+  g.NX = nx + 1; g.NY = ny + 1; g.NZ = nz + 1;
+  g.nn = (long long)g.NX * g.NY * g.NZ;
+  g.ne = (long long)nx * ny * nz;
+  g.h = h;
+  return g;
+}
+
+template <typename R> struct Vec2;
+template <> struct Vec2<double> { typedef double2 type; };
+template <> struct Vec2<float> { typedef float2 type; };
+
+template <typename R>
+__device__ __forceinline__ typename Vec2<R>::type mk2(R a, R b) {
+  typename Vec2<R>::type v; v.x = a; v.y = b; return v;
+}
+
+// Node index of local corner a = ax + 2 ay + 4 az of element (i,j,k).
+__device__ __forceinline__ long long corner_node(const Grid& g, int i, int j, int k, int a) {
+  return (long long)(i + (a & 1)) + (long long)g.NX * ((j + ((a >> 1) & 1)) + (long long)g.NY * (k + (a >> 2)));
+}
+
+__device__ __forceinline__ void elem_ijk(const Grid& g, long long e, int& i, int& j, int& k) {
+  i = (int)(e % g.nx);
+  long long r = e / g.nx;
+  j = (int)(r % g.ny);
+  k = (int)(r / g.ny);
+}
+
+__device__ __forceinline__ void node_ijk(const Grid& g, long long n, int& i, int& j, int& k) {
+  i = (int)(n % g.NX);
+  long long r = n / g.NX;
+  j = (int)(r % g.NY);
+  k = (int)(r / g.NY);
+}
+
+inline unsigned grid_blocks(long long work, int threads, long long cap = 1LL << 30) {
+  long long b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+}  // namespace nc

@@ -1,0 +1,306 @@
+// Element-level arithmetic of the stabilised Darcy-Boussinesq weak form (App. A of the paper),
+// written once, templated on the arithmetic type (double or float).
+//
+// Weak form (Eq. weakstable), per element with permeability kappa, conductivity k, source Q:
+//   R^P_a = sum_q w ( -grad N_a . u_q )                                 (continuity rows)
+//   R^T_a = sum_q w ( N*_a,q (rho0 c_p u_q . grad T_q - Q) + k grad N_a . grad T_q )
+// with the Darcy velocity u = -kappa/mu (grad P + rho0 alpha g T), g = (0, 0, -g) (Eq. finaldarcy),
+// the SUPG test function N* = N + tau u0 . grad N (App. A), u0 the centroid velocity (the mean of
+// the Gauss-point velocities for a trilinear field), and
+//   tau = (4 |u0|^2 / h_e^2 + 1 / tau3^2)^(-1/2),  h_e = sqrt(3) h,
+// the Tezduyar combination of tau1 = h_e / (2 |u0|) and tau3 (App. A; tau3 = rho0 c_p h_e^2 /(4 k_f),
+// which is the printed h_e^2/4 for unit properties).
+// Quadrature: 2x2x2 Gauss-Legendre. Values and gradients at the 8 Gauss points are obtained by
+// sum factorisation (three 1D stages of 2x2 interpolation / differencing), and the test-function
+// side (sum over points of N_a A_q + grad N_a . B_q) by the transposed stages.
+//
+// Index conventions: local node a = ax + 2 ay + 4 az; Gauss point q = qx + 2 qy + 4 qz with
+// reference coordinate (2 q_d - 1)/sqrt(3) along each axis.
+#pragma once
+
+#include "nc_common.cuh"
+
+namespace nc {
+
+template <typename R>
+struct ElemConst {
+  R cp, cm;     // 1D interpolation weights at a Gauss point: (1 + 1/sqrt3)/2, (1 - 1/sqrt3)/2
+  R ih;         // 1 / h
+  R w;          // Gauss weight x det J = (h/2)^3
+  R beta;       // rho0 alpha g
+  R rc;         // rho0 c_p
+  R imu;        // 1 / mu
+  R c4he2;      // 4 / h_e^2
+  R itau3sq;    // 1 / tau3^2
+};
+
+// Values and Cartesian gradients of the trilinear interpolant of nodal values f at the 8 Gauss
+// points.
+template <typename R>
+__device__ __forceinline__ void q1_forward(const R f[8], const R cp, const R cm, const R ih,
+                                           R v[8], R gx[8], R gy[8], R gz[8]) {
+  R A[8], Dx[4];
+#pragma unroll
+  for (int yz = 0; yz < 4; ++yz) {          // yz = ay + 2 az
+    const R f0 = f[2 * yz], f1 = f[2 * yz + 1];
+    A[2 * yz] = cp * f0 + cm * f1;          // A index qx + 2 ay + 4 az
+    A[2 * yz + 1] = cm * f0 + cp * f1;
+    Dx[yz] = (f1 - f0) * ih;                // Dx index ay + 2 az
+  }
+  R B[8], Dy[4], Cx[4];
+#pragma unroll
+  for (int qx = 0; qx < 2; ++qx)
+#pragma unroll
+    for (int az = 0; az < 2; ++az) {
+      const R a0 = A[qx + 4 * az], a1 = A[qx + 2 + 4 * az];
+      B[qx + 4 * az] = cp * a0 + cm * a1;   // B index qx + 2 qy + 4 az
+      B[qx + 2 + 4 * az] = cm * a0 + cp * a1;
+      Dy[qx + 2 * az] = (a1 - a0) * ih;     // Dy index qx + 2 az
+    }
+#pragma unroll
+  for (int az = 0; az < 2; ++az) {
+    const R d0 = Dx[2 * az], d1 = Dx[1 + 2 * az];
+    Cx[2 * az] = cp * d0 + cm * d1;         // Cx index qy + 2 az
+    Cx[1 + 2 * az] = cm * d0 + cp * d1;
+  }
+  R Gz[4], Gy[4], Gx[4];
+#pragma unroll
+  for (int xy = 0; xy < 4; ++xy) {          // xy = qx + 2 qy
+    const R b0 = B[xy], b1 = B[xy + 4];
+    v[xy] = cp * b0 + cm * b1;
+    v[xy + 4] = cm * b0 + cp * b1;
+    Gz[xy] = (b1 - b0) * ih;                // Gz index qx + 2 qy
+  }
+#pragma unroll
+  for (int qx = 0; qx < 2; ++qx) {
+    const R y0 = Dy[qx], y1 = Dy[qx + 2];
+    Gy[qx] = cp * y0 + cm * y1;             // Gy index qx + 2 qz
+    Gy[qx + 2] = cm * y0 + cp * y1;
+  }
+#pragma unroll
+  for (int qy = 0; qy < 2; ++qy) {
+    const R x0 = Cx[qy], x1 = Cx[qy + 2];
+    Gx[qy] = cp * x0 + cm * x1;             // Gx index qy + 2 qz
+    Gx[qy + 2] = cm * x0 + cp * x1;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int qx = q & 1, qy = (q >> 1) & 1, qz = q >> 2;
+    gx[q] = Gx[qy + 2 * qz];
+    gy[q] = Gy[qx + 2 * qz];
+    gz[q] = Gz[qx + 2 * qy];
+  }
+}
+
+// out_a = sum_q ( N_a(q) A_q + dN_a/dx(q) Bx_q + dN_a/dy(q) By_q + dN_a/dz(q) Bz_q ).
+// HAS_A = false treats A as zero.
+template <typename R, bool HAS_A>
+__device__ __forceinline__ void q1_test(const R* A, const R Bx[8], const R By[8], const R Bz[8],
+                                        const R cp, const R cm, const R ih, R out[8]) {
+  R bx[4], by[4], bz[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int lo = i & 1, hi = i >> 1;
+    bx[i] = Bx[2 * lo + 4 * hi] + Bx[1 + 2 * lo + 4 * hi];   // bx index qy + 2 qz
+    by[i] = By[lo + 4 * hi] + By[lo + 2 + 4 * hi];           // by index qx + 2 qz
+    bz[i] = Bz[lo + 2 * hi] + Bz[lo + 2 * hi + 4];           // bz index qx + 2 qy
+  }
+  R Az[8];                                                    // index qx + 2 qy + 4 az
+#pragma unroll
+  for (int xy = 0; xy < 4; ++xy) {
+    const R a0 = HAS_A ? A[xy] : R(0), a1 = HAS_A ? A[xy + 4] : R(0);
+    const R d = bz[xy] * ih;
+    Az[xy] = cp * a0 + cm * a1 - d;
+    Az[xy + 4] = cm * a0 + cp * a1 + d;
+  }
+  R byz[4], bxz[4];                                           // index qx + 2 az, qy + 2 az
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    const R b0 = by[l], b1 = by[l + 2];
+    byz[l] = cp * b0 + cm * b1;
+    byz[l + 2] = cm * b0 + cp * b1;
+    const R c0 = bx[l], c1 = bx[l + 2];
+    bxz[l] = cp * c0 + cm * c1;
+    bxz[l + 2] = cm * c0 + cp * c1;
+  }
+  R Ay[8];                                                    // index qx + 2 ay + 4 az
+#pragma unroll
+  for (int qx = 0; qx < 2; ++qx)
+#pragma unroll
+    for (int az = 0; az < 2; ++az) {
+      const R a0 = Az[qx + 4 * az], a1 = Az[qx + 2 + 4 * az];
+      const R d = byz[qx + 2 * az] * ih;
+      Ay[qx + 4 * az] = cp * a0 + cm * a1 - d;
+      Ay[qx + 2 + 4 * az] = cm * a0 + cp * a1 + d;
+    }
+  R bxy[4];                                                   // index ay + 2 az
+#pragma unroll
+  for (int az = 0; az < 2; ++az) {
+    const R b0 = bxz[2 * az], b1 = bxz[1 + 2 * az];
+    bxy[2 * az] = cp * b0 + cm * b1;
+    bxy[1 + 2 * az] = cm * b0 + cp * b1;
+  }
+#pragma unroll
+  for (int yz = 0; yz < 4; ++yz) {
+    const R a0 = Ay[2 * yz], a1 = Ay[2 * yz + 1];
+    const R d = bxy[yz] * ih;
+    out[2 * yz] = cp * a0 + cm * a1 - d;
+    out[2 * yz + 1] = cm * a0 + cp * a1 + d;
+  }
+}
+
+template <typename R> __device__ __forceinline__ R nc_rsqrt(R x);
+template <> __device__ __forceinline__ double nc_rsqrt<double>(double x) { return rsqrt(x); }
+template <> __device__ __forceinline__ float nc_rsqrt<float>(float x) { return rsqrtf(x); }
+
+// Gauss-point state of an element: V_q = grad P_q - beta T_q e_z (so u_q = -c V_q, c = kappa/mu),
+// grad T_q, S_q = rho0 c_p u_q . grad T_q - Q, centroid velocity u0 and tau.
+template <typename R>
+struct ElemState {
+  R vx[8], vy[8], vz[8];
+  R hx[8], hy[8], hz[8];
+  R S[8];
+  R u0x, u0y, u0z, tau, c;
+};
+
+template <typename R>
+__device__ __forceinline__ void elem_state(const ElemConst<R>& C, const R p[8], const R t[8],
+                                           const R kappa, const R Q, ElemState<R>& st) {
+  R T[8];
+  q1_forward(p, C.cp, C.cm, C.ih, T, st.vx, st.vy, st.vz);   // T reused as scratch for P values
+  q1_forward(t, C.cp, C.cm, C.ih, T, st.hx, st.hy, st.hz);
+  st.c = kappa * C.imu;
+  R sx = 0, sy = 0, sz = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    st.vz[q] -= C.beta * T[q];
+    sx += st.vx[q]; sy += st.vy[q]; sz += st.vz[q];
+  }
+  const R m = -st.c * R(0.125);
+  st.u0x = m * sx; st.u0y = m * sy; st.u0z = m * sz;
+  st.tau = nc_rsqrt<R>(C.c4he2 * (st.u0x * st.u0x + st.u0y * st.u0y + st.u0z * st.u0z) + C.itau3sq);
+  const R mrc = -st.c * C.rc;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    st.S[q] = mrc * (st.vx[q] * st.hx[q] + st.vy[q] * st.hy[q] + st.vz[q] * st.hz[q]) - Q;
+}
+
+// Element residual (R^P, R^T) of Eq. weakstable / Eq. finalsyseq.
+template <typename R>
+__device__ __forceinline__ void elem_residual(const ElemConst<R>& C, const R p[8], const R t[8],
+                                              const R kappa, const R kc, const R Q,
+                                              R RP[8], R RT[8]) {
+  ElemState<R> st;
+  elem_state(C, p, t, kappa, Q, st);
+  const R wc = C.w * st.c;       // B^P = -w u = w c V
+  R bx[8], by[8], bz[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { bx[q] = wc * st.vx[q]; by[q] = wc * st.vy[q]; bz[q] = wc * st.vz[q]; }
+  q1_test<R, false>(nullptr, bx, by, bz, C.cp, C.cm, C.ih, RP);
+  R A[8];
+  const R wk = C.w * kc;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    A[q] = C.w * st.S[q];
+    const R s = A[q] * st.tau;
+    bx[q] = s * st.u0x + wk * st.hx[q];
+    by[q] = s * st.u0y + wk * st.hy[q];
+    bz[q] = s * st.u0z + wk * st.hz[q];
+  }
+  q1_test<R, true>(A, bx, by, bz, C.cp, C.cm, C.ih, RT);
+}
+
+// Exact Newton Jacobian product J_e (dp, dt) at the element state st (includes d tau and d N*).
+template <typename R>
+__device__ __forceinline__ void elem_jv_dir(const ElemConst<R>& C, const ElemState<R>& st,
+                                            const R kc, const R dp[8], const R dt[8],
+                                            R oP[8], R oT[8]) {
+  R dvx[8], dvy[8], dvz[8], dT[8];
+  q1_forward(dp, C.cp, C.cm, C.ih, dT, dvx, dvy, dvz);
+  R dhx[8], dhy[8], dhz[8];
+  q1_forward(dt, C.cp, C.cm, C.ih, dT, dhx, dhy, dhz);
+  R sx = 0, sy = 0, sz = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    dvz[q] -= C.beta * dT[q];
+    sx += dvx[q]; sy += dvy[q]; sz += dvz[q];
+  }
+  const R m = -st.c * R(0.125);
+  const R du0x = m * sx, du0y = m * sy, du0z = m * sz;
+  const R tau = st.tau;
+  const R dtau = -tau * tau * tau * C.c4he2 * (st.u0x * du0x + st.u0y * du0y + st.u0z * du0z);
+  const R wc = C.w * st.c;
+  const R mrc = -st.c * C.rc;
+  const R wk = C.w * kc;
+  R A[8], bx[8], by[8], bz[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    // dS = rho0 c_p (du . H + u . dH), u = -c V
+    const R dS = mrc * (dvx[q] * st.hx[q] + dvy[q] * st.hy[q] + dvz[q] * st.hz[q]
+                      + st.vx[q] * dhx[q] + st.vy[q] * dhy[q] + st.vz[q] * dhz[q]);
+    A[q] = C.w * dS;
+    const R a = C.w * (tau * dS + dtau * st.S[q]);      // coefficient of u0
+    const R b = C.w * tau * st.S[q];                    // coefficient of du0
+    bx[q] = a * st.u0x + b * du0x + wk * dhx[q];
+    by[q] = a * st.u0y + b * du0y + wk * dhy[q];
+    bz[q] = a * st.u0z + b * du0z + wk * dhz[q];
+  }
+  q1_test<R, true>(A, bx, by, bz, C.cp, C.cm, C.ih, oT);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { bx[q] = wc * dvx[q]; by[q] = wc * dvy[q]; bz[q] = wc * dvz[q]; }
+  q1_test<R, false>(nullptr, bx, by, bz, C.cp, C.cm, C.ih, oP);
+}
+
+// Adjoint side: given multipliers (lp, lt) of the element rows, the gradient of
+// L = lp . R^P + lt . R^T with respect to the element state (J_e^T l), and optionally the
+// derivatives dL/dkappa and dL/dk used by the design sensitivities.
+template <typename R, bool SENS>
+__device__ __forceinline__ void elem_jtv(const ElemConst<R>& C, const ElemState<R>& st,
+                                         const R kc, const R lp[8], const R lt[8],
+                                         R oP[8], R oT[8], R* dL_dkappa, R* dL_dk) {
+  R Mx[8], My[8], Mz[8], m[8];
+  q1_forward(lp, C.cp, C.cm, C.ih, m, Mx, My, Mz);
+  R Nx[8], Ny[8], Nz[8];
+  q1_forward(lt, C.cp, C.cm, C.ih, m, Nx, Ny, Nz);
+  const R c = st.c;
+  const R rc = C.rc;
+  const R wk = C.w * kc;
+  R gx[8], gy[8], gz[8];         // dL/du_q (without the centroid part)
+  R g0x = 0, g0y = 0, g0z = 0, sdot = 0, kdot = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const R u0M = st.u0x * Nx[q] + st.u0y * Ny[q] + st.u0z * Nz[q];
+    const R W = m[q] + st.tau * u0M;
+    const R wWrc = C.w * W * rc;
+    gx[q] = -C.w * Mx[q] + wWrc * st.hx[q];
+    gy[q] = -C.w * My[q] + wWrc * st.hy[q];
+    gz[q] = -C.w * Mz[q] + wWrc * st.hz[q];
+    const R wS = C.w * st.S[q];
+    g0x += wS * Nx[q]; g0y += wS * Ny[q]; g0z += wS * Nz[q];
+    sdot += wS * u0M;
+    if (SENS) kdot += C.w * (Nx[q] * st.hx[q] + Ny[q] * st.hy[q] + Nz[q] * st.hz[q]);
+    // dL/dH_q = w (W rho0 c_p u_q + k grad lt_q), u_q = -c V_q; stored in N*
+    const R a = -wWrc * c;
+    Nx[q] = a * st.vx[q] + wk * Nx[q];
+    Ny[q] = a * st.vy[q] + wk * Ny[q];
+    Nz[q] = a * st.vz[q] + wk * Nz[q];
+  }
+  const R t3 = -st.tau * st.tau * st.tau * C.c4he2 * sdot;
+  g0x = R(0.125) * (st.tau * g0x + t3 * st.u0x);
+  g0y = R(0.125) * (st.tau * g0y + t3 * st.u0y);
+  g0z = R(0.125) * (st.tau * g0z + t3 * st.u0z);
+  R kap = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    gx[q] += g0x; gy[q] += g0y; gz[q] += g0z;
+    if (SENS) kap += gx[q] * st.vx[q] + gy[q] * st.vy[q] + gz[q] * st.vz[q];
+    m[q] = c * C.beta * gz[q];   // dL/dT_q
+  }
+  if (SENS) { *dL_dkappa = -C.imu * kap; *dL_dk = kdot; }
+  q1_test<R, true>(m, Nx, Ny, Nz, C.cp, C.cm, C.ih, oT);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { gx[q] *= -c; gy[q] *= -c; gz[q] *= -c; }
+  q1_test<R, false>(nullptr, gx, gy, gz, C.cp, C.cm, C.ih, oP);
+}
+
+}  // namespace nc

@@ -1,0 +1,198 @@
+// Element-sweep kernels: residual R(s), Jacobian products J v and J^T w, design sensitivities and
+// centroid velocities. One thread per element gathers its 8 nodes, evaluates the element
+// arithmetic of nc_element.cuh and scatters the 16 row contributions with atomic adds
+// (Dirichlet rows on the top plane are skipped and set by the caller's convention).
+#include "nc_launch.h"
+
+namespace nc {
+
+namespace {
+
+template <typename R, typename V>
+__device__ __forceinline__ void gather_state(const Grid& g, const V* __restrict__ s, int i, int j, int k,
+                                             R p[8], R t[8]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const V v = s[corner_node(g, i, j, k, a)];
+    p[a] = (R)v.x;
+    t[a] = (R)v.y;
+  }
+}
+
+// Gather a direction vector with its Dirichlet (top-plane) entries treated as zero.
+template <typename R, typename V>
+__device__ __forceinline__ void gather_dir(const Grid& g, const V* __restrict__ v, int i, int j, int k,
+                                           R p[8], R t[8]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    if (k + (a >> 2) == g.nz) { p[a] = R(0); t[a] = R(0); continue; }
+    const V x = v[corner_node(g, i, j, k, a)];
+    p[a] = (R)x.x;
+    t[a] = (R)x.y;
+  }
+}
+
+template <typename O, typename R>
+__device__ __forceinline__ void scatter_add(const Grid& g, O* __restrict__ out, int i, int j, int k,
+                                            const R oP[8], const R oT[8]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    if (k + (a >> 2) == g.nz) continue;
+    const long long n = corner_node(g, i, j, k, a);
+    atomicAdd(out + 2 * n, (O)oP[a]);
+    atomicAdd(out + 2 * n + 1, (O)oT[a]);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R elem_source(const Phys& ph, int k) {
+  return k < ph.heated_layers ? (R)ph.Q : R(0);
+}
+
+__global__ void k_residual(Grid g, Phys ph, ElemConst<double> C, const double2* __restrict__ s,
+                           const double2* __restrict__ mat, double* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.ne) return;
+  int i, j, k;
+  elem_ijk(g, e, i, j, k);
+  double p[8], t[8];
+  gather_state<double>(g, s, i, j, k, p, t);
+  const double2 m = mat[e];
+  double RP[8], RT[8];
+  elem_residual<double>(C, p, t, m.x, m.y, elem_source<double>(ph, k), RP, RT);
+  scatter_add(g, out, i, j, k, RP, RT);
+}
+
+// Dirichlet rows of the residual: R_d = s_d (boundary value 0).
+__global__ void k_residual_bc(Grid g, const double2* __restrict__ s, double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long plane = (long long)g.NX * g.NY;
+  if (t >= plane) return;
+  const long long n = (long long)g.nz * plane + t;
+  out[2 * n] = s[n].x;
+  out[2 * n + 1] = s[n].y;
+}
+
+template <typename R, typename SV, typename O, bool TRANSPOSE>
+__global__ void k_jprod(Grid g, Phys ph, ElemConst<R> C, const SV* __restrict__ s,
+                        const typename Vec2<R>::type* __restrict__ mat, const double2* __restrict__ v,
+                        O* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.ne) return;
+  int i, j, k;
+  elem_ijk(g, e, i, j, k);
+  R p[8], t[8], dp[8], dt[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const SV x = s[corner_node(g, i, j, k, a)];
+    p[a] = (R)x.x;
+    t[a] = (R)x.y;
+  }
+  gather_dir<R>(g, v, i, j, k, dp, dt);
+  const typename Vec2<R>::type m = mat[e];
+  ElemState<R> st;
+  elem_state(C, p, t, m.x, elem_source<R>(ph, k), st);
+  R oP[8], oT[8];
+  if (TRANSPOSE)
+    elem_jtv<R, false>(C, st, m.y, dp, dt, oP, oT, nullptr, nullptr);
+  else
+    elem_jv_dir<R>(C, st, m.y, dp, dt, oP, oT);
+  scatter_add(g, out, i, j, k, oP, oT);
+}
+
+__global__ void k_sens(Grid g, Phys ph, ElemConst<double> C, const double2* __restrict__ s,
+                       const double2* __restrict__ lam, const double2* __restrict__ mat,
+                       const double2* __restrict__ dmat, double* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.ne) return;
+  int i, j, k;
+  elem_ijk(g, e, i, j, k);
+  if (k < ph.heated_layers) { out[e] = 0.0; return; }
+  double p[8], t[8], lp[8], lt[8];
+  gather_state<double>(g, s, i, j, k, p, t);
+  gather_dir<double>(g, lam, i, j, k, lp, lt);
+  const double2 m = mat[e];
+  ElemState<double> st;
+  elem_state(C, p, t, m.x, 0.0, st);
+  double oP[8], oT[8], dkap, dk;
+  elem_jtv<double, true>(C, st, m.y, lp, lt, oP, oT, &dkap, &dk);
+  const double2 d = dmat[e];
+  out[e] = -(dkap * d.x + dk * d.y);
+}
+
+__global__ void k_u_centroid(Grid g, Phys ph, ElemConst<double> C, const double2* __restrict__ s,
+                             const double2* __restrict__ mat, double* __restrict__ u) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.ne) return;
+  int i, j, k;
+  elem_ijk(g, e, i, j, k);
+  double p[8], t[8];
+  gather_state<double>(g, s, i, j, k, p, t);
+  ElemState<double> st;
+  elem_state(C, p, t, mat[e].x, 0.0, st);
+  u[3 * e] = st.u0x;
+  u[3 * e + 1] = st.u0y;
+  u[3 * e + 2] = st.u0z;
+}
+
+}  // namespace
+
+static const int kElemThreads = 128;
+
+cudaError_t launch_residual(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
+                            double* out, cudaStream_t st, Counters* c) {
+  cudaError_t err = cudaMemsetAsync(out, 0, sizeof(double) * 2 * g.nn, st);
+  if (err != cudaSuccess) return err;
+  k_residual<<<grid_blocks(g.ne, kElemThreads), kElemThreads, 0, st>>>(g, ph, make_econst<double>(ph), s, mat, out);
+  const long long plane = (long long)g.NX * g.NY;
+  k_residual_bc<<<grid_blocks(plane, 256), 256, 0, st>>>(g, s, out);
+  if (c) { c->launches += 2; c->bytes += 16.0 * g.nn * 2 + 16.0 * g.ne; }
+  return cudaGetLastError();
+}
+
+template <typename R, typename SV, bool TR>
+static cudaError_t jprod(const Grid& g, const Phys& ph, const SV* s, const typename Vec2<R>::type* mat,
+                         const double2* v, double* out, cudaStream_t st, Counters* c) {
+  cudaError_t err = cudaMemsetAsync(out, 0, sizeof(double) * 2 * g.nn, st);
+  if (err != cudaSuccess) return err;
+  k_jprod<R, SV, double, TR><<<grid_blocks(g.ne, kElemThreads), kElemThreads, 0, st>>>(
+      g, ph, make_econst<R>(ph), s, mat, v, out);
+  if (c) { c->launches += 1; c->bytes += (2.0 * sizeof(SV) + 32.0) * g.nn + 2.0 * sizeof(R) * g.ne; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jv_f64(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
+                          const double2* v, double* out, cudaStream_t st, Counters* c) {
+  return jprod<double, double2, false>(g, ph, s, mat, v, out, st, c);
+}
+cudaError_t launch_jv_f32_io64(const Grid& g, const Phys& ph, const float2* s32, const float2* mat32,
+                               const double2* v, double* out, cudaStream_t st, Counters* c) {
+  return jprod<float, float2, false>(g, ph, s32, mat32, v, out, st, c);
+}
+cudaError_t launch_jtv_f64(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
+                           const double2* w, double* out, cudaStream_t st, Counters* c) {
+  return jprod<double, double2, true>(g, ph, s, mat, w, out, st, c);
+}
+cudaError_t launch_jtv_f32_io64(const Grid& g, const Phys& ph, const float2* s32, const float2* mat32,
+                                const double2* w, double* out, cudaStream_t st, Counters* c) {
+  return jprod<float, float2, true>(g, ph, s32, mat32, w, out, st, c);
+}
+
+cudaError_t launch_sens_elem(const Grid& g, const Phys& ph, const double2* s, const double2* lam,
+                             const double2* mat, const double2* dmat, double* out, cudaStream_t st,
+                             Counters* c) {
+  k_sens<<<grid_blocks(g.ne, kElemThreads), kElemThreads, 0, st>>>(g, ph, make_econst<double>(ph), s, lam,
+                                                                   mat, dmat, out);
+  if (c) { c->launches += 1; c->bytes += 32.0 * g.nn + 40.0 * g.ne; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_u_centroid(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
+                              double* u, cudaStream_t st, Counters* c) {
+  k_u_centroid<<<grid_blocks(g.ne, kElemThreads), kElemThreads, 0, st>>>(g, ph, make_econst<double>(ph), s,
+                                                                         mat, u);
+  if (c) { c->launches += 1; c->bytes += 16.0 * g.nn + 40.0 * g.ne; }
+  return cudaGetLastError();
+}
+
+}  // namespace nc

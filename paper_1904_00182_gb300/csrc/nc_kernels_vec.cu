@@ -1,0 +1,359 @@
+// Vector, reduction and design-pipeline kernels.
+//
+// Reductions are deterministic: each block sums a fixed contiguous segment, the partial sums are
+// added in a fixed order by one block, so results do not depend on scheduling.
+#include "nc_launch.h"
+
+namespace nc {
+
+namespace {
+
+const int kRedThreads = 256;
+const int kRedBlocksMax = 608;   // 4 x 152 SMs
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+  __syncthreads();
+  return r;
+}
+
+// part[i * gridDim.x + b] = sum over segment b of V_i . w
+__global__ void k_multidot_part(const double* __restrict__ V, long long ld, int nvec,
+                                const double* __restrict__ w, long long n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const long long seg = (n + gridDim.x - 1) / gridDim.x;
+  const long long lo = seg * blockIdx.x;
+  const long long hi = min(n, lo + seg);
+  for (int i = 0; i < nvec; ++i) {
+    const double* v = V + (long long)i * ld;
+    double acc = 0.0;
+    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) acc += v[t] * w[t];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int nb, int nvec, double* __restrict__ res) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvec) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(long long)i * nb + b];
+  res[i] = s;
+}
+
+// Sum of squares over the free rows of a state vector (rows of nodes below the top plane).
+__global__ void k_norm2_free_part(const double* __restrict__ a, long long nfree2, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const long long seg = (nfree2 + gridDim.x - 1) / gridDim.x;
+  const long long lo = seg * blockIdx.x;
+  const long long hi = min(nfree2, lo + seg);
+  double acc = 0.0;
+  for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) acc += a[t] * a[t];
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+struct Coef64 { double c[64]; };
+
+__global__ void k_axpy_multi(double* __restrict__ y, const double* __restrict__ V, long long ld, int nvec,
+                             Coef64 coef, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    double acc = y[t];
+    for (int i = 0; i < nvec; ++i) acc += coef.c[i] * V[(long long)i * ld + t];
+    y[t] = acc;
+  }
+}
+
+__global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, double a, double b, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = a * x[t] + b * y[t];
+}
+
+__global__ void k_scale_copy(double* __restrict__ y, const double* __restrict__ x, double a, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = a * x[t];
+}
+
+__global__ void k_vmul(double* __restrict__ z, const double* __restrict__ a, const double* __restrict__ b,
+                       long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    z[t] = a[t] * b[t];
+}
+
+__global__ void k_cast_d2f(float* __restrict__ y, const double* __restrict__ x, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = (float)x[t];
+}
+
+__global__ void k_cast_f2d(double* __restrict__ y, const float* __restrict__ x, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = (double)x[t];
+}
+
+__global__ void k_zero_dirichlet(Grid g, double* __restrict__ a) {
+  const long long plane = (long long)g.NX * g.NY;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= plane) return;
+  const long long n = (long long)g.nz * plane + t;
+  a[2 * n] = 0.0;
+  a[2 * n + 1] = 0.0;
+}
+
+__global__ void k_check_design(const double* __restrict__ rho, long long n, int* flag) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double v = rho[t];
+    if (!(v >= 0.0 && v <= 1.0)) atomicExch(flag, 1);   // NaN fails both comparisons
+  }
+}
+
+// Node n gathers from the (up to 8) elements around it. Element (ei,ej,ek) contains node n as
+// local corner a = (i-ei) + 2 (j-ej) + 4 (k-ek).
+__global__ void k_filter_rhs(Grid g, const double* __restrict__ gamma, int heated_layers, double t0,
+                             double* __restrict__ b) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nn) return;
+  int i, j, k;
+  node_ijk(g, n, i, j, k);
+  double acc = 0.0;
+  for (int dk = -1; dk <= 0; ++dk) {
+    const int ek = k + dk;
+    if (ek < 0 || ek >= g.nz) continue;
+    for (int dj = -1; dj <= 0; ++dj) {
+      const int ej = j + dj;
+      if (ej < 0 || ej >= g.ny) continue;
+      for (int di = -1; di <= 0; ++di) {
+        const int ei = i + di;
+        if (ei < 0 || ei >= g.nx) continue;
+        const double v = ek < heated_layers ? 1.0 : gamma[ei + (long long)g.nx * (ej + (long long)g.ny * ek)];
+        acc += v;
+      }
+    }
+  }
+  b[n] = t0 * acc;
+}
+
+__global__ void k_helmholtz(Grid g, FilterConst F, const double* __restrict__ x, double* __restrict__ y) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nn) return;
+  int i, j, k;
+  node_ijk(g, n, i, j, k);
+  double acc = 0.0;
+  for (int dk = -1; dk <= 0; ++dk) {
+    const int ek = k + dk;
+    if (ek < 0 || ek >= g.nz) continue;
+    for (int dj = -1; dj <= 0; ++dj) {
+      const int ej = j + dj;
+      if (ej < 0 || ej >= g.ny) continue;
+      for (int di = -1; di <= 0; ++di) {
+        const int ei = i + di;
+        if (ei < 0 || ei >= g.nx) continue;
+        const int a = -di + 2 * (-dj) + 4 * (-dk);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc += F.A[a * 8 + b] * x[corner_node(g, ei, ej, ek, b)];
+      }
+    }
+  }
+  y[n] = acc;
+}
+
+__global__ void k_helmholtz_diag(Grid g, double d, double* __restrict__ dinv) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nn) return;
+  int i, j, k;
+  node_ijk(g, n, i, j, k);
+  const int cx = (i > 0) + (i < g.nx), cy = (j > 0) + (j < g.ny), cz = (k > 0) + (k < g.nz);
+  dinv[n] = 1.0 / (d * cx * cy * cz);
+}
+
+__global__ void k_elem_from_nodes(Grid g, const double* __restrict__ x, double scale, int heated_layers,
+                                  double heated_value, double* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.ne) return;
+  int i, j, k;
+  elem_ijk(g, e, i, j, k);
+  if (heated_value >= 0.0 && k < heated_layers) { out[e] = heated_value; return; }
+  double acc = 0.0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) acc += x[corner_node(g, i, j, k, a)];
+  out[e] = scale * acc;
+}
+
+__global__ void k_ramp(const double* __restrict__ gt, long long n, RampConst r, double2* __restrict__ mat,
+                       double2* __restrict__ dmat, float2* __restrict__ mat32) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double x = gt[e];
+    const double dc = 1.0 + r.q_c * (1.0 - x);
+    const double k = r.k_f + x / dc * (r.k_s - r.k_f);
+    const double dk = (r.k_s - r.k_f) * (1.0 + r.q_c) / (dc * dc);
+    const double dp = 1.0 + r.q_p * x;
+    const double kap = r.kappa_s + (1.0 - x) / dp * (r.kappa_f - r.kappa_s);
+    const double dkap = -(r.kappa_f - r.kappa_s) * (1.0 + r.q_p) / (dp * dp);
+    mat[e] = make_double2(kap, k);
+    dmat[e] = make_double2(dkap, dk);
+    mat32[e] = make_float2((float)kap, (float)k);
+  }
+}
+
+// df/ds for f = (1/|Omega_h|) sum_{e in Omega_h} int_e N t_e: T entry = w_node x (number of heated
+// elements around the node), P entry 0, Dirichlet rows 0.
+__global__ void k_dfds(Grid g, int heated_layers, double w_node, double* __restrict__ out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nn) return;
+  int i, j, k;
+  node_ijk(g, n, i, j, k);
+  int cnt = 0;
+  if (k < g.nz) {
+    const int cx = (i > 0) + (i < g.nx), cy = (j > 0) + (j < g.ny);
+    const int cz = (k > 0 && k - 1 < heated_layers) + (k < g.nz && k < heated_layers);
+    cnt = cx * cy * cz;
+  }
+  out[2 * n] = 0.0;
+  out[2 * n + 1] = w_node * cnt;
+}
+
+unsigned stream_blocks(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+int reduce_blocks(long long n) {
+  long long b = (n + 4095) / 4096;
+  if (b > kRedBlocksMax) b = kRedBlocksMax;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+cudaError_t launch_multidot(const double* V, long long ld, int nvec, const double* w, long long n,
+                            double* part, double* res, cudaStream_t st, Counters* c) {
+  const int nb = reduce_blocks(n);
+  k_multidot_part<<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
+  k_sum_parts<<<(nvec + 63) / 64, 64, 0, st>>>(part, nb, nvec, res);
+  if (c) { c->launches += 2; c->bytes += 8.0 * n * (nvec + 1); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, double* res, cudaStream_t st,
+                              Counters* c) {
+  const long long nfree2 = 2LL * g.NX * g.NY * g.nz;
+  const int nb = reduce_blocks(nfree2);
+  k_norm2_free_part<<<nb, kRedThreads, 0, st>>>(a, nfree2, part);
+  k_sum_parts<<<1, 64, 0, st>>>(part, nb, 1, res);
+  if (c) { c->launches += 2; c->bytes += 8.0 * nfree2; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_multi(double* y, const double* V, long long ld, int nvec, const double* coef,
+                              long long n, cudaStream_t st, Counters* c) {
+  if (nvec > 64) return cudaErrorInvalidValue;
+  Coef64 cf;
+  for (int i = 0; i < nvec; ++i) cf.c[i] = coef[i];
+  k_axpy_multi<<<stream_blocks(n), 256, 0, st>>>(y, V, ld, nvec, cf, n);
+  if (c) { c->launches += 1; c->bytes += 8.0 * n * (nvec + 2); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st,
+                         Counters* c) {
+  k_axpby<<<stream_blocks(n), 256, 0, st>>>(y, x, a, b, n);
+  if (c) { c->launches += 1; c->bytes += 24.0 * n; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(double* y, const double* x, double a, long long n, cudaStream_t st,
+                              Counters* c) {
+  k_scale_copy<<<stream_blocks(n), 256, 0, st>>>(y, x, a, n);
+  if (c) { c->launches += 1; c->bytes += 16.0 * n; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vmul(double* z, const double* a, const double* b, long long n, cudaStream_t st,
+                        Counters* c) {
+  k_vmul<<<stream_blocks(n), 256, 0, st>>>(z, a, b, n);
+  if (c) { c->launches += 1; c->bytes += 24.0 * n; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_d2f(float* y, const double* x, long long n, cudaStream_t st, Counters* c) {
+  k_cast_d2f<<<stream_blocks(n), 256, 0, st>>>(y, x, n);
+  if (c) { c->launches += 1; c->bytes += 12.0 * n; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_f2d(double* y, const float* x, long long n, cudaStream_t st, Counters* c) {
+  k_cast_f2d<<<stream_blocks(n), 256, 0, st>>>(y, x, n);
+  if (c) { c->launches += 1; c->bytes += 12.0 * n; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_dirichlet(const Grid& g, double* a, cudaStream_t st, Counters* c) {
+  const long long plane = (long long)g.NX * g.NY;
+  k_zero_dirichlet<<<grid_blocks(plane, 256), 256, 0, st>>>(g, a);
+  if (c) c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_design(const double* rho, long long ne, int* flag, cudaStream_t st) {
+  k_check_design<<<stream_blocks(ne), 256, 0, st>>>(rho, ne, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filter_rhs(const Grid& g, const double* gamma, int heated_layers, double t0, double* b,
+                              cudaStream_t st, Counters* c) {
+  k_filter_rhs<<<grid_blocks(g.nn, 256), 256, 0, st>>>(g, gamma, heated_layers, t0, b);
+  if (c) { c->launches += 1; c->bytes += 8.0 * (g.ne + g.nn); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_helmholtz(const Grid& g, const FilterConst& F, const double* x, double* y, cudaStream_t st,
+                             Counters* c) {
+  k_helmholtz<<<grid_blocks(g.nn, 256), 256, 0, st>>>(g, F, x, y);
+  if (c) { c->launches += 1; c->bytes += 16.0 * g.nn; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_helmholtz_diag(const Grid& g, const FilterConst& F, double* dinv, cudaStream_t st) {
+  k_helmholtz_diag<<<grid_blocks(g.nn, 256), 256, 0, st>>>(g, F.diag, dinv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elem_from_nodes(const Grid& g, const double* x, double scale, int heated_layers,
+                                   double heated_value, double* out, cudaStream_t st, Counters* c) {
+  k_elem_from_nodes<<<grid_blocks(g.ne, 256), 256, 0, st>>>(g, x, scale, heated_layers, heated_value, out);
+  if (c) { c->launches += 1; c->bytes += 8.0 * (g.ne + g.nn); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ramp(const double* gt, long long ne, const RampConst& r, double2* mat, double2* dmat,
+                        float2* mat32, cudaStream_t st, Counters* c) {
+  k_ramp<<<stream_blocks(ne), 256, 0, st>>>(gt, ne, r, mat, dmat, mat32);
+  if (c) { c->launches += 1; c->bytes += 48.0 * ne; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dfds(const Grid& g, int heated_layers, double w_node, double* out, cudaStream_t st,
+                        Counters* c) {
+  k_dfds<<<grid_blocks(g.nn, 256), 256, 0, st>>>(g, heated_layers, w_node, out);
+  if (c) { c->launches += 1; c->bytes += 16.0 * g.nn; }
+  return cudaGetLastError();
+}
+
+}  // namespace nc

@@ -1,0 +1,177 @@
+// Host-side launchers of the natconv kernels (all asynchronous on the given stream).
+#pragma once
+
+#include <cuda_runtime.h>
+#include "nc_common.cuh"
+#include "nc_element.cuh"
+
+namespace nc {
+
+// Physical constants of one problem, in FP64; converted to ElemConst<R> per launch.
+struct Phys {
+  double h, beta, rc, mu, he, tau3, Q;  // Q: source in the heated layers (already ramped)
+  int heated_layers;
+};
+
+template <typename R>
+inline ElemConst<R> make_econst(const Phys& p) {
+  ElemConst<R> C;
+  const double g = 1.0 / 1.7320508075688772935;   // 1/sqrt(3)
+  C.cp = (R)(0.5 * (1.0 + g));
+  C.cm = (R)(0.5 * (1.0 - g));
+  C.ih = (R)(1.0 / p.h);
+  C.w = (R)(0.125 * p.h * p.h * p.h);
+  C.beta = (R)p.beta;
+  C.rc = (R)p.rc;
+  C.imu = (R)(1.0 / p.mu);
+  C.c4he2 = (R)(4.0 / (p.he * p.he));
+  C.itau3sq = (R)(1.0 / (p.tau3 * p.tau3));
+  return C;
+}
+
+// Counters of one call (kernel launches and algorithmic bytes).
+struct Counters {
+  long long launches = 0;
+  double bytes = 0.0;
+};
+
+// ---------------- element operators (nc_kernels_elem.cu) ----------------
+// out (2N doubles) = R(s); Dirichlet rows = s. s: double2 per node; mat: (kappa, k) per element.
+cudaError_t launch_residual(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
+                            double* out, cudaStream_t st, Counters* c);
+// out = J(s) v (projected: Dirichlet inputs ignored, Dirichlet outputs 0); FP64 arithmetic.
+cudaError_t launch_jv_f64(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
+                          const double2* v, double* out, cudaStream_t st, Counters* c);
+// Same product in FP32 arithmetic; s32/mat32 FP32 copies, v and out FP64.
+cudaError_t launch_jv_f32_io64(const Grid& g, const Phys& ph, const float2* s32, const float2* mat32,
+                               const double2* v, double* out, cudaStream_t st, Counters* c);
+// out = J(s)^T w (projected), FP64, and the FP32 variant.
+cudaError_t launch_jtv_f64(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
+                           const double2* w, double* out, cudaStream_t st, Counters* c);
+cudaError_t launch_jtv_f32_io64(const Grid& g, const Phys& ph, const float2* s32, const float2* mat32,
+                                const double2* w, double* out, cudaStream_t st, Counters* c);
+// d f / d gamma~_e = -(dL/dkappa kappa' + dL/dk k'), 0 on heated elements; dmat: (kappa', k').
+cudaError_t launch_sens_elem(const Grid& g, const Phys& ph, const double2* s, const double2* lam,
+                             const double2* mat, const double2* dmat, double* out, cudaStream_t st,
+                             Counters* c);
+// Centroid Darcy velocity (3 per element).
+cudaError_t launch_u_centroid(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
+                              double* u, cudaStream_t st, Counters* c);
+
+// ---------------- vector / reduction / design kernels (nc_kernels_vec.cu) ----------------
+// Deterministic reductions: partial sums per block, then a fixed-order final sum.
+int reduce_blocks(long long n);
+// res[i] = <V_i, w> for i < nvec, V_i = V + i*ld; n doubles each. part: nvec*reduce_blocks(n).
+cudaError_t launch_multidot(const double* V, long long ld, int nvec, const double* w, long long n,
+                            double* part, double* res, cudaStream_t st, Counters* c);
+// res[0] = sum over free entries (Dirichlet rows excluded) of a^2, for a state vector.
+cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, double* res,
+                              cudaStream_t st, Counters* c);
+// y += sum_i coef[i] * V_i (nvec <= 64), n doubles.
+cudaError_t launch_axpy_multi(double* y, const double* V, long long ld, int nvec, const double* coef,
+                              long long n, cudaStream_t st, Counters* c);
+// y = a*x + b*y
+cudaError_t launch_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st,
+                         Counters* c);
+// y = x * a
+cudaError_t launch_scale_copy(double* y, const double* x, double a, long long n, cudaStream_t st,
+                              Counters* c);
+cudaError_t launch_cast_d2f(float* y, const double* x, long long n, cudaStream_t st, Counters* c);
+cudaError_t launch_cast_f2d(double* y, const float* x, long long n, cudaStream_t st, Counters* c);
+// Zero the Dirichlet (top plane) entries of a state vector.
+cudaError_t launch_zero_dirichlet(const Grid& g, double* a, cudaStream_t st, Counters* c);
+// Design check: flag = 1 if any value is NaN or outside [0,1].
+cudaError_t launch_check_design(const double* rho, long long ne, int* flag, cudaStream_t st);
+// Filter pieces (Helmholtz (r^2 K + M) x = T^T gamma, Q1 nodal, element mean out).
+struct FilterConst { double A[64]; double t0; double diag; };
+cudaError_t launch_filter_rhs(const Grid& g, const double* gamma, int heated_layers, double scale_elem,
+                              double* b, cudaStream_t st, Counters* c);
+cudaError_t launch_helmholtz(const Grid& g, const FilterConst& F, const double* x, double* y,
+                             cudaStream_t st, Counters* c);
+cudaError_t launch_helmholtz_diag(const Grid& g, const FilterConst& F, double* dinv, cudaStream_t st);
+// out_e = scale * sum_a x_{n(e,a)}; heated elements get `heated_value` if heated_value >= 0
+cudaError_t launch_elem_from_nodes(const Grid& g, const double* x, double scale, int heated_layers,
+                                   double heated_value, double* out, cudaStream_t st, Counters* c);
+// RAMP (Eqs. condRAMP, permRAMP): mat = (kappa, k), dmat = (kappa', k'), mat32 FP32 copy.
+struct RampConst { double kappa_f, kappa_s, k_f, k_s, q_c, q_p; };
+cudaError_t launch_ramp(const double* gt, long long ne, const RampConst& r, double2* mat, double2* dmat,
+                        float2* mat32, cudaStream_t st, Counters* c);
+// PCG helpers: z = dinv .* r
+cudaError_t launch_vmul(double* z, const double* a, const double* b, long long n, cudaStream_t st,
+                        Counters* c);
+// Objective weights df/ds (mean T over the heated region) and objective value.
+cudaError_t launch_dfds(const Grid& g, int heated_layers, double w_node, double* out, cudaStream_t st,
+                        Counters* c);
+
+// ---------------- multigrid (nc_kernels_mg.cu) ----------------
+template <typename R> struct MGLevelDev {
+  Grid g;
+  typename Vec2<R>::type* x;
+  typename Vec2<R>::type* xn;
+  typename Vec2<R>::type* b;
+  typename Vec2<R>::type* y;
+  R* ebe;       // 256 per element (levels >= 1)
+  R* dinv;      // 4 per node (2x2 block-diagonal inverse, row major), 0 on Dirichlet nodes
+};
+
+// Level-0 set-up: element Jacobians of J(s) (R arithmetic) -> block diagonal of level 0 and
+// Galerkin element matrices of level 1 (P^T J P with trilinear P).
+template <typename R>
+cudaError_t launch_galerkin_fine(const Grid& gf, const Grid& gc, const Phys& ph,
+                                 const typename Vec2<R>::type* s, const typename Vec2<R>::type* mat,
+                                 R* diag_f, R* ebe_c, cudaStream_t st, Counters* c);
+// Level l -> l+1 Galerkin from stored element matrices; accumulates the block diagonal of level l.
+template <typename R>
+cudaError_t launch_galerkin_coarse(const Grid& gf, const Grid& gc, const R* ebe_f, R* diag_f, R* ebe_c,
+                                   cudaStream_t st, Counters* c);
+// Block diagonal of a level from its element matrices (coarsest level is not smoothed).
+template <typename R>
+cudaError_t launch_diag_from_ebe(const Grid& g, const R* ebe, R* diag, cudaStream_t st, Counters* c);
+// Invert the 2x2 blocks in place (Dirichlet nodes -> 0). flag = 1 on a singular block.
+template <typename R>
+cudaError_t launch_invert_diag(const Grid& g, R* diag, int* flag, cudaStream_t st, Counters* c);
+// y = A x on a level: level 0 matrix-free J(s) (or J^T), otherwise EBE (or its transpose).
+template <typename R>
+cudaError_t launch_level0_apply(const Grid& g, const Phys& ph, const typename Vec2<R>::type* s,
+                                const typename Vec2<R>::type* mat, const typename Vec2<R>::type* x,
+                                typename Vec2<R>::type* y, bool transpose, cudaStream_t st, Counters* c);
+template <typename R>
+cudaError_t launch_ebe_apply(const Grid& g, const R* ebe, const typename Vec2<R>::type* x,
+                             typename Vec2<R>::type* y, bool transpose, cudaStream_t st, Counters* c);
+// x_new = x + omega D^-1 (b - y)   (y = A x; first == true: x = 0, y unused)
+template <typename R>
+cudaError_t launch_jacobi_update(const Grid& g, const R* dinv, const typename Vec2<R>::type* b,
+                                 const typename Vec2<R>::type* y, const typename Vec2<R>::type* x,
+                                 typename Vec2<R>::type* xn, R omega, bool transpose, bool first,
+                                 cudaStream_t st, Counters* c);
+// r = b - y
+template <typename R>
+cudaError_t launch_sub(const Grid& g, const typename Vec2<R>::type* b, const typename Vec2<R>::type* y,
+                       typename Vec2<R>::type* r, cudaStream_t st, Counters* c);
+// b_c = P^T r_f (full weighting, Dirichlet coarse rows 0)
+template <typename R>
+cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* rf,
+                            typename Vec2<R>::type* bc, cudaStream_t st, Counters* c);
+// x_f += P x_c
+template <typename R>
+cudaError_t launch_prolong_add(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* xc,
+                               typename Vec2<R>::type* xf, cudaStream_t st, Counters* c);
+// Coarsest level: dense FP64 matrix of the free DOFs from element matrices, its inverse, and
+// the solve x = A^-1 b (or A^-T b).
+template <typename R>
+cudaError_t launch_dense_assemble(const Grid& g, const R* ebe, double* A, int nf, cudaStream_t st,
+                                  Counters* c);
+cudaError_t launch_dense_invert(double* A, double* work, int nf, int* flag, cudaStream_t st, Counters* c);
+template <typename R>
+cudaError_t launch_dense_solve(const double* Ainv, int nf, const typename Vec2<R>::type* b,
+                               typename Vec2<R>::type* x, long long nn, bool transpose, cudaStream_t st,
+                               Counters* c);
+// Cast a FP64 state vector into the multigrid type and back.
+template <typename R>
+cudaError_t launch_to_mg(const double* v, typename Vec2<R>::type* b, long long nn, cudaStream_t st,
+                         Counters* c);
+template <typename R>
+cudaError_t launch_from_mg(const typename Vec2<R>::type* x, double* z, long long nn, cudaStream_t st,
+                           Counters* c);
+
+}  // namespace nc

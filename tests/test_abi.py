@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads and exports every symbol declared in include/natconv.h.
+
+These tests make no compute call (they run on CPU-only machines)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1904_00182_gb300 import build
+    build.build()
+    from paper_1904_00182_gb300 import _abi
+    return _abi.load_library()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "natconv.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nc_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 16
+    for name in names:
+        assert hasattr(lib, name), name
+    from paper_1904_00182_gb300 import _abi
+    assert sorted(_abi.EXPORTS) == names
+
+
+def test_default_params_and_footprint(lib):
+    from paper_1904_00182_gb300 import Grid, default_params, footprint_bytes
+    p = default_params()
+    assert p.alpha == 1e3 and p.k_s == 100.0 and p.q_c == pytest.approx(8.81)
+    assert p.newton_rtol == 1e-8 and p.restart == 30
+    b16 = footprint_bytes(Grid(16, 16, 16, 1 / 16), p)
+    b32 = footprint_bytes(Grid(32, 32, 32, 1 / 32), p)
+    assert 0 < b16 < b32
+    # 128^3 mixed fits easily in the 288 GB of one GB300
+    assert footprint_bytes(Grid(128, 128, 128, 1 / 128), p) < 8e9
+
+
+def test_invalid_arguments_are_rejected_without_a_device(lib):
+    from paper_1904_00182_gb300 import Grid, NatConvError, default_params, footprint_bytes
+    p = default_params()
+    with pytest.raises(NatConvError) as e:
+        footprint_bytes(Grid(15, 16, 16, 1 / 16), p)          # odd: no multigrid hierarchy
+    assert e.value.status_name == "NC_ERR_ARG"
+    with pytest.raises(NatConvError):
+        footprint_bytes(Grid(16, 16, 16, -1.0), p)
+    p.heated_layers = 16
+    with pytest.raises(NatConvError):
+        footprint_bytes(Grid(16, 16, 16, 1 / 16), p)
+    assert lib.nc_last_error(None)
+    p = default_params()
+    p.restart = 0
+    with pytest.raises(NatConvError):
+        footprint_bytes(Grid(16, 16, 16, 1 / 16), p)
+
+
+def test_product_has_no_cpu_fallback():
+    """The package never imports the oracle and raises when the library is missing."""
+    pkg = os.path.join(ROOT, "paper_1904_00182_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            src = open(os.path.join(pkg, f)).read()
+            assert "import oracle" not in src and "from oracle" not in src, f
+    from paper_1904_00182_gb300 import _abi
+    with pytest.raises(ImportError):
+        _abi.load_library(os.path.join(ROOT, "does_not_exist.so"))

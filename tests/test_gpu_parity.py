@@ -1,0 +1,123 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Sizes the oracle finishes in seconds: 16^3 (4096 elements, 32 blocks of the element kernels) and
+a ragged 12 x 10 x 6 box. Tolerances: FP64 operators 1e-12 relative (only the summation order
+differs), FP32 operators 1e-4, solved fields 1e-8 (FP64 path) / 1e-6 (mixed path) relative L2,
+sensitivities 1e-6 relative L2 (the targets stated for this method's GPU path).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from synthetic import filtered_random
+
+pytestmark = pytest.mark.gpu
+
+CASES = [((16, 16, 16), 1e3, 0), ((12, 10, 6), 1e4, 1)]
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1904_00182_gb300 import build
+    build.build()
+    import paper_1904_00182_gb300 as nc
+    return nc
+
+
+def make_pair(nc, shape, alpha, seed, precision=1, volfrac=0.2, rtol=1e-10):
+    nx, ny, nz = shape
+    h = 1.0 / nz
+    rho = filtered_random(nx, ny, nz, seed, volfrac=volfrac)
+    gp = nc.Problem(nx, ny, nz, h, alpha=alpha, precision=precision, newton_rtol=rtol)
+    gp.set_design(rho)
+    op = oracle.Problem(oracle.Mesh(nx, ny, nz, h), oracle.Params(alpha=alpha, newton_rtol=rtol))
+    op.set_design(rho)
+    return gp, op, rho
+
+
+def random_state(op, seed):
+    rng = np.random.default_rng(seed)
+    n = op.mesh.n_nodes
+    s = np.empty(2 * n)
+    s[0::2] = 50.0 * rng.standard_normal(n)
+    s[1::2] = 0.3 * rng.random(n)
+    s[op.dir_mask] = 0.0
+    return s
+
+
+@pytest.mark.parametrize("shape,alpha,seed", CASES)
+def test_design_fields(lib, shape, alpha, seed):
+    gp, op, _ = make_pair(lib, shape, alpha, seed)
+    gt, kap, k = [x.cpu().numpy() for x in gp.design_fields()]
+    assert rel(gt, op.gamma_t) < 1e-10
+    assert np.abs(gt - op.gamma_t).max() < 1e-10
+    assert rel(kap, op.kappa) < 1e-9
+    assert rel(k, op.k) < 1e-10
+    gp.close()
+
+
+@pytest.mark.parametrize("shape,alpha,seed", CASES)
+def test_residual(lib, shape, alpha, seed):
+    gp, op, _ = make_pair(lib, shape, alpha, seed)
+    for trial in range(2):
+        s = random_state(op, 10 + trial)
+        R, n2 = gp.eval_residual(s)
+        Ro = op.residual(s)
+        assert rel(R.cpu().numpy(), Ro) < 1e-12
+        assert n2 == pytest.approx(np.dot(Ro[op.free], Ro[op.free]), rel=1e-12)
+    gp.close()
+
+
+@pytest.mark.parametrize("shape,alpha,seed", CASES)
+def test_jacobian_products(lib, shape, alpha, seed):
+    gp, op, _ = make_pair(lib, shape, alpha, seed)
+    s = random_state(op, 3)
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal(s.shape)
+    v[op.dir_mask] = 0.0
+    expect = op.jvp_raw(s, v)
+    expect[op.dir_mask] = 0.0
+    j64 = gp.apply_jacobian(s, v, lib.NC_PREC_FP64).cpu().numpy()
+    assert rel(j64, expect) < 1e-12
+    j32 = gp.apply_jacobian(s, v, lib.NC_PREC_MIXED).cpu().numpy()
+    assert rel(j32, expect) < 1e-4
+    # transpose: (J_ff)^T w on the free rows
+    w = rng.standard_normal(s.shape)
+    w[op.dir_mask] = 0.0
+    J = op.jacobian_full(s)
+    f = op.free
+    jt_expect = np.zeros_like(w)
+    jt_expect[f] = J[f][:, f].T @ w[f]
+    jt = gp.apply_jacobian_transpose(s, w).cpu().numpy()
+    assert rel(jt, jt_expect) < 1e-12
+    # adjoint identity on the GPU products alone
+    assert np.dot(j64, w) == pytest.approx(np.dot(v, jt), rel=1e-11)
+    gp.close()
+
+
+@pytest.mark.parametrize("shape,alpha,seed", CASES)
+@pytest.mark.parametrize("precision,tol", [(1, 1e-8), (0, 1e-6)])
+def test_state_adjoint_sensitivities(lib, shape, alpha, seed, precision, tol):
+    gp, op, rho = make_pair(lib, shape, alpha, seed, precision=precision)
+    stats = gp.solve_state()
+    assert stats["rel_residual"] <= 1e-10
+    op.solve_state()
+    P, T, u = gp.get_fields()
+    Po, To = op.fields()
+    assert rel(P.cpu().numpy(), Po) < tol
+    assert rel(T.cpu().numpy(), To) < tol
+    assert rel(u.cpu().numpy(), op.velocities()) < tol
+    f, ast = gp.solve_adjoint()
+    assert f == pytest.approx(op.objective(), rel=tol)
+    op.solve_adjoint()
+    g = gp.sensitivities().cpu().numpy()
+    go = op.sensitivities()
+    assert rel(g, go) < 1e-6
+    gp.close()
