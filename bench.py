@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the Darcy-Boussinesq state solve + adjoint on GB300.
+
+One step = one pass of the whole path on one synthetic design: design pipeline (PDE filter,
+RAMP) -> damped Newton state solve to relative residual 1e-8 -> adjoint solve -> sensitivities.
+Workload (default): 128 x 128 x 128 Q1 elements (unit cube, h = 1/128), filtered-random density
+at volume fraction 0.2, buoyancy factor alpha = 1e4, mixed-precision multigrid with 6 levels,
+FP64 outer Newton. Metric: state solves per second (each including its adjoint and
+sensitivities), whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this method) on the host cores,
+on a bounded sample of the same workload. N > 1 runs one independent replica per GPU (the path
+does not shard across GPUs here) with max-over-ranks timing.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synthetic import filtered_random  # noqa: E402
+
+METRIC = "state solves/s at 128^3 (mixed precision, rel. res 1e-8, with adjoint + sensitivities)"
+UNIT = "solves/s"
+CPU_SAMPLE_N = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--alpha", type=float, default=1e4)
+    ap.add_argument("--volfrac", type=float, default=0.2)
+    ap.add_argument("--levels", type=int, default=6)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------- clocks ------
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, util, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                util.append(float(parts[4]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[6:10]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        loaded = [s for s, u in zip(sm, util) if u > 0] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------- CPU oracle --
+def oracle_steps(seconds, n=CPU_SAMPLE_N, alpha=1e4, volfrac=0.2, max_steps=None):
+    """Time the FP64 oracle's whole path (design, state, adjoint, sensitivities) on n^3 designs."""
+    try:
+        from threadpoolctl import threadpool_limits
+        limiter = threadpool_limits(limits=1)
+    except ImportError:  # the GPU machine has no threadpoolctl; NumPy/SciPy work here is single-threaded
+        limiter = None
+    import oracle
+    times = []
+    t_end = time.perf_counter() + seconds
+    k = 0
+    while True:
+        rho = filtered_random(n, n, n, seed=1000 + k, volfrac=volfrac)
+        t0 = time.perf_counter()
+        op = oracle.Problem(oracle.Mesh(n, n, n, 1.0 / n), oracle.Params(alpha=alpha, newton_rtol=1e-8))
+        op.set_design(rho)
+        op.solve_state()
+        op.solve_adjoint()
+        op.sensitivities()
+        times.append(time.perf_counter() - t0)
+        k += 1
+        if (max_steps is not None and k >= max_steps) or (max_steps is None and time.perf_counter() > t_end):
+            break
+    if limiter is not None:
+        limiter.unregister() if hasattr(limiter, "unregister") else None
+    return times
+
+
+def scale_to_workload(sec_per_solve, n_sample, n_work):
+    """Solves/s at the workload size assuming the oracle's cost grows linearly with the node count
+    (optimistic for the oracle: its sparse direct solves grow faster than linearly)."""
+    ratio = ((n_work + 1) ** 3) / ((n_sample + 1) ** 3)
+    return 1.0 / (sec_per_solve * ratio)
+
+
+# ------------------------------------------------------------------------------- reference ---
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_steps(0, max_steps=1, alpha=args.alpha, volfrac=args.volfrac)
+    t0 = time.perf_counter()
+    times = oracle_steps(0, max_steps=args.steps, alpha=args.alpha, volfrac=args.volfrac)
+    wall = time.perf_counter() - t0
+    per = wall / args.steps
+    value = scale_to_workload(per, CPU_SAMPLE_N, args.n)
+    sample = ("oracle whole path (filter, Newton to 1e-8, adjoint, sensitivities) on %d^3 designs, "
+              "scaled to %d^3 by node count" % (CPU_SAMPLE_N, args.n))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args):
+    return {"workload": "%dx%dx%d Q1 Darcy-Boussinesq, filtered-random density V=%.1f, alpha=%g, "
+                        "mixed-precision GMG (%d levels), Newton to rel. res 1e-8 + adjoint + sensitivities"
+                        % (args.n, args.n, args.n, args.volfrac, args.alpha, args.levels),
+            "grid": [args.n, args.n, args.n], "alpha": args.alpha, "volfrac": args.volfrac,
+            "mg_levels": args.levels, "newton_rtol": 1e-8, "precision": "mixed (FP32 MG + FP32 Krylov operator, "
+            "FP64 residual / orthogonalisation / coarse solve)",
+            "l2": "inputs larger than L2 (Krylov basis ~1 GB, multigrid hierarchy ~0.4 GB per solve)",
+            "parallelism": "replicas (one independent problem per GPU)"}
+
+
+# ------------------------------------------------------------------------------- GPU arm -----
+DOMINANT_BYTES_NOTE = {
+    "mg_op0": "FP32 matrix-free Jacobian of the finest multigrid level: reads s, x (8 B/node each), "
+              "(kappa,k) (8 B/element), writes y (8 B/node) = 32 B per node",
+}
+
+
+def run_gpu(args, rank, world, local):
+    import torch
+    import paper_1904_00182_gb300 as nc
+    from paper_1904_00182_gb300 import build as ncbuild
+
+    ncbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+        dist = tdist
+    n = args.n
+    E = n ** 3
+    ndes = max(1, min(3, args.steps + args.warmup))
+    designs = [filtered_random(n, n, n, seed=100 * rank + i, volfrac=args.volfrac) for i in range(ndes)]
+    rho_dev = [torch.from_numpy(d).to(dev) for d in designs]
+    rho_host = [torch.from_numpy(d).pin_memory() for d in designs]
+    grad_dev = torch.empty(E, dtype=torch.float64, device=dev)
+    grad_host = torch.empty(E, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.Stream(device=dev)
+    pb = nc.Problem(n, n, n, 1.0 / n, stream=stream.cuda_stream, device=dev, alpha=args.alpha,
+                    mg_levels=args.levels, precision=nc.NC_PREC_MIXED)
+    stats_log = []
+
+    def step(i, host=False):
+        if host:
+            pb.set_design(rho_host[i % ndes])
+        else:
+            pb.set_design(rho_dev[i % ndes])
+        st = pb.solve_state()
+        f, ast = pb.solve_adjoint()
+        pb.sensitivities(out=grad_host if host else grad_dev)
+        stats_log.append((st, ast))
+        return f
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    pb.set_profiling(True)
+    l0, _ = pb.counters()
+    clocks = ClockSampler(local)
+    clocks.start()
+    stats_log.clear()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    l1, _ = pb.counters()
+    prof = pb.profile()
+    pb.set_profiling(False)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(t.item())
+    timed_stats = list(stats_log)
+    value = world * args.steps / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers (H2D of the design, D2H of f and the gradient)
+    e2e = None
+    if not args.no_e2e:
+        step(0, host=True)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            step(i, host=True)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([wall], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            wall = float(t.item())
+        e2e = {"value": world * args.steps / wall, "unit": UNIT, "h2d_bytes_per_step": 8 * E,
+               "d2h_bytes_per_step": 8 * E + 8}
+
+    # the all-FP64 path on the same workload, for the mixed-vs-FP64 comparison
+    fp64 = None
+    if args.fp64_steps > 0:
+        pb.close()
+        p64 = nc.Problem(n, n, n, 1.0 / n, stream=stream.cuda_stream, device=dev, alpha=args.alpha,
+                         mg_levels=args.levels, precision=nc.NC_PREC_FP64)
+        def step64(i):
+            p64.set_design(rho_dev[i % ndes])
+            st = p64.solve_state()
+            p64.solve_adjoint()
+            p64.sensitivities(out=grad_dev)
+            return st
+        step64(0)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st64 = [step64(args.warmup + i) for i in range(args.fp64_steps)]
+        e1.record(stream)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": args.fp64_steps / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
+                "newton_its": [s["newton_its"] for s in st64], "krylov_its": [s["krylov_its"] for s in st64],
+                "rel_residual": [s["rel_residual"] for s in st64]}
+        p64.close()
+    else:
+        pb.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel class, from the live CUDA-event timing of the timed region
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        peaks = json.load(fh)
+    dom = max(prof, key=lambda k: prof[k][0])
+    dms, dn, dbytes = prof[dom]
+    roof = None
+    if dn > 0:
+        per_launch_s = dms * 1e-3 / dn
+        per_launch_bytes = dbytes / dn
+        achieved = per_launch_bytes / per_launch_s / 1e9
+        roof = {"bound": "hbm", "kernel_class": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "per_launch_us": per_launch_s * 1e6, "launches": dn,
+                "alg_bytes_per_launch": per_launch_bytes, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    breakdown = {k: {"ms": v[0], "launches": v[1], "share": v[0] / ms} for k, v in prof.items() if v[1] > 0}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        times = oracle_steps(args.cpu_seconds, alpha=args.alpha, volfrac=args.volfrac)
+        per = float(np.mean(times))
+        cpu = {"value": scale_to_workload(per, CPU_SAMPLE_N, n), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d oracle whole-path solves (filter, Newton to 1e-8, adjoint, sensitivities) on %d^3 "
+                         "designs, %.2f s each, scaled to %d^3 by node count" % (len(times), CPU_SAMPLE_N, per, n)}
+
+    st_last = timed_stats[-1][0] if timed_stats else {}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
+            "config": workload_config(args), "clocks": clk, "e2e": e2e,
+            "gpu_launches": int(l1 - l0), "roofline": roof, "cpu_baseline": cpu,
+            "fp64_path": fp64,
+            "solver": {"newton_its": [s[0]["newton_its"] for s in timed_stats],
+                       "krylov_its": [s[0]["krylov_its"] for s in timed_stats],
+                       "adjoint_krylov_its": [s[1]["krylov_its"] for s in timed_stats],
+                       "rel_residual": [s[0]["rel_residual"] for s in timed_stats],
+                       "state_ms": [s[0]["t_total_ms"] for s in timed_stats],
+                       "adjoint_ms": [s[1]["t_total_ms"] for s in timed_stats],
+                       "krylov_hist_last": st_last.get("krylov_hist")},
+            "kernel_time_share": breakdown}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

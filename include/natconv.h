@@ -177,6 +177,32 @@ nc_status nc_apply_jacobian(nc_problem* pb, const double* s, const double* v, do
 nc_status nc_apply_jacobian_transpose(nc_problem* pb, const double* s, const double* w,
                                       double* out);
 
+/* Kernel classes timed when profiling is on (nc_set_profiling). */
+enum {
+  NC_PROF_RESIDUAL = 0,     /* FP64 residual element sweep */
+  NC_PROF_OUTER_OP64 = 1,   /* FP64 J v / J^T w of the Krylov solver */
+  NC_PROF_OUTER_OP32 = 2,   /* FP32 J v / J^T w of the Krylov solver */
+  NC_PROF_MG_OP0 = 3,       /* multigrid finest-level operator (matrix-free Jacobian) */
+  NC_PROF_MG_EBE = 4,       /* multigrid coarse-level element-matrix operators */
+  NC_PROF_MG_SETUP = 5,     /* Galerkin set-up of the finest level */
+  NC_PROF_SMOOTH = 6,       /* block-Jacobi update, restriction, prolongation */
+  NC_PROF_KRYLOV_VEC = 7,   /* FGMRES dot products and vector updates */
+  NC_PROF_FILTER = 8,       /* PDE filter operator and vectors */
+  NC_PROF_NCLASSES = 9
+};
+
+/* Turn per-launch CUDA-event timing of the kernel classes above on (1) or off (0) for calls on
+ * pb; turning it on resets the accumulated times. Timing adds two event records per launch. */
+nc_status nc_set_profiling(nc_problem* pb, int on);
+
+/* Accumulated device time (ms), launches and algorithmic bytes of kernel class cls since
+ * profiling was turned on. Any output pointer may be NULL. */
+nc_status nc_get_profile(const nc_problem* pb, int cls, double* ms, long long* launches, double* bytes);
+
+/* Kernel launches and algorithmic bytes of every library kernel on pb since creation
+ * (monotonic counters; any output pointer may be NULL). */
+nc_status nc_counters(const nc_problem* pb, long long* launches, double* bytes);
+
 /* Message of the last failed call on pb (or of the last failed nc_create_problem if pb is
  * NULL). Never NULL. */
 const char* nc_last_error(const nc_problem* pb);

@@ -18,7 +18,11 @@ STATUS_NAMES = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_OOM", 3: "NC_ERR_CUDA", 
 EXPORTS = ("nc_default_params", "nc_create_problem", "nc_destroy_problem", "nc_footprint_bytes",
            "nc_set_design", "nc_set_state", "nc_solve_state", "nc_objective", "nc_solve_adjoint",
            "nc_sensitivities", "nc_get_fields", "nc_get_design_fields", "nc_eval_residual",
-           "nc_apply_jacobian", "nc_apply_jacobian_transpose", "nc_last_error")
+           "nc_apply_jacobian", "nc_apply_jacobian_transpose", "nc_set_profiling", "nc_get_profile",
+           "nc_counters", "nc_last_error")
+
+PROF_CLASSES = ("residual", "outer_op64", "outer_op32", "mg_op0", "mg_ebe", "mg_setup", "smooth",
+                "krylov_vec", "filter")
 
 
 class NatConvError(RuntimeError):
@@ -97,6 +101,9 @@ def load_library(path=None):
         "nc_eval_residual": ([vp, vp, vp, dp], i),
         "nc_apply_jacobian": ([vp, vp, vp, vp, i], i),
         "nc_apply_jacobian_transpose": ([vp, vp, vp, vp], i),
+        "nc_set_profiling": ([vp, i], i),
+        "nc_get_profile": ([vp, i, dp, ctypes.POINTER(ctypes.c_longlong), dp], i),
+        "nc_counters": ([vp, ctypes.POINTER(ctypes.c_longlong), dp], i),
         "nc_last_error": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():

@@ -103,7 +103,16 @@ struct nc_problem {
   int stage = 0;         // 0 created, 1 design set, 2 state solved, 3 adjoint solved
   double ref_norm = 0.0; // ||R_free(0)|| with the full source
   double t_start = 0.0;
-  Counters cnt;
+  Counters cnt;       // per call
+  Counters total;     // since creation
+  // per-launch event timing of kernel classes (nc_set_profiling)
+  struct Pending { int cls; cudaEvent_t a, b; double bytes; };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> evpool;
+  std::vector<Pending> pending;
+  double prof_ms[NC_PROF_NCLASSES] = {0};
+  long long prof_n[NC_PROF_NCLASSES] = {0};
+  double prof_bytes[NC_PROF_NCLASSES] = {0};
 };
 
 namespace {
@@ -133,6 +142,63 @@ nc_status cuda_fail(nc_problem* pb, cudaError_t e, const char* what) {
     if (_s != NC_OK) return _s;                                 \
   } while (0)
 
+cudaEvent_t prof_event(nc_problem* pb) {
+  if (!pb->evpool.empty()) {
+    cudaEvent_t e = pb->evpool.back();
+    pb->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return e;
+}
+
+// Accumulate the timed launches whose events have completed (called after a stream sync).
+void prof_flush(nc_problem* pb) {
+  for (auto& p : pb->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      pb->prof_ms[p.cls] += ms;
+      pb->prof_n[p.cls] += 1;
+      pb->prof_bytes[p.cls] += p.bytes;
+    } else {
+      cudaGetLastError();
+    }
+    pb->evpool.push_back(p.a);
+    pb->evpool.push_back(p.b);
+  }
+  pb->pending.clear();
+}
+
+// Brackets one launch of class cls with timing events when profiling is on.
+struct ProfScope {
+  nc_problem* pb;
+  int cls;
+  cudaEvent_t a = nullptr;
+  double bytes0;
+  ProfScope(nc_problem* p, int c) : pb(p), cls(c), bytes0(p->cnt.bytes) {
+    if (pb->prof_on && (a = prof_event(pb))) cudaEventRecord(a, pb->st);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = prof_event(pb);
+    if (!b) { pb->evpool.push_back(a); return; }
+    cudaEventRecord(b, pb->st);
+    pb->pending.push_back({cls, a, b, pb->cnt.bytes - bytes0});
+    if (pb->pending.size() > 4096) {
+      cudaStreamSynchronize(pb->st);
+      prof_flush(pb);
+    }
+  }
+};
+
+#define PCK(cls, x)                                             \
+  do {                                                          \
+    ProfScope _ps(pb, cls);                                     \
+    cudaError_t _e = (x);                                       \
+    if (_e != cudaSuccess) return cuda_fail(pb, _e, #x);        \
+  } while (0)
+
 template <typename T>
 nc_status dalloc(nc_problem* pb, T** p, size_t count) {
   size_t b = sizeof(T) * std::max<size_t>(count, 1);
@@ -155,6 +221,7 @@ nc_status sync(nc_problem* pb, const char* what) {
   cudaError_t e = cudaStreamSynchronize(pb->st);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(pb, e, what);
+  if (!pb->pending.empty()) prof_flush(pb);
   return NC_OK;
 }
 
@@ -166,7 +233,7 @@ nc_status check_timeout(nc_problem* pb) {
 // ---------------------------------------------------------------- reductions -------
 nc_status dots(nc_problem* pb, const double* V, long long ld, int nvec, const double* w, long long n,
                double* out) {
-  CK(launch_multidot(V, ld, nvec, w, n, pb->part, pb->dres, pb->st, &pb->cnt));
+  PCK(NC_PROF_KRYLOV_VEC, launch_multidot(V, ld, nvec, w, n, pb->part, pb->dres, pb->st, &pb->cnt));
   CK(cudaMemcpyAsync(pb->hres, pb->dres, sizeof(double) * nvec, cudaMemcpyDeviceToHost, pb->st));
   CKS(sync(pb, "dot products"));
   for (int i = 0; i < nvec; ++i) out[i] = pb->hres[i];
@@ -196,7 +263,7 @@ nc_status filter_solve(nc_problem* pb) {
   if (bb == 0.0) return NC_OK;
   const double tol2 = pb->par.filter_rtol * pb->par.filter_rtol * bb;
   for (int it = 0; it < 2000; ++it) {
-    CK(launch_helmholtz(g, pb->F, pb->fp, pb->fq, pb->st, &pb->cnt));
+    PCK(NC_PROF_FILTER, launch_helmholtz(g, pb->F, pb->fp, pb->fq, pb->st, &pb->cnt));
     double pq;
     CKS(dots(pb, pb->fp, 0, 1, pb->fq, n, &pq));
     const double a = rz / pq;
@@ -217,7 +284,7 @@ nc_status filter_solve(nc_problem* pb) {
 
 // ---------------------------------------------------------------- operators --------
 nc_status residual(nc_problem* pb, const double2* s, double* R, double* phi) {
-  CK(launch_residual(pb->g, pb->ph, s, pb->mat, R, pb->st, &pb->cnt));
+  PCK(NC_PROF_RESIDUAL, launch_residual(pb->g, pb->ph, s, pb->mat, R, pb->st, &pb->cnt));
   CKS(norm2_free(pb, R, phi));
   if (!std::isfinite(*phi)) return fail(pb, NC_ERR_NAN, "non-finite residual");
   return NC_OK;
@@ -227,11 +294,11 @@ nc_status residual(nc_problem* pb, const double2* s, double* R, double* phi) {
 nc_status outer_op(nc_problem* pb, bool transpose, bool fp32, const double* x, double* y) {
   const Grid& g = pb->g;
   if (fp32) {
-    if (transpose) CK(launch_jtv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)x, y, pb->st, &pb->cnt));
-    else CK(launch_jv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)x, y, pb->st, &pb->cnt));
+    if (transpose) PCK(NC_PROF_OUTER_OP32, launch_jtv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)x, y, pb->st, &pb->cnt));
+    else PCK(NC_PROF_OUTER_OP32, launch_jv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)x, y, pb->st, &pb->cnt));
   } else {
-    if (transpose) CK(launch_jtv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, pb->st, &pb->cnt));
-    else CK(launch_jv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, pb->st, &pb->cnt));
+    if (transpose) PCK(NC_PROF_OUTER_OP64, launch_jtv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, pb->st, &pb->cnt));
+    else PCK(NC_PROF_OUTER_OP64, launch_jv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, pb->st, &pb->cnt));
   }
   return NC_OK;
 }
@@ -281,7 +348,7 @@ nc_status mg_setup(nc_problem* pb) {
   for (int l = 0; l < L - 1; ++l) CK(cudaMemsetAsync(mg.lev[l].dinv, 0, sizeof(R) * 4 * mg.lev[l].g.nn, pb->st));
   CK(cudaMemsetAsync(pb->dflag, 0, sizeof(int), pb->st));
   if (L == 1) return fail(pb, NC_ERR_ARG, "grid dimensions must be even for the multigrid hierarchy");
-  CK(launch_galerkin_fine<R>(mg.lev[0].g, mg.lev[1].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), mg.lev[0].dinv,
+  PCK(NC_PROF_MG_SETUP, launch_galerkin_fine<R>(mg.lev[0].g, mg.lev[1].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), mg.lev[0].dinv,
                              mg.lev[1].ebe, pb->st, &pb->cnt));
   for (int l = 1; l < L - 1; ++l)
     CK(launch_galerkin_coarse<R>(mg.lev[l].g, mg.lev[l + 1].g, mg.lev[l].ebe, mg.lev[l].dinv, mg.lev[l + 1].ebe,
@@ -298,8 +365,8 @@ nc_status mg_setup(nc_problem* pb) {
 template <typename R>
 nc_status level_apply(nc_problem* pb, int l, bool tr, const typename Vec2<R>::type* x, typename Vec2<R>::type* y) {
   MG<R>& mg = mg_of<R>(pb);
-  if (l == 0) CK(launch_level0_apply<R>(mg.lev[0].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), x, y, tr, pb->st, &pb->cnt));
-  else CK(launch_ebe_apply<R>(mg.lev[l].g, mg.lev[l].ebe, x, y, tr, pb->st, &pb->cnt));
+  if (l == 0) PCK(NC_PROF_MG_OP0, launch_level0_apply<R>(mg.lev[0].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), x, y, tr, pb->st, &pb->cnt));
+  else PCK(NC_PROF_MG_EBE, launch_ebe_apply<R>(mg.lev[l].g, mg.lev[l].ebe, x, y, tr, pb->st, &pb->cnt));
   return NC_OK;
 }
 
@@ -316,21 +383,21 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
   }
   const R om = (R)pb->par.omega;
   const int nu1 = std::max(1, pb->par.nu_pre), nu2 = std::max(0, pb->par.nu_post);
-  CK(launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.x, om, tr, true, pb->st, &pb->cnt));
+  PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.x, om, tr, true, pb->st, &pb->cnt));
   for (int it = 1; it < nu1; ++it) {
     CKS(level_apply<R>(pb, l, tr, d.x, d.y));
-    CK(launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.xn, om, tr, false, pb->st, &pb->cnt));
+    PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.xn, om, tr, false, pb->st, &pb->cnt));
     std::swap(d.x, d.xn);
   }
   CKS(level_apply<R>(pb, l, tr, d.x, d.y));
-  CK(launch_sub<R>(d.g, d.b, d.y, d.xn, pb->st, &pb->cnt));
+  PCK(NC_PROF_SMOOTH, launch_sub<R>(d.g, d.b, d.y, d.xn, pb->st, &pb->cnt));
   MGLevelDev<R>& c = mg.lev[l + 1];
-  CK(launch_restrict<R>(d.g, c.g, d.xn, c.b, pb->st, &pb->cnt));
+  PCK(NC_PROF_SMOOTH, launch_restrict<R>(d.g, c.g, d.xn, c.b, pb->st, &pb->cnt));
   CKS(vcycle<R>(pb, l + 1, tr));
-  CK(launch_prolong_add<R>(d.g, c.g, c.x, d.x, pb->st, &pb->cnt));
+  PCK(NC_PROF_SMOOTH, launch_prolong_add<R>(d.g, c.g, c.x, d.x, pb->st, &pb->cnt));
   for (int it = 0; it < nu2; ++it) {
     CKS(level_apply<R>(pb, l, tr, d.x, d.y));
-    CK(launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.xn, om, tr, false, pb->st, &pb->cnt));
+    PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.xn, om, tr, false, pb->st, &pb->cnt));
     std::swap(d.x, d.xn);
   }
   return NC_OK;
@@ -393,12 +460,12 @@ nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x,
       CKS(outer_op(pb, tr, fp32, zj, wv));
       CKS(dots(pb, V, n, j + 1, wv, n, h.data()));
       for (int i = 0; i <= j; ++i) h2[i] = -h[i];
-      CK(launch_axpy_multi(wv, V, n, j + 1, h2.data(), n, pb->st, &pb->cnt));
+      PCK(NC_PROF_KRYLOV_VEC, launch_axpy_multi(wv, V, n, j + 1, h2.data(), n, pb->st, &pb->cnt));
       CKS(dots(pb, V, n, j + 2, wv, n, h2.data()));   // second pass dots and ||w||^2
       double ww = h2[j + 1];
       double corr = 0.0;
       for (int i = 0; i <= j; ++i) { h[i] += h2[i]; corr += h2[i] * h2[i]; h2[i] = -h2[i]; }
-      CK(launch_axpy_multi(wv, V, n, j + 1, h2.data(), n, pb->st, &pb->cnt));
+      PCK(NC_PROF_KRYLOV_VEC, launch_axpy_multi(wv, V, n, j + 1, h2.data(), n, pb->st, &pb->cnt));
       double hn2 = ww - corr;
       if (!std::isfinite(hn2)) return fail(pb, NC_ERR_NAN, "non-finite Krylov vector");
       double hn = hn2 > 0.0 ? std::sqrt(hn2) : 0.0;
@@ -771,6 +838,8 @@ nc_status nc_destroy_problem(nc_problem* pb) {
   if (!pb) return NC_OK;
   DeviceGuard dg(pb->device);
   if (pb->st) cudaStreamSynchronize(pb->st);
+  prof_flush(pb);
+  for (cudaEvent_t e : pb->evpool) cudaEventDestroy(e);
   for (void* q : pb->allocs) cudaFree(q);
   if (pb->hres) cudaFreeHost(pb->hres);
   if (pb->hflag) cudaFreeHost(pb->hflag);
@@ -823,6 +892,8 @@ nc_status nc_solve_state(nc_problem* pb, nc_stats* stats) {
   if (pb->stage < 1) return fail(pb, NC_ERR_STATE, "solve_state needs a design");
   DeviceGuard dg(pb->device);
   pb->t_start = now_s();
+  pb->total.launches += pb->cnt.launches;
+  pb->total.bytes += pb->cnt.bytes;
   pb->cnt = Counters();
   if (stats) memset(stats, 0, sizeof(*stats));
   const long long nn = pb->g.nn;
@@ -868,6 +939,8 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
   if (pb->stage < 2) return fail(pb, NC_ERR_STATE, "solve_adjoint needs a solved state");
   DeviceGuard dg(pb->device);
   pb->t_start = now_s();
+  pb->total.launches += pb->cnt.launches;
+  pb->total.bytes += pb->cnt.bytes;
   pb->cnt = Counters();
   if (stats) memset(stats, 0, sizeof(*stats));
   double f;
@@ -1021,6 +1094,34 @@ nc_status nc_apply_jacobian(nc_problem* pb, const double* s, const double* v, do
 
 nc_status nc_apply_jacobian_transpose(nc_problem* pb, const double* s, const double* w, double* out) {
   return apply_generic(pb, s, w, out, true, false);
+}
+
+nc_status nc_set_profiling(nc_problem* pb, int on) {
+  if (!pb) return NC_ERR_ARG;
+  DeviceGuard dg(pb->device);
+  CKS(sync(pb, "set_profiling"));
+  pb->prof_on = on != 0;
+  for (int c = 0; c < NC_PROF_NCLASSES; ++c) { pb->prof_ms[c] = 0; pb->prof_n[c] = 0; pb->prof_bytes[c] = 0; }
+  return NC_OK;
+}
+
+nc_status nc_get_profile(const nc_problem* cpb, int cls, double* ms, long long* launches, double* bytes) {
+  nc_problem* pb = const_cast<nc_problem*>(cpb);
+  if (!pb || cls < 0 || cls >= NC_PROF_NCLASSES) return NC_ERR_ARG;
+  DeviceGuard dg(pb->device);
+  CKS(sync(pb, "get_profile"));
+  if (ms) *ms = pb->prof_ms[cls];
+  if (launches) *launches = pb->prof_n[cls];
+  if (bytes) *bytes = pb->prof_bytes[cls];
+  return NC_OK;
+}
+
+nc_status nc_counters(const nc_problem* cpb, long long* launches, double* bytes) {
+  nc_problem* pb = const_cast<nc_problem*>(cpb);
+  if (!pb) return NC_ERR_ARG;
+  if (launches) *launches = pb->total.launches + pb->cnt.launches;
+  if (bytes) *bytes = pb->total.bytes + pb->cnt.bytes;
+  return NC_OK;
 }
 
 const char* nc_last_error(const nc_problem* pb) {

@@ -132,6 +132,24 @@ class Problem:
         self._check(self.lib.nc_get_design_fields(self.h, _ptr(gt), _ptr(kap), _ptr(k)))
         return gt, kap, k
 
+    # -- measurement ---------------------------------------------------------------------------
+    def set_profiling(self, on=True):
+        self._check(self.lib.nc_set_profiling(self.h, 1 if on else 0))
+
+    def profile(self):
+        """{class: (ms, launches, algorithmic bytes)} accumulated since set_profiling(True)."""
+        out = {}
+        for cls, name in enumerate(_abi.PROF_CLASSES):
+            ms, n, b = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+            self._check(self.lib.nc_get_profile(self.h, cls, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
+            out[name] = (ms.value, n.value, b.value)
+        return out
+
+    def counters(self):
+        n, b = ctypes.c_longlong(), ctypes.c_double()
+        self._check(self.lib.nc_counters(self.h, ctypes.byref(n), ctypes.byref(b)))
+        return n.value, b.value
+
     # -- operator-level entry points -----------------------------------------------------------
     def eval_residual(self, s):
         s = _as_f64(s)
