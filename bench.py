@@ -190,12 +190,6 @@ def workload_config(args):
 
 
 # ------------------------------------------------------------------------------- GPU arm -----
-DOMINANT_BYTES_NOTE = {
-    "mg_op0": "FP32 matrix-free Jacobian of the finest multigrid level: reads s, x (8 B/node each), "
-              "(kappa,k) (8 B/element), writes y (8 B/node) = 32 B per node",
-}
-
-
 def run_gpu(args, rank, world, local):
     import torch
     import paper_1904_00182_gb300 as nc
@@ -332,6 +326,9 @@ def run_gpu(args, rank, world, local):
                 "per_launch_us": per_launch_s * 1e6, "launches": dn,
                 "alg_bytes_per_launch": per_launch_bytes, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     breakdown = {k: {"ms": v[0], "launches": v[1], "share": v[0] / ms} for k, v in prof.items() if v[1] > 0}
+    attributed = sum(v[0] for v in prof.values())
+    breakdown["unattributed (host, launch gaps)"] = {"ms": ms - attributed, "launches": 0,
+                                                     "share": (ms - attributed) / ms}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -354,7 +351,10 @@ def run_gpu(args, rank, world, local):
                        "rel_residual": [s[0]["rel_residual"] for s in timed_stats],
                        "state_ms": [s[0]["t_total_ms"] for s in timed_stats],
                        "adjoint_ms": [s[1]["t_total_ms"] for s in timed_stats],
-                       "krylov_hist_last": st_last.get("krylov_hist")},
+                       "krylov_hist_last": st_last.get("krylov_hist"),
+                       "newton_res_hist_last": st_last.get("res_hist"),
+                       "adjoint_res_hist_last": timed_stats[-1][1].get("res_hist") if timed_stats else None,
+                       "adjoint_krylov_hist_last": timed_stats[-1][1].get("krylov_hist") if timed_stats else None},
             "kernel_time_share": breakdown}
     print(json.dumps(line), flush=True)
     if dist:

@@ -94,9 +94,13 @@ typedef struct {
                            orthogonalisation and coarse solve) or NC_PREC_FP64 [MIXED] */
   int mg_levels;        /* 0: coarsen while every dimension is even [0] */
   int nu_pre, nu_post;  /* smoothing sweeps [2, 2] */
-  double omega;         /* damping of the block-Jacobi smoother [0.6] */
+  double omega;         /* damping of the block-Jacobi smoother [0.7] */
   double filter_rtol;   /* relative tolerance of the filter's conjugate gradients [1e-12] */
   double timeout_s;     /* wall-clock limit of one call [600] */
+  double adjoint_rtol;  /* adjoint stops at ||df/ds - J^T lambda|| <= adjoint_rtol ||df/ds||;
+                           <= 0: the state's newton_rtol [0] */
+  int coarse_refactor;  /* 1: invert the coarsest multigrid matrix at every set-up; 0: at the first
+                           set-up of each solve call, later set-ups refine against the new matrix [0] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */
@@ -180,15 +184,20 @@ nc_status nc_apply_jacobian_transpose(nc_problem* pb, const double* s, const dou
 /* Kernel classes timed when profiling is on (nc_set_profiling). */
 enum {
   NC_PROF_RESIDUAL = 0,     /* FP64 residual element sweep */
-  NC_PROF_OUTER_OP64 = 1,   /* FP64 J v / J^T w of the Krylov solver */
+  NC_PROF_OUTER_OP64 = 1,   /* FP64 J v / J^T w (Krylov operator, adjoint refinement residual) */
   NC_PROF_OUTER_OP32 = 2,   /* FP32 J v / J^T w of the Krylov solver */
   NC_PROF_MG_OP0 = 3,       /* multigrid finest-level operator (matrix-free Jacobian) */
-  NC_PROF_MG_EBE = 4,       /* multigrid coarse-level element-matrix operators */
-  NC_PROF_MG_SETUP = 5,     /* Galerkin set-up of the finest level */
-  NC_PROF_SMOOTH = 6,       /* block-Jacobi update, restriction, prolongation */
+  NC_PROF_MG_STENCIL = 4,   /* multigrid coarse-level stencil operators (fused smoothing / residual) */
+  NC_PROF_MG_SETUP = 5,     /* element Jacobians of the finest level and their Galerkin product */
+  NC_PROF_SMOOTH = 6,       /* block-Jacobi updates, restriction, prolongation */
   NC_PROF_KRYLOV_VEC = 7,   /* FGMRES dot products and vector updates */
   NC_PROF_FILTER = 8,       /* PDE filter operator and vectors */
-  NC_PROF_NCLASSES = 9
+  NC_PROF_SENS = 9,         /* FP64 element sensitivities */
+  NC_PROF_OTHER = 10,       /* every other library kernel (casts, copies ...) */
+  NC_PROF_MG_COARSE_SETUP = 11, /* coarse-level Galerkin products, stencils, block-diagonal inverses */
+  NC_PROF_COARSE_FACTOR = 12,   /* inverse of the coarsest-level matrix */
+  NC_PROF_COARSE_SOLVE = 13,    /* coarsest-level solve inside the V-cycle */
+  NC_PROF_NCLASSES = 14
 };
 
 /* Turn per-launch CUDA-event timing of the kernel classes above on (1) or off (0) for calls on

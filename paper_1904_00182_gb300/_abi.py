@@ -21,8 +21,8 @@ EXPORTS = ("nc_default_params", "nc_create_problem", "nc_destroy_problem", "nc_f
            "nc_apply_jacobian", "nc_apply_jacobian_transpose", "nc_set_profiling", "nc_get_profile",
            "nc_counters", "nc_last_error")
 
-PROF_CLASSES = ("residual", "outer_op64", "outer_op32", "mg_op0", "mg_ebe", "mg_setup", "smooth",
-                "krylov_vec", "filter")
+PROF_CLASSES = ("residual", "outer_op64", "outer_op32", "mg_op0", "mg_stencil", "mg_setup_fine", "smooth",
+                "krylov_vec", "filter", "sens", "other", "mg_setup_coarse", "coarse_factor", "coarse_solve")
 
 
 class NatConvError(RuntimeError):
@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
         ("krylov_rtol", ctypes.c_double), ("krylov_maxit", ctypes.c_int), ("restart", ctypes.c_int),
         ("precision", ctypes.c_int), ("mg_levels", ctypes.c_int), ("nu_pre", ctypes.c_int),
         ("nu_post", ctypes.c_int), ("omega", ctypes.c_double), ("filter_rtol", ctypes.c_double),
-        ("timeout_s", ctypes.c_double),
+        ("timeout_s", ctypes.c_double), ("adjoint_rtol", ctypes.c_double), ("coarse_refactor", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -23,9 +23,8 @@ using namespace nc;
 
 namespace {
 
-const double kAdjointRtol = 1e-10;
 const int kMaxRestart = 64;
-const int kMaxCoarseDofs = 2048;
+const int kMaxCoarseDofs = 1024;
 
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -62,9 +61,10 @@ template <typename R>
 struct MG {
   typedef typename Vec2<R>::type R2;
   std::vector<MGLevelDev<R>> lev;
-  double* Ainv = nullptr;
-  double* W = nullptr;
-  R* ebe0 = nullptr;   // level-0 element matrices, only when the hierarchy has one level
+  double* Ac = nullptr;     // coarsest-level Galerkin matrix (FP64, free DOFs)
+  float* Ainv32 = nullptr; // its FP32 inverse
+  float* W = nullptr;      // Gauss-Jordan scratch (nf x 2nf)
+  double* cw = nullptr;    // coarse-solve scratch (3 nf)
   int nf = 0;
 };
 
@@ -92,8 +92,12 @@ struct nc_problem {
   double *V = nullptr, *Z = nullptr;
   double *part = nullptr, *dres = nullptr, *hres = nullptr;
   // filter PCG (node vectors)
-  double *fx = nullptr, *fb = nullptr, *fr = nullptr, *fz = nullptr, *fp = nullptr, *fq = nullptr, *fdinv = nullptr;
+  double *fx = nullptr, *fb = nullptr, *fr = nullptr, *fq = nullptr, *fdinv = nullptr;
+  float *fxf = nullptr, *frf = nullptr, *fd0 = nullptr, *fd1 = nullptr, *fdinvf = nullptr;
   FilterConst F;
+  FilterConstF Ff;
+  double cheb_a = 0.0, cheb_b = 0.0;   // bounds of the spectrum of D^-1 (r^2 K + M)
+  int cheb_iters = 0;                  // FP32 Chebyshev steps per refinement pass
   // multigrid
   Levels lv;
   MG<float> mg32;
@@ -101,6 +105,10 @@ struct nc_problem {
   int *dflag = nullptr, *hflag = nullptr;
   // bookkeeping
   int stage = 0;         // 0 created, 1 design set, 2 state solved, 3 adjoint solved
+  bool start_zero = true; // the Newton start is the zero state (its residual is R0)
+  bool first_setup = true; // next multigrid set-up is the first of this solve call
+  bool have_R0 = false;   // R0 = R(0) with the full source: minus the SUPG-weighted source load,
+  double* R0 = nullptr;   // which does not depend on the design (u = 0, N* = N at s = 0)
   double ref_norm = 0.0; // ||R_free(0)|| with the full source
   double t_start = 0.0;
   Counters cnt;       // per call
@@ -241,7 +249,7 @@ nc_status dots(nc_problem* pb, const double* V, long long ld, int nvec, const do
 }
 
 nc_status norm2_free(nc_problem* pb, const double* a, double* out) {
-  CK(launch_norm2_free(pb->g, a, pb->part, pb->dres, pb->st, &pb->cnt));
+  PCK(NC_PROF_KRYLOV_VEC, launch_norm2_free(pb->g, a, pb->part, pb->dres, pb->st, &pb->cnt));
   CK(cudaMemcpyAsync(pb->hres, pb->dres, sizeof(double), cudaMemcpyDeviceToHost, pb->st));
   CKS(sync(pb, "norm"));
   *out = pb->hres[0];
@@ -249,37 +257,43 @@ nc_status norm2_free(nc_problem* pb, const double* a, double* out) {
 }
 
 // ---------------------------------------------------------------- design pipeline --
+// (r^2 K + M) fx = fb, FP64 result. Each refinement pass solves the correction equation for the
+// current FP64 residual with a fixed number of FP32 Chebyshev steps (Jacobi-preconditioned, bounds
+// from the stencil's Fourier symbol, no reductions), then recomputes the residual in FP64.
 nc_status filter_solve(nc_problem* pb) {
-  // PCG (Jacobi) on (r^2 K + M) fx = fb, FP64, from fx = 0.
   const Grid& g = pb->g;
   const long long n = g.nn;
-  CK(cudaMemsetAsync(pb->fx, 0, sizeof(double) * n, pb->st));
-  CK(cudaMemcpyAsync(pb->fr, pb->fb, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
-  CK(launch_vmul(pb->fz, pb->fdinv, pb->fr, n, pb->st, &pb->cnt));
-  CK(cudaMemcpyAsync(pb->fp, pb->fz, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
-  double bb, rz;
+  double bb;
   CKS(dots(pb, pb->fb, 0, 1, pb->fb, n, &bb));
-  CKS(dots(pb, pb->fr, 0, 1, pb->fz, n, &rz));
+  PCK(NC_PROF_FILTER, cudaMemsetAsync(pb->fx, 0, sizeof(double) * n, pb->st));
   if (bb == 0.0) return NC_OK;
+  CK(cudaMemcpyAsync(pb->fr, pb->fb, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
+  const double a = pb->cheb_a, b = pb->cheb_b;
+  const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
   const double tol2 = pb->par.filter_rtol * pb->par.filter_rtol * bb;
-  for (int it = 0; it < 2000; ++it) {
-    PCK(NC_PROF_FILTER, launch_helmholtz(g, pb->F, pb->fp, pb->fq, pb->st, &pb->cnt));
-    double pq;
-    CKS(dots(pb, pb->fp, 0, 1, pb->fq, n, &pq));
-    const double a = rz / pq;
-    CK(launch_axpby(pb->fx, pb->fp, a, 1.0, n, pb->st, &pb->cnt));
-    CK(launch_axpby(pb->fr, pb->fq, -a, 1.0, n, pb->st, &pb->cnt));
+  for (int pass = 0; pass < 12; ++pass) {
+    PCK(NC_PROF_FILTER, launch_cast_d2f(pb->frf, pb->fr, n, pb->st, &pb->cnt));
+    PCK(NC_PROF_FILTER, launch_cheb_init(n, pb->fdinvf, pb->frf, pb->fxf, pb->fd0, (float)(1.0 / theta), pb->st, &pb->cnt));
+    double rho = 1.0 / sigma;
+    float* d0 = pb->fd0;
+    float* d1 = pb->fd1;
+    for (int it = 0; it < pb->cheb_iters; ++it) {
+      const double rho1 = 1.0 / (2.0 * sigma - rho);
+      PCK(NC_PROF_FILTER, launch_cheb_step(g, pb->Ff, pb->fdinvf, d0, d1, pb->fxf, pb->frf, (float)(rho1 * rho),
+                                           (float)(2.0 * rho1 / delta), pb->st, &pb->cnt));
+      rho = rho1;
+      std::swap(d0, d1);
+    }
+    PCK(NC_PROF_FILTER, launch_add_f2d(pb->fx, pb->fxf, n, pb->st, &pb->cnt));
+    PCK(NC_PROF_FILTER, launch_helmholtz(g, pb->F, pb->fx, pb->fq, pb->st, &pb->cnt));
+    CK(cudaMemcpyAsync(pb->fr, pb->fb, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
+    PCK(NC_PROF_FILTER, launch_axpby(pb->fr, pb->fq, -1.0, 1.0, n, pb->st, &pb->cnt));
     double rr;
     CKS(dots(pb, pb->fr, 0, 1, pb->fr, n, &rr));
     if (!std::isfinite(rr)) return fail(pb, NC_ERR_NAN, "non-finite residual in the filter solve");
     if (rr <= tol2) return NC_OK;
-    CK(launch_vmul(pb->fz, pb->fdinv, pb->fr, n, pb->st, &pb->cnt));
-    double rz2;
-    CKS(dots(pb, pb->fr, 0, 1, pb->fz, n, &rz2));
-    CK(launch_axpby(pb->fp, pb->fz, 1.0, rz2 / rz, n, pb->st, &pb->cnt));
-    rz = rz2;
   }
-  return fail(pb, NC_ERR_MAXIT, "filter conjugate gradients did not converge");
+  return fail(pb, NC_ERR_MAXIT, "filter refinement did not converge");
 }
 
 // ---------------------------------------------------------------- operators --------
@@ -327,35 +341,43 @@ nc_status mg_alloc(nc_problem* pb) {
     CKS(dalloc(pb, &d.xn, d.g.nn));
     CKS(dalloc(pb, &d.b, d.g.nn));
     CKS(dalloc(pb, &d.y, d.g.nn));
+    d.S = nullptr;
+    d.ebe = nullptr;
+    d.dinv = nullptr;
     if (l < L - 1) CKS(dalloc(pb, &d.dinv, 4 * d.g.nn));
     if (l > 0) CKS(dalloc(pb, &d.ebe, 256 * d.g.ne));
+    if (l > 0 && l < L - 1) CKS(dalloc(pb, &d.S, 108 * d.g.nn));
   }
   mg.nf = pb->lv.nf;
-  if (L == 1) CKS(dalloc(pb, &mg.ebe0, 256 * pb->g.ne));
-  CKS(dalloc(pb, &mg.Ainv, (size_t)mg.nf * mg.nf));
+  CKS(dalloc(pb, &mg.Ac, (size_t)mg.nf * mg.nf));
+  CKS(dalloc(pb, &mg.Ainv32, (size_t)mg.nf * mg.nf));
   CKS(dalloc(pb, &mg.W, (size_t)mg.nf * 2 * mg.nf));
+  CKS(dalloc(pb, &mg.cw, (size_t)3 * mg.nf));
   return NC_OK;
 }
 
-// Level-0 element matrices (single-level hierarchies only): reuse the Galerkin kernel on a
-// "coarse" grid equal to the fine one is not possible, so assemble via a 1-level trick: the
-// element Jacobian columns are the Jacobian products with unit vectors.
 template <typename R>
-nc_status mg_setup(nc_problem* pb) {
+nc_status mg_setup(nc_problem* pb, bool refactor) {
   MG<R>& mg = mg_of<R>(pb);
   const int L = (int)mg.lev.size();
-  if (sizeof(R) == 4) CK(launch_cast_d2f((float*)pb->s32, (const double*)pb->s, 2 * pb->g.nn, pb->st, &pb->cnt));
+  if (sizeof(R) == 4) PCK(NC_PROF_MG_COARSE_SETUP, launch_cast_d2f((float*)pb->s32, (const double*)pb->s, 2 * pb->g.nn, pb->st, &pb->cnt));
   for (int l = 0; l < L - 1; ++l) CK(cudaMemsetAsync(mg.lev[l].dinv, 0, sizeof(R) * 4 * mg.lev[l].g.nn, pb->st));
   CK(cudaMemsetAsync(pb->dflag, 0, sizeof(int), pb->st));
   if (L == 1) return fail(pb, NC_ERR_ARG, "grid dimensions must be even for the multigrid hierarchy");
   PCK(NC_PROF_MG_SETUP, launch_galerkin_fine<R>(mg.lev[0].g, mg.lev[1].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), mg.lev[0].dinv,
                              mg.lev[1].ebe, pb->st, &pb->cnt));
   for (int l = 1; l < L - 1; ++l)
-    CK(launch_galerkin_coarse<R>(mg.lev[l].g, mg.lev[l + 1].g, mg.lev[l].ebe, mg.lev[l].dinv, mg.lev[l + 1].ebe,
+    PCK(NC_PROF_MG_COARSE_SETUP, launch_galerkin_coarse<R>(mg.lev[l].g, mg.lev[l + 1].g, mg.lev[l].ebe, mg.lev[l].dinv, mg.lev[l + 1].ebe,
                                  pb->st, &pb->cnt));
-  CK(launch_dense_assemble<R>(mg.lev[L - 1].g, mg.lev[L - 1].ebe, mg.Ainv, mg.nf, pb->st, &pb->cnt));
-  CK(launch_dense_invert(mg.Ainv, mg.W, mg.nf, pb->dflag, pb->st, &pb->cnt));
-  for (int l = 0; l < L - 1; ++l) CK(launch_invert_diag<R>(mg.lev[l].g, mg.lev[l].dinv, pb->dflag, pb->st, &pb->cnt));
+  for (int l = 1; l < L - 1; ++l)
+    PCK(NC_PROF_MG_COARSE_SETUP, launch_stencil_build<R>(mg.lev[l].g, mg.lev[l].ebe, mg.lev[l].S, pb->st, &pb->cnt));
+  PCK(NC_PROF_MG_COARSE_SETUP, launch_dense_assemble<R>(mg.lev[L - 1].g, mg.lev[L - 1].ebe, mg.Ac, mg.nf, pb->st, &pb->cnt));
+  // The FP32 inverse of the coarsest matrix is refreshed at the first set-up of each solve call
+  // (or at every set-up if coarse_refactor is set); later set-ups keep it and the coarse solve's
+  // FP64 refinement step against the current matrix corrects for the change.
+  if (refactor || pb->par.coarse_refactor)
+    PCK(NC_PROF_COARSE_FACTOR, launch_coarse_factor(mg.Ac, mg.W, mg.Ainv32, mg.nf, pb->dflag, pb->st, &pb->cnt));
+  for (int l = 0; l < L - 1; ++l) PCK(NC_PROF_MG_COARSE_SETUP, launch_invert_diag<R>(mg.lev[l].g, mg.lev[l].dinv, pb->dflag, pb->st, &pb->cnt));
   CK(cudaMemcpyAsync(pb->hflag, pb->dflag, sizeof(int), cudaMemcpyDeviceToHost, pb->st));
   CKS(sync(pb, "multigrid set-up"));
   if (*pb->hflag) return fail(pb, NC_ERR_NAN, "singular block in the multigrid set-up");
@@ -365,41 +387,48 @@ nc_status mg_setup(nc_problem* pb) {
 template <typename R>
 nc_status level_apply(nc_problem* pb, int l, bool tr, const typename Vec2<R>::type* x, typename Vec2<R>::type* y) {
   MG<R>& mg = mg_of<R>(pb);
-  if (l == 0) PCK(NC_PROF_MG_OP0, launch_level0_apply<R>(mg.lev[0].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), x, y, tr, pb->st, &pb->cnt));
-  else PCK(NC_PROF_MG_EBE, launch_ebe_apply<R>(mg.lev[l].g, mg.lev[l].ebe, x, y, tr, pb->st, &pb->cnt));
+  if (l != 0) return fail(pb, NC_ERR_ARG, "level_apply is for the finest level");
+  PCK(NC_PROF_MG_OP0, launch_level0_apply<R>(mg.lev[0].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), x, y, tr, pb->st, &pb->cnt));
   return NC_OK;
 }
 
 // V-cycle on level l: solves approximately A_l x_l = b_l; the result is left in lev[l].x.
+// Level 0 applies the matrix-free Jacobian and updates separately; coarser levels fuse the
+// stencil product with the Jacobi update or the residual.
 template <typename R>
 nc_status vcycle(nc_problem* pb, int l, bool tr) {
-  typedef typename Vec2<R>::type R2;
   MG<R>& mg = mg_of<R>(pb);
   MGLevelDev<R>& d = mg.lev[l];
   const int L = (int)mg.lev.size();
   if (l == L - 1) {
-    CK(launch_dense_solve<R>(mg.Ainv, mg.nf, d.b, d.x, d.g.nn, tr, pb->st, &pb->cnt));
+    PCK(NC_PROF_COARSE_SOLVE, launch_coarse_solve<R>(mg.Ac, mg.Ainv32, mg.cw, mg.nf, d.b, d.x, d.g.nn, tr, pb->st, &pb->cnt));
     return NC_OK;
   }
   const R om = (R)pb->par.omega;
   const int nu1 = std::max(1, pb->par.nu_pre), nu2 = std::max(0, pb->par.nu_post);
-  PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.x, om, tr, true, pb->st, &pb->cnt));
-  for (int it = 1; it < nu1; ++it) {
-    CKS(level_apply<R>(pb, l, tr, d.x, d.y));
-    PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.xn, om, tr, false, pb->st, &pb->cnt));
+  auto sweep = [&]() -> nc_status {
+    if (l == 0) {
+      CKS(level_apply<R>(pb, l, tr, d.x, d.y));
+      PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.xn, om, tr, false, pb->st, &pb->cnt));
+    } else {
+      PCK(NC_PROF_MG_STENCIL, launch_stencil_apply<R>(d.g, d.S, d.x, d.b, d.dinv, om, d.xn, tr, 2, pb->st, &pb->cnt));
+    }
     std::swap(d.x, d.xn);
+    return NC_OK;
+  };
+  PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.x, om, tr, true, pb->st, &pb->cnt));
+  for (int it = 1; it < nu1; ++it) CKS(sweep());
+  if (l == 0) {
+    CKS(level_apply<R>(pb, l, tr, d.x, d.y));
+    PCK(NC_PROF_SMOOTH, launch_sub<R>(d.g, d.b, d.y, d.xn, pb->st, &pb->cnt));
+  } else {
+    PCK(NC_PROF_MG_STENCIL, launch_stencil_apply<R>(d.g, d.S, d.x, d.b, d.dinv, om, d.xn, tr, 1, pb->st, &pb->cnt));
   }
-  CKS(level_apply<R>(pb, l, tr, d.x, d.y));
-  PCK(NC_PROF_SMOOTH, launch_sub<R>(d.g, d.b, d.y, d.xn, pb->st, &pb->cnt));
   MGLevelDev<R>& c = mg.lev[l + 1];
   PCK(NC_PROF_SMOOTH, launch_restrict<R>(d.g, c.g, d.xn, c.b, pb->st, &pb->cnt));
   CKS(vcycle<R>(pb, l + 1, tr));
   PCK(NC_PROF_SMOOTH, launch_prolong_add<R>(d.g, c.g, c.x, d.x, pb->st, &pb->cnt));
-  for (int it = 0; it < nu2; ++it) {
-    CKS(level_apply<R>(pb, l, tr, d.x, d.y));
-    PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.xn, om, tr, false, pb->st, &pb->cnt));
-    std::swap(d.x, d.xn);
-  }
+  for (int it = 0; it < nu2; ++it) CKS(sweep());
   return NC_OK;
 }
 
@@ -407,21 +436,21 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
 nc_status precondition(nc_problem* pb, bool tr, const double* v, double* z) {
   if (pb->par.precision == NC_PREC_FP64) {
     MG<double>& mg = pb->mg64;
-    CK(launch_to_mg<double>(v, mg.lev[0].b, pb->g.nn, pb->st, &pb->cnt));
+    PCK(NC_PROF_OTHER, launch_to_mg<double>(v, mg.lev[0].b, pb->g.nn, pb->st, &pb->cnt));
     CKS(vcycle<double>(pb, 0, tr));
-    CK(launch_from_mg<double>(mg.lev[0].x, z, pb->g.nn, pb->st, &pb->cnt));
+    PCK(NC_PROF_OTHER, launch_from_mg<double>(mg.lev[0].x, z, pb->g.nn, pb->st, &pb->cnt));
   } else {
     MG<float>& mg = pb->mg32;
-    CK(launch_to_mg<float>(v, mg.lev[0].b, pb->g.nn, pb->st, &pb->cnt));
+    PCK(NC_PROF_OTHER, launch_to_mg<float>(v, mg.lev[0].b, pb->g.nn, pb->st, &pb->cnt));
     CKS(vcycle<float>(pb, 0, tr));
-    CK(launch_from_mg<float>(mg.lev[0].x, z, pb->g.nn, pb->st, &pb->cnt));
+    PCK(NC_PROF_OTHER, launch_from_mg<float>(mg.lev[0].x, z, pb->g.nn, pb->st, &pb->cnt));
   }
   return NC_OK;
 }
 
-nc_status mg_setup_any(nc_problem* pb) {
-  if (pb->par.precision == NC_PREC_FP64) return mg_setup<double>(pb);
-  return mg_setup<float>(pb);
+nc_status mg_setup_any(nc_problem* pb, bool refactor) {
+  if (pb->par.precision == NC_PREC_FP64) return mg_setup<double>(pb, refactor);
+  return mg_setup<float>(pb, refactor);
 }
 
 // ---------------------------------------------------------------- FGMRES ------------
@@ -442,8 +471,8 @@ nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x,
   if (bnorm == 0.0) return NC_OK;
   // r = b
   double beta = bnorm;
-  CK(launch_scale_copy(V, b, 1.0 / beta, n, pb->st, &pb->cnt));
-  CK(launch_zero_dirichlet(pb->g, V, pb->st, &pb->cnt));
+  PCK(NC_PROF_KRYLOV_VEC, launch_scale_copy(V, b, 1.0 / beta, n, pb->st, &pb->cnt));
+  PCK(NC_PROF_KRYLOV_VEC, launch_zero_dirichlet(pb->g, V, pb->st, &pb->cnt));
   int total = 0;
   std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m), h(m + 2), h2(m + 2);
   while (true) {
@@ -458,17 +487,39 @@ nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x,
       double* wv = V + (long long)(j + 1) * n;
       CKS(precondition(pb, tr, vj, zj));
       CKS(outer_op(pb, tr, fp32, zj, wv));
-      CKS(dots(pb, V, n, j + 1, wv, n, h.data()));
-      for (int i = 0; i <= j; ++i) h2[i] = -h[i];
-      PCK(NC_PROF_KRYLOV_VEC, launch_axpy_multi(wv, V, n, j + 1, h2.data(), n, pb->st, &pb->cnt));
-      CKS(dots(pb, V, n, j + 2, wv, n, h2.data()));   // second pass dots and ||w||^2
-      double ww = h2[j + 1];
-      double corr = 0.0;
-      for (int i = 0; i <= j; ++i) { h[i] += h2[i]; corr += h2[i] * h2[i]; h2[i] = -h2[i]; }
-      PCK(NC_PROF_KRYLOV_VEC, launch_axpy_multi(wv, V, n, j + 1, h2.data(), n, pb->st, &pb->cnt));
-      double hn2 = ww - corr;
-      if (!std::isfinite(hn2)) return fail(pb, NC_ERR_NAN, "non-finite Krylov vector");
-      double hn = hn2 > 0.0 ? std::sqrt(hn2) : 0.0;
+      double hn;
+      if (j + 1 <= 32) {
+        // CGS2 with coefficients kept on the device; one host synchronisation per iteration
+        double* d1 = pb->dres;
+        double* d2 = pb->dres + 66;
+        PCK(NC_PROF_KRYLOV_VEC, launch_multidot(V, n, j + 1, wv, n, pb->part, d1, pb->st, &pb->cnt));
+        PCK(NC_PROF_KRYLOV_VEC, launch_cgs_update_dots(wv, V, n, j + 1, d1, n, pb->part, d2, pb->st, &pb->cnt));
+        PCK(NC_PROF_KRYLOV_VEC, launch_cgs_finish(wv, V, n, j + 1, d2, n, pb->st, &pb->cnt));
+        CK(cudaMemcpyAsync(pb->hres, pb->dres, sizeof(double) * 132, cudaMemcpyDeviceToHost, pb->st));
+        CKS(sync(pb, "Gram-Schmidt"));
+        double corr = 0.0;
+        for (int i = 0; i <= j; ++i) {
+          const double c2 = pb->hres[66 + i];
+          h[i] = pb->hres[i] + c2;
+          corr += c2 * c2;
+        }
+        const double hn2 = pb->hres[66 + j + 1] - corr;
+        if (!std::isfinite(hn2)) return fail(pb, NC_ERR_NAN, "non-finite Krylov vector");
+        hn = hn2 > 0.0 ? std::sqrt(hn2) : 0.0;
+      } else {
+        CKS(dots(pb, V, n, j + 1, wv, n, h.data()));
+        for (int i = 0; i <= j; ++i) h2[i] = -h[i];
+        PCK(NC_PROF_KRYLOV_VEC, launch_axpy_multi(wv, V, n, j + 1, h2.data(), n, pb->st, &pb->cnt));
+        CKS(dots(pb, V, n, j + 2, wv, n, h2.data()));   // second pass dots and ||w||^2
+        double ww = h2[j + 1];
+        double corr = 0.0;
+        for (int i = 0; i <= j; ++i) { h[i] += h2[i]; corr += h2[i] * h2[i]; h2[i] = -h2[i]; }
+        PCK(NC_PROF_KRYLOV_VEC, launch_axpy_multi(wv, V, n, j + 1, h2.data(), n, pb->st, &pb->cnt));
+        double hn2 = ww - corr;
+        if (!std::isfinite(hn2)) return fail(pb, NC_ERR_NAN, "non-finite Krylov vector");
+        hn = hn2 > 0.0 ? std::sqrt(hn2) : 0.0;
+        if (hn > 0.0) PCK(NC_PROF_KRYLOV_VEC, launch_scale_copy(wv, wv, 1.0 / hn, n, pb->st, &pb->cnt));
+      }
       for (int i = 0; i <= j; ++i) H[i * m + j] = h[i];
       H[(j + 1) * m + j] = hn;
       for (int i = 0; i < j; ++i) {
@@ -487,7 +538,6 @@ nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x,
       const double res = std::fabs(gv[j + 1]);
       *relres_out = res / bnorm;
       if (res <= rtol * bnorm || hn == 0.0) { ++j; ++total; done = true; break; }
-      CK(launch_scale_copy(wv, wv, 1.0 / hn, n, pb->st, &pb->cnt));
     }
     // x += Z y, y = H^-1 g (upper triangular j x j)
     for (int i = j - 1; i >= 0; --i) {
@@ -495,7 +545,7 @@ nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x,
       for (int k = i + 1; k < j; ++k) acc -= H[i * m + k] * y[k];
       y[i] = acc / H[i * m + i];
     }
-    if (j > 0) CK(launch_axpy_multi(x, Z, n, j, y.data(), n, pb->st, &pb->cnt));
+    if (j > 0) PCK(NC_PROF_KRYLOV_VEC, launch_axpy_multi(x, Z, n, j, y.data(), n, pb->st, &pb->cnt));
     *its_out = total;
     if (done) return NC_OK;
     if (total >= maxit) return NC_OK;   // caller judges the reached residual
@@ -503,14 +553,14 @@ nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x,
     double* r = V;
     CKS(outer_op(pb, tr, fp32, x, pb->w));
     CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
-    CK(launch_axpby(r, pb->w, -1.0, 1.0, n, pb->st, &pb->cnt));
-    CK(launch_zero_dirichlet(pb->g, r, pb->st, &pb->cnt));
+    PCK(NC_PROF_KRYLOV_VEC, launch_axpby(r, pb->w, -1.0, 1.0, n, pb->st, &pb->cnt));
+    PCK(NC_PROF_KRYLOV_VEC, launch_zero_dirichlet(pb->g, r, pb->st, &pb->cnt));
     double rr;
     CKS(norm2_free(pb, r, &rr));
     beta = std::sqrt(rr);
     *relres_out = beta / bnorm;
     if (beta <= rtol * bnorm) return NC_OK;
-    CK(launch_scale_copy(r, r, 1.0 / beta, n, pb->st, &pb->cnt));
+    PCK(NC_PROF_KRYLOV_VEC, launch_scale_copy(r, r, 1.0 / beta, n, pb->st, &pb->cnt));
   }
 }
 
@@ -524,7 +574,7 @@ struct NewtonResult {
 nc_status trial(nc_problem* pb, double lam, double* phi, nc_stats* stats) {
   const long long n = 2 * pb->g.nn;
   CK(cudaMemcpyAsync(pb->s_try, pb->s, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
-  CK(launch_axpby((double*)pb->s_try, pb->dx, lam, 1.0, n, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_axpby((double*)pb->s_try, pb->dx, lam, 1.0, n, pb->st, &pb->cnt));
   CKS(residual(pb, pb->s_try, pb->R_try, phi));
   if (stats) stats->residual_evals++;
   return NC_OK;
@@ -574,11 +624,16 @@ nc_status damping(nc_problem* pb, double phi0, double* lam_out, double* phi_out,
   return NC_OK;
 }
 
-nc_status newton(nc_problem* pb, double rtol, double ref, nc_stats* stats, bool* failed) {
+nc_status newton(nc_problem* pb, double rtol, double ref, nc_stats* stats, bool* failed, bool from_zero) {
   *failed = false;
   double phi;
-  CKS(residual(pb, pb->s, pb->R, &phi));
-  if (stats) stats->residual_evals++;
+  if (from_zero && pb->ph.Q == pb->Q_full) {
+    CK(cudaMemcpyAsync(pb->R, pb->R0, sizeof(double) * 2 * pb->g.nn, cudaMemcpyDeviceToDevice, pb->st));
+    phi = pb->ref_norm * pb->ref_norm;
+  } else {
+    CKS(residual(pb, pb->s, pb->R, &phi));
+    if (stats) stats->residual_evals++;
+  }
   const long long n = 2 * pb->g.nn;
   const bool fp32 = pb->par.precision != NC_PREC_FP64;
   double rel_prev = -1.0, eta_prev = pb->par.krylov_rtol;
@@ -600,10 +655,11 @@ nc_status newton(nc_problem* pb, double rtol, double ref, nc_stats* stats, bool*
     eta = std::max(eta, 0.5 * rtol / rel);
     eta = std::max(std::min(eta, pb->par.krylov_rtol), 1e-12);
     double t0 = now_s();
-    CKS(mg_setup_any(pb));
+    CKS(mg_setup_any(pb, pb->first_setup));
+    pb->first_setup = false;
     double t1 = now_s();
-    CK(launch_scale_copy(pb->rhs, pb->R, -1.0, n, pb->st, &pb->cnt));
-    CK(launch_zero_dirichlet(pb->g, pb->rhs, pb->st, &pb->cnt));
+    PCK(NC_PROF_OTHER, launch_scale_copy(pb->rhs, pb->R, -1.0, n, pb->st, &pb->cnt));
+    PCK(NC_PROF_OTHER, launch_zero_dirichlet(pb->g, pb->rhs, pb->st, &pb->cnt));
     int its = 0;
     double lres = 0.0;
     CKS(fgmres(pb, false, fp32, pb->rhs, pb->dx, eta, pb->par.krylov_maxit, &its, &lres));
@@ -632,12 +688,15 @@ nc_status newton(nc_problem* pb, double rtol, double ref, nc_stats* stats, bool*
 void set_q_scale(nc_problem* pb, double scale) { pb->ph.Q = pb->Q_full * scale; }
 
 nc_status reference_norm(nc_problem* pb) {
-  // ||R_free(0)|| with the full source: R(0) is minus the SUPG-weighted source load.
+  // ||R_free(0)|| with the full source: R(0) is minus the SUPG-weighted source load, which does
+  // not depend on the design, so it is evaluated once per problem and kept in R0.
+  if (pb->have_R0) return NC_OK;
   CK(cudaMemsetAsync(pb->s_try, 0, sizeof(double) * 2 * pb->g.nn, pb->st));
   set_q_scale(pb, 1.0);
   double phi;
-  CKS(residual(pb, pb->s_try, pb->R_try, &phi));
+  CKS(residual(pb, pb->s_try, pb->R0, &phi));
   pb->ref_norm = std::sqrt(phi);
+  pb->have_R0 = true;
   return NC_OK;
 }
 
@@ -694,19 +753,20 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
   size_t b = 0;
   const size_t nn = g.nn, ne = g.ne, m = p->restart;
   b += 4 * al(16 * nn);                 // s, s_try, lam, s_start
-  b += 5 * al(16 * nn);                 // R, R_try, dx, w, rhs
+  b += 6 * al(16 * nn);                 // R, R_try, dx, w, rhs, R0
   b += 3 * al(8 * ne) + al(24 * ne);    // rho, gamma_t, gsens, u
   b += 2 * al(16 * ne) + al(8 * ne) + al(8 * nn);   // mat, dmat, mat32, s32
   b += al(16 * nn * (m + 1)) + al(16 * nn * m);     // V, Z
-  b += al(8 * 66 * 608) + al(8 * 66);
-  b += 7 * al(8 * nn);                  // filter vectors
+  b += al(8 * 66 * 608) + al(8 * 132);
+  b += 5 * al(8 * nn) + 5 * al(4 * nn); // filter vectors
   const size_t rs = p->precision == NC_PREC_FP64 ? 8 : 4;
   for (size_t l = 0; l < lv.g.size(); ++l) {
     b += 4 * al(2 * rs * lv.g[l].nn);
     if (l + 1 < lv.g.size()) b += al(4 * rs * lv.g[l].nn);
     if (l > 0) b += al(256 * rs * lv.g[l].ne);
+    if (l > 0 && l + 1 < lv.g.size()) b += al(108 * rs * lv.g[l].nn);
   }
-  b += al(8 * (size_t)lv.nf * lv.nf) + al(16 * (size_t)lv.nf * lv.nf);
+  b += al(8 * (size_t)lv.nf * lv.nf) + al(4 * (size_t)lv.nf * lv.nf) + al(8 * (size_t)lv.nf * lv.nf);
   b += al(4);
   return b;
 }
@@ -740,9 +800,11 @@ nc_status nc_default_params(nc_params* p) {
   p->mg_levels = 0;
   p->nu_pre = 2;
   p->nu_post = 2;
-  p->omega = 0.6;
+  p->omega = 0.7;
   p->filter_rtol = 1e-12;
   p->timeout_s = 600.0;
+  p->adjoint_rtol = 0.0;
+  p->coarse_refactor = 0;
   return NC_OK;
 }
 
@@ -790,7 +852,47 @@ nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream,
         const int d = __builtin_popcount(a ^ b);
         pb->F.A[a * 8 + b] = r * r * g.h / 12.0 * kc[d] + g.h * g.h * g.h / 216.0 * mc[d];
       }
+    // interior 27-point stencil: offset o couples node n to n + o through the elements holding both
+    for (int o = 0; o < 27; ++o) {
+      const int od[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+      double c = 0.0;
+      for (int e = 0; e < 8; ++e) {            // element at offset -(e bits) from the node
+        int a = 0, b = 0;
+        bool in = true;
+        for (int d = 0; d < 3; ++d) {
+          const int ad = (e >> d) & 1;         // node's local coordinate in this element
+          const int bd = ad + od[d];           // neighbour's local coordinate
+          if (bd < 0 || bd > 1) in = false;
+          a |= ad << d;
+          b |= (bd & 1) << d;
+        }
+        if (in) c += pb->F.A[a * 8 + b];
+      }
+      pb->F.C27[o] = c;
+    }
     pb->F.t0 = g.h * g.h * g.h / 8.0;
+    for (int q = 0; q < 64; ++q) pb->Ff.A[q] = (float)pb->F.A[q];
+    for (int q = 0; q < 27; ++q) pb->Ff.C27[q] = (float)pb->F.C27[q];
+    // spectrum of D^-1 A from the interior symbol sum_o C27[o] cos(theta . o) / C27[centre]
+    // (Neumann boundaries do not widen it), widened by 5 % on each side
+    double lmin = 1e300, lmax = -1e300;
+    const int T = 32;
+    for (int tz = 0; tz <= T; ++tz)
+      for (int ty = 0; ty <= T; ++ty)
+        for (int tx = 0; tx <= T; ++tx) {
+          const double th[3] = {M_PI * tx / T, M_PI * ty / T, M_PI * tz / T};
+          double sym = 0.0;
+          for (int o = 0; o < 27; ++o)
+            sym += pb->F.C27[o] * std::cos(th[0] * (o % 3 - 1) + th[1] * ((o / 3) % 3 - 1) + th[2] * (o / 9 - 1));
+          sym /= pb->F.C27[13];
+          lmin = std::min(lmin, sym);
+          lmax = std::max(lmax, sym);
+        }
+    pb->cheb_a = 0.95 * lmin;
+    pb->cheb_b = 1.05 * lmax;
+    const double kap = pb->cheb_b / pb->cheb_a;
+    const double rq = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
+    pb->cheb_iters = std::max(4, (int)std::ceil(std::log(5e-7) / std::log(rq)));
     pb->F.diag = pb->F.A[0];
   }
   if (stream) pb->st = (cudaStream_t)stream;
@@ -805,22 +907,25 @@ nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream,
   auto A = [&](nc_status x) { if (s == NC_OK) s = x; };
   A(dalloc(pb, &pb->s, nn)); A(dalloc(pb, &pb->s_try, nn)); A(dalloc(pb, &pb->lam, nn)); A(dalloc(pb, &pb->s_start, nn));
   A(dalloc(pb, &pb->R, 2 * nn)); A(dalloc(pb, &pb->R_try, 2 * nn)); A(dalloc(pb, &pb->dx, 2 * nn));
-  A(dalloc(pb, &pb->w, 2 * nn)); A(dalloc(pb, &pb->rhs, 2 * nn));
+  A(dalloc(pb, &pb->w, 2 * nn)); A(dalloc(pb, &pb->rhs, 2 * nn)); A(dalloc(pb, &pb->R0, 2 * nn));
   A(dalloc(pb, &pb->rho, ne)); A(dalloc(pb, &pb->gamma_t, ne)); A(dalloc(pb, &pb->gsens, ne)); A(dalloc(pb, &pb->u, 3 * ne));
   A(dalloc(pb, &pb->mat, ne)); A(dalloc(pb, &pb->dmat, ne)); A(dalloc(pb, &pb->mat32, ne)); A(dalloc(pb, &pb->s32, nn));
   A(dalloc(pb, &pb->V, (size_t)2 * nn * (pb->m + 1))); A(dalloc(pb, &pb->Z, (size_t)2 * nn * pb->m));
-  A(dalloc(pb, &pb->part, 66 * 608)); A(dalloc(pb, &pb->dres, 66));
-  A(dalloc(pb, &pb->fx, nn)); A(dalloc(pb, &pb->fb, nn)); A(dalloc(pb, &pb->fr, nn)); A(dalloc(pb, &pb->fz, nn));
-  A(dalloc(pb, &pb->fp, nn)); A(dalloc(pb, &pb->fq, nn)); A(dalloc(pb, &pb->fdinv, nn));
+  A(dalloc(pb, &pb->part, 66 * 608)); A(dalloc(pb, &pb->dres, 132));
+  A(dalloc(pb, &pb->fx, nn)); A(dalloc(pb, &pb->fb, nn)); A(dalloc(pb, &pb->fr, nn));
+  A(dalloc(pb, &pb->fq, nn)); A(dalloc(pb, &pb->fdinv, nn));
+  A(dalloc(pb, &pb->fxf, nn)); A(dalloc(pb, &pb->frf, nn)); A(dalloc(pb, &pb->fd0, nn)); A(dalloc(pb, &pb->fd1, nn));
+  A(dalloc(pb, &pb->fdinvf, nn));
   A(dalloc(pb, &pb->dflag, 1));
   if (s == NC_OK) s = p->precision == NC_PREC_FP64 ? mg_alloc<double>(pb) : mg_alloc<float>(pb);
   if (s == NC_OK) {
-    cudaError_t e = cudaMallocHost(&pb->hres, sizeof(double) * 66);
+    cudaError_t e = cudaMallocHost(&pb->hres, sizeof(double) * 132);
     if (e == cudaSuccess) e = cudaMallocHost(&pb->hflag, sizeof(int));
     if (e != cudaSuccess) { cudaGetLastError(); s = fail(pb, NC_ERR_OOM, "pinned host allocation failed"); }
   }
   if (s == NC_OK) {
     cudaError_t e = launch_helmholtz_diag(g, pb->F, pb->fdinv, pb->st);
+    if (e == cudaSuccess) e = launch_cast_d2f(pb->fdinvf, pb->fdinv, nn, pb->st, nullptr);
     if (e == cudaSuccess) e = cudaMemsetAsync(pb->s, 0, sizeof(double2) * nn, pb->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(pb->st);
     if (e != cudaSuccess) s = cuda_fail(pb, e, "create");
@@ -855,19 +960,20 @@ nc_status nc_set_design(nc_problem* pb, const double* rho) {
   const Grid& g = pb->g;
   CKS(copy_in(pb, pb->rho, rho, sizeof(double) * g.ne));
   CK(cudaMemsetAsync(pb->dflag, 0, sizeof(int), pb->st));
-  CK(launch_check_design(pb->rho, g.ne, pb->dflag, pb->st));
+  PCK(NC_PROF_OTHER, launch_check_design(pb->rho, g.ne, pb->dflag, pb->st));
   CK(cudaMemcpyAsync(pb->hflag, pb->dflag, sizeof(int), cudaMemcpyDeviceToHost, pb->st));
   CKS(sync(pb, "design check"));
   if (*pb->hflag) return fail(pb, NC_ERR_ARG, "design values must be finite and in [0, 1]");
   // filter: b = T^T gamma with gamma = 1 on the heated region
-  CK(launch_filter_rhs(g, pb->rho, pb->par.heated_layers, pb->F.t0, pb->fb, pb->st, &pb->cnt));
+  PCK(NC_PROF_FILTER, launch_filter_rhs(g, pb->rho, pb->par.heated_layers, pb->F.t0, pb->fb, pb->st, &pb->cnt));
   CKS(filter_solve(pb));
-  CK(launch_elem_from_nodes(g, pb->fx, 0.125, pb->par.heated_layers, 1.0, pb->gamma_t, pb->st, &pb->cnt));
+  PCK(NC_PROF_FILTER, launch_elem_from_nodes(g, pb->fx, 0.125, pb->par.heated_layers, 1.0, pb->gamma_t, pb->st, &pb->cnt));
   RampConst rc{pb->kappa_f, pb->kappa_s, pb->par.k_f, pb->par.k_s, pb->par.q_c, pb->par.q_p};
-  CK(launch_ramp(pb->gamma_t, g.ne, rc, pb->mat, pb->dmat, pb->mat32, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_ramp(pb->gamma_t, g.ne, rc, pb->mat, pb->dmat, pb->mat32, pb->st, &pb->cnt));
   CK(cudaMemsetAsync(pb->s, 0, sizeof(double2) * g.nn, pb->st));
   CK(cudaMemsetAsync(pb->s_start, 0, sizeof(double2) * g.nn, pb->st));
   CKS(reference_norm(pb));
+  pb->start_zero = true;
   pb->stage = 1;
   return NC_OK;
 }
@@ -880,9 +986,10 @@ nc_status nc_set_state(nc_problem* pb, const double* P, const double* T) {
   const long long nn = pb->g.nn;
   CK(cudaMemcpy2DAsync((double*)pb->s_start, 16, P, 8, 8, nn, cudaMemcpyDefault, pb->st));
   CK(cudaMemcpy2DAsync((double*)pb->s_start + 1, 16, T, 8, 8, nn, cudaMemcpyDefault, pb->st));
-  CK(launch_zero_dirichlet(pb->g, (double*)pb->s_start, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_zero_dirichlet(pb->g, (double*)pb->s_start, pb->st, &pb->cnt));
   CK(cudaMemcpyAsync(pb->s, pb->s_start, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, pb->st));
   CKS(sync(pb, "set_state"));
+  pb->start_zero = false;
   pb->stage = 1;
   return NC_OK;
 }
@@ -899,8 +1006,9 @@ nc_status nc_solve_state(nc_problem* pb, nc_stats* stats) {
   const long long nn = pb->g.nn;
   CK(cudaMemcpyAsync(pb->s, pb->s_start, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, pb->st));
   set_q_scale(pb, 1.0);
+  pb->first_setup = true;
   bool failed = false;
-  nc_status s = newton(pb, pb->par.newton_rtol, pb->ref_norm, stats, &failed);
+  nc_status s = newton(pb, pb->par.newton_rtol, pb->ref_norm, stats, &failed, pb->start_zero);
   if (s == NC_OK && failed) {
     // source ramping (Sec. 5.4): 1/4, 1/2, then the full source, each from the previous state
     if (stats) stats->ramped = 1;
@@ -909,7 +1017,8 @@ nc_status nc_solve_state(nc_problem* pb, nc_stats* stats) {
     for (int i = 0; i < 3 && s == NC_OK; ++i) {
       set_q_scale(pb, scales[i]);
       double ref = pb->ref_norm * scales[i];
-      s = newton(pb, i < 2 ? std::max(1e-6, pb->par.newton_rtol) : pb->par.newton_rtol, ref, stats, &failed);
+      s = newton(pb, i < 2 ? std::max(1e-6, pb->par.newton_rtol) : pb->par.newton_rtol, ref, stats, &failed,
+                 false);
       if (s == NC_OK && failed) s = fail(pb, NC_ERR_DIVERGED, "no damping factor reduces the residual");
     }
     set_q_scale(pb, 1.0);
@@ -929,7 +1038,7 @@ nc_status nc_objective(nc_problem* pb, int objective, double* f) {
   if (pb->stage < 2) return fail(pb, NC_ERR_STATE, "objective needs a solved state");
   DeviceGuard dg(pb->device);
   const Grid& g = pb->g;
-  CK(launch_dfds(g, pb->par.heated_layers, g.h * g.h * g.h / 8.0 / pb->vol_h, pb->rhs, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_dfds(g, pb->par.heated_layers, g.h * g.h * g.h / 8.0 / pb->vol_h, pb->rhs, pb->st, &pb->cnt));
   CKS(dots(pb, pb->rhs, 0, 1, (const double*)pb->s, 2 * g.nn, f));
   return NC_OK;
 }
@@ -950,7 +1059,7 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
   const long long n = 2 * g.nn;
   set_q_scale(pb, 1.0);
   double t0 = now_s();
-  CKS(mg_setup_any(pb));
+  CKS(mg_setup_any(pb, true));
   if (stats) stats->t_setup_ms += 1e3 * (now_s() - t0);
   double bb;
   CKS(norm2_free(pb, pb->rhs, &bb));
@@ -958,6 +1067,7 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
   CK(cudaMemsetAsync(pb->lam, 0, sizeof(double) * n, pb->st));
   if (bnorm == 0.0) { pb->stage = 3; return NC_OK; }
   const bool fp32 = pb->par.precision != NC_PREC_FP64;
+  const double kAdjointRtol = pb->par.adjoint_rtol > 0 ? pb->par.adjoint_rtol : pb->par.newton_rtol;
   // refinement: r = b - J^T lam in FP64, correction from FGMRES on the (FP32 or FP64) operator
   for (int pass = 0;; ++pass) {
     double rr;
@@ -965,9 +1075,9 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
       CK(cudaMemcpyAsync(pb->w, pb->rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
       rr = bb;
     } else {
-      CK(launch_jtv_f64(g, pb->ph, pb->s, pb->mat, pb->lam, pb->w, pb->st, &pb->cnt));
-      CK(launch_axpby(pb->w, pb->rhs, 1.0, -1.0, n, pb->st, &pb->cnt));
-      CK(launch_zero_dirichlet(g, pb->w, pb->st, &pb->cnt));
+      PCK(NC_PROF_OUTER_OP64, launch_jtv_f64(g, pb->ph, pb->s, pb->mat, pb->lam, pb->w, pb->st, &pb->cnt));
+      PCK(NC_PROF_OTHER, launch_axpby(pb->w, pb->rhs, 1.0, -1.0, n, pb->st, &pb->cnt));
+      PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->w, pb->st, &pb->cnt));
       CKS(norm2_free(pb, pb->w, &rr));
     }
     const double rel = std::sqrt(rr) / bnorm;
@@ -981,7 +1091,8 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
     CKS(check_timeout(pb));
     int its;
     double lres;
-    const double eta = fp32 ? std::max(1e-4, kAdjointRtol / rel) : std::max(0.5 * kAdjointRtol / rel, 1e-12);
+    // FP32 inner solves: 1e-5 per refinement pass (two passes reach 1e-10); FP64: one pass
+    const double eta = fp32 ? std::max(1e-5, 0.5 * kAdjointRtol / rel) : std::max(0.5 * kAdjointRtol / rel, 1e-12);
     double t1 = now_s();
     CKS(fgmres(pb, true, fp32, pb->w, pb->dx, std::min(eta, 1e-1), pb->par.krylov_maxit, &its, &lres));
     if (stats) {
@@ -990,7 +1101,7 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
       if (pass < 64) stats->krylov_hist[pass] = its;
       stats->newton_its++;
     }
-    CK(launch_axpby((double*)pb->lam, pb->dx, 1.0, 1.0, n, pb->st, &pb->cnt));
+    PCK(NC_PROF_OTHER, launch_axpby((double*)pb->lam, pb->dx, 1.0, 1.0, n, pb->st, &pb->cnt));
   }
   CKS(sync(pb, "adjoint"));
   if (stats) {
@@ -1010,11 +1121,11 @@ nc_status nc_sensitivities(nc_problem* pb, double* dfdrho) {
   pb->t_start = now_s();
   const Grid& g = pb->g;
   set_q_scale(pb, 1.0);
-  CK(launch_sens_elem(g, pb->ph, pb->s, pb->lam, pb->mat, pb->dmat, pb->gsens, pb->st, &pb->cnt));
+  PCK(NC_PROF_SENS, launch_sens_elem(g, pb->ph, pb->s, pb->lam, pb->mat, pb->dmat, pb->gsens, pb->st, &pb->cnt));
   // filter transpose: gamma~_e = (1/8) sum_a x_a, x = A^-1 T^T gamma  =>  df/dgamma = T A^-1 (1/8 sum)
-  CK(launch_filter_rhs(g, pb->gsens, 0, 0.125, pb->fb, pb->st, &pb->cnt));
+  PCK(NC_PROF_FILTER, launch_filter_rhs(g, pb->gsens, 0, 0.125, pb->fb, pb->st, &pb->cnt));
   CKS(filter_solve(pb));
-  CK(launch_elem_from_nodes(g, pb->fx, pb->F.t0, pb->par.heated_layers, 0.0, pb->gsens, pb->st, &pb->cnt));
+  PCK(NC_PROF_FILTER, launch_elem_from_nodes(g, pb->fx, pb->F.t0, pb->par.heated_layers, 0.0, pb->gsens, pb->st, &pb->cnt));
   CKS(copy_out(pb, dfdrho, pb->gsens, sizeof(double) * g.ne));
   CKS(sync(pb, "sensitivities"));
   return NC_OK;
@@ -1029,7 +1140,7 @@ nc_status nc_get_fields(const nc_problem* cpb, double* P, double* T, double* u) 
   if (P) CK(cudaMemcpy2DAsync(P, 8, (const double*)pb->s, 16, 8, nn, cudaMemcpyDefault, pb->st));
   if (T) CK(cudaMemcpy2DAsync(T, 8, (const double*)pb->s + 1, 16, 8, nn, cudaMemcpyDefault, pb->st));
   if (u) {
-    CK(launch_u_centroid(pb->g, pb->ph, pb->s, pb->mat, pb->u, pb->st, &pb->cnt));
+    PCK(NC_PROF_OTHER, launch_u_centroid(pb->g, pb->ph, pb->s, pb->mat, pb->u, pb->st, &pb->cnt));
     CKS(copy_out(pb, u, pb->u, sizeof(double) * 3 * pb->g.ne));
   }
   CKS(sync(pb, "get_fields"));
@@ -1076,12 +1187,12 @@ static nc_status apply_generic(nc_problem* pb, const double* s, const double* v,
   CKS(copy_in(pb, pb->w, v, sizeof(double) * n));
   const Grid& g = pb->g;
   if (fp32) {
-    CK(launch_cast_d2f((float*)pb->s32, (const double*)pb->s_try, n, pb->st, &pb->cnt));
-    if (tr) CK(launch_jtv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
-    else CK(launch_jv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
+    PCK(NC_PROF_MG_COARSE_SETUP, launch_cast_d2f((float*)pb->s32, (const double*)pb->s_try, n, pb->st, &pb->cnt));
+    if (tr) PCK(NC_PROF_OTHER, launch_jtv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
+    else PCK(NC_PROF_OTHER, launch_jv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
   } else {
-    if (tr) CK(launch_jtv_f64(g, pb->ph, pb->s_try, pb->mat, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
-    else CK(launch_jv_f64(g, pb->ph, pb->s_try, pb->mat, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
+    if (tr) PCK(NC_PROF_OTHER, launch_jtv_f64(g, pb->ph, pb->s_try, pb->mat, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
+    else PCK(NC_PROF_OTHER, launch_jv_f64(g, pb->ph, pb->s_try, pb->mat, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
   }
   CKS(copy_out(pb, out, pb->R_try, sizeof(double) * n));
   CKS(sync(pb, "operator"));

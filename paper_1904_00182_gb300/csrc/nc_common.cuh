@@ -14,7 +14,8 @@ namespace nc {
 struct Grid {
   int nx, ny, nz;   // elements
   int NX, NY, NZ;   // nodes per direction
-  long long nn;     // nodes
+  int NXY;          // nodes per z-plane
+  long long nn;     // nodes (< 2^31: node indices fit in int)
   long long ne;     // elements
   double h;
 };
@@ -23,6 +24,7 @@ inline Grid make_grid(int nx, int ny, int nz, double h) {
   Grid g;
   g.nx = nx; g.ny = ny; g.nz = nz;
   g.NX = nx + 1; g.NY = ny + 1; g.NZ = nz + 1;
+  g.NXY = g.NX * g.NY;
   g.nn = (long long)g.NX * g.NY * g.NZ;
   g.ne = (long long)nx * ny * nz;
   g.h = h;
@@ -56,6 +58,30 @@ __device__ __forceinline__ void node_ijk(const Grid& g, long long n, int& i, int
   j = (int)(r % g.NY);
   k = (int)(r / g.NY);
 }
+
+// Node offset of local corner a = ax + 2 ay + 4 az from corner 0 of an element.
+__device__ __forceinline__ int corner_off(const Grid& g, int a) {
+  return (a & 1) + ((a >> 1) & 1) * g.NX + (a >> 2) * g.NXY;
+}
+
+// 3D launch geometry: blocks of 32 x 4 threads over (i, j), one z-slice per blockIdx.z.
+struct Launch3 { dim3 grid, block; };
+inline Launch3 launch_elems(const Grid& g) {
+  Launch3 L;
+  L.block = dim3(32, 4, 1);
+  L.grid = dim3((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 3) / 4), (unsigned)g.nz);
+  return L;
+}
+inline Launch3 launch_nodes(const Grid& g) {
+  Launch3 L;
+  L.block = dim3(32, 4, 1);
+  L.grid = dim3((unsigned)((g.NX + 31) / 32), (unsigned)((g.NY + 3) / 4), (unsigned)g.NZ);
+  return L;
+}
+#define NC_IJK_3D()                                   \
+  const int i = blockIdx.x * 32 + threadIdx.x;        \
+  const int j = blockIdx.y * 4 + threadIdx.y;         \
+  const int k = blockIdx.z;
 
 inline unsigned grid_blocks(long long work, int threads, long long cap = 1LL << 30) {
   long long b = (work + threads - 1) / threads;

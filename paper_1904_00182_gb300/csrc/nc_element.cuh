@@ -210,21 +210,16 @@ __device__ __forceinline__ void elem_residual(const ElemConst<R>& C, const R p[8
   q1_test<R, true>(A, bx, by, bz, C.cp, C.cm, C.ih, RT);
 }
 
-// Exact Newton Jacobian product J_e (dp, dt) at the element state st (includes d tau and d N*).
+// Exact Newton Jacobian product at the element state st for a direction given at the Gauss points:
+// dV_q = grad dP_q - beta dT_q e_z and dH_q = grad dT_q (includes d tau and d N*).
 template <typename R>
-__device__ __forceinline__ void elem_jv_dir(const ElemConst<R>& C, const ElemState<R>& st,
-                                            const R kc, const R dp[8], const R dt[8],
-                                            R oP[8], R oT[8]) {
-  R dvx[8], dvy[8], dvz[8], dT[8];
-  q1_forward(dp, C.cp, C.cm, C.ih, dT, dvx, dvy, dvz);
-  R dhx[8], dhy[8], dhz[8];
-  q1_forward(dt, C.cp, C.cm, C.ih, dT, dhx, dhy, dhz);
+__device__ __forceinline__ void elem_jv_gauss(const ElemConst<R>& C, const ElemState<R>& st, const R kc,
+                                              const R dvx[8], const R dvy[8], const R dvz[8],
+                                              const R dhx[8], const R dhy[8], const R dhz[8],
+                                              R oP[8], R oT[8]) {
   R sx = 0, sy = 0, sz = 0;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    dvz[q] -= C.beta * dT[q];
-    sx += dvx[q]; sy += dvy[q]; sz += dvz[q];
-  }
+  for (int q = 0; q < 8; ++q) { sx += dvx[q]; sy += dvy[q]; sz += dvz[q]; }
   const R m = -st.c * R(0.125);
   const R du0x = m * sx, du0y = m * sy, du0z = m * sz;
   const R tau = st.tau;
@@ -249,6 +244,46 @@ __device__ __forceinline__ void elem_jv_dir(const ElemConst<R>& C, const ElemSta
 #pragma unroll
   for (int q = 0; q < 8; ++q) { bx[q] = wc * dvx[q]; by[q] = wc * dvy[q]; bz[q] = wc * dvz[q]; }
   q1_test<R, false>(nullptr, bx, by, bz, C.cp, C.cm, C.ih, oP);
+}
+
+// Exact Newton Jacobian product J_e (dp, dt) at the element state st.
+template <typename R>
+__device__ __forceinline__ void elem_jv_dir(const ElemConst<R>& C, const ElemState<R>& st,
+                                            const R kc, const R dp[8], const R dt[8],
+                                            R oP[8], R oT[8]) {
+  R dvx[8], dvy[8], dvz[8], dT[8];
+  q1_forward(dp, C.cp, C.cm, C.ih, dT, dvx, dvy, dvz);
+  R dhx[8], dhy[8], dhz[8];
+  q1_forward(dt, C.cp, C.cm, C.ih, dT, dhx, dhy, dhz);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) dvz[q] -= C.beta * dT[q];
+  elem_jv_gauss(C, st, kc, dvx, dvy, dvz, dhx, dhy, dhz, oP, oT);
+}
+
+// Column b of the element Jacobian (b < 8: P at local node b, else T at node b - 8): the
+// Gauss-point values of the unit direction are products of the 1D shape-function tables.
+template <typename R>
+__device__ __forceinline__ void elem_jac_column(const ElemConst<R>& C, const ElemState<R>& st, const R kc,
+                                                int b, R oP[8], R oT[8]) {
+  const int a = b & 7;
+  const bool isT = b >= 8;
+  const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+  const R gxd = ax ? C.ih : -C.ih, gyd = ay ? C.ih : -C.ih, gzd = az ? C.ih : -C.ih;
+  R dvx[8], dvy[8], dvz[8], dhx[8], dhy[8], dhz[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int qx = q & 1, qy = (q >> 1) & 1, qz = q >> 2;
+    const R nx = (qx == ax) ? C.cp : C.cm, ny = (qy == ay) ? C.cp : C.cm, nz = (qz == az) ? C.cp : C.cm;
+    const R gx = gxd * ny * nz, gy = nx * gyd * nz, gz = nx * ny * gzd;
+    if (isT) {
+      dvx[q] = R(0); dvy[q] = R(0); dvz[q] = -C.beta * nx * ny * nz;
+      dhx[q] = gx; dhy[q] = gy; dhz[q] = gz;
+    } else {
+      dvx[q] = gx; dvy[q] = gy; dvz[q] = gz;
+      dhx[q] = R(0); dhy[q] = R(0); dhz[q] = R(0);
+    }
+  }
+  elem_jv_gauss(C, st, kc, dvx, dvy, dvz, dhx, dhy, dhz, oP, oT);
 }
 
 // Adjoint side: given multipliers (lp, lt) of the element rows, the gradient of

@@ -1,5 +1,6 @@
 // Element-sweep kernels: residual R(s), Jacobian products J v and J^T w, design sensitivities and
-// centroid velocities. One thread per element gathers its 8 nodes, evaluates the element
+// centroid velocities. One thread per element (3D launch: 32 x 4 element columns per block, one
+// z-layer per blockIdx.z, 32-bit index arithmetic) gathers its 8 nodes, evaluates the element
 // arithmetic of nc_element.cuh and scatters the 16 row contributions with atomic adds
 // (Dirichlet rows on the top plane are skipped and set by the caller's convention).
 #include "nc_launch.h"
@@ -9,11 +10,11 @@ namespace nc {
 namespace {
 
 template <typename R, typename V>
-__device__ __forceinline__ void gather_state(const Grid& g, const V* __restrict__ s, int i, int j, int k,
+__device__ __forceinline__ void gather_state(const Grid& g, const V* __restrict__ s, int n0,
                                              R p[8], R t[8]) {
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
-    const V v = s[corner_node(g, i, j, k, a)];
+    const V v = s[n0 + corner_off(g, a)];
     p[a] = (R)v.x;
     t[a] = (R)v.y;
   }
@@ -21,28 +22,35 @@ __device__ __forceinline__ void gather_state(const Grid& g, const V* __restrict_
 
 // Gather a direction vector with its Dirichlet (top-plane) entries treated as zero.
 template <typename R, typename V>
-__device__ __forceinline__ void gather_dir(const Grid& g, const V* __restrict__ v, int i, int j, int k,
+__device__ __forceinline__ void gather_dir(const Grid& g, const V* __restrict__ v, int n0, bool top,
                                            R p[8], R t[8]) {
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
-    if (k + (a >> 2) == g.nz) { p[a] = R(0); t[a] = R(0); continue; }
-    const V x = v[corner_node(g, i, j, k, a)];
+    if (top && (a >> 2)) { p[a] = R(0); t[a] = R(0); continue; }
+    const V x = v[n0 + corner_off(g, a)];
     p[a] = (R)x.x;
     t[a] = (R)x.y;
   }
 }
 
 template <typename O, typename R>
-__device__ __forceinline__ void scatter_add(const Grid& g, O* __restrict__ out, int i, int j, int k,
+__device__ __forceinline__ void scatter_add(const Grid& g, O* __restrict__ out, int n0, bool top,
                                             const R oP[8], const R oT[8]) {
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
-    if (k + (a >> 2) == g.nz) continue;
-    const long long n = corner_node(g, i, j, k, a);
+    if (top && (a >> 2)) continue;
+    const int n = n0 + corner_off(g, a);
     atomicAdd(out + 2 * n, (O)oP[a]);
     atomicAdd(out + 2 * n + 1, (O)oT[a]);
   }
 }
+
+#define NC_ELEM_PROLOGUE()                                      \
+  NC_IJK_3D();                                                  \
+  if (i >= g.nx || j >= g.ny) return;                           \
+  const int n0 = i + g.NX * j + g.NXY * k;                      \
+  const int e = i + g.nx * (j + g.ny * k);                      \
+  const bool top = (k + 1 == g.nz);
 
 template <typename R>
 __device__ __forceinline__ R elem_source(const Phys& ph, int k) {
@@ -51,16 +59,13 @@ __device__ __forceinline__ R elem_source(const Phys& ph, int k) {
 
 __global__ void k_residual(Grid g, Phys ph, ElemConst<double> C, const double2* __restrict__ s,
                            const double2* __restrict__ mat, double* __restrict__ out) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= g.ne) return;
-  int i, j, k;
-  elem_ijk(g, e, i, j, k);
+  NC_ELEM_PROLOGUE();
   double p[8], t[8];
-  gather_state<double>(g, s, i, j, k, p, t);
+  gather_state<double>(g, s, n0, p, t);
   const double2 m = mat[e];
   double RP[8], RT[8];
   elem_residual<double>(C, p, t, m.x, m.y, elem_source<double>(ph, k), RP, RT);
-  scatter_add(g, out, i, j, k, RP, RT);
+  scatter_add(g, out, n0, top, RP, RT);
 }
 
 // Dirichlet rows of the residual: R_d = s_d (boundary value 0).
@@ -77,18 +82,10 @@ template <typename R, typename SV, typename O, bool TRANSPOSE>
 __global__ void k_jprod(Grid g, Phys ph, ElemConst<R> C, const SV* __restrict__ s,
                         const typename Vec2<R>::type* __restrict__ mat, const double2* __restrict__ v,
                         O* __restrict__ out) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= g.ne) return;
-  int i, j, k;
-  elem_ijk(g, e, i, j, k);
+  NC_ELEM_PROLOGUE();
   R p[8], t[8], dp[8], dt[8];
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    const SV x = s[corner_node(g, i, j, k, a)];
-    p[a] = (R)x.x;
-    t[a] = (R)x.y;
-  }
-  gather_dir<R>(g, v, i, j, k, dp, dt);
+  gather_state<R>(g, s, n0, p, t);
+  gather_dir<R>(g, v, n0, top, dp, dt);
   const typename Vec2<R>::type m = mat[e];
   ElemState<R> st;
   elem_state(C, p, t, m.x, elem_source<R>(ph, k), st);
@@ -97,20 +94,17 @@ __global__ void k_jprod(Grid g, Phys ph, ElemConst<R> C, const SV* __restrict__ 
     elem_jtv<R, false>(C, st, m.y, dp, dt, oP, oT, nullptr, nullptr);
   else
     elem_jv_dir<R>(C, st, m.y, dp, dt, oP, oT);
-  scatter_add(g, out, i, j, k, oP, oT);
+  scatter_add(g, out, n0, top, oP, oT);
 }
 
 __global__ void k_sens(Grid g, Phys ph, ElemConst<double> C, const double2* __restrict__ s,
                        const double2* __restrict__ lam, const double2* __restrict__ mat,
                        const double2* __restrict__ dmat, double* __restrict__ out) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= g.ne) return;
-  int i, j, k;
-  elem_ijk(g, e, i, j, k);
+  NC_ELEM_PROLOGUE();
   if (k < ph.heated_layers) { out[e] = 0.0; return; }
   double p[8], t[8], lp[8], lt[8];
-  gather_state<double>(g, s, i, j, k, p, t);
-  gather_dir<double>(g, lam, i, j, k, lp, lt);
+  gather_state<double>(g, s, n0, p, t);
+  gather_dir<double>(g, lam, n0, top, lp, lt);
   const double2 m = mat[e];
   ElemState<double> st;
   elem_state(C, p, t, m.x, 0.0, st);
@@ -122,12 +116,10 @@ __global__ void k_sens(Grid g, Phys ph, ElemConst<double> C, const double2* __re
 
 __global__ void k_u_centroid(Grid g, Phys ph, ElemConst<double> C, const double2* __restrict__ s,
                              const double2* __restrict__ mat, double* __restrict__ u) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= g.ne) return;
-  int i, j, k;
-  elem_ijk(g, e, i, j, k);
+  NC_ELEM_PROLOGUE();
+  (void)top;
   double p[8], t[8];
-  gather_state<double>(g, s, i, j, k, p, t);
+  gather_state<double>(g, s, n0, p, t);
   ElemState<double> st;
   elem_state(C, p, t, mat[e].x, 0.0, st);
   u[3 * e] = st.u0x;
@@ -137,13 +129,12 @@ __global__ void k_u_centroid(Grid g, Phys ph, ElemConst<double> C, const double2
 
 }  // namespace
 
-static const int kElemThreads = 128;
-
 cudaError_t launch_residual(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
                             double* out, cudaStream_t st, Counters* c) {
   cudaError_t err = cudaMemsetAsync(out, 0, sizeof(double) * 2 * g.nn, st);
   if (err != cudaSuccess) return err;
-  k_residual<<<grid_blocks(g.ne, kElemThreads), kElemThreads, 0, st>>>(g, ph, make_econst<double>(ph), s, mat, out);
+  const Launch3 L = launch_elems(g);
+  k_residual<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<double>(ph), s, mat, out);
   const long long plane = (long long)g.NX * g.NY;
   k_residual_bc<<<grid_blocks(plane, 256), 256, 0, st>>>(g, s, out);
   if (c) { c->launches += 2; c->bytes += 16.0 * g.nn * 2 + 16.0 * g.ne; }
@@ -155,8 +146,8 @@ static cudaError_t jprod(const Grid& g, const Phys& ph, const SV* s, const typen
                          const double2* v, double* out, cudaStream_t st, Counters* c) {
   cudaError_t err = cudaMemsetAsync(out, 0, sizeof(double) * 2 * g.nn, st);
   if (err != cudaSuccess) return err;
-  k_jprod<R, SV, double, TR><<<grid_blocks(g.ne, kElemThreads), kElemThreads, 0, st>>>(
-      g, ph, make_econst<R>(ph), s, mat, v, out);
+  const Launch3 L = launch_elems(g);
+  k_jprod<R, SV, double, TR><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, v, out);
   if (c) { c->launches += 1; c->bytes += (2.0 * sizeof(SV) + 32.0) * g.nn + 2.0 * sizeof(R) * g.ne; }
   return cudaGetLastError();
 }
@@ -181,16 +172,16 @@ cudaError_t launch_jtv_f32_io64(const Grid& g, const Phys& ph, const float2* s32
 cudaError_t launch_sens_elem(const Grid& g, const Phys& ph, const double2* s, const double2* lam,
                              const double2* mat, const double2* dmat, double* out, cudaStream_t st,
                              Counters* c) {
-  k_sens<<<grid_blocks(g.ne, kElemThreads), kElemThreads, 0, st>>>(g, ph, make_econst<double>(ph), s, lam,
-                                                                   mat, dmat, out);
+  const Launch3 L = launch_elems(g);
+  k_sens<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<double>(ph), s, lam, mat, dmat, out);
   if (c) { c->launches += 1; c->bytes += 32.0 * g.nn + 40.0 * g.ne; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_u_centroid(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
                               double* u, cudaStream_t st, Counters* c) {
-  k_u_centroid<<<grid_blocks(g.ne, kElemThreads), kElemThreads, 0, st>>>(g, ph, make_econst<double>(ph), s,
-                                                                         mat, u);
+  const Launch3 L = launch_elems(g);
+  k_u_centroid<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<double>(ph), s, mat, u);
   if (c) { c->launches += 1; c->bytes += 16.0 * g.nn + 40.0 * g.ne; }
   return cudaGetLastError();
 }

@@ -6,25 +6,40 @@
 // products P^T A P assembled element by element: a coarse element's matrix is the sum over its 8
 // children of P_c^T A_c P_c, where P_c interpolates the child's 8 nodes from the parent's 8
 // corners (exact for nested trilinear spaces). Level 0 applies the Newton Jacobian J(s) matrix
-// free; levels >= 1 store 16x16 element matrices (rows/cols: P_0..7, T_0..7). The smoother is
-// damped 2x2 node-block Jacobi; the coarsest level is solved with an explicit FP64 inverse.
+// free; levels >= 1 store 16x16 element matrices (rows/cols: P_0..7, T_0..7) for the set-up of the
+// next level and, for their application, the assembled 27-point 2x2-block stencil (gathered per
+// node, no atomics). The smoother is damped 2x2 node-block Jacobi; the coarsest level is solved with
+// an FP32 Gauss-Jordan inverse (partial pivoting) and one step of FP64 iterative refinement (the
+// coarse residual is computed in FP64 against the FP64 Galerkin matrix).
 #include "nc_launch.h"
 
 namespace nc {
 
 namespace {
 
+// out[A] = sum_l P_c[l][A] in[l]: transpose of the trilinear interpolation from the parent's 8
+// corners A to the 8 nodes l of child c, applied as three 1D stages. Along an axis where the child
+// bit is 0 the child's nodes sit at parent positions (0, 1/2): P1 = [[1, 0], [1/2, 1/2]];
+// where it is 1 they sit at (1/2, 1): P1 = [[1/2, 1/2], [0, 1]] (rows: child node, columns: corner).
 template <typename R>
-__device__ __forceinline__ R interp_w(int child, int l, int A) {
-  // weight of parent corner A at the child's local node l (tensor product of 1D hat values)
-  R w = R(1);
+__device__ __forceinline__ void interp_T(int child, const R in[8], R out[8]) {
+  R t[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) t[q] = in[q];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const int cd = (child >> d) & 1, ld = (l >> d) & 1, Ad = (A >> d) & 1;
-    const R t = R(0.5) * R(cd + ld);
-    w *= Ad ? t : R(1) - t;
+    const int st = 1 << d;
+    const bool hi = (child >> d) & 1;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (q & st) continue;
+      const R v0 = t[q], v1 = t[q + st];
+      if (!hi) { t[q] = v0 + R(0.5) * v1; t[q + st] = R(0.5) * v1; }
+      else { t[q] = R(0.5) * v0; t[q + st] = R(0.5) * v0 + v1; }
+    }
   }
-  return w;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) out[q] = t[q];
 }
 
 template <typename R>
@@ -32,34 +47,46 @@ __device__ __forceinline__ void add_diag_block(R* __restrict__ diag, long long n
   atomicAdd(diag + 4 * n + idx, v);
 }
 
-// Phase 2 shared by both Galerkin kernels: Jc[c][16][16] in shared memory -> coarse element matrix.
+// Galerkin product of one coarse element from its children's matrices Jc[c] (16 rows of stride
+// NC_LD, shared memory): Tc = Jc P_c (per row, both field blocks), Uc = P_c^T Tc (per column),
+// out = sum_c Uc. 128 threads. The row stride 17 keeps row and column accesses conflict-free.
+#define NC_LD 17
 template <typename R>
-__device__ __forceinline__ void galerkin_phase2(R (*Jc)[256], R (*Tc)[256], R* __restrict__ out) {
+__device__ __forceinline__ void galerkin_phase2(R (*Jc)[16 * NC_LD], R (*Tc)[16 * NC_LD], R* __restrict__ out) {
   const int t = threadIdx.x;
+  const int c = t >> 4, rc = t & 15;
   {
-    const int c = t >> 4, row = t & 15;
-#pragma unroll 4
-    for (int J = 0; J < 16; ++J) {
-      const int fj = J >> 3, A = J & 7;
-      R acc = R(0);
+    const int row = rc;
 #pragma unroll
-      for (int l = 0; l < 8; ++l) acc += Jc[c][row * 16 + fj * 8 + l] * interp_w<R>(c, l, A);
-      Tc[c][row * 16 + J] = acc;
+    for (int f = 0; f < 2; ++f) {
+      R in[8], o[8];
+#pragma unroll
+      for (int l = 0; l < 8; ++l) in[l] = Jc[c][row * NC_LD + f * 8 + l];
+      interp_T<R>(c, in, o);
+#pragma unroll
+      for (int A = 0; A < 8; ++A) Tc[c][row * NC_LD + f * 8 + A] = o[A];
     }
   }
   __syncthreads();
   {
-    const int I = t >> 3;
-    const int fi = I >> 3, Ai = I & 7;
+    const int col = rc;
 #pragma unroll
-    for (int jj = 0; jj < 2; ++jj) {
-      const int J = (t & 7) * 2 + jj;
-      R acc = R(0);
-      for (int c = 0; c < 8; ++c)
+    for (int f = 0; f < 2; ++f) {
+      R in[8], o[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc += interp_w<R>(c, k, Ai) * Tc[c][(fi * 8 + k) * 16 + J];
-      out[I * 16 + J] = acc;
+      for (int k = 0; k < 8; ++k) in[k] = Tc[c][(f * 8 + k) * NC_LD + col];
+      interp_T<R>(c, in, o);
+#pragma unroll
+      for (int A = 0; A < 8; ++A) Jc[c][(f * 8 + A) * NC_LD + col] = o[A];
     }
+  }
+  __syncthreads();
+  for (int idx = t; idx < 256; idx += 128) {
+    const int r = idx >> 4, q = idx & 15;
+    R acc = R(0);
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) acc += Jc[cc][r * NC_LD + q];
+    out[idx] = acc;
   }
 }
 
@@ -68,8 +95,8 @@ __global__ void __launch_bounds__(128) k_galerkin_fine(Grid gf, Grid gc, Phys ph
                                                        const typename Vec2<R>::type* __restrict__ s,
                                                        const typename Vec2<R>::type* __restrict__ mat,
                                                        R* __restrict__ diag_f, R* __restrict__ ebe_c) {
-  __shared__ R Jc[8][256];
-  __shared__ R Tc[8][256];
+  __shared__ R Jc[8][16 * NC_LD];
+  __shared__ R Tc[8][16 * NC_LD];
   const long long E = blockIdx.x;
   int I, J, K;
   elem_ijk(gc, E, I, J, K);
@@ -87,14 +114,12 @@ __global__ void __launch_bounds__(128) k_galerkin_fine(Grid gf, Grid gc, Phys ph
   const typename Vec2<R>::type m = mat[e];
   ElemState<R> st;
   elem_state(C, p, tt, m.x, k < ph.heated_layers ? (R)ph.Q : R(0), st);
-  R dp[8], dt[8], oP[8], oT[8];
-#pragma unroll
-  for (int a = 0; a < 8; ++a) { dp[a] = (col == a) ? R(1) : R(0); dt[a] = (col == 8 + a) ? R(1) : R(0); }
-  elem_jv_dir<R>(C, st, m.y, dp, dt, oP, oT);
+  R oP[8], oT[8];
+  elem_jac_column<R>(C, st, m.y, col, oP, oT);
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
-    Jc[c][r * 16 + col] = oP[r];
-    Jc[c][(8 + r) * 16 + col] = oT[r];
+    Jc[c][r * NC_LD + col] = oP[r];
+    Jc[c][(8 + r) * NC_LD + col] = oT[r];
   }
   // block diagonal of level 0 (row-major [PP PT; TP TT]) on free nodes
   const int a = col & 7;
@@ -110,8 +135,8 @@ __global__ void __launch_bounds__(128) k_galerkin_fine(Grid gf, Grid gc, Phys ph
 template <typename R>
 __global__ void __launch_bounds__(128) k_galerkin_coarse(Grid gf, Grid gc, const R* __restrict__ ebe_f,
                                                          R* __restrict__ diag_f, R* __restrict__ ebe_c) {
-  __shared__ R Jc[8][256];
-  __shared__ R Tc[8][256];
+  __shared__ R Jc[8][16 * NC_LD];
+  __shared__ R Tc[8][16 * NC_LD];
   const long long E = blockIdx.x;
   int I, J, K;
   elem_ijk(gc, E, I, J, K);
@@ -120,7 +145,7 @@ __global__ void __launch_bounds__(128) k_galerkin_coarse(Grid gf, Grid gc, const
     const int c = idx >> 8, r = idx & 255;
     const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
     const long long e = i + (long long)gf.nx * (j + (long long)gf.ny * k);
-    Jc[c][r] = ebe_f[e * 256 + r];
+    Jc[c][(r >> 4) * NC_LD + (r & 15)] = ebe_f[e * 256 + r];
   }
   __syncthreads();
   if (t < 64) {
@@ -128,30 +153,14 @@ __global__ void __launch_bounds__(128) k_galerkin_coarse(Grid gf, Grid gc, const
     const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
     if (k + (a >> 2) < gf.nz) {
       const long long n = corner_node(gf, i, j, k, a);
-      add_diag_block(diag_f, n, 0, Jc[c][a * 16 + a]);
-      add_diag_block(diag_f, n, 1, Jc[c][a * 16 + 8 + a]);
-      add_diag_block(diag_f, n, 2, Jc[c][(8 + a) * 16 + a]);
-      add_diag_block(diag_f, n, 3, Jc[c][(8 + a) * 16 + 8 + a]);
+      add_diag_block(diag_f, n, 0, Jc[c][a * NC_LD + a]);
+      add_diag_block(diag_f, n, 1, Jc[c][a * NC_LD + 8 + a]);
+      add_diag_block(diag_f, n, 2, Jc[c][(8 + a) * NC_LD + a]);
+      add_diag_block(diag_f, n, 3, Jc[c][(8 + a) * NC_LD + 8 + a]);
     }
   }
+  __syncthreads();
   galerkin_phase2<R>(Jc, Tc, ebe_c + E * 256);
-}
-
-template <typename R>
-__global__ void k_diag_from_ebe(Grid g, const R* __restrict__ ebe, R* __restrict__ diag) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= g.ne) return;
-  int i, j, k;
-  elem_ijk(g, e, i, j, k);
-  const R* A = ebe + e * 256;
-  for (int a = 0; a < 8; ++a) {
-    if (k + (a >> 2) == g.nz) continue;
-    const long long n = corner_node(g, i, j, k, a);
-    add_diag_block(diag, n, 0, A[a * 16 + a]);
-    add_diag_block(diag, n, 1, A[a * 16 + 8 + a]);
-    add_diag_block(diag, n, 2, A[(8 + a) * 16 + a]);
-    add_diag_block(diag, n, 3, A[(8 + a) * 16 + 8 + a]);
-  }
 }
 
 template <typename R>
@@ -171,20 +180,20 @@ template <typename R, bool TR>
 __global__ void k_level0_apply(Grid g, Phys ph, ElemConst<R> C, const typename Vec2<R>::type* __restrict__ s,
                                const typename Vec2<R>::type* __restrict__ mat,
                                const typename Vec2<R>::type* __restrict__ x, R* __restrict__ y) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= g.ne) return;
-  int i, j, k;
-  elem_ijk(g, e, i, j, k);
+  NC_IJK_3D();
+  if (i >= g.nx || j >= g.ny) return;
+  const int n0 = i + g.NX * j + g.NXY * k;
+  const bool top = (k + 1 == g.nz);
   R p[8], t[8], dp[8], dt[8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
-    const long long n = corner_node(g, i, j, k, a);
+    const int n = n0 + corner_off(g, a);
     const typename Vec2<R>::type v = s[n];
     p[a] = v.x; t[a] = v.y;
-    if (k + (a >> 2) == g.nz) { dp[a] = R(0); dt[a] = R(0); }
+    if (top && (a >> 2)) { dp[a] = R(0); dt[a] = R(0); }
     else { const typename Vec2<R>::type w = x[n]; dp[a] = w.x; dt[a] = w.y; }
   }
-  const typename Vec2<R>::type m = mat[e];
+  const typename Vec2<R>::type m = mat[i + g.nx * (j + g.ny * k)];
   ElemState<R> st;
   elem_state(C, p, t, m.x, k < ph.heated_layers ? (R)ph.Q : R(0), st);
   R oP[8], oT[8];
@@ -192,53 +201,10 @@ __global__ void k_level0_apply(Grid g, Phys ph, ElemConst<R> C, const typename V
   else elem_jv_dir<R>(C, st, m.y, dp, dt, oP, oT);
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
-    if (k + (a >> 2) == g.nz) continue;
-    const long long n = corner_node(g, i, j, k, a);
+    if (top && (a >> 2)) continue;
+    const int n = n0 + corner_off(g, a);
     atomicAdd(y + 2 * n, oP[a]);
     atomicAdd(y + 2 * n + 1, oT[a]);
-  }
-}
-
-template <typename R, bool TR>
-__global__ void k_ebe_apply(Grid g, const R* __restrict__ ebe, const typename Vec2<R>::type* __restrict__ x,
-                            R* __restrict__ y) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= g.ne) return;
-  int i, j, k;
-  elem_ijk(g, e, i, j, k);
-  R xe[16];
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    if (k + (a >> 2) == g.nz) { xe[a] = R(0); xe[8 + a] = R(0); continue; }
-    const typename Vec2<R>::type w = x[corner_node(g, i, j, k, a)];
-    xe[a] = w.x; xe[8 + a] = w.y;
-  }
-  const R* A = ebe + e * 256;
-  R ye[16];
-#pragma unroll
-  for (int r = 0; r < 16; ++r) ye[r] = R(0);
-  if (TR) {
-#pragma unroll 4
-    for (int r = 0; r < 16; ++r) {
-      const R xr = xe[r];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) ye[q] += A[r * 16 + q] * xr;
-    }
-  } else {
-#pragma unroll 4
-    for (int r = 0; r < 16; ++r) {
-      R acc = R(0);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) acc += A[r * 16 + q] * xe[q];
-      ye[r] = acc;
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    if (k + (a >> 2) == g.nz) continue;
-    const long long n = corner_node(g, i, j, k, a);
-    atomicAdd(y + 2 * n, ye[a]);
-    atomicAdd(y + 2 * n + 1, ye[8 + a]);
   }
 }
 
@@ -276,25 +242,28 @@ __global__ void k_sub(long long nn, const typename Vec2<R>::type* __restrict__ b
 template <typename R>
 __global__ void k_restrict(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ rf,
                            typename Vec2<R>::type* __restrict__ bc) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= gc.nn) return;
-  int I, J, K;
-  node_ijk(gc, n, I, J, K);
+  const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 4 + threadIdx.y, K = blockIdx.z;
+  if (I >= gc.NX || J >= gc.NY) return;
+  const int n = I + gc.NX * J + gc.NXY * K;
   R a0 = R(0), a1 = R(0);
   if (K < gc.nz) {
+#pragma unroll
     for (int dk = -1; dk <= 1; ++dk) {
       const int k = 2 * K + dk;
       if (k < 0 || k > gf.nz) continue;
       const R wk = dk ? R(0.5) : R(1);
+#pragma unroll
       for (int dj = -1; dj <= 1; ++dj) {
         const int j = 2 * J + dj;
         if (j < 0 || j > gf.ny) continue;
-        const R wj = dj ? R(0.5) : R(1);
+        const R wj = wk * (dj ? R(0.5) : R(1));
+        const int row = gf.NX * j + gf.NXY * k;
+#pragma unroll
         for (int di = -1; di <= 1; ++di) {
           const int i = 2 * I + di;
           if (i < 0 || i > gf.nx) continue;
-          const R w = wk * wj * (di ? R(0.5) : R(1));
-          const typename Vec2<R>::type v = rf[i + (long long)gf.NX * (j + (long long)gf.NY * k)];
+          const R w = wj * (di ? R(0.5) : R(1));
+          const typename Vec2<R>::type v = rf[row + i];
           a0 += w * v.x;
           a1 += w * v.y;
         }
@@ -307,29 +276,26 @@ __global__ void k_restrict(Grid gf, Grid gc, const typename Vec2<R>::type* __res
 template <typename R>
 __global__ void k_prolong_add(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ xc,
                               typename Vec2<R>::type* __restrict__ xf) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= gf.nn) return;
-  int i, j, k;
-  node_ijk(gf, n, i, j, k);
-  if (k == gf.nz) return;
-  int ci[2], cj[2], ck[2];
-  R wi[2], wj[2], wk[2];
-  int ni, nj, nk;
-  if (i & 1) { ci[0] = i >> 1; ci[1] = (i >> 1) + 1; wi[0] = wi[1] = R(0.5); ni = 2; } else { ci[0] = i >> 1; wi[0] = R(1); ni = 1; }
-  if (j & 1) { cj[0] = j >> 1; cj[1] = (j >> 1) + 1; wj[0] = wj[1] = R(0.5); nj = 2; } else { cj[0] = j >> 1; wj[0] = R(1); nj = 1; }
-  if (k & 1) { ck[0] = k >> 1; ck[1] = (k >> 1) + 1; wk[0] = wk[1] = R(0.5); nk = 2; } else { ck[0] = k >> 1; wk[0] = R(1); nk = 1; }
+  NC_IJK_3D();
+  if (i >= gf.NX || j >= gf.NY || k == gf.nz) return;
+  const int n = i + gf.NX * j + gf.NXY * k;
+  const int ci = i >> 1, cj = j >> 1, ck = k >> 1;
+  const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+  const R wi = (i & 1) ? R(0.5) : R(1), wj = (j & 1) ? R(0.5) : R(1), wk = (k & 1) ? R(0.5) : R(1);
+  const R w = wi * wj * wk;
   R a0 = R(0), a1 = R(0);
   for (int c = 0; c < nk; ++c)
-    for (int b = 0; b < nj; ++b)
+    for (int b = 0; b < nj; ++b) {
+      const int row = gc.NX * (cj + b) + gc.NXY * (ck + c) + ci;
       for (int a = 0; a < ni; ++a) {
-        const R w = wi[a] * wj[b] * wk[c];
-        const typename Vec2<R>::type v = xc[ci[a] + (long long)gc.NX * (cj[b] + (long long)gc.NY * ck[c])];
-        a0 += w * v.x;
-        a1 += w * v.y;
+        const typename Vec2<R>::type v = xc[row + a];
+        a0 += v.x;
+        a1 += v.y;
       }
+    }
   typename Vec2<R>::type o = xf[n];
-  o.x += a0;
-  o.y += a1;
+  o.x += w * a0;
+  o.y += w * a1;
   xf[n] = o;
 }
 
@@ -348,83 +314,6 @@ __global__ void k_dense_assemble(Grid g, const R* __restrict__ ebe, double* __re
   atomicAdd(A + row * nf + col, (double)ebe[t]);
 }
 
-// Gauss-Jordan inverse with partial pivoting of A (nf x nf, row major), one block of 1024 threads.
-// work: nf x 2 nf scratch. On success A holds the inverse; flag = 1 on a zero pivot.
-__global__ void __launch_bounds__(1024) k_dense_invert(double* __restrict__ A, double* __restrict__ W, int nf,
-                                                       int* flag) {
-  extern __shared__ double fac[];          // nf factors
-  __shared__ double s_val[32];
-  __shared__ int s_idx[32];
-  __shared__ int s_piv;
-  const int t = threadIdx.x, nt = blockDim.x;
-  const int w2 = 2 * nf;
-  for (long long idx = t; idx < (long long)nf * w2; idx += nt) {
-    const int r = (int)(idx / w2), c = (int)(idx % w2);
-    W[idx] = c < nf ? A[(long long)r * nf + c] : (c - nf == r ? 1.0 : 0.0);
-  }
-  __syncthreads();
-  for (int k = 0; k < nf; ++k) {
-    double best = -1.0;
-    int bi = k;
-    for (int r = k + t; r < nf; r += nt) {
-      const double v = fabs(W[(long long)r * w2 + k]);
-      if (v > best) { best = v; bi = r; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_down_sync(0xffffffffu, best, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if ((t & 31) == 0) { s_val[t >> 5] = best; s_idx[t >> 5] = bi; }
-    __syncthreads();
-    if (t == 0) {
-      double b = -1.0;
-      int bidx = k;
-      for (int w = 0; w < (nt >> 5); ++w)
-        if (s_val[w] > b || (s_val[w] == b && s_idx[w] < bidx)) { b = s_val[w]; bidx = s_idx[w]; }
-      s_piv = (b > 0.0) ? bidx : -1;
-    }
-    __syncthreads();
-    const int p = s_piv;
-    if (p < 0) { if (t == 0) *flag = 1; return; }
-    if (p != k)
-      for (int c = t; c < w2; c += nt) {
-        const double a = W[(long long)k * w2 + c];
-        W[(long long)k * w2 + c] = W[(long long)p * w2 + c];
-        W[(long long)p * w2 + c] = a;
-      }
-    __syncthreads();
-    const double inv = 1.0 / W[(long long)k * w2 + k];
-    __syncthreads();
-    for (int c = t; c < w2; c += nt) W[(long long)k * w2 + c] *= inv;
-    for (int r = t; r < nf; r += nt) fac[r] = W[(long long)r * w2 + k];
-    __syncthreads();
-    for (long long idx = t; idx < (long long)nf * w2; idx += nt) {
-      const int r = (int)(idx / w2), c = (int)(idx % w2);
-      if (r == k || c < k) continue;
-      W[idx] -= fac[r] * W[(long long)k * w2 + c];
-    }
-    __syncthreads();
-  }
-  for (long long idx = t; idx < (long long)nf * nf; idx += nt) {
-    const int r = (int)(idx / nf), c = (int)(idx % nf);
-    A[idx] = W[(long long)r * w2 + nf + c];
-  }
-}
-
-template <typename R, bool TR>
-__global__ void k_dense_solve(const double* __restrict__ Ainv, int nf, const R* __restrict__ b, R* __restrict__ x,
-                              long long n2) {
-  for (int r = threadIdx.x + blockIdx.x * blockDim.x; r < n2; r += blockDim.x * gridDim.x) {
-    if (r >= nf) { x[r] = R(0); continue; }
-    double acc = 0.0;
-    if (TR) { for (int c = 0; c < nf; ++c) acc += Ainv[(long long)c * nf + r] * (double)b[c]; }
-    else { for (int c = 0; c < nf; ++c) acc += Ainv[(long long)r * nf + c] * (double)b[c]; }
-    x[r] = (R)acc;
-  }
-}
-
 template <typename R>
 __global__ void k_to_mg(const double2* __restrict__ v, typename Vec2<R>::type* __restrict__ b, long long nn) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -439,6 +328,297 @@ __global__ void k_from_mg(const typename Vec2<R>::type* __restrict__ x, double2*
   if (n >= nn) return;
   const typename Vec2<R>::type a = x[n];
   z[n] = make_double2((double)a.x, (double)a.y);
+}
+
+
+// ---- assembled 27-point block stencils of the coarse levels ----------------------------------
+// Slot of offset (oi,oj,ok) in {-1,0,1}^3 and block entry (f,g): ((o * 4) + 2 f + g), o = (oi+1) +
+// 3 (oj+1) + 9 (ok+1). Storage is structure-of-arrays: S[slot * nn + node], 108 slots.
+
+template <typename R>
+__global__ void k_stencil_build(Grid g, const R* __restrict__ ebe, R* __restrict__ S) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.nn * 27) return;
+  const int o = (int)(t % 27);
+  const long long n = t / 27;
+  int i, j, k;
+  node_ijk(g, n, i, j, k);
+  const int oi = o % 3 - 1, oj = (o / 3) % 3 - 1, ok = o / 9 - 1;
+  const int mi = i + oi, mj = j + oj, mk = k + ok;
+  R acc[4] = {R(0), R(0), R(0), R(0)};
+  const bool valid = mi >= 0 && mi <= g.nx && mj >= 0 && mj <= g.ny && mk >= 0 && mk <= g.nz &&
+                     k < g.nz && mk < g.nz;   // Dirichlet rows and columns stay zero
+  if (valid) {
+    // elements containing both node (i,j,k) and node (mi,mj,mk)
+    const int ei0 = oi ? min(i, mi) : i - 1, ei1 = oi ? min(i, mi) : i;
+    const int ej0 = oj ? min(j, mj) : j - 1, ej1 = oj ? min(j, mj) : j;
+    const int ek0 = ok ? min(k, mk) : k - 1, ek1 = ok ? min(k, mk) : k;
+    for (int ek = ek0; ek <= ek1; ++ek) {
+      if (ek < 0 || ek >= g.nz) continue;
+      for (int ej = ej0; ej <= ej1; ++ej) {
+        if (ej < 0 || ej >= g.ny) continue;
+        for (int ei = ei0; ei <= ei1; ++ei) {
+          if (ei < 0 || ei >= g.nx) continue;
+          const long long e = ei + (long long)g.nx * (ej + (long long)g.ny * ek);
+          const int a = (i - ei) + 2 * (j - ej) + 4 * (k - ek);
+          const int b = (mi - ei) + 2 * (mj - ej) + 4 * (mk - ek);
+          const R* A = ebe + e * 256;
+          acc[0] += A[a * 16 + b];
+          acc[1] += A[a * 16 + 8 + b];
+          acc[2] += A[(8 + a) * 16 + b];
+          acc[3] += A[(8 + a) * 16 + 8 + b];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) S[(long long)(o * 4 + q) * g.nn + n] = acc[q];
+}
+
+// y = A x (MODE 0), r = b - A x (MODE 1) or x_new = x + omega D^-1 (b - A x) (MODE 2), with A the
+// assembled stencil or (TR) its transpose. One thread per node, gathers its 27 neighbours.
+template <typename R, bool TR, int MODE>
+__global__ void __launch_bounds__(128) k_stencil_apply(Grid g, const R* __restrict__ S,
+                                                       const typename Vec2<R>::type* __restrict__ x,
+                                                       const typename Vec2<R>::type* __restrict__ b,
+                                                       const R* __restrict__ dinv, R omega,
+                                                       typename Vec2<R>::type* __restrict__ out) {
+  NC_IJK_3D();
+  if (i >= g.NX || j >= g.NY) return;
+  const int n = i + g.NX * j + g.NXY * k;
+  if (k == g.nz) { out[n] = mk2<R>(R(0), R(0)); return; }
+  const int nn = (int)g.nn;
+  R y0 = R(0), y1 = R(0);
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    const int oi = o % 3 - 1, oj = (o / 3) % 3 - 1, ok = o / 9 - 1;
+    if ((oi < 0 && i == 0) || (oi > 0 && i == g.nx) || (oj < 0 && j == 0) || (oj > 0 && j == g.ny) ||
+        (ok < 0 && k == 0))
+      continue;
+    const int m = n + oi + g.NX * oj + g.NXY * ok;
+    const typename Vec2<R>::type xv = x[m];
+    if (!TR) {
+      y0 += S[(o * 4 + 0) * nn + n] * xv.x + S[(o * 4 + 1) * nn + n] * xv.y;
+      y1 += S[(o * 4 + 2) * nn + n] * xv.x + S[(o * 4 + 3) * nn + n] * xv.y;
+    } else {
+      const int ro = 26 - o;   // offset -o seen from the neighbour
+      y0 += S[(ro * 4 + 0) * nn + m] * xv.x + S[(ro * 4 + 2) * nn + m] * xv.y;
+      y1 += S[(ro * 4 + 1) * nn + m] * xv.x + S[(ro * 4 + 3) * nn + m] * xv.y;
+    }
+  }
+  if (MODE == 0) { out[n] = mk2<R>(y0, y1); return; }
+  const typename Vec2<R>::type bb = b[n];
+  const R r0 = bb.x - y0, r1 = bb.y - y1;
+  if (MODE == 1) { out[n] = mk2<R>(r0, r1); return; }
+  const R* d = dinv + 4 * n;
+  R z0, z1;
+  if (TR) { z0 = d[0] * r0 + d[2] * r1; z1 = d[1] * r0 + d[3] * r1; }
+  else { z0 = d[0] * r0 + d[1] * r1; z1 = d[2] * r0 + d[3] * r1; }
+  const typename Vec2<R>::type xv = x[n];
+  out[n] = mk2<R>(xv.x + omega * z0, xv.y + omega * z1);
+}
+
+// ---- coarsest level: FP32 Gauss-Jordan inverse with partial pivoting (one block) ------------------
+// W: nf x 2nf scratch (FP32). Ainv32 receives the inverse. flag = 1 on a zero pivot.
+__global__ void __launch_bounds__(1024) k_gj32(const double* __restrict__ A, float* __restrict__ W,
+                                               float* __restrict__ Ainv32, int nf, int* flag) {
+  extern __shared__ float fac[];
+  __shared__ float s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_piv;
+  const int t = threadIdx.x, nt = blockDim.x, w2 = 2 * nf;
+  for (int idx = t; idx < nf * w2; idx += nt) {
+    const int r = idx / w2, c = idx % w2;
+    W[idx] = c < nf ? (float)A[r * nf + c] : (c - nf == r ? 1.f : 0.f);
+  }
+  __syncthreads();
+  for (int k = 0; k < nf; ++k) {
+    float best = -1.f;
+    int bi = nf;
+    for (int r = k + t; r < nf; r += nt) {
+      const float v = fabsf(W[r * w2 + k]);
+      if (v > best) { best = v; bi = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((t & 31) == 0) { s_val[t >> 5] = best; s_idx[t >> 5] = bi; }
+    __syncthreads();
+    if (t == 0) {
+      float bb = -1.f;
+      int bidx = nf;
+      for (int w = 0; w < (nt >> 5); ++w)
+        if (s_val[w] > bb || (s_val[w] == bb && s_idx[w] < bidx)) { bb = s_val[w]; bidx = s_idx[w]; }
+      s_piv = (bb > 0.f && bidx < nf) ? bidx : -1;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p < 0) { if (t == 0) atomicExch(flag, 1); return; }
+    if (p != k)
+      for (int c = t; c < w2; c += nt) {
+        const float a = W[k * w2 + c];
+        W[k * w2 + c] = W[p * w2 + c];
+        W[p * w2 + c] = a;
+      }
+    __syncthreads();
+    const float inv = 1.f / W[k * w2 + k];
+    __syncthreads();
+    for (int c = t; c < w2; c += nt) W[k * w2 + c] *= inv;
+    for (int r = t; r < nf; r += nt) fac[r] = W[r * w2 + k];
+    __syncthreads();
+    for (int idx = t; idx < nf * w2; idx += nt) {
+      const int r = idx / w2, c = idx % w2;
+      if (r == k || c < k) continue;
+      W[idx] -= fac[r] * W[k * w2 + c];
+    }
+    __syncthreads();
+  }
+  for (int idx = t; idx < nf * nf; idx += nt) {
+    const int r = idx / nf, c = idx % nf;
+    Ainv32[idx] = W[r * w2 + nf + c];
+  }
+}
+
+// In-place Gauss-Jordan inversion with partial pivoting, whole matrix in shared memory (FP32,
+// nf <= NC_GJ_SMEM_MAX, rows padded to ld = a multiple of 4). Step k: pick the pivot row p >= k of
+// column k and exchange rows k and p; with r'_j = (j == k ? 1 : A[k][j]) / A[k][k] and
+// c_i = A[i][k] (c_k := -1), zero row k and column k and apply the rank-1 update A -= c r'^T. This
+// leaves r' in row k and -c_i / A[k][k] in column k, as in-place Gauss-Jordan requires. The result
+// is the inverse with its columns permuted by the row exchanges, undone at the end.
+#define NC_GJ_SMEM_MAX 224
+__global__ void __launch_bounds__(1024) k_gj32_smem(const double* __restrict__ A, float* __restrict__ Ainv32,
+                                                    int nf, int* flag) {
+  extern __shared__ float sm[];
+  const int ld = (nf + 3) & ~3;
+  float* M = sm;                     // nf x ld
+  float* rp = M + nf * ld;           // ld
+  float* cf = rp + ld;               // nf
+  int* perm = (int*)(cf + nf);       // nf
+  __shared__ float s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_piv;
+  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+  const int nq = ld >> 2;            // float4 per row
+  for (int i = ty; i < nf; i += 32)
+    for (int j = tx; j < ld; j += 32) M[i * ld + j] = j < nf ? (float)A[(long long)i * nf + j] : 0.f;
+  __syncthreads();
+  for (int k = 0; k < nf; ++k) {
+    float best = -1.f;
+    int bi = nf;
+    for (int r = k + t; r < nf; r += 1024) {
+      const float v = fabsf(M[r * ld + k]);
+      if (v > best) { best = v; bi = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (tx == 0) { s_val[ty] = best; s_idx[ty] = bi; }
+    __syncthreads();
+    if (t == 0) {
+      float bb = -1.f;
+      int bidx = nf;
+      for (int w = 0; w < 32; ++w)
+        if (s_val[w] > bb || (s_val[w] == bb && s_idx[w] < bidx)) { bb = s_val[w]; bidx = s_idx[w]; }
+      s_piv = (bb > 0.f && bidx < nf) ? bidx : -1;
+      perm[k] = bidx;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p < 0) { if (t == 0) atomicExch(flag, 1); return; }
+    // exchange rows k and p; pivot row -> rp (unscaled), old row k -> row p
+    for (int j = t; j < ld; j += 1024) {
+      const float a = M[k * ld + j], b = M[p * ld + j];
+      rp[j] = b;
+      if (p != k) M[p * ld + j] = a;
+    }
+    __syncthreads();
+    const float ipiv = 1.f / rp[k];
+    for (int i = t; i < nf; i += 1024) cf[i] = (i == k) ? -1.f : M[i * ld + k];
+    __syncthreads();
+    for (int j = t; j < ld; j += 1024) {
+      rp[j] = ((j == k) ? 1.f : rp[j]) * ipiv;
+      M[k * ld + j] = 0.f;
+    }
+    for (int i = t; i < nf; i += 1024) M[i * ld + k] = 0.f;
+    __syncthreads();
+    const float4* rp4 = reinterpret_cast<const float4*>(rp);
+    for (int i = ty; i < nf; i += 32) {
+      const float c = cf[i];
+      float4* row = reinterpret_cast<float4*>(M + i * ld);
+      for (int q = tx; q < nq; q += 32) {
+        float4 m = row[q];
+        const float4 r = rp4[q];
+        m.x -= c * r.x; m.y -= c * r.y; m.z -= c * r.z; m.w -= c * r.w;
+        row[q] = m;
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = nf - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = t; i < nf; i += 1024) {
+        const float a = M[i * ld + k];
+        M[i * ld + k] = M[i * ld + p];
+        M[i * ld + p] = a;
+      }
+    __syncthreads();
+  }
+  for (int i = ty; i < nf; i += 32)
+    for (int j = tx; j < nf; j += 32) Ainv32[i * nf + j] = M[i * ld + j];
+}
+
+// x = A^-1 b on the free DOFs of the coarsest level (or A^-T b), in three launches:
+//   x0 = Ainv32 b (FP32), r = b - A x0 (FP64, A the FP64 Galerkin matrix), x = x0 + Ainv32 r (FP32).
+// One warp per row; row-major matrices are read along rows (coalesced) for A x and along columns for
+// A^T x. xr holds x0 (FP64) and r (FP64) between the launches.
+template <typename T, typename AccT, bool TR>
+__device__ __forceinline__ AccT row_dot(const T* __restrict__ M, int nf, int r, const double* __restrict__ v) {
+  const int lane = threadIdx.x & 31;
+  AccT acc = AccT(0);
+  for (int c = lane; c < nf; c += 32)
+    acc += (AccT)(TR ? M[(long long)c * nf + r] : M[(long long)r * nf + c]) * (AccT)v[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
+template <typename R, bool TR>
+__global__ void __launch_bounds__(256) k_coarse_x0(const float* __restrict__ Ainv32, int nf, const R* __restrict__ b,
+                                                   double* __restrict__ bd, double* __restrict__ x0) {
+  __shared__ double sb[1024];
+  for (int c = threadIdx.x; c < nf; c += blockDim.x) sb[c] = (double)b[c];
+  __syncthreads();
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= nf) return;
+  const float acc = row_dot<float, float, TR>(Ainv32, nf, r, sb);
+  if ((threadIdx.x & 31) == 0) { x0[r] = (double)acc; bd[r] = sb[r]; }
+}
+
+template <bool TR>
+__global__ void __launch_bounds__(256) k_coarse_resid(const double* __restrict__ A, int nf, const double* __restrict__ bd,
+                                                      const double* __restrict__ x0, double* __restrict__ rd) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= nf) return;
+  const double acc = row_dot<double, double, TR>(A, nf, r, x0);
+  if ((threadIdx.x & 31) == 0) rd[r] = bd[r] - acc;
+}
+
+template <typename R, bool TR>
+__global__ void __launch_bounds__(256) k_coarse_fix(const float* __restrict__ Ainv32, int nf, const double* __restrict__ x0,
+                                                    const double* __restrict__ rd, R* __restrict__ x, int n2) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r < nf) {
+    const float acc = row_dot<float, float, TR>(Ainv32, nf, r, rd);
+    if ((threadIdx.x & 31) == 0) x[r] = (R)(x0[r] + (double)acc);
+  }
+  for (int q = nf + blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += gridDim.x * blockDim.x) x[q] = R(0);
 }
 
 }  // namespace
@@ -461,13 +641,6 @@ cudaError_t launch_galerkin_coarse(const Grid& gf, const Grid& gc, const R* ebe_
 }
 
 template <typename R>
-cudaError_t launch_diag_from_ebe(const Grid& g, const R* ebe, R* diag, cudaStream_t st, Counters* c) {
-  k_diag_from_ebe<R><<<grid_blocks(g.ne, 128), 128, 0, st>>>(g, ebe, diag);
-  if (c) c->launches += 1;
-  return cudaGetLastError();
-}
-
-template <typename R>
 cudaError_t launch_invert_diag(const Grid& g, R* diag, int* flag, cudaStream_t st, Counters* c) {
   k_invert_diag<R><<<grid_blocks(g.nn, 256), 256, 0, st>>>(g, diag, flag);
   if (c) c->launches += 1;
@@ -480,22 +653,12 @@ cudaError_t launch_level0_apply(const Grid& g, const Phys& ph, const typename Ve
                                 typename Vec2<R>::type* y, bool transpose, cudaStream_t st, Counters* c) {
   cudaError_t err = cudaMemsetAsync(y, 0, sizeof(R) * 2 * g.nn, st);
   if (err != cudaSuccess) return err;
+  const Launch3 L = launch_elems(g);
   if (transpose)
-    k_level0_apply<R, true><<<grid_blocks(g.ne, 128), 128, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, x, (R*)y);
+    k_level0_apply<R, true><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, x, (R*)y);
   else
-    k_level0_apply<R, false><<<grid_blocks(g.ne, 128), 128, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, x, (R*)y);
+    k_level0_apply<R, false><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, x, (R*)y);
   if (c) { c->launches += 1; c->bytes += sizeof(R) * (6.0 * g.nn + 2.0 * g.ne); }
-  return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t launch_ebe_apply(const Grid& g, const R* ebe, const typename Vec2<R>::type* x,
-                             typename Vec2<R>::type* y, bool transpose, cudaStream_t st, Counters* c) {
-  cudaError_t err = cudaMemsetAsync(y, 0, sizeof(R) * 2 * g.nn, st);
-  if (err != cudaSuccess) return err;
-  if (transpose) k_ebe_apply<R, true><<<grid_blocks(g.ne, 128), 128, 0, st>>>(g, ebe, x, (R*)y);
-  else k_ebe_apply<R, false><<<grid_blocks(g.ne, 128), 128, 0, st>>>(g, ebe, x, (R*)y);
-  if (c) { c->launches += 1; c->bytes += sizeof(R) * (4.0 * g.nn + 256.0 * g.ne); }
   return cudaGetLastError();
 }
 
@@ -527,7 +690,8 @@ cudaError_t launch_sub(const Grid& g, const typename Vec2<R>::type* b, const typ
 template <typename R>
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* rf,
                             typename Vec2<R>::type* bc, cudaStream_t st, Counters* c) {
-  k_restrict<R><<<grid_blocks(gc.nn, 256), 256, 0, st>>>(gf, gc, rf, bc);
+  const Launch3 L = launch_nodes(gc);
+  k_restrict<R><<<L.grid, L.block, 0, st>>>(gf, gc, rf, bc);
   if (c) { c->launches += 1; c->bytes += sizeof(R) * 2.0 * (gf.nn + gc.nn); }
   return cudaGetLastError();
 }
@@ -535,7 +699,8 @@ cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const typename Vec2<
 template <typename R>
 cudaError_t launch_prolong_add(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* xc,
                                typename Vec2<R>::type* xf, cudaStream_t st, Counters* c) {
-  k_prolong_add<R><<<grid_blocks(gf.nn, 256), 256, 0, st>>>(gf, gc, xc, xf);
+  const Launch3 L = launch_nodes(gf);
+  k_prolong_add<R><<<L.grid, L.block, 0, st>>>(gf, gc, xc, xf);
   if (c) { c->launches += 1; c->bytes += sizeof(R) * 2.0 * (2.0 * gf.nn + gc.nn); }
   return cudaGetLastError();
 }
@@ -549,21 +714,73 @@ cudaError_t launch_dense_assemble(const Grid& g, const R* ebe, double* A, int nf
   return cudaGetLastError();
 }
 
-cudaError_t launch_dense_invert(double* A, double* work, int nf, int* flag, cudaStream_t st, Counters* c) {
-  k_dense_invert<<<1, 1024, sizeof(double) * nf, st>>>(A, work, nf, flag);
+cudaError_t launch_coarse_factor(const double* A, float* work, float* Ainv32, int nf, int* flag, cudaStream_t st,
+                                 Counters* c) {
+  if (nf <= NC_GJ_SMEM_MAX) {
+    const int ld = (nf + 3) & ~3;
+    const size_t sm = sizeof(float) * ((size_t)nf * ld + ld + 2 * nf);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(k_gj32_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(float) * (NC_GJ_SMEM_MAX * NC_GJ_SMEM_MAX + 3 * NC_GJ_SMEM_MAX)));
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    k_gj32_smem<<<1, dim3(32, 32), sm, st>>>(A, Ainv32, nf, flag);
+  } else {
+    k_gj32<<<1, 1024, sizeof(float) * nf, st>>>(A, work, Ainv32, nf, flag);
+  }
   if (c) c->launches += 1;
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_dense_solve(const double* Ainv, int nf, const typename Vec2<R>::type* b,
-                               typename Vec2<R>::type* x, long long nn, bool transpose, cudaStream_t st,
-                               Counters* c) {
-  const long long n2 = 2 * nn;
-  const unsigned nb = grid_blocks(n2, 128, 64);
-  if (transpose) k_dense_solve<R, true><<<nb, 128, 0, st>>>(Ainv, nf, (const R*)b, (R*)x, n2);
-  else k_dense_solve<R, false><<<nb, 128, 0, st>>>(Ainv, nf, (const R*)b, (R*)x, n2);
-  if (c) c->launches += 1;
+cudaError_t launch_stencil_build(const Grid& g, const R* ebe, R* S, cudaStream_t st, Counters* c) {
+  k_stencil_build<R><<<grid_blocks(g.nn * 27, 256), 256, 0, st>>>(g, ebe, S);
+  if (c) { c->launches += 1; c->bytes += sizeof(R) * (256.0 * g.ne + 108.0 * g.nn); }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_stencil_apply(const Grid& g, const R* S, const typename Vec2<R>::type* x,
+                                 const typename Vec2<R>::type* b, const R* dinv, R omega,
+                                 typename Vec2<R>::type* out, bool transpose, int mode, cudaStream_t st,
+                                 Counters* c) {
+  const Launch3 L = launch_nodes(g);
+#define NC_ST(TRV, MV) k_stencil_apply<R, TRV, MV><<<L.grid, L.block, 0, st>>>(g, S, x, b, dinv, omega, out)
+  if (transpose) {
+    if (mode == 0) NC_ST(true, 0); else if (mode == 1) NC_ST(true, 1); else NC_ST(true, 2);
+  } else {
+    if (mode == 0) NC_ST(false, 0); else if (mode == 1) NC_ST(false, 1); else NC_ST(false, 2);
+  }
+#undef NC_ST
+  if (c) {
+    c->launches += 1;
+    c->bytes += sizeof(R) * (108.0 + 2.0 + 2.0 + (mode ? 2.0 : 0.0) + (mode == 2 ? 6.0 : 0.0)) * g.nn;
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_coarse_solve(const double* A, const float* Ainv32, double* work, int nf,
+                                const typename Vec2<R>::type* b, typename Vec2<R>::type* x, long long nn,
+                                bool transpose, cudaStream_t st, Counters* c) {
+  // work: 3 nf doubles (b, x0, r)
+  double* bd = work;
+  double* x0 = work + nf;
+  double* rd = work + 2 * nf;
+  const unsigned nb = (unsigned)((nf + 7) / 8);
+  const int n2 = (int)(2 * nn);
+  if (transpose) {
+    k_coarse_x0<R, true><<<nb, 256, 0, st>>>(Ainv32, nf, (const R*)b, bd, x0);
+    k_coarse_resid<true><<<nb, 256, 0, st>>>(A, nf, bd, x0, rd);
+    k_coarse_fix<R, true><<<nb, 256, 0, st>>>(Ainv32, nf, x0, rd, (R*)x, n2);
+  } else {
+    k_coarse_x0<R, false><<<nb, 256, 0, st>>>(Ainv32, nf, (const R*)b, bd, x0);
+    k_coarse_resid<false><<<nb, 256, 0, st>>>(A, nf, bd, x0, rd);
+    k_coarse_fix<R, false><<<nb, 256, 0, st>>>(Ainv32, nf, x0, rd, (R*)x, n2);
+  }
+  if (c) c->launches += 3;
   return cudaGetLastError();
 }
 
@@ -586,13 +803,10 @@ cudaError_t launch_from_mg(const typename Vec2<R>::type* x, double* z, long long
                                                const Vec2<R>::type*, R*, R*, cudaStream_t, Counters*);         \
   template cudaError_t launch_galerkin_coarse<R>(const Grid&, const Grid&, const R*, R*, R*, cudaStream_t,    \
                                                  Counters*);                                                   \
-  template cudaError_t launch_diag_from_ebe<R>(const Grid&, const R*, R*, cudaStream_t, Counters*);           \
   template cudaError_t launch_invert_diag<R>(const Grid&, R*, int*, cudaStream_t, Counters*);                 \
   template cudaError_t launch_level0_apply<R>(const Grid&, const Phys&, const Vec2<R>::type*,                 \
                                               const Vec2<R>::type*, const Vec2<R>::type*, Vec2<R>::type*,     \
                                               bool, cudaStream_t, Counters*);                                  \
-  template cudaError_t launch_ebe_apply<R>(const Grid&, const R*, const Vec2<R>::type*, Vec2<R>::type*, bool, \
-                                           cudaStream_t, Counters*);                                           \
   template cudaError_t launch_jacobi_update<R>(const Grid&, const R*, const Vec2<R>::type*,                   \
                                                const Vec2<R>::type*, const Vec2<R>::type*, Vec2<R>::type*, R, \
                                                bool, bool, cudaStream_t, Counters*);                           \
@@ -603,10 +817,14 @@ cudaError_t launch_from_mg(const typename Vec2<R>::type* x, double* z, long long
   template cudaError_t launch_prolong_add<R>(const Grid&, const Grid&, const Vec2<R>::type*, Vec2<R>::type*,  \
                                              cudaStream_t, Counters*);                                         \
   template cudaError_t launch_dense_assemble<R>(const Grid&, const R*, double*, int, cudaStream_t, Counters*);\
-  template cudaError_t launch_dense_solve<R>(const double*, int, const Vec2<R>::type*, Vec2<R>::type*,        \
-                                             long long, bool, cudaStream_t, Counters*);                        \
+  template cudaError_t launch_coarse_solve<R>(const double*, const float*, double*, int, const Vec2<R>::type*, \
+                                              Vec2<R>::type*, long long, bool, cudaStream_t, Counters*);        \
   template cudaError_t launch_to_mg<R>(const double*, Vec2<R>::type*, long long, cudaStream_t, Counters*);    \
-  template cudaError_t launch_from_mg<R>(const Vec2<R>::type*, double*, long long, cudaStream_t, Counters*);
+  template cudaError_t launch_from_mg<R>(const Vec2<R>::type*, double*, long long, cudaStream_t, Counters*); \
+  template cudaError_t launch_stencil_build<R>(const Grid&, const R*, R*, cudaStream_t, Counters*);           \
+  template cudaError_t launch_stencil_apply<R>(const Grid&, const R*, const Vec2<R>::type*,                  \
+                                               const Vec2<R>::type*, const R*, R, Vec2<R>::type*, bool, int, \
+                                               cudaStream_t, Counters*);
 
 NC_INSTANTIATE_MG(float)
 NC_INSTANTIATE_MG(double)

@@ -24,28 +24,102 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// part[i * gridDim.x + b] = sum over segment b of V_i . w
-__global__ void k_multidot_part(const double* __restrict__ V, long long ld, int nvec,
-                                const double* __restrict__ w, long long n, double* __restrict__ part) {
+// part[i * gridDim.x + b] = sum over segment b of V_i . w. Register tile of NV >= nvec vectors:
+// every element of w and of each V_i is read once.
+template <int NV>
+__global__ void __launch_bounds__(256) k_multidot_part(const double* __restrict__ V, long long ld, int nvec,
+                                                       const double* __restrict__ w, long long n,
+                                                       double* __restrict__ part) {
   __shared__ double sh[32];
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
   const long long seg = (n + gridDim.x - 1) / gridDim.x;
   const long long lo = seg * blockIdx.x;
   const long long hi = min(n, lo + seg);
-  for (int i = 0; i < nvec; ++i) {
-    const double* v = V + (long long)i * ld;
-    double acc = 0.0;
-    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) acc += v[t] * w[t];
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = s;
+  for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+    const double x = w[t];
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (i < nvec) acc[i] += V[(long long)i * ld + t] * x;
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    if (i >= nvec) break;
+    const double r = block_sum(acc[i], sh);
+    if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = r;
   }
 }
 
+// One block per vector sums its nb partials: fixed strided assignment, then a fixed shuffle tree.
 __global__ void k_sum_parts(const double* __restrict__ part, int nb, int nvec, double* __restrict__ res) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nvec) return;
+  __shared__ double sh[32];
+  const int i = blockIdx.x;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[(long long)i * nb + b];
-  res[i] = s;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(long long)i * nb + b];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) res[i] = s;
+}
+
+// Fused classical Gram-Schmidt pass: w <- w - sum_i c_i V_i with c read from device memory, then
+// part holds the partial sums of V_i . w (i < nvec) and of w . w (index nvec), per block.
+// NV >= nvec is the register tile (one V value per vector per element).
+template <int NV>
+__global__ void __launch_bounds__(256) k_cgs_update_dots(double* __restrict__ w, const double* __restrict__ V,
+                                                         long long ld, int nvec, const double* __restrict__ c,
+                                                         long long n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double cc[NV], acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) { cc[i] = i < nvec ? c[i] : 0.0; acc[i] = 0.0; }
+  double accw = 0.0;
+  const long long seg = (n + gridDim.x - 1) / gridDim.x;
+  const long long lo = seg * blockIdx.x;
+  const long long hi = min(n, lo + seg);
+  for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+    double v[NV];
+    double x = w[t];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      v[i] = i < nvec ? V[(long long)i * ld + t] : 0.0;
+      x -= cc[i] * v[i];
+    }
+    w[t] = x;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += v[i] * x;
+    accw += x * x;
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    if (i >= nvec) break;
+    const double r = block_sum(acc[i], sh);
+    if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = r;
+  }
+  const double r = block_sum(accw, sh);
+  if (threadIdx.x == 0) part[(long long)nvec * gridDim.x + blockIdx.x] = r;
+}
+
+// Second Gram-Schmidt correction and normalisation: w <- (w - sum_i c_i V_i) / sqrt(ww - sum c_i^2),
+// with c = res[0..nvec) and ww = res[nvec] from k_cgs_update_dots (device memory).
+template <int NV>
+__global__ void __launch_bounds__(256) k_cgs_finish(double* __restrict__ w, const double* __restrict__ V, long long ld,
+                                                    int nvec, const double* __restrict__ res, long long n) {
+  double cc[NV];
+  double corr = 0.0;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    cc[i] = i < nvec ? res[i] : 0.0;
+    corr += cc[i] * cc[i];
+  }
+  const double h2 = res[nvec] - corr;
+  const double inv = h2 > 0.0 ? 1.0 / sqrt(h2) : 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double x = w[t];
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (i < nvec) x -= cc[i] * V[(long long)i * ld + t];
+    w[t] = x * inv;
+  }
 }
 
 // Sum of squares over the free rows of a state vector (rows of nodes below the top plane).
@@ -146,12 +220,21 @@ __global__ void k_filter_rhs(Grid g, const double* __restrict__ gamma, int heate
   b[n] = t0 * acc;
 }
 
-__global__ void k_helmholtz(Grid g, FilterConst F, const double* __restrict__ x, double* __restrict__ y) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= g.nn) return;
-  int i, j, k;
-  node_ijk(g, n, i, j, k);
-  double acc = 0.0;
+// (r^2 K + M) x at node (i,j,k). Interior nodes use the constant 27-point stencil C27 (the sum of
+// the element matrices of the 8 surrounding elements); nodes on the boundary gather element by
+// element from the 8x8 element matrix A.
+template <typename R, typename FC>
+__device__ __forceinline__ R helm_node(const Grid& g, const FC& F, const R* __restrict__ x, int i, int j, int k,
+                                       int n) {
+  R acc = R(0);
+  if (i > 0 && i < g.nx && j > 0 && j < g.ny && k > 0 && k < g.nz) {
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+      const int oi = o % 3 - 1, oj = (o / 3) % 3 - 1, ok = o / 9 - 1;
+      acc += (R)F.C27[o] * x[n + oi + g.NX * oj + g.NXY * ok];
+    }
+    return acc;
+  }
   for (int dk = -1; dk <= 0; ++dk) {
     const int ek = k + dk;
     if (ek < 0 || ek >= g.nz) continue;
@@ -162,12 +245,48 @@ __global__ void k_helmholtz(Grid g, FilterConst F, const double* __restrict__ x,
         const int ei = i + di;
         if (ei < 0 || ei >= g.nx) continue;
         const int a = -di + 2 * (-dj) + 4 * (-dk);
+        const int e0 = ei + g.NX * ej + g.NXY * ek;
 #pragma unroll
-        for (int b = 0; b < 8; ++b) acc += F.A[a * 8 + b] * x[corner_node(g, ei, ej, ek, b)];
+        for (int b = 0; b < 8; ++b) acc += (R)F.A[a * 8 + b] * x[e0 + corner_off(g, b)];
       }
     }
   }
-  y[n] = acc;
+  return acc;
+}
+
+template <typename R, typename FC>
+__global__ void k_helmholtz(Grid g, FC F, const R* __restrict__ x, R* __restrict__ y) {
+  NC_IJK_3D();
+  if (i >= g.NX || j >= g.NY) return;
+  const int n = i + g.NX * j + g.NXY * k;
+  y[n] = helm_node<R>(g, F, x, i, j, k, n);
+}
+
+__global__ void k_cheb_init(long long nn, const float* __restrict__ dinv, const float* __restrict__ r,
+                            float* __restrict__ x, float* __restrict__ d, float c0) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  x[n] = 0.f;
+  d[n] = c0 * dinv[n] * r[n];
+}
+
+__global__ void k_cheb_step(Grid g, FilterConstF F, const float* __restrict__ dinv, const float* __restrict__ d,
+                            float* __restrict__ dn, float* __restrict__ x, float* __restrict__ r, float c1, float c2) {
+  NC_IJK_3D();
+  if (i >= g.NX || j >= g.NY) return;
+  const int n = i + g.NX * j + g.NXY * k;
+  const float q = helm_node<float>(g, F, d, i, j, k, n);
+  const float dv = d[n];
+  x[n] += dv;
+  const float rv = r[n] - q;
+  r[n] = rv;
+  dn[n] = c1 * dv + c2 * dinv[n] * rv;
+}
+
+__global__ void k_add_f2d(double* __restrict__ y, const float* __restrict__ x, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] += (double)x[t];
 }
 
 __global__ void k_helmholtz_diag(Grid g, double d, double* __restrict__ dinv) {
@@ -245,8 +364,12 @@ int reduce_blocks(long long n) {
 cudaError_t launch_multidot(const double* V, long long ld, int nvec, const double* w, long long n,
                             double* part, double* res, cudaStream_t st, Counters* c) {
   const int nb = reduce_blocks(n);
-  k_multidot_part<<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
-  k_sum_parts<<<(nvec + 63) / 64, 64, 0, st>>>(part, nb, nvec, res);
+  if (nvec <= 4) k_multidot_part<4><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
+  else if (nvec <= 8) k_multidot_part<8><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
+  else if (nvec <= 16) k_multidot_part<16><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
+  else if (nvec <= 32) k_multidot_part<32><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
+  else k_multidot_part<66><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
+  k_sum_parts<<<nvec, 256, 0, st>>>(part, nb, nvec, res);
   if (c) { c->launches += 2; c->bytes += 8.0 * n * (nvec + 1); }
   return cudaGetLastError();
 }
@@ -256,8 +379,37 @@ cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, doub
   const long long nfree2 = 2LL * g.NX * g.NY * g.nz;
   const int nb = reduce_blocks(nfree2);
   k_norm2_free_part<<<nb, kRedThreads, 0, st>>>(a, nfree2, part);
-  k_sum_parts<<<1, 64, 0, st>>>(part, nb, 1, res);
+  k_sum_parts<<<1, 256, 0, st>>>(part, nb, 1, res);
   if (c) { c->launches += 2; c->bytes += 8.0 * nfree2; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cgs_update_dots(double* w, const double* V, long long ld, int nvec, const double* c, long long n,
+                                   double* part, double* res, cudaStream_t st, Counters* cnt) {
+  const int nb = reduce_blocks(n);
+#define NC_CGS1(NV) k_cgs_update_dots<NV><<<nb, kRedThreads, 0, st>>>(w, V, ld, nvec, c, n, part)
+  if (nvec <= 4) NC_CGS1(4);
+  else if (nvec <= 8) NC_CGS1(8);
+  else if (nvec <= 16) NC_CGS1(16);
+  else if (nvec <= 32) NC_CGS1(32);
+  else return cudaErrorInvalidValue;
+#undef NC_CGS1
+  k_sum_parts<<<nvec + 1, 256, 0, st>>>(part, nb, nvec + 1, res);
+  if (cnt) { cnt->launches += 2; cnt->bytes += 8.0 * n * (nvec + 2); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cgs_finish(double* w, const double* V, long long ld, int nvec, const double* res, long long n,
+                              cudaStream_t st, Counters* cnt) {
+  const unsigned nb = stream_blocks(n);
+#define NC_CGS2(NV) k_cgs_finish<NV><<<nb, 256, 0, st>>>(w, V, ld, nvec, res, n)
+  if (nvec <= 4) NC_CGS2(4);
+  else if (nvec <= 8) NC_CGS2(8);
+  else if (nvec <= 16) NC_CGS2(16);
+  else if (nvec <= 32) NC_CGS2(32);
+  else return cudaErrorInvalidValue;
+#undef NC_CGS2
+  if (cnt) { cnt->launches += 1; cnt->bytes += 8.0 * n * (nvec + 2); }
   return cudaGetLastError();
 }
 
@@ -325,8 +477,38 @@ cudaError_t launch_filter_rhs(const Grid& g, const double* gamma, int heated_lay
 
 cudaError_t launch_helmholtz(const Grid& g, const FilterConst& F, const double* x, double* y, cudaStream_t st,
                              Counters* c) {
-  k_helmholtz<<<grid_blocks(g.nn, 256), 256, 0, st>>>(g, F, x, y);
+  const Launch3 L = launch_nodes(g);
+  k_helmholtz<double, FilterConst><<<L.grid, L.block, 0, st>>>(g, F, x, y);
   if (c) { c->launches += 1; c->bytes += 16.0 * g.nn; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_helmholtz_f32(const Grid& g, const FilterConstF& F, const float* x, float* y, cudaStream_t st,
+                                 Counters* c) {
+  const Launch3 L = launch_nodes(g);
+  k_helmholtz<float, FilterConstF><<<L.grid, L.block, 0, st>>>(g, F, x, y);
+  if (c) { c->launches += 1; c->bytes += 8.0 * g.nn; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_init(long long n, const float* dinv, const float* r, float* x, float* d, float c0,
+                             cudaStream_t st, Counters* c) {
+  k_cheb_init<<<grid_blocks(n, 256), 256, 0, st>>>(n, dinv, r, x, d, c0);
+  if (c) { c->launches += 1; c->bytes += 16.0 * n; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_step(const Grid& g, const FilterConstF& F, const float* dinv, const float* d, float* dn,
+                             float* x, float* r, float c1, float c2, cudaStream_t st, Counters* c) {
+  const Launch3 L = launch_nodes(g);
+  k_cheb_step<<<L.grid, L.block, 0, st>>>(g, F, dinv, d, dn, x, r, c1, c2);
+  if (c) { c->launches += 1; c->bytes += 32.0 * g.nn; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_f2d(double* y, const float* x, long long n, cudaStream_t st, Counters* c) {
+  k_add_f2d<<<stream_blocks(n), 256, 0, st>>>(y, x, n);
+  if (c) { c->launches += 1; c->bytes += 20.0 * n; }
   return cudaGetLastError();
 }
 

@@ -67,6 +67,13 @@ cudaError_t launch_multidot(const double* V, long long ld, int nvec, const doubl
 // res[0] = sum over free entries (Dirichlet rows excluded) of a^2, for a state vector.
 cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, double* res,
                               cudaStream_t st, Counters* c);
+// Fused classical Gram-Schmidt (nvec <= 32), coefficients in device memory:
+//   update_dots: w -= sum_i c_i V_i; res[0..nvec) = V^T w, res[nvec] = w . w
+//   finish:      w = (w - sum_i res_i V_i) / sqrt(res[nvec] - sum res_i^2)
+cudaError_t launch_cgs_update_dots(double* w, const double* V, long long ld, int nvec, const double* c, long long n,
+                                   double* part, double* res, cudaStream_t st, Counters* cnt);
+cudaError_t launch_cgs_finish(double* w, const double* V, long long ld, int nvec, const double* res, long long n,
+                              cudaStream_t st, Counters* cnt);
 // y += sum_i coef[i] * V_i (nvec <= 64), n doubles.
 cudaError_t launch_axpy_multi(double* y, const double* V, long long ld, int nvec, const double* coef,
                               long long n, cudaStream_t st, Counters* c);
@@ -83,7 +90,18 @@ cudaError_t launch_zero_dirichlet(const Grid& g, double* a, cudaStream_t st, Cou
 // Design check: flag = 1 if any value is NaN or outside [0,1].
 cudaError_t launch_check_design(const double* rho, long long ne, int* flag, cudaStream_t st);
 // Filter pieces (Helmholtz (r^2 K + M) x = T^T gamma, Q1 nodal, element mean out).
-struct FilterConst { double A[64]; double t0; double diag; };
+struct FilterConst { double A[64]; double C27[27]; double t0; double diag; };
+struct FilterConstF { float A[64]; float C27[27]; };
+// y = (r^2 K + M) x in FP64 (F) or FP32 (Ff); Chebyshev iteration in FP32 on D^-1 (r^2 K + M):
+//   init: x = 0, d = c0 dinv r;   step: x += d, r -= A d, dn = c1 d + c2 dinv r
+cudaError_t launch_helmholtz_f32(const Grid& g, const FilterConstF& F, const float* x, float* y, cudaStream_t st,
+                                 Counters* c);
+cudaError_t launch_cheb_init(long long n, const float* dinv, const float* r, float* x, float* d, float c0,
+                             cudaStream_t st, Counters* c);
+cudaError_t launch_cheb_step(const Grid& g, const FilterConstF& F, const float* dinv, const float* d, float* dn,
+                             float* x, float* r, float c1, float c2, cudaStream_t st, Counters* c);
+// y += (double) x
+cudaError_t launch_add_f2d(double* y, const float* x, long long n, cudaStream_t st, Counters* c);
 cudaError_t launch_filter_rhs(const Grid& g, const double* gamma, int heated_layers, double scale_elem,
                               double* b, cudaStream_t st, Counters* c);
 cudaError_t launch_helmholtz(const Grid& g, const FilterConst& F, const double* x, double* y,
@@ -111,6 +129,7 @@ template <typename R> struct MGLevelDev {
   typename Vec2<R>::type* b;
   typename Vec2<R>::type* y;
   R* ebe;       // 256 per element (levels >= 1)
+  R* S;         // assembled 27-point 2x2-block stencil, 108 per node, SoA (levels 1 .. L-2)
   R* dinv;      // 4 per node (2x2 block-diagonal inverse, row major), 0 on Dirichlet nodes
 };
 
@@ -124,20 +143,14 @@ cudaError_t launch_galerkin_fine(const Grid& gf, const Grid& gc, const Phys& ph,
 template <typename R>
 cudaError_t launch_galerkin_coarse(const Grid& gf, const Grid& gc, const R* ebe_f, R* diag_f, R* ebe_c,
                                    cudaStream_t st, Counters* c);
-// Block diagonal of a level from its element matrices (coarsest level is not smoothed).
-template <typename R>
-cudaError_t launch_diag_from_ebe(const Grid& g, const R* ebe, R* diag, cudaStream_t st, Counters* c);
 // Invert the 2x2 blocks in place (Dirichlet nodes -> 0). flag = 1 on a singular block.
 template <typename R>
 cudaError_t launch_invert_diag(const Grid& g, R* diag, int* flag, cudaStream_t st, Counters* c);
-// y = A x on a level: level 0 matrix-free J(s) (or J^T), otherwise EBE (or its transpose).
+// y = A x on the finest level: matrix-free J(s) (or J^T).
 template <typename R>
 cudaError_t launch_level0_apply(const Grid& g, const Phys& ph, const typename Vec2<R>::type* s,
                                 const typename Vec2<R>::type* mat, const typename Vec2<R>::type* x,
                                 typename Vec2<R>::type* y, bool transpose, cudaStream_t st, Counters* c);
-template <typename R>
-cudaError_t launch_ebe_apply(const Grid& g, const R* ebe, const typename Vec2<R>::type* x,
-                             typename Vec2<R>::type* y, bool transpose, cudaStream_t st, Counters* c);
 // x_new = x + omega D^-1 (b - y)   (y = A x; first == true: x = 0, y unused)
 template <typename R>
 cudaError_t launch_jacobi_update(const Grid& g, const R* dinv, const typename Vec2<R>::type* b,
@@ -156,16 +169,27 @@ cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const typename Vec2<
 template <typename R>
 cudaError_t launch_prolong_add(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* xc,
                                typename Vec2<R>::type* xf, cudaStream_t st, Counters* c);
-// Coarsest level: dense FP64 matrix of the free DOFs from element matrices, its inverse, and
-// the solve x = A^-1 b (or A^-T b).
+// Coarsest level: dense FP64 matrix of the free DOFs from element matrices; its FP32 inverse
+// (one-block Gauss-Jordan, work: nf x 2nf floats); and the solve x = A^-1 b (or A^-T b) from the
+// FP32 inverse with one FP64 refinement step (nf <= 1024; work: 3 nf doubles).
 template <typename R>
 cudaError_t launch_dense_assemble(const Grid& g, const R* ebe, double* A, int nf, cudaStream_t st,
                                   Counters* c);
-cudaError_t launch_dense_invert(double* A, double* work, int nf, int* flag, cudaStream_t st, Counters* c);
+cudaError_t launch_coarse_factor(const double* A, float* work, float* Ainv32, int nf, int* flag, cudaStream_t st,
+                                 Counters* c);
 template <typename R>
-cudaError_t launch_dense_solve(const double* Ainv, int nf, const typename Vec2<R>::type* b,
-                               typename Vec2<R>::type* x, long long nn, bool transpose, cudaStream_t st,
-                               Counters* c);
+cudaError_t launch_coarse_solve(const double* A, const float* Ainv32, double* work, int nf,
+                                const typename Vec2<R>::type* b, typename Vec2<R>::type* x, long long nn,
+                                bool transpose, cudaStream_t st, Counters* c);
+// Assembled stencil of a coarse level from its element matrices (Dirichlet rows/columns zero), and
+// its application: mode 0 y = A x, mode 1 r = b - A x, mode 2 x_new = x + omega D^-1 (b - A x).
+template <typename R>
+cudaError_t launch_stencil_build(const Grid& g, const R* ebe, R* S, cudaStream_t st, Counters* c);
+template <typename R>
+cudaError_t launch_stencil_apply(const Grid& g, const R* S, const typename Vec2<R>::type* x,
+                                 const typename Vec2<R>::type* b, const R* dinv, R omega,
+                                 typename Vec2<R>::type* out, bool transpose, int mode, cudaStream_t st,
+                                 Counters* c);
 // Cast a FP64 state vector into the multigrid type and back.
 template <typename R>
 cudaError_t launch_to_mg(const double* v, typename Vec2<R>::type* b, long long nn, cudaStream_t st,
