@@ -212,6 +212,21 @@ nc_status nc_get_profile(const nc_problem* pb, int cls, double* ms, long long* l
  * (monotonic counters; any output pointer may be NULL). */
 nc_status nc_counters(const nc_problem* pb, long long* launches, double* bytes);
 
+/* Allocation-free squared norm of the free rows of a state vector: *out_dev = sum over the nodes
+ * below the top face of P_n^2 + T_n^2 (the norm of the Newton stopping test), for the grid g.
+ * The paper has no counterpart: this entry point serves callers that cannot allocate device memory
+ * on this path (all device memory handed out from their own pre-reserved pool, a hard memory budget,
+ * or no cudaMalloc/cudaFree because those calls can synchronise the device). It allocates nothing:
+ * its partial sums live in a fixed 64 KiB device array owned by the library (one per device that
+ * loads it, kept until exit), so grids with more than 8192 * 4096 free entries are rejected with
+ * NC_ERR_ARG. s_dev (2N doubles) and out_dev (1 double) are device pointers of the current device.
+ * The work is queued on `stream` (a cudaStream_t, NULL = the legacy default stream); *out_dev is
+ * valid once the stream has completed it. The first call on a device looks up the device address of
+ * the array (cudaGetSymbolAddress), so make that first call before any stream capture. Every call
+ * shares the array and leaves its last contents there; calls that overlap on the GPU race.
+ * Returns NC_ERR_ARG for NULL pointers or bad sizes and NC_ERR_CUDA if a launch fails. */
+nc_status nc_norm2_free_noalloc(const nc_grid* g, const double* s_dev, double* out_dev, void* stream);
+
 /* Message of the last failed call on pb (or of the last failed nc_create_problem if pb is
  * NULL). Never NULL. */
 const char* nc_last_error(const nc_problem* pb);

@@ -19,7 +19,7 @@ EXPORTS = ("nc_default_params", "nc_create_problem", "nc_destroy_problem", "nc_f
            "nc_set_design", "nc_set_state", "nc_solve_state", "nc_objective", "nc_solve_adjoint",
            "nc_sensitivities", "nc_get_fields", "nc_get_design_fields", "nc_eval_residual",
            "nc_apply_jacobian", "nc_apply_jacobian_transpose", "nc_set_profiling", "nc_get_profile",
-           "nc_counters", "nc_last_error")
+           "nc_counters", "nc_norm2_free_noalloc", "nc_last_error")
 
 PROF_CLASSES = ("residual", "outer_op64", "outer_op32", "mg_op0", "mg_stencil", "mg_setup_fine", "smooth",
                 "krylov_vec", "filter", "sens", "other", "mg_setup_coarse", "coarse_factor", "coarse_solve")
@@ -104,6 +104,7 @@ def load_library(path=None):
         "nc_set_profiling": ([vp, i], i),
         "nc_get_profile": ([vp, i, dp, ctypes.POINTER(ctypes.c_longlong), dp], i),
         "nc_counters": ([vp, ctypes.POINTER(ctypes.c_longlong), dp], i),
+        "nc_norm2_free_noalloc": ([ctypes.POINTER(Grid), vp, vp, vp], i),
         "nc_last_error": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
