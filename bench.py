@@ -190,6 +190,34 @@ def workload_config(args):
 
 
 # ------------------------------------------------------------------------------- GPU arm -----
+# Bound of each kernel class: "alu" classes are arithmetic-bound element kernels (their roofline is
+# the plain FP32 or FP64 ALU peak derived from 152 SMs x lanes x 2 flops x 2.07 GHz: FP32 128 FMA
+# lanes per SM -> 80.5 TFLOP/s, FP64 2 FMA units per SM -> 1.26 TFLOP/s); the rest stream vectors
+# or stencils and are bound by HBM (measured copy bandwidth).
+ALU_CLASSES = {"mg_op0": "fp32", "outer_op32": "fp32", "mg_setup_fine": "fp32",
+               "residual": "fp64", "outer_op64": "fp64", "sens": "fp64"}
+ALU_PEAK_TFLOPS = {"fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "fp64": 152 * 2 * 2 * 2.07e9 / 1e12}
+
+
+def roofline_entry(name, v, peaks):
+    ms, n, nbytes, flops = v
+    per_launch_s = ms * 1e-3 / n
+    if name in ALU_CLASSES:
+        kind = ALU_CLASSES[name]
+        achieved = flops / n / per_launch_s / 1e12
+        peak = ALU_PEAK_TFLOPS[kind]
+        return {"bound": "alu", "kernel_class": name, "arith": kind, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "per_launch_us": per_launch_s * 1e6,
+                "launches": n, "alg_flops_per_launch": flops / n, "alg_bytes_per_launch": nbytes / n,
+                "hbm_frac": nbytes / n / per_launch_s / 1e9 / peaks["hbm_gbs"],
+                "peak_source": "derived from unit counts and the 2.07 GHz maximum SM clock"}
+    achieved = nbytes / n / per_launch_s / 1e9
+    return {"bound": "hbm", "kernel_class": name, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "per_launch_us": per_launch_s * 1e6,
+            "launches": n, "alg_bytes_per_launch": nbytes / n,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+
+
 def run_gpu(args, rank, world, local):
     import torch
     import paper_1904_00182_gb300 as nc
@@ -314,17 +342,9 @@ def run_gpu(args, rank, world, local):
     # roofline of the dominant kernel class, from the live CUDA-event timing of the timed region
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
         peaks = json.load(fh)
+    rooflines = {k: roofline_entry(k, v, peaks) for k, v in prof.items() if v[1] > 0}
     dom = max(prof, key=lambda k: prof[k][0])
-    dms, dn, dbytes = prof[dom]
-    roof = None
-    if dn > 0:
-        per_launch_s = dms * 1e-3 / dn
-        per_launch_bytes = dbytes / dn
-        achieved = per_launch_bytes / per_launch_s / 1e9
-        roof = {"bound": "hbm", "kernel_class": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "per_launch_us": per_launch_s * 1e6, "launches": dn,
-                "alg_bytes_per_launch": per_launch_bytes, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    roof = rooflines.get(dom)
     breakdown = {k: {"ms": v[0], "launches": v[1], "share": v[0] / ms} for k, v in prof.items() if v[1] > 0}
     attributed = sum(v[0] for v in prof.values())
     breakdown["unattributed (host, launch gaps)"] = {"ms": ms - attributed, "launches": 0,
@@ -355,7 +375,7 @@ def run_gpu(args, rank, world, local):
                        "newton_res_hist_last": st_last.get("res_hist"),
                        "adjoint_res_hist_last": timed_stats[-1][1].get("res_hist") if timed_stats else None,
                        "adjoint_krylov_hist_last": timed_stats[-1][1].get("krylov_hist") if timed_stats else None},
-            "kernel_time_share": breakdown}
+            "kernel_time_share": breakdown, "rooflines": rooflines}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -204,9 +204,10 @@ enum {
  * pb; turning it on resets the accumulated times. Timing adds two event records per launch. */
 nc_status nc_set_profiling(nc_problem* pb, int on);
 
-/* Accumulated device time (ms), launches and algorithmic bytes of kernel class cls since
- * profiling was turned on. Any output pointer may be NULL. */
-nc_status nc_get_profile(const nc_problem* pb, int cls, double* ms, long long* launches, double* bytes);
+/* Accumulated device time (ms), launches, algorithmic bytes and algorithmic floating-point
+ * operations of kernel class cls since profiling was turned on. Any output pointer may be NULL. */
+nc_status nc_get_profile(const nc_problem* pb, int cls, double* ms, long long* launches, double* bytes,
+                         double* flops);
 
 /* Kernel launches and algorithmic bytes of every library kernel on pb since creation
  * (monotonic counters; any output pointer may be NULL). */

@@ -102,7 +102,7 @@ def load_library(path=None):
         "nc_apply_jacobian": ([vp, vp, vp, vp, i], i),
         "nc_apply_jacobian_transpose": ([vp, vp, vp, vp], i),
         "nc_set_profiling": ([vp, i], i),
-        "nc_get_profile": ([vp, i, dp, ctypes.POINTER(ctypes.c_longlong), dp], i),
+        "nc_get_profile": ([vp, i, dp, ctypes.POINTER(ctypes.c_longlong), dp, dp], i),
         "nc_counters": ([vp, ctypes.POINTER(ctypes.c_longlong), dp], i),
         "nc_norm2_free_noalloc": ([ctypes.POINTER(Grid), vp, vp, vp], i),
         "nc_last_error": ([vp], ctypes.c_char_p),

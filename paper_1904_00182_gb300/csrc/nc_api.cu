@@ -114,13 +114,14 @@ struct nc_problem {
   Counters cnt;       // per call
   Counters total;     // since creation
   // per-launch event timing of kernel classes (nc_set_profiling)
-  struct Pending { int cls; cudaEvent_t a, b; double bytes; };
+  struct Pending { int cls; cudaEvent_t a, b; double bytes, flops; };
   bool prof_on = false;
   std::vector<cudaEvent_t> evpool;
   std::vector<Pending> pending;
   double prof_ms[NC_PROF_NCLASSES] = {0};
   long long prof_n[NC_PROF_NCLASSES] = {0};
   double prof_bytes[NC_PROF_NCLASSES] = {0};
+  double prof_flops[NC_PROF_NCLASSES] = {0};
 };
 
 namespace {
@@ -169,6 +170,7 @@ void prof_flush(nc_problem* pb) {
       pb->prof_ms[p.cls] += ms;
       pb->prof_n[p.cls] += 1;
       pb->prof_bytes[p.cls] += p.bytes;
+      pb->prof_flops[p.cls] += p.flops;
     } else {
       cudaGetLastError();
     }
@@ -183,8 +185,8 @@ struct ProfScope {
   nc_problem* pb;
   int cls;
   cudaEvent_t a = nullptr;
-  double bytes0;
-  ProfScope(nc_problem* p, int c) : pb(p), cls(c), bytes0(p->cnt.bytes) {
+  double bytes0, flops0;
+  ProfScope(nc_problem* p, int c) : pb(p), cls(c), bytes0(p->cnt.bytes), flops0(p->cnt.flops) {
     if (pb->prof_on && (a = prof_event(pb))) cudaEventRecord(a, pb->st);
   }
   ~ProfScope() {
@@ -192,7 +194,7 @@ struct ProfScope {
     cudaEvent_t b = prof_event(pb);
     if (!b) { pb->evpool.push_back(a); return; }
     cudaEventRecord(b, pb->st);
-    pb->pending.push_back({cls, a, b, pb->cnt.bytes - bytes0});
+    pb->pending.push_back({cls, a, b, pb->cnt.bytes - bytes0, pb->cnt.flops - flops0});
     if (pb->pending.size() > 4096) {
       cudaStreamSynchronize(pb->st);
       prof_flush(pb);
@@ -1212,11 +1214,14 @@ nc_status nc_set_profiling(nc_problem* pb, int on) {
   DeviceGuard dg(pb->device);
   CKS(sync(pb, "set_profiling"));
   pb->prof_on = on != 0;
-  for (int c = 0; c < NC_PROF_NCLASSES; ++c) { pb->prof_ms[c] = 0; pb->prof_n[c] = 0; pb->prof_bytes[c] = 0; }
+  for (int c = 0; c < NC_PROF_NCLASSES; ++c) {
+    pb->prof_ms[c] = 0; pb->prof_n[c] = 0; pb->prof_bytes[c] = 0; pb->prof_flops[c] = 0;
+  }
   return NC_OK;
 }
 
-nc_status nc_get_profile(const nc_problem* cpb, int cls, double* ms, long long* launches, double* bytes) {
+nc_status nc_get_profile(const nc_problem* cpb, int cls, double* ms, long long* launches, double* bytes,
+                         double* flops) {
   nc_problem* pb = const_cast<nc_problem*>(cpb);
   if (!pb || cls < 0 || cls >= NC_PROF_NCLASSES) return NC_ERR_ARG;
   DeviceGuard dg(pb->device);
@@ -1224,6 +1229,7 @@ nc_status nc_get_profile(const nc_problem* cpb, int cls, double* ms, long long* 
   if (ms) *ms = pb->prof_ms[cls];
   if (launches) *launches = pb->prof_n[cls];
   if (bytes) *bytes = pb->prof_bytes[cls];
+  if (flops) *flops = pb->prof_flops[cls];
   return NC_OK;
 }
 

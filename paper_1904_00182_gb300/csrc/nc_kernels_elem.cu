@@ -137,7 +137,7 @@ cudaError_t launch_residual(const Grid& g, const Phys& ph, const double2* s, con
   k_residual<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<double>(ph), s, mat, out);
   const long long plane = (long long)g.NX * g.NY;
   k_residual_bc<<<grid_blocks(plane, 256), 256, 0, st>>>(g, s, out);
-  if (c) { c->launches += 2; c->bytes += 16.0 * g.nn * 2 + 16.0 * g.ne; }
+  if (c) { c->launches += 2; c->bytes += 16.0 * g.nn * 2 + 16.0 * g.ne; c->flops += kFlopsResidual * g.ne; }
   return cudaGetLastError();
 }
 
@@ -148,7 +148,11 @@ static cudaError_t jprod(const Grid& g, const Phys& ph, const SV* s, const typen
   if (err != cudaSuccess) return err;
   const Launch3 L = launch_elems(g);
   k_jprod<R, SV, double, TR><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, v, out);
-  if (c) { c->launches += 1; c->bytes += (2.0 * sizeof(SV) + 32.0) * g.nn + 2.0 * sizeof(R) * g.ne; }
+  if (c) {
+    c->launches += 1;
+    c->bytes += (2.0 * sizeof(SV) + 32.0) * g.nn + 2.0 * sizeof(R) * g.ne;
+    c->flops += (kFlopsState + (TR ? kFlopsJtv : kFlopsJv)) * g.ne;
+  }
   return cudaGetLastError();
 }
 
@@ -174,7 +178,7 @@ cudaError_t launch_sens_elem(const Grid& g, const Phys& ph, const double2* s, co
                              Counters* c) {
   const Launch3 L = launch_elems(g);
   k_sens<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<double>(ph), s, lam, mat, dmat, out);
-  if (c) { c->launches += 1; c->bytes += 32.0 * g.nn + 40.0 * g.ne; }
+  if (c) { c->launches += 1; c->bytes += 32.0 * g.nn + 40.0 * g.ne; c->flops += (kFlopsState + kFlopsSens) * g.ne; }
   return cudaGetLastError();
 }
 

@@ -628,7 +628,11 @@ cudaError_t launch_galerkin_fine(const Grid& gf, const Grid& gc, const Phys& ph,
                                  const typename Vec2<R>::type* mat, R* diag_f, R* ebe_c, cudaStream_t st,
                                  Counters* c) {
   k_galerkin_fine<R><<<(unsigned)gc.ne, 128, 0, st>>>(gf, gc, ph, make_econst<R>(ph), s, mat, diag_f, ebe_c);
-  if (c) { c->launches += 1; c->bytes += sizeof(R) * (2.0 * gf.nn + 2.0 * gf.ne + 4.0 * gf.nn + 256.0 * gc.ne); }
+  if (c) {
+    c->launches += 1;
+    c->bytes += sizeof(R) * (2.0 * gf.nn + 2.0 * gf.ne + 4.0 * gf.nn + 256.0 * gc.ne);
+    c->flops += 16.0 * (kFlopsState + kFlopsJacColumn) * gf.ne;
+  }
   return cudaGetLastError();
 }
 
@@ -658,7 +662,11 @@ cudaError_t launch_level0_apply(const Grid& g, const Phys& ph, const typename Ve
     k_level0_apply<R, true><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, x, (R*)y);
   else
     k_level0_apply<R, false><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, x, (R*)y);
-  if (c) { c->launches += 1; c->bytes += sizeof(R) * (6.0 * g.nn + 2.0 * g.ne); }
+  if (c) {
+    c->launches += 1;
+    c->bytes += sizeof(R) * (6.0 * g.nn + 2.0 * g.ne);   // s, x, y per node; (kappa, k) per element
+    c->flops += (kFlopsState + (transpose ? kFlopsJtv : kFlopsJv)) * g.ne;
+  }
   return cudaGetLastError();
 }
 
@@ -756,7 +764,8 @@ cudaError_t launch_stencil_apply(const Grid& g, const R* S, const typename Vec2<
 #undef NC_ST
   if (c) {
     c->launches += 1;
-    c->bytes += sizeof(R) * (108.0 + 2.0 + 2.0 + (mode ? 2.0 : 0.0) + (mode == 2 ? 6.0 : 0.0)) * g.nn;
+    // 108 stencil coefficients, x and the output per node; + b (modes 1, 2); + D^-1 (mode 2)
+    c->bytes += sizeof(R) * (108.0 + 2.0 + 2.0 + (mode ? 2.0 : 0.0) + (mode == 2 ? 4.0 : 0.0)) * g.nn;
   }
   return cudaGetLastError();
 }

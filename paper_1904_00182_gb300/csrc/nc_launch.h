@@ -33,7 +33,14 @@ inline ElemConst<R> make_econst(const Phys& p) {
 struct Counters {
   long long launches = 0;
   double bytes = 0.0;
+  double flops = 0.0;
 };
+
+// Floating-point operations per element of the element kernels (adds + multiplies, an FMA counts
+// two), counted from nc_element.cuh: residual; element state; J v direction part; J^T w part;
+// J^T w with design derivatives; one element-Jacobian column.
+const double kFlopsResidual = 801.0, kFlopsState = 375.0, kFlopsJv = 928.0, kFlopsJtv = 953.0,
+             kFlopsSens = 1058.0, kFlopsJacColumn = 696.0;
 
 // ---------------- element operators (nc_kernels_elem.cu) ----------------
 // out (2N doubles) = R(s); Dirichlet rows = s. s: double2 per node; mat: (kappa, k) per element.

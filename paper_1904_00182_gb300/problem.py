@@ -137,12 +137,13 @@ class Problem:
         self._check(self.lib.nc_set_profiling(self.h, 1 if on else 0))
 
     def profile(self):
-        """{class: (ms, launches, algorithmic bytes)} accumulated since set_profiling(True)."""
+        """{class: (ms, launches, algorithmic bytes, algorithmic flops)} since set_profiling(True)."""
         out = {}
         for cls, name in enumerate(_abi.PROF_CLASSES):
-            ms, n, b = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
-            self._check(self.lib.nc_get_profile(self.h, cls, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
-            out[name] = (ms.value, n.value, b.value)
+            ms, n, b, f = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+            self._check(self.lib.nc_get_profile(self.h, cls, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
+                                                ctypes.byref(f)))
+            out[name] = (ms.value, n.value, b.value, f.value)
         return out
 
     def counters(self):
