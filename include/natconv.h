@@ -133,6 +133,11 @@ nc_status nc_destroy_problem(nc_problem* pb);
 /* Device bytes nc_create_problem would allocate for (g, p) (for admission control). */
 nc_status nc_footprint_bytes(const nc_grid* g, const nc_params* p, size_t* bytes);
 
+/* Replace the parameters of an existing problem without reallocating (e.g. a new buoyancy factor
+ * for a pooled problem). precision, mg_levels and restart must equal the creation values
+ * (NC_ERR_ARG otherwise). The problem then needs a new nc_set_design. */
+nc_status nc_set_params(nc_problem* pb, const nc_params* p);
+
 /* Design pipeline, Sec. 5.1-5.2: rho (E values in [0,1], finite; NC_ERR_ARG otherwise) ->
  * gamma = 1 on Omega_h -> PDE filter -> gamma~ = 1 on Omega_h -> RAMP kappa_e, k_e.
  * Resets the state to zero unless nc_set_state is called afterwards. */

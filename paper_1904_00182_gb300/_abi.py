@@ -15,7 +15,7 @@ STATUS_NAMES = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_OOM", 3: "NC_ERR_CUDA", 
                 5: "NC_ERR_MAXIT", 6: "NC_ERR_NAN", 7: "NC_ERR_TIMEOUT", 8: "NC_ERR_STATE"}
 
 # Every exported symbol of include/natconv.h.
-EXPORTS = ("nc_default_params", "nc_create_problem", "nc_destroy_problem", "nc_footprint_bytes",
+EXPORTS = ("nc_default_params", "nc_create_problem", "nc_destroy_problem", "nc_footprint_bytes", "nc_set_params",
            "nc_set_design", "nc_set_state", "nc_solve_state", "nc_objective", "nc_solve_adjoint",
            "nc_sensitivities", "nc_get_fields", "nc_get_design_fields", "nc_eval_residual",
            "nc_apply_jacobian", "nc_apply_jacobian_transpose", "nc_set_profiling", "nc_get_profile",
@@ -90,6 +90,7 @@ def load_library(path=None):
         "nc_create_problem": ([ctypes.POINTER(Grid), ctypes.POINTER(Params), vp, ctypes.POINTER(vp)], i),
         "nc_destroy_problem": ([vp], i),
         "nc_footprint_bytes": ([ctypes.POINTER(Grid), ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)], i),
+        "nc_set_params": ([vp, ctypes.POINTER(Params)], i),
         "nc_set_design": ([vp, vp], i),
         "nc_set_state": ([vp, vp, vp], i),
         "nc_solve_state": ([vp, ctypes.POINTER(Stats)], i),

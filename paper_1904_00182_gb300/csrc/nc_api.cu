@@ -773,65 +773,10 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
   return b;
 }
 
-}  // namespace
-
-// ====================================================================================
-extern "C" {
-
-nc_status nc_default_params(nc_params* p) {
-  if (!p) return NC_ERR_ARG;
-  memset(p, 0, sizeof(*p));
-  p->alpha = 1e3;
-  p->kappa_f = 0.0;
-  p->tune_dT = 1.0;
-  p->kappa_ratio = 1e-6;
-  p->k_f = 1.0;
-  p->k_s = 100.0;
-  p->q_c = 8.81;
-  p->q_p = 8.0;
-  p->Q = 0.0;
-  p->heated_layers = 2;
-  p->rho0 = p->mu = p->cp = p->g = 1.0;
-  p->filter_radius = 2.5;
-  p->newton_rtol = 1e-8;
-  p->newton_maxit = 50;
-  p->krylov_rtol = 1e-2;
-  p->krylov_maxit = 300;
-  p->restart = 30;
-  p->precision = NC_PREC_MIXED;
-  p->mg_levels = 0;
-  p->nu_pre = 2;
-  p->nu_post = 2;
-  p->omega = 0.7;
-  p->filter_rtol = 1e-12;
-  p->timeout_s = 600.0;
-  p->adjoint_rtol = 0.0;
-  p->coarse_refactor = 0;
-  return NC_OK;
-}
-
-nc_status nc_footprint_bytes(const nc_grid* g, const nc_params* p, size_t* bytes) {
-  std::string why;
-  if (!bytes) return NC_ERR_ARG;
-  nc_status s = validate(g, p, &why);
-  if (s != NC_OK) return fail(nullptr, s, why);
-  *bytes = footprint(g, p);
-  return NC_OK;
-}
-
-nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream, nc_problem** out) {
-  if (!out) return fail(nullptr, NC_ERR_ARG, "NULL output pointer");
-  *out = nullptr;
-  std::string why;
-  nc_status vs = validate(gr, p, &why);
-  if (vs != NC_OK) return fail(nullptr, vs, why);
-  nc_problem* pb = new nc_problem();
-  cudaGetDevice(&pb->device);
-  pb->g = make_grid(gr->nx, gr->ny, gr->nz, gr->h);
+// Derived constants of a problem from its parameters (physics, filter, Chebyshev bounds).
+void apply_params(nc_problem* pb, const nc_params* p) {
   pb->par = *p;
-  pb->m = p->restart;
   const Grid& g = pb->g;
-  // physical constants
   pb->kappa_f = p->kappa_f > 0 ? p->kappa_f : kappa_f_tuned(p->alpha, p->tune_dT);
   pb->kappa_s = p->kappa_ratio * pb->kappa_f;
   pb->vol_h = (double)g.nx * g.ny * p->heated_layers * g.h * g.h * g.h;
@@ -897,6 +842,67 @@ nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream,
     pb->cheb_iters = std::max(4, (int)std::ceil(std::log(5e-7) / std::log(rq)));
     pb->F.diag = pb->F.A[0];
   }
+}
+
+}  // namespace
+
+// ====================================================================================
+extern "C" {
+
+nc_status nc_default_params(nc_params* p) {
+  if (!p) return NC_ERR_ARG;
+  memset(p, 0, sizeof(*p));
+  p->alpha = 1e3;
+  p->kappa_f = 0.0;
+  p->tune_dT = 1.0;
+  p->kappa_ratio = 1e-6;
+  p->k_f = 1.0;
+  p->k_s = 100.0;
+  p->q_c = 8.81;
+  p->q_p = 8.0;
+  p->Q = 0.0;
+  p->heated_layers = 2;
+  p->rho0 = p->mu = p->cp = p->g = 1.0;
+  p->filter_radius = 2.5;
+  p->newton_rtol = 1e-8;
+  p->newton_maxit = 50;
+  p->krylov_rtol = 1e-2;
+  p->krylov_maxit = 300;
+  p->restart = 30;
+  p->precision = NC_PREC_MIXED;
+  p->mg_levels = 0;
+  p->nu_pre = 2;
+  p->nu_post = 2;
+  p->omega = 0.7;
+  p->filter_rtol = 1e-12;
+  p->timeout_s = 600.0;
+  p->adjoint_rtol = 0.0;
+  p->coarse_refactor = 0;
+  return NC_OK;
+}
+
+nc_status nc_footprint_bytes(const nc_grid* g, const nc_params* p, size_t* bytes) {
+  std::string why;
+  if (!bytes) return NC_ERR_ARG;
+  nc_status s = validate(g, p, &why);
+  if (s != NC_OK) return fail(nullptr, s, why);
+  *bytes = footprint(g, p);
+  return NC_OK;
+}
+
+nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream, nc_problem** out) {
+  if (!out) return fail(nullptr, NC_ERR_ARG, "NULL output pointer");
+  *out = nullptr;
+  std::string why;
+  nc_status vs = validate(gr, p, &why);
+  if (vs != NC_OK) return fail(nullptr, vs, why);
+  nc_problem* pb = new nc_problem();
+  cudaGetDevice(&pb->device);
+  pb->g = make_grid(gr->nx, gr->ny, gr->nz, gr->h);
+  pb->par = *p;
+  pb->m = p->restart;
+  const Grid& g = pb->g;
+  apply_params(pb, p);
   if (stream) pb->st = (cudaStream_t)stream;
   else {
     cudaError_t e = cudaStreamCreateWithFlags(&pb->st, cudaStreamNonBlocking);
@@ -952,6 +958,25 @@ nc_status nc_destroy_problem(nc_problem* pb) {
   if (pb->hflag) cudaFreeHost(pb->hflag);
   if (pb->own_stream && pb->st) cudaStreamDestroy(pb->st);
   delete pb;
+  return NC_OK;
+}
+
+nc_status nc_set_params(nc_problem* pb, const nc_params* p) {
+  if (!pb || !p) return NC_ERR_ARG;
+  nc_grid gr{pb->g.nx, pb->g.ny, pb->g.nz, pb->g.h};
+  std::string why;
+  nc_status vs = validate(&gr, p, &why);
+  if (vs != NC_OK) return fail(pb, vs, why);
+  if (p->precision != pb->par.precision || p->mg_levels != pb->par.mg_levels || p->restart != pb->par.restart)
+    return fail(pb, NC_ERR_ARG, "precision, mg_levels and restart are fixed at creation");
+  DeviceGuard dg(pb->device);
+  CKS(sync(pb, "set_params"));
+  apply_params(pb, p);
+  CK(launch_helmholtz_diag(pb->g, pb->F, pb->fdinv, pb->st));   // the filter radius may have changed
+  CK(launch_cast_d2f(pb->fdinvf, pb->fdinv, pb->g.nn, pb->st, nullptr));
+  CKS(sync(pb, "set_params"));
+  pb->have_R0 = false;   // R(0) depends on the source and the heated layers
+  pb->stage = 0;
   return NC_OK;
 }
 

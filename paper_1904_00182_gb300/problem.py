@@ -89,6 +89,17 @@ class Problem:
     def _empty(self, n):
         return torch.empty(n, dtype=torch.float64, device=self.device)
 
+    def set_params(self, **overrides):
+        """Change parameters in place (not precision, mg_levels or restart); needs a new design."""
+        p = _abi.Params()
+        ctypes.memmove(ctypes.byref(p), ctypes.byref(self.params), ctypes.sizeof(p))
+        for k, v in overrides.items():
+            if not hasattr(p, k):
+                raise KeyError("unknown parameter %r" % k)
+            setattr(p, k, v)
+        self._check(self.lib.nc_set_params(self.h, ctypes.byref(p)))
+        self.params = p
+
     # -- the path -----------------------------------------------------------------------------
     def set_design(self, rho):
         rho = _as_f64(rho)
