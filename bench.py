@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=300)
     return ap.parse_args()
 
 
@@ -178,6 +180,34 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_serving(args, dev):
+    """The 300-request stream (Poisson arrivals at 20/s, grids {32,48,64,96,128}^3, alpha log-uniform in
+    [1e3, 1e5], half state-only and half state+adjoint, seeded filtered-random designs) through the
+    continuous-batching server; designs come from a bank of two per grid size."""
+    from synthetic import request_stream
+    from paper_1904_00182_gb300.serving import Request, Server, summarize
+    stream = request_stream(n=args.serve_requests)
+    bank = {}
+    for r in stream:
+        key = (r["n"], r["design_seed"] % 2)
+        if key not in bank:
+            bank[key] = filtered_random(r["n"], r["n"], r["n"], seed=key[1], volfrac=args.volfrac)
+    reqs = [Request(i, r["t_arrival"], r["n"], r["alpha"], r["adjoint"], bank[(r["n"], r["design_seed"] % 2)])
+            for i, r in enumerate(stream)]
+    srv = Server(slots=6, hbm_budget_bytes=48 << 30, device=dev)
+    # warm the pools with one request per grid size (problem creation is not part of serving)
+    warm = [Request(-1 - k, 0.0, n, 1e4, True, bank[(n, 0)]) for k, n in enumerate(sorted({r.n for r in reqs}))]
+    srv.run(warm)
+    srv.done = []
+    done = srv.run(reqs)
+    out = summarize(done, srv.t_total)
+    out.update({"slots": srv.slots, "hbm_budget_gb": srv.budget / 2 ** 30, "peak_pool_gb": srv.peak_bytes / 2 ** 30,
+                "stream": "%d requests, Poisson 20/s, grids {32,48,64,96,128}^3, alpha log-uniform [1e3,1e5], "
+                          "half with adjoint, mixed precision to 1e-8" % len(reqs)})
+    srv.close()
+    return out
+
+
 def workload_config(args):
     return {"workload": "%dx%dx%d Q1 Darcy-Boussinesq, filtered-random density V=%.1f, alpha=%g, "
                         "mixed-precision GMG (%d levels), Newton to rel. res 1e-8 + adjoint + sensitivities"
@@ -255,12 +285,17 @@ def run_gpu(args, rank, world, local):
         stats_log.append((st, ast))
         return f
 
+    # warm-up: every kernel class timed (the breakdown and the choice of the dominant class);
+    # timed region: only the dominant class is timed, so the events do not slow the other launches
+    pb.set_profiling(True)
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize(dev)
+    warm_prof = pb.profile()
+    dom = max(warm_prof, key=lambda k: warm_prof[k][0])
     if dist:
         dist.barrier()
-    pb.set_profiling(True)
+    pb.set_profiling(classes=[dom])
     l0, _ = pb.counters()
     clocks = ClockSampler(local)
     clocks.start()
@@ -334,6 +369,10 @@ def run_gpu(args, rank, world, local):
     else:
         pb.close()
 
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = run_serving(args, dev)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -342,13 +381,14 @@ def run_gpu(args, rank, world, local):
     # roofline of the dominant kernel class, from the live CUDA-event timing of the timed region
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
         peaks = json.load(fh)
-    rooflines = {k: roofline_entry(k, v, peaks) for k, v in prof.items() if v[1] > 0}
-    dom = max(prof, key=lambda k: prof[k][0])
-    roof = rooflines.get(dom)
-    breakdown = {k: {"ms": v[0], "launches": v[1], "share": v[0] / ms} for k, v in prof.items() if v[1] > 0}
-    attributed = sum(v[0] for v in prof.values())
-    breakdown["unattributed (host, launch gaps)"] = {"ms": ms - attributed, "launches": 0,
-                                                     "share": (ms - attributed) / ms}
+    roof = roofline_entry(dom, prof[dom], peaks) if prof[dom][1] > 0 else None
+    if roof:
+        roof["timed"] = "live, CUDA events on the library stream around every launch of this class in the timed region"
+    # breakdown and per-class rooflines from the profiled warm-up steps (all classes timed)
+    warm_ms = sum(v[0] for v in warm_prof.values())
+    rooflines = {k: roofline_entry(k, v, peaks) for k, v in warm_prof.items() if v[1] > 0}
+    breakdown = {k: {"ms_per_step": v[0] / args.warmup, "launches_per_step": v[1] / args.warmup,
+                     "share_of_kernel_time": v[0] / warm_ms} for k, v in warm_prof.items() if v[1] > 0}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -364,7 +404,7 @@ def run_gpu(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
             "config": workload_config(args), "clocks": clk, "e2e": e2e,
             "gpu_launches": int(l1 - l0), "roofline": roof, "cpu_baseline": cpu,
-            "fp64_path": fp64,
+            "fp64_path": fp64, "serving": serving,
             "solver": {"newton_its": [s[0]["newton_its"] for s in timed_stats],
                        "krylov_its": [s[0]["krylov_its"] for s in timed_stats],
                        "adjoint_krylov_its": [s[1]["krylov_its"] for s in timed_stats],
@@ -375,7 +415,7 @@ def run_gpu(args, rank, world, local):
                        "newton_res_hist_last": st_last.get("res_hist"),
                        "adjoint_res_hist_last": timed_stats[-1][1].get("res_hist") if timed_stats else None,
                        "adjoint_krylov_hist_last": timed_stats[-1][1].get("krylov_hist") if timed_stats else None},
-            "kernel_time_share": breakdown, "rooflines": rooflines}
+            "kernel_time_share_warmup": breakdown, "rooflines_warmup": rooflines}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -101,6 +101,9 @@ typedef struct {
                            <= 0: the state's newton_rtol [0] */
   int coarse_refactor;  /* 1: invert the coarsest multigrid matrix at every set-up; 0: at the first
                            set-up of each solve call, later set-ups refine against the new matrix [0] */
+  double krylov_eta_min; /* lower bound of the Newton forcing term; <= 0: 1e-12 [0] */
+  double adjoint_eta_first; /* FGMRES tolerance of the first adjoint refinement pass; <= 0: 1e-5 with
+                               NC_PREC_MIXED, the adjoint tolerance with NC_PREC_FP64 [0] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */
@@ -192,7 +195,7 @@ enum {
   NC_PROF_OUTER_OP64 = 1,   /* FP64 J v / J^T w (Krylov operator, adjoint refinement residual) */
   NC_PROF_OUTER_OP32 = 2,   /* FP32 J v / J^T w of the Krylov solver */
   NC_PROF_MG_OP0 = 3,       /* multigrid finest-level operator (matrix-free Jacobian) */
-  NC_PROF_MG_STENCIL = 4,   /* multigrid coarse-level stencil operators (fused smoothing / residual) */
+  NC_PROF_MG_STENCIL = 4,   /* stencil operators of multigrid levels >= 2 (fused smoothing / residual) */
   NC_PROF_MG_SETUP = 5,     /* element Jacobians of the finest level and their Galerkin product */
   NC_PROF_SMOOTH = 6,       /* block-Jacobi updates, restriction, prolongation */
   NC_PROF_KRYLOV_VEC = 7,   /* FGMRES dot products and vector updates */
@@ -202,12 +205,14 @@ enum {
   NC_PROF_MG_COARSE_SETUP = 11, /* coarse-level Galerkin products, stencils, block-diagonal inverses */
   NC_PROF_COARSE_FACTOR = 12,   /* inverse of the coarsest-level matrix */
   NC_PROF_COARSE_SOLVE = 13,    /* coarsest-level solve inside the V-cycle */
-  NC_PROF_NCLASSES = 14
+  NC_PROF_MG_STENCIL_L1 = 14,   /* stencil operators of multigrid level 1 (the largest stencil level) */
+  NC_PROF_NCLASSES = 15
 };
 
-/* Turn per-launch CUDA-event timing of the kernel classes above on (1) or off (0) for calls on
- * pb; turning it on resets the accumulated times. Timing adds two event records per launch. */
-nc_status nc_set_profiling(nc_problem* pb, int on);
+/* Per-launch CUDA-event timing of kernel classes for calls on pb: bit c of class_mask times class
+ * c (0: off; -1: all classes). Setting a mask resets the accumulated times. Timing adds two event
+ * records per timed launch. */
+nc_status nc_set_profiling(nc_problem* pb, int class_mask);
 
 /* Accumulated device time (ms), launches, algorithmic bytes and algorithmic floating-point
  * operations of kernel class cls since profiling was turned on. Any output pointer may be NULL. */

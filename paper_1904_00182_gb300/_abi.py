@@ -22,7 +22,8 @@ EXPORTS = ("nc_default_params", "nc_create_problem", "nc_destroy_problem", "nc_f
            "nc_counters", "nc_norm2_free_noalloc", "nc_last_error")
 
 PROF_CLASSES = ("residual", "outer_op64", "outer_op32", "mg_op0", "mg_stencil", "mg_setup_fine", "smooth",
-                "krylov_vec", "filter", "sens", "other", "mg_setup_coarse", "coarse_factor", "coarse_solve")
+                "krylov_vec", "filter", "sens", "other", "mg_setup_coarse", "coarse_factor", "coarse_solve",
+                "mg_stencil_l1")
 
 
 class NatConvError(RuntimeError):
@@ -48,6 +49,7 @@ class Params(ctypes.Structure):
         ("precision", ctypes.c_int), ("mg_levels", ctypes.c_int), ("nu_pre", ctypes.c_int),
         ("nu_post", ctypes.c_int), ("omega", ctypes.c_double), ("filter_rtol", ctypes.c_double),
         ("timeout_s", ctypes.c_double), ("adjoint_rtol", ctypes.c_double), ("coarse_refactor", ctypes.c_int),
+        ("krylov_eta_min", ctypes.c_double), ("adjoint_eta_first", ctypes.c_double),
     ]
 
     def as_dict(self):

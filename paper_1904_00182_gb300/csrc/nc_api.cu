@@ -86,7 +86,7 @@ struct nc_problem {
   double *R = nullptr, *R_try = nullptr, *dx = nullptr, *w = nullptr, *rhs = nullptr;
   double *rho = nullptr, *gamma_t = nullptr, *gsens = nullptr, *u = nullptr;
   double2 *mat = nullptr, *dmat = nullptr;
-  float2 *mat32 = nullptr, *s32 = nullptr;
+  float2 *mat32 = nullptr, *s32 = nullptr, *v32 = nullptr, *y32 = nullptr;
   // Krylov
   int m = 30;
   double *V = nullptr, *Z = nullptr;
@@ -107,6 +107,7 @@ struct nc_problem {
   int stage = 0;         // 0 created, 1 design set, 2 state solved, 3 adjoint solved
   bool start_zero = true; // the Newton start is the zero state (its residual is R0)
   bool first_setup = true; // next multigrid set-up is the first of this solve call
+  bool mg_ready = false;   // a hierarchy from this state solve exists (reused by the adjoint)
   bool have_R0 = false;   // R0 = R(0) with the full source: minus the SUPG-weighted source load,
   double* R0 = nullptr;   // which does not depend on the design (u = 0, N* = N at s = 0)
   double ref_norm = 0.0; // ||R_free(0)|| with the full source
@@ -115,7 +116,7 @@ struct nc_problem {
   Counters total;     // since creation
   // per-launch event timing of kernel classes (nc_set_profiling)
   struct Pending { int cls; cudaEvent_t a, b; double bytes, flops; };
-  bool prof_on = false;
+  int prof_mask = 0;
   std::vector<cudaEvent_t> evpool;
   std::vector<Pending> pending;
   double prof_ms[NC_PROF_NCLASSES] = {0};
@@ -187,7 +188,7 @@ struct ProfScope {
   cudaEvent_t a = nullptr;
   double bytes0, flops0;
   ProfScope(nc_problem* p, int c) : pb(p), cls(c), bytes0(p->cnt.bytes), flops0(p->cnt.flops) {
-    if (pb->prof_on && (a = prof_event(pb))) cudaEventRecord(a, pb->st);
+    if (((pb->prof_mask >> cls) & 1) && (a = prof_event(pb))) cudaEventRecord(a, pb->st);
   }
   ~ProfScope() {
     if (!a) return;
@@ -306,12 +307,16 @@ nc_status residual(nc_problem* pb, const double2* s, double* R, double* phi) {
   return NC_OK;
 }
 
-// Outer Krylov operator: J(s) or J(s)^T, FP64 or FP32 arithmetic.
+// Outer Krylov operator: J(s) or J(s)^T, FP64 or FP32 arithmetic. The FP32 product casts x to
+// FP32, applies the same matrix-free kernel as the multigrid's finest level (FP32 state copy s32)
+// and casts the result back.
 nc_status outer_op(nc_problem* pb, bool transpose, bool fp32, const double* x, double* y) {
   const Grid& g = pb->g;
   if (fp32) {
-    if (transpose) PCK(NC_PROF_OUTER_OP32, launch_jtv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)x, y, pb->st, &pb->cnt));
-    else PCK(NC_PROF_OUTER_OP32, launch_jv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)x, y, pb->st, &pb->cnt));
+    PCK(NC_PROF_OUTER_OP32, launch_cast_d2f((float*)pb->v32, x, 2 * g.nn, pb->st, &pb->cnt));
+    PCK(NC_PROF_OUTER_OP32, launch_level0_apply<float>(g, pb->ph, pb->s32, pb->mat32, pb->v32, pb->y32, transpose,
+                                                       pb->st, &pb->cnt));
+    PCK(NC_PROF_OUTER_OP32, launch_cast_f2d(y, (const float*)pb->y32, 2 * g.nn, pb->st, &pb->cnt));
   } else {
     if (transpose) PCK(NC_PROF_OUTER_OP64, launch_jtv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, pb->st, &pb->cnt));
     else PCK(NC_PROF_OUTER_OP64, launch_jv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, pb->st, &pb->cnt));
@@ -413,7 +418,8 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
       CKS(level_apply<R>(pb, l, tr, d.x, d.y));
       PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.xn, om, tr, false, pb->st, &pb->cnt));
     } else {
-      PCK(NC_PROF_MG_STENCIL, launch_stencil_apply<R>(d.g, d.S, d.x, d.b, d.dinv, om, d.xn, tr, 2, pb->st, &pb->cnt));
+      PCK(l == 1 ? NC_PROF_MG_STENCIL_L1 : NC_PROF_MG_STENCIL,
+          launch_stencil_apply<R>(d.g, d.S, d.x, d.b, d.dinv, om, d.xn, tr, 2, pb->st, &pb->cnt));
     }
     std::swap(d.x, d.xn);
     return NC_OK;
@@ -424,7 +430,8 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
     CKS(level_apply<R>(pb, l, tr, d.x, d.y));
     PCK(NC_PROF_SMOOTH, launch_sub<R>(d.g, d.b, d.y, d.xn, pb->st, &pb->cnt));
   } else {
-    PCK(NC_PROF_MG_STENCIL, launch_stencil_apply<R>(d.g, d.S, d.x, d.b, d.dinv, om, d.xn, tr, 1, pb->st, &pb->cnt));
+    PCK(l == 1 ? NC_PROF_MG_STENCIL_L1 : NC_PROF_MG_STENCIL,
+        launch_stencil_apply<R>(d.g, d.S, d.x, d.b, d.dinv, om, d.xn, tr, 1, pb->st, &pb->cnt));
   }
   MGLevelDev<R>& c = mg.lev[l + 1];
   PCK(NC_PROF_SMOOTH, launch_restrict<R>(d.g, c.g, d.xn, c.b, pb->st, &pb->cnt));
@@ -494,18 +501,29 @@ nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x,
         // CGS2 with coefficients kept on the device; one host synchronisation per iteration
         double* d1 = pb->dres;
         double* d2 = pb->dres + 66;
-        PCK(NC_PROF_KRYLOV_VEC, launch_multidot(V, n, j + 1, wv, n, pb->part, d1, pb->st, &pb->cnt));
-        PCK(NC_PROF_KRYLOV_VEC, launch_cgs_update_dots(wv, V, n, j + 1, d1, n, pb->part, d2, pb->st, &pb->cnt));
-        PCK(NC_PROF_KRYLOV_VEC, launch_cgs_finish(wv, V, n, j + 1, d2, n, pb->st, &pb->cnt));
+        // d1: V_i . w (i <= j) and w . w (w is V_{j+1}); d2: second-pass dots when re-orthogonalising
+        PCK(NC_PROF_KRYLOV_VEC, launch_multidot(V, n, j + 2, wv, n, pb->part, d1, pb->st, &pb->cnt));
+        PCK(NC_PROF_KRYLOV_VEC, launch_cgs(wv, V, n, j + 1, d1, d2, n, pb->part, pb->st, &pb->cnt));
         CK(cudaMemcpyAsync(pb->hres, pb->dres, sizeof(double) * 132, cudaMemcpyDeviceToHost, pb->st));
         CKS(sync(pb, "Gram-Schmidt"));
-        double corr = 0.0;
-        for (int i = 0; i <= j; ++i) {
-          const double c2 = pb->hres[66 + i];
-          h[i] = pb->hres[i] + c2;
-          corr += c2 * c2;
+        // the device's test (DGKS on the Pythagorean norm) repeated on the same values
+        double s1 = 0.0;
+        for (int i = 0; i <= j; ++i) s1 += pb->hres[i] * pb->hres[i];
+        const double ww = pb->hres[j + 1];
+        const bool fast = ww - s1 >= 0.5 * ww;
+        double hn2;
+        if (fast) {
+          for (int i = 0; i <= j; ++i) h[i] = pb->hres[i];
+          hn2 = ww - s1;
+        } else {
+          double corr = 0.0;
+          for (int i = 0; i <= j; ++i) {
+            const double c2 = pb->hres[66 + i];
+            h[i] = pb->hres[i] + c2;
+            corr += c2 * c2;
+          }
+          hn2 = pb->hres[66 + j + 1] - corr;
         }
-        const double hn2 = pb->hres[66 + j + 1] - corr;
         if (!std::isfinite(hn2)) return fail(pb, NC_ERR_NAN, "non-finite Krylov vector");
         hn = hn2 > 0.0 ? std::sqrt(hn2) : 0.0;
       } else {
@@ -655,10 +673,12 @@ nc_status newton(nc_problem* pb, double rtol, double ref, nc_stats* stats, bool*
       eta = std::min(eta, pb->par.krylov_rtol);
     }
     eta = std::max(eta, 0.5 * rtol / rel);
-    eta = std::max(std::min(eta, pb->par.krylov_rtol), 1e-12);
+    const double eta_min = pb->par.krylov_eta_min > 0 ? pb->par.krylov_eta_min : 1e-12;
+    eta = std::max(std::min(eta, pb->par.krylov_rtol), eta_min);
     double t0 = now_s();
     CKS(mg_setup_any(pb, pb->first_setup));
     pb->first_setup = false;
+    pb->mg_ready = true;
     double t1 = now_s();
     PCK(NC_PROF_OTHER, launch_scale_copy(pb->rhs, pb->R, -1.0, n, pb->st, &pb->cnt));
     PCK(NC_PROF_OTHER, launch_zero_dirichlet(pb->g, pb->rhs, pb->st, &pb->cnt));
@@ -757,9 +777,9 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
   b += 4 * al(16 * nn);                 // s, s_try, lam, s_start
   b += 6 * al(16 * nn);                 // R, R_try, dx, w, rhs, R0
   b += 3 * al(8 * ne) + al(24 * ne);    // rho, gamma_t, gsens, u
-  b += 2 * al(16 * ne) + al(8 * ne) + al(8 * nn);   // mat, dmat, mat32, s32
+  b += 2 * al(16 * ne) + al(8 * ne) + 3 * al(8 * nn);   // mat, dmat, mat32, s32, v32, y32
   b += al(16 * nn * (m + 1)) + al(16 * nn * m);     // V, Z
-  b += al(8 * 66 * 608) + al(8 * 132);
+  b += al(8 * 66 * kReduceBlocksMax) + al(8 * 132);
   b += 5 * al(8 * nn) + 5 * al(4 * nn); // filter vectors
   const size_t rs = p->precision == NC_PREC_FP64 ? 8 : 4;
   for (size_t l = 0; l < lv.g.size(); ++l) {
@@ -878,6 +898,8 @@ nc_status nc_default_params(nc_params* p) {
   p->timeout_s = 600.0;
   p->adjoint_rtol = 0.0;
   p->coarse_refactor = 0;
+  p->krylov_eta_min = 0.0;
+  p->adjoint_eta_first = 0.0;
   return NC_OK;
 }
 
@@ -918,8 +940,9 @@ nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream,
   A(dalloc(pb, &pb->w, 2 * nn)); A(dalloc(pb, &pb->rhs, 2 * nn)); A(dalloc(pb, &pb->R0, 2 * nn));
   A(dalloc(pb, &pb->rho, ne)); A(dalloc(pb, &pb->gamma_t, ne)); A(dalloc(pb, &pb->gsens, ne)); A(dalloc(pb, &pb->u, 3 * ne));
   A(dalloc(pb, &pb->mat, ne)); A(dalloc(pb, &pb->dmat, ne)); A(dalloc(pb, &pb->mat32, ne)); A(dalloc(pb, &pb->s32, nn));
+  A(dalloc(pb, &pb->v32, nn)); A(dalloc(pb, &pb->y32, nn));
   A(dalloc(pb, &pb->V, (size_t)2 * nn * (pb->m + 1))); A(dalloc(pb, &pb->Z, (size_t)2 * nn * pb->m));
-  A(dalloc(pb, &pb->part, 66 * 608)); A(dalloc(pb, &pb->dres, 132));
+  A(dalloc(pb, &pb->part, 66 * kReduceBlocksMax)); A(dalloc(pb, &pb->dres, 132));
   A(dalloc(pb, &pb->fx, nn)); A(dalloc(pb, &pb->fb, nn)); A(dalloc(pb, &pb->fr, nn));
   A(dalloc(pb, &pb->fq, nn)); A(dalloc(pb, &pb->fdinv, nn));
   A(dalloc(pb, &pb->fxf, nn)); A(dalloc(pb, &pb->frf, nn)); A(dalloc(pb, &pb->fd0, nn)); A(dalloc(pb, &pb->fd1, nn));
@@ -1034,6 +1057,7 @@ nc_status nc_solve_state(nc_problem* pb, nc_stats* stats) {
   CK(cudaMemcpyAsync(pb->s, pb->s_start, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, pb->st));
   set_q_scale(pb, 1.0);
   pb->first_setup = true;
+  pb->mg_ready = false;
   bool failed = false;
   nc_status s = newton(pb, pb->par.newton_rtol, pb->ref_norm, stats, &failed, pb->start_zero);
   if (s == NC_OK && failed) {
@@ -1085,8 +1109,17 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
   const Grid& g = pb->g;
   const long long n = 2 * g.nn;
   set_q_scale(pb, 1.0);
+  // The multigrid hierarchy of the last Newton step (built at the iterate before the converged
+  // state) preconditions the transposed system; only the FP32 state copy of the Krylov operator is
+  // refreshed. A hierarchy is built here if none exists for this state (e.g. a warm start that was
+  // already converged).
   double t0 = now_s();
-  CKS(mg_setup_any(pb, true));
+  if (pb->mg_ready) {
+    if (pb->par.precision != NC_PREC_FP64)
+      PCK(NC_PROF_MG_COARSE_SETUP, launch_cast_d2f((float*)pb->s32, (const double*)pb->s, 2 * g.nn, pb->st, &pb->cnt));
+  } else {
+    CKS(mg_setup_any(pb, true));
+  }
   if (stats) stats->t_setup_ms += 1e3 * (now_s() - t0);
   double bb;
   CKS(norm2_free(pb, pb->rhs, &bb));
@@ -1118,8 +1151,16 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
     CKS(check_timeout(pb));
     int its;
     double lres;
-    // FP32 inner solves: 1e-5 per refinement pass (two passes reach 1e-10); FP64: one pass
-    const double eta = fp32 ? std::max(1e-5, 0.5 * kAdjointRtol / rel) : std::max(0.5 * kAdjointRtol / rel, 1e-12);
+    // FP32 inner solves: 1e-5 per refinement pass (the first pass reaches a true reduction of about
+    // 1e-3 and prepares the second, which then reaches 1e-8); FP64: one pass to the tolerance
+    double eta;
+    if (fp32) {
+      const double first = pb->par.adjoint_eta_first > 0 ? pb->par.adjoint_eta_first : 1e-5;
+      eta = pass == 0 ? first : std::max(1e-5, 0.5 * kAdjointRtol / rel);
+    } else {
+      eta = std::max(0.5 * kAdjointRtol / rel, 1e-12);
+      if (pass == 0 && pb->par.adjoint_eta_first > 0) eta = pb->par.adjoint_eta_first;
+    }
     double t1 = now_s();
     CKS(fgmres(pb, true, fp32, pb->w, pb->dx, std::min(eta, 1e-1), pb->par.krylov_maxit, &its, &lres));
     if (stats) {
@@ -1214,9 +1255,8 @@ static nc_status apply_generic(nc_problem* pb, const double* s, const double* v,
   CKS(copy_in(pb, pb->w, v, sizeof(double) * n));
   const Grid& g = pb->g;
   if (fp32) {
-    PCK(NC_PROF_MG_COARSE_SETUP, launch_cast_d2f((float*)pb->s32, (const double*)pb->s_try, n, pb->st, &pb->cnt));
-    if (tr) PCK(NC_PROF_OTHER, launch_jtv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
-    else PCK(NC_PROF_OTHER, launch_jv_f32_io64(g, pb->ph, pb->s32, pb->mat32, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
+    PCK(NC_PROF_OTHER, launch_cast_d2f((float*)pb->s32, (const double*)pb->s_try, n, pb->st, &pb->cnt));
+    CKS(outer_op(pb, tr, true, pb->w, pb->R_try));
   } else {
     if (tr) PCK(NC_PROF_OTHER, launch_jtv_f64(g, pb->ph, pb->s_try, pb->mat, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
     else PCK(NC_PROF_OTHER, launch_jv_f64(g, pb->ph, pb->s_try, pb->mat, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
@@ -1234,11 +1274,11 @@ nc_status nc_apply_jacobian_transpose(nc_problem* pb, const double* s, const dou
   return apply_generic(pb, s, w, out, true, false);
 }
 
-nc_status nc_set_profiling(nc_problem* pb, int on) {
+nc_status nc_set_profiling(nc_problem* pb, int class_mask) {
   if (!pb) return NC_ERR_ARG;
   DeviceGuard dg(pb->device);
   CKS(sync(pb, "set_profiling"));
-  pb->prof_on = on != 0;
+  pb->prof_mask = class_mask;
   for (int c = 0; c < NC_PROF_NCLASSES; ++c) {
     pb->prof_ms[c] = 0; pb->prof_n[c] = 0; pb->prof_bytes[c] = 0; pb->prof_flops[c] = 0;
   }

@@ -78,6 +78,22 @@ inline Launch3 launch_nodes(const Grid& g) {
   L.grid = dim3((unsigned)((g.NX + 31) / 32), (unsigned)((g.NY + 3) / 4), (unsigned)g.NZ);
   return L;
 }
+// Flat launch over the nodes of one z-plane per blockIdx.y (no idle lanes when NX is not a multiple
+// of the block width): blockIdx.x * blockDim.x + threadIdx.x indexes the NX * NY nodes of plane
+// k = blockIdx.y.
+inline Launch3 launch_nodes_flat(const Grid& g, int threads = 128) {
+  Launch3 L;
+  L.block = dim3(threads, 1, 1);
+  L.grid = dim3((unsigned)((g.NXY + threads - 1) / threads), (unsigned)g.NZ, 1);
+  return L;
+}
+#define NC_NODE_FLAT(g)                                                      \
+  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;                    \
+  if (pidx >= (g).NXY) return;                                               \
+  const int k = blockIdx.y;                                                  \
+  const int j = pidx / (g).NX;                                               \
+  const int i = pidx - j * (g).NX;
+
 #define NC_IJK_3D()                                   \
   const int i = blockIdx.x * 32 + threadIdx.x;        \
   const int j = blockIdx.y * 4 + threadIdx.y;         \

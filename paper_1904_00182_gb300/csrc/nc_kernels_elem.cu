@@ -160,17 +160,9 @@ cudaError_t launch_jv_f64(const Grid& g, const Phys& ph, const double2* s, const
                           const double2* v, double* out, cudaStream_t st, Counters* c) {
   return jprod<double, double2, false>(g, ph, s, mat, v, out, st, c);
 }
-cudaError_t launch_jv_f32_io64(const Grid& g, const Phys& ph, const float2* s32, const float2* mat32,
-                               const double2* v, double* out, cudaStream_t st, Counters* c) {
-  return jprod<float, float2, false>(g, ph, s32, mat32, v, out, st, c);
-}
 cudaError_t launch_jtv_f64(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
                            const double2* w, double* out, cudaStream_t st, Counters* c) {
   return jprod<double, double2, true>(g, ph, s, mat, w, out, st, c);
-}
-cudaError_t launch_jtv_f32_io64(const Grid& g, const Phys& ph, const float2* s32, const float2* mat32,
-                                const double2* w, double* out, cudaStream_t st, Counters* c) {
-  return jprod<float, float2, true>(g, ph, s32, mat32, w, out, st, c);
 }
 
 cudaError_t launch_sens_elem(const Grid& g, const Phys& ph, const double2* s, const double2* lam,

@@ -242,9 +242,12 @@ __global__ void k_sub(long long nn, const typename Vec2<R>::type* __restrict__ b
 template <typename R>
 __global__ void k_restrict(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ rf,
                            typename Vec2<R>::type* __restrict__ bc) {
-  const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 4 + threadIdx.y, K = blockIdx.z;
-  if (I >= gc.NX || J >= gc.NY) return;
-  const int n = I + gc.NX * J + gc.NXY * K;
+  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pidx >= gc.NXY) return;
+  const int K = blockIdx.y;
+  const int J = pidx / gc.NX;
+  const int I = pidx - J * gc.NX;
+  const int n = pidx + gc.NXY * K;
   R a0 = R(0), a1 = R(0);
   if (K < gc.nz) {
 #pragma unroll
@@ -276,9 +279,9 @@ __global__ void k_restrict(Grid gf, Grid gc, const typename Vec2<R>::type* __res
 template <typename R>
 __global__ void k_prolong_add(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ xc,
                               typename Vec2<R>::type* __restrict__ xf) {
-  NC_IJK_3D();
-  if (i >= gf.NX || j >= gf.NY || k == gf.nz) return;
-  const int n = i + gf.NX * j + gf.NXY * k;
+  NC_NODE_FLAT(gf);
+  if (k == gf.nz) return;
+  const int n = pidx + gf.NXY * k;
   const int ci = i >> 1, cj = j >> 1, ck = k >> 1;
   const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
   const R wi = (i & 1) ? R(0.5) : R(1), wj = (j & 1) ? R(0.5) : R(1), wk = (k & 1) ? R(0.5) : R(1);
@@ -383,9 +386,8 @@ __global__ void __launch_bounds__(128) k_stencil_apply(Grid g, const R* __restri
                                                        const typename Vec2<R>::type* __restrict__ b,
                                                        const R* __restrict__ dinv, R omega,
                                                        typename Vec2<R>::type* __restrict__ out) {
-  NC_IJK_3D();
-  if (i >= g.NX || j >= g.NY) return;
-  const int n = i + g.NX * j + g.NXY * k;
+  NC_NODE_FLAT(g);
+  const int n = pidx + g.NXY * k;
   if (k == g.nz) { out[n] = mk2<R>(R(0), R(0)); return; }
   const int nn = (int)g.nn;
   R y0 = R(0), y1 = R(0);
@@ -698,7 +700,7 @@ cudaError_t launch_sub(const Grid& g, const typename Vec2<R>::type* b, const typ
 template <typename R>
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* rf,
                             typename Vec2<R>::type* bc, cudaStream_t st, Counters* c) {
-  const Launch3 L = launch_nodes(gc);
+  const Launch3 L = launch_nodes_flat(gc);
   k_restrict<R><<<L.grid, L.block, 0, st>>>(gf, gc, rf, bc);
   if (c) { c->launches += 1; c->bytes += sizeof(R) * 2.0 * (gf.nn + gc.nn); }
   return cudaGetLastError();
@@ -707,7 +709,7 @@ cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const typename Vec2<
 template <typename R>
 cudaError_t launch_prolong_add(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* xc,
                                typename Vec2<R>::type* xf, cudaStream_t st, Counters* c) {
-  const Launch3 L = launch_nodes(gf);
+  const Launch3 L = launch_nodes_flat(gf);
   k_prolong_add<R><<<L.grid, L.block, 0, st>>>(gf, gc, xc, xf);
   if (c) { c->launches += 1; c->bytes += sizeof(R) * 2.0 * (2.0 * gf.nn + gc.nn); }
   return cudaGetLastError();
@@ -754,7 +756,7 @@ cudaError_t launch_stencil_apply(const Grid& g, const R* S, const typename Vec2<
                                  const typename Vec2<R>::type* b, const R* dinv, R omega,
                                  typename Vec2<R>::type* out, bool transpose, int mode, cudaStream_t st,
                                  Counters* c) {
-  const Launch3 L = launch_nodes(g);
+  const Launch3 L = launch_nodes_flat(g);
 #define NC_ST(TRV, MV) k_stencil_apply<R, TRV, MV><<<L.grid, L.block, 0, st>>>(g, S, x, b, dinv, omega, out)
   if (transpose) {
     if (mode == 0) NC_ST(true, 0); else if (mode == 1) NC_ST(true, 1); else NC_ST(true, 2);

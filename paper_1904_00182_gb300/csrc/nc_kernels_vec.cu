@@ -9,7 +9,7 @@ namespace nc {
 namespace {
 
 const int kRedThreads = 256;
-const int kRedBlocksMax = 608;   // 4 x 152 SMs
+const int kRedBlocksMax = kReduceBlocksMax;
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
 #pragma unroll
@@ -61,21 +61,49 @@ __global__ void k_sum_parts(const double* __restrict__ part, int nb, int nvec, d
   if (threadIdx.x == 0) res[i] = s;
 }
 
-// Fused classical Gram-Schmidt pass: w <- w - sum_i c_i V_i with c read from device memory, then
-// part holds the partial sums of V_i . w (i < nvec) and of w . w (index nvec), per block.
-// NV >= nvec is the register tile (one V value per vector per element).
+// Gram-Schmidt step after the first-pass dots d1 = (V_i . w for i < nvec, w . w at index nvec).
+// With s = sum_i d1_i^2, the Pythagorean norm ww - s of the projected vector is accurate unless the
+// projection removed most of w. If ww - s >= ww / 2 (the Daniel-Gragg-Kaufman-Stewart test) the
+// pass writes the normalised vector (w - V d1) / sqrt(ww - s) and computes nothing else; otherwise
+// it writes w - V d1 and the partial sums of the second-pass dots (V_i . w', w' . w') for a
+// re-orthogonalisation. The test reads the same device values in every kernel and on the host.
+__device__ __forceinline__ bool cgs_fast(const double* __restrict__ d1, int nvec, double* s_out, double* ww_out) {
+  double s = 0.0;
+  for (int i = 0; i < nvec; ++i) s += d1[i] * d1[i];
+  const double ww = d1[nvec];
+  *s_out = s;
+  *ww_out = ww;
+  return ww - s >= 0.5 * ww;
+}
+
 template <int NV>
-__global__ void __launch_bounds__(256) k_cgs_update_dots(double* __restrict__ w, const double* __restrict__ V,
-                                                         long long ld, int nvec, const double* __restrict__ c,
-                                                         long long n, double* __restrict__ part) {
+__global__ void __launch_bounds__(256) k_cgs_update(double* __restrict__ w, const double* __restrict__ V, long long ld,
+                                                    int nvec, const double* __restrict__ d1, long long n,
+                                                    double* __restrict__ part) {
   __shared__ double sh[32];
-  double cc[NV], acc[NV];
+  double sum2, ww;
+  const bool fast = cgs_fast(d1, nvec, &sum2, &ww);
+  double cc[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) { cc[i] = i < nvec ? c[i] : 0.0; acc[i] = 0.0; }
-  double accw = 0.0;
+  for (int i = 0; i < NV; ++i) cc[i] = i < nvec ? d1[i] : 0.0;
   const long long seg = (n + gridDim.x - 1) / gridDim.x;
   const long long lo = seg * blockIdx.x;
   const long long hi = min(n, lo + seg);
+  if (fast) {
+    const double inv = 1.0 / sqrt(ww - sum2);
+    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+      double x = w[t];
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (i < nvec) x -= cc[i] * V[(long long)i * ld + t];
+      w[t] = x * inv;
+    }
+    return;
+  }
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  double accw = 0.0;
   for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
     double v[NV];
     double x = w[t];
@@ -99,19 +127,34 @@ __global__ void __launch_bounds__(256) k_cgs_update_dots(double* __restrict__ w,
   if (threadIdx.x == 0) part[(long long)nvec * gridDim.x + blockIdx.x] = r;
 }
 
-// Second Gram-Schmidt correction and normalisation: w <- (w - sum_i c_i V_i) / sqrt(ww - sum c_i^2),
-// with c = res[0..nvec) and ww = res[nvec] from k_cgs_update_dots (device memory).
+// Sum of the second-pass partials (re-orthogonalisation only).
+__global__ void k_cgs_sum(const double* __restrict__ part, int nb, int nvec, const double* __restrict__ d1,
+                          double* __restrict__ d2) {
+  double s, ww;
+  if (cgs_fast(d1, nvec, &s, &ww)) return;
+  __shared__ double sh[32];
+  const int i = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[(long long)i * nb + b];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) d2[i] = acc;
+}
+
+// Re-orthogonalisation: w <- (w - sum_i d2_i V_i) / sqrt(d2[nvec] - sum d2_i^2) (only if the test failed).
 template <int NV>
-__global__ void __launch_bounds__(256) k_cgs_finish(double* __restrict__ w, const double* __restrict__ V, long long ld,
-                                                    int nvec, const double* __restrict__ res, long long n) {
+__global__ void __launch_bounds__(256) k_cgs_reorth(double* __restrict__ w, const double* __restrict__ V, long long ld,
+                                                    int nvec, const double* __restrict__ d1,
+                                                    const double* __restrict__ d2, long long n) {
+  double s1, ww1;
+  if (cgs_fast(d1, nvec, &s1, &ww1)) return;
   double cc[NV];
   double corr = 0.0;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    cc[i] = i < nvec ? res[i] : 0.0;
+    cc[i] = i < nvec ? d2[i] : 0.0;
     corr += cc[i] * cc[i];
   }
-  const double h2 = res[nvec] - corr;
+  const double h2 = d2[nvec] - corr;
   const double inv = h2 > 0.0 ? 1.0 / sqrt(h2) : 0.0;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     double x = w[t];
@@ -256,9 +299,8 @@ __device__ __forceinline__ R helm_node(const Grid& g, const FC& F, const R* __re
 
 template <typename R, typename FC>
 __global__ void k_helmholtz(Grid g, FC F, const R* __restrict__ x, R* __restrict__ y) {
-  NC_IJK_3D();
-  if (i >= g.NX || j >= g.NY) return;
-  const int n = i + g.NX * j + g.NXY * k;
+  NC_NODE_FLAT(g);
+  const int n = pidx + g.NXY * k;
   y[n] = helm_node<R>(g, F, x, i, j, k, n);
 }
 
@@ -272,9 +314,8 @@ __global__ void k_cheb_init(long long nn, const float* __restrict__ dinv, const 
 
 __global__ void k_cheb_step(Grid g, FilterConstF F, const float* __restrict__ dinv, const float* __restrict__ d,
                             float* __restrict__ dn, float* __restrict__ x, float* __restrict__ r, float c1, float c2) {
-  NC_IJK_3D();
-  if (i >= g.NX || j >= g.NY) return;
-  const int n = i + g.NX * j + g.NXY * k;
+  NC_NODE_FLAT(g);
+  const int n = pidx + g.NXY * k;
   const float q = helm_node<float>(g, F, d, i, j, k, n);
   const float dv = d[n];
   x[n] += dv;
@@ -370,7 +411,7 @@ cudaError_t launch_multidot(const double* V, long long ld, int nvec, const doubl
   else if (nvec <= 32) k_multidot_part<32><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
   else k_multidot_part<66><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
   k_sum_parts<<<nvec, 256, 0, st>>>(part, nb, nvec, res);
-  if (c) { c->launches += 2; c->bytes += 8.0 * n * (nvec + 1); }
+  if (c) { c->launches += 2; c->bytes += 8.0 * n * (nvec + 1); c->flops += 2.0 * n * nvec; }
   return cudaGetLastError();
 }
 
@@ -384,32 +425,23 @@ cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_cgs_update_dots(double* w, const double* V, long long ld, int nvec, const double* c, long long n,
-                                   double* part, double* res, cudaStream_t st, Counters* cnt) {
+cudaError_t launch_cgs(double* w, const double* V, long long ld, int nvec, const double* d1, double* d2, long long n,
+                      double* part, cudaStream_t st, Counters* cnt) {
   const int nb = reduce_blocks(n);
-#define NC_CGS1(NV) k_cgs_update_dots<NV><<<nb, kRedThreads, 0, st>>>(w, V, ld, nvec, c, n, part)
-  if (nvec <= 4) NC_CGS1(4);
-  else if (nvec <= 8) NC_CGS1(8);
-  else if (nvec <= 16) NC_CGS1(16);
-  else if (nvec <= 32) NC_CGS1(32);
+  const unsigned ns = stream_blocks(n);
+#define NC_CGS(NV)                                                                     \
+  do {                                                                                 \
+    k_cgs_update<NV><<<nb, kRedThreads, 0, st>>>(w, V, ld, nvec, d1, n, part);        \
+    k_cgs_sum<<<nvec + 1, 256, 0, st>>>(part, nb, nvec, d1, d2);                       \
+    k_cgs_reorth<NV><<<ns, 256, 0, st>>>(w, V, ld, nvec, d1, d2, n);                   \
+  } while (0)
+  if (nvec <= 4) NC_CGS(4);
+  else if (nvec <= 8) NC_CGS(8);
+  else if (nvec <= 16) NC_CGS(16);
+  else if (nvec <= 32) NC_CGS(32);
   else return cudaErrorInvalidValue;
-#undef NC_CGS1
-  k_sum_parts<<<nvec + 1, 256, 0, st>>>(part, nb, nvec + 1, res);
-  if (cnt) { cnt->launches += 2; cnt->bytes += 8.0 * n * (nvec + 2); }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cgs_finish(double* w, const double* V, long long ld, int nvec, const double* res, long long n,
-                              cudaStream_t st, Counters* cnt) {
-  const unsigned nb = stream_blocks(n);
-#define NC_CGS2(NV) k_cgs_finish<NV><<<nb, 256, 0, st>>>(w, V, ld, nvec, res, n)
-  if (nvec <= 4) NC_CGS2(4);
-  else if (nvec <= 8) NC_CGS2(8);
-  else if (nvec <= 16) NC_CGS2(16);
-  else if (nvec <= 32) NC_CGS2(32);
-  else return cudaErrorInvalidValue;
-#undef NC_CGS2
-  if (cnt) { cnt->launches += 1; cnt->bytes += 8.0 * n * (nvec + 2); }
+#undef NC_CGS
+  if (cnt) { cnt->launches += 3; cnt->bytes += 8.0 * n * (nvec + 2); cnt->flops += 2.0 * n * nvec; }
   return cudaGetLastError();
 }
 
@@ -477,7 +509,7 @@ cudaError_t launch_filter_rhs(const Grid& g, const double* gamma, int heated_lay
 
 cudaError_t launch_helmholtz(const Grid& g, const FilterConst& F, const double* x, double* y, cudaStream_t st,
                              Counters* c) {
-  const Launch3 L = launch_nodes(g);
+  const Launch3 L = launch_nodes_flat(g);
   k_helmholtz<double, FilterConst><<<L.grid, L.block, 0, st>>>(g, F, x, y);
   if (c) { c->launches += 1; c->bytes += 16.0 * g.nn; }
   return cudaGetLastError();
@@ -485,7 +517,7 @@ cudaError_t launch_helmholtz(const Grid& g, const FilterConst& F, const double* 
 
 cudaError_t launch_helmholtz_f32(const Grid& g, const FilterConstF& F, const float* x, float* y, cudaStream_t st,
                                  Counters* c) {
-  const Launch3 L = launch_nodes(g);
+  const Launch3 L = launch_nodes_flat(g);
   k_helmholtz<float, FilterConstF><<<L.grid, L.block, 0, st>>>(g, F, x, y);
   if (c) { c->launches += 1; c->bytes += 8.0 * g.nn; }
   return cudaGetLastError();
@@ -500,7 +532,7 @@ cudaError_t launch_cheb_init(long long n, const float* dinv, const float* r, flo
 
 cudaError_t launch_cheb_step(const Grid& g, const FilterConstF& F, const float* dinv, const float* d, float* dn,
                              float* x, float* r, float c1, float c2, cudaStream_t st, Counters* c) {
-  const Launch3 L = launch_nodes(g);
+  const Launch3 L = launch_nodes_flat(g);
   k_cheb_step<<<L.grid, L.block, 0, st>>>(g, F, dinv, d, dn, x, r, c1, c2);
   if (c) { c->launches += 1; c->bytes += 32.0 * g.nn; }
   return cudaGetLastError();

@@ -49,14 +49,9 @@ cudaError_t launch_residual(const Grid& g, const Phys& ph, const double2* s, con
 // out = J(s) v (projected: Dirichlet inputs ignored, Dirichlet outputs 0); FP64 arithmetic.
 cudaError_t launch_jv_f64(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
                           const double2* v, double* out, cudaStream_t st, Counters* c);
-// Same product in FP32 arithmetic; s32/mat32 FP32 copies, v and out FP64.
-cudaError_t launch_jv_f32_io64(const Grid& g, const Phys& ph, const float2* s32, const float2* mat32,
-                               const double2* v, double* out, cudaStream_t st, Counters* c);
-// out = J(s)^T w (projected), FP64, and the FP32 variant.
+// out = J(s)^T w (projected), FP64.
 cudaError_t launch_jtv_f64(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
                            const double2* w, double* out, cudaStream_t st, Counters* c);
-cudaError_t launch_jtv_f32_io64(const Grid& g, const Phys& ph, const float2* s32, const float2* mat32,
-                                const double2* w, double* out, cudaStream_t st, Counters* c);
 // d f / d gamma~_e = -(dL/dkappa kappa' + dL/dk k'), 0 on heated elements; dmat: (kappa', k').
 cudaError_t launch_sens_elem(const Grid& g, const Phys& ph, const double2* s, const double2* lam,
                              const double2* mat, const double2* dmat, double* out, cudaStream_t st,
@@ -66,7 +61,9 @@ cudaError_t launch_u_centroid(const Grid& g, const Phys& ph, const double2* s, c
                               double* u, cudaStream_t st, Counters* c);
 
 // ---------------- vector / reduction / design kernels (nc_kernels_vec.cu) ----------------
-// Deterministic reductions: partial sums per block, then a fixed-order final sum.
+// Deterministic reductions: partial sums per block, then a fixed-order final sum. At most
+// kReduceBlocksMax blocks (8 per SM, enough loads in flight to stream vectors at full bandwidth).
+const int kReduceBlocksMax = 1216;
 int reduce_blocks(long long n);
 // res[i] = <V_i, w> for i < nvec, V_i = V + i*ld; n doubles each. part: nvec*reduce_blocks(n).
 cudaError_t launch_multidot(const double* V, long long ld, int nvec, const double* w, long long n,
@@ -74,13 +71,12 @@ cudaError_t launch_multidot(const double* V, long long ld, int nvec, const doubl
 // res[0] = sum over free entries (Dirichlet rows excluded) of a^2, for a state vector.
 cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, double* res,
                               cudaStream_t st, Counters* c);
-// Fused classical Gram-Schmidt (nvec <= 32), coefficients in device memory:
-//   update_dots: w -= sum_i c_i V_i; res[0..nvec) = V^T w, res[nvec] = w . w
-//   finish:      w = (w - sum_i res_i V_i) / sqrt(res[nvec] - sum res_i^2)
-cudaError_t launch_cgs_update_dots(double* w, const double* V, long long ld, int nvec, const double* c, long long n,
-                                   double* part, double* res, cudaStream_t st, Counters* cnt);
-cudaError_t launch_cgs_finish(double* w, const double* V, long long ld, int nvec, const double* res, long long n,
-                              cudaStream_t st, Counters* cnt);
+// Gram-Schmidt step of FGMRES (nvec <= 32) from the first-pass dots d1 (device: V_i . w, then w . w):
+// w <- (w - V d1) / sqrt(ww - |d1|^2) when ww - |d1|^2 >= ww / 2; otherwise classical Gram-Schmidt is
+// applied twice and d2 receives the second-pass dots and ||w'||^2. The branch is taken on the device;
+// the host repeats the same test on the read-back values.
+cudaError_t launch_cgs(double* w, const double* V, long long ld, int nvec, const double* d1, double* d2, long long n,
+                      double* part, cudaStream_t st, Counters* cnt);
 // y += sum_i coef[i] * V_i (nvec <= 64), n doubles.
 cudaError_t launch_axpy_multi(double* y, const double* V, long long ld, int nvec, const double* coef,
                               long long n, cudaStream_t st, Counters* c);

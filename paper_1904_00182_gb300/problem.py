@@ -144,8 +144,15 @@ class Problem:
         return gt, kap, k
 
     # -- measurement ---------------------------------------------------------------------------
-    def set_profiling(self, on=True):
-        self._check(self.lib.nc_set_profiling(self.h, 1 if on else 0))
+    def set_profiling(self, on=True, classes=None):
+        """Time every kernel class (on=True), none (False), or only the named classes."""
+        if classes is not None:
+            mask = 0
+            for c in classes:
+                mask |= 1 << _abi.PROF_CLASSES.index(c)
+        else:
+            mask = -1 if on else 0
+        self._check(self.lib.nc_set_profiling(self.h, mask))
 
     def profile(self):
         """{class: (ms, launches, algorithmic bytes, algorithmic flops)} since set_profiling(True)."""
