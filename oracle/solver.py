@@ -343,7 +343,39 @@ class Problem:
         g[self.heated] = 0.0
         return g
 
-    # ---- sampled residual (large-grid checks) ------------------------------------------------
+    # ---- sampled rows (large-grid checks) -----------------------------------------------------
+    def _elements_around(self, nodes):
+        m = self.mesh
+        ijk = m.node_ijk()[np.asarray(nodes)]
+        elems = set()
+        for (i, j, k) in ijk:
+            for dk in (-1, 0):
+                for dj in (-1, 0):
+                    for di in (-1, 0):
+                        a, b, c = i + di, j + dj, k + dk
+                        if 0 <= a < m.nx and 0 <= b < m.ny and 0 <= c < m.nz:
+                            elems.add(a + m.nx * (b + m.ny * c))
+        return np.array(sorted(elems))
+
+    def jt_at_nodes(self, s, lam, nodes):
+        """(J(s)^T lam) at the given nodes (P and T entries), from the element Jacobians around them.
+        lam is taken as 0 on the Dirichlet rows (the adjoint lives on the free DOFs)."""
+        nodes = np.asarray(nodes)
+        el = self._elements_around(nodes)
+        s2 = s.reshape(-1, 2)
+        l2 = np.where(self.dir_mask, 0.0, lam).reshape(-1, 2)
+        cn = self.conn[el]
+        Qq = np.repeat(self.q_scale * self.Qe[el, None], 8, axis=1)
+        Je = self.em.jacobian(s2[cn, 0], s2[cn, 1], self.kappa[el], self.k[el], Qq)
+        le = np.concatenate([l2[cn, 0], l2[cn, 1]], axis=1)          # (E, 16) row multipliers
+        contrib = np.einsum("er,erc->ec", le, Je)                     # (E, 16) column sums
+        out = np.zeros((len(nodes), 2))
+        for r, nd in enumerate(nodes):
+            hit = cn == nd
+            out[r, 0] = contrib[:, :8][hit].sum()
+            out[r, 1] = contrib[:, 8:][hit].sum()
+        return out
+
     def residual_at_nodes(self, s, nodes):
         """R(s) at the given nodes (P and T rows), from the elements around them only."""
         nodes = np.asarray(nodes)
