@@ -170,6 +170,10 @@ nc_status nc_sensitivities(nc_problem* pb, double* dfdrho);
  * Darcy velocity u (3E values, Eq. finaldarcy, may be NULL). */
 nc_status nc_get_fields(const nc_problem* pb, double* P, double* T, double* u);
 
+/* Copy the adjoint solution lambda out (2N doubles, node-interleaved like a state vector; 0 on
+ * the Dirichlet rows). Requires a solved adjoint. */
+nc_status nc_get_adjoint(const nc_problem* pb, double* lam);
+
 /* Filtered design gamma~, kappa_e and k_e (E values each; any may be NULL). */
 nc_status nc_get_design_fields(const nc_problem* pb, double* gamma_tilde, double* kappa, double* k);
 

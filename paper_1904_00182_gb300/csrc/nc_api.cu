@@ -1215,6 +1215,16 @@ nc_status nc_get_fields(const nc_problem* cpb, double* P, double* T, double* u) 
   return NC_OK;
 }
 
+nc_status nc_get_adjoint(const nc_problem* cpb, double* lam) {
+  nc_problem* pb = const_cast<nc_problem*>(cpb);
+  if (!pb || !lam) return NC_ERR_ARG;
+  if (pb->stage < 3) return fail(pb, NC_ERR_STATE, "no adjoint solution yet");
+  DeviceGuard dg(pb->device);
+  CKS(copy_out(pb, lam, pb->lam, sizeof(double) * 2 * pb->g.nn));
+  CKS(sync(pb, "get_adjoint"));
+  return NC_OK;
+}
+
 nc_status nc_get_design_fields(const nc_problem* cpb, double* gamma_tilde, double* kappa, double* k) {
   nc_problem* pb = const_cast<nc_problem*>(cpb);
   if (!pb) return NC_ERR_ARG;

@@ -138,6 +138,12 @@ class Problem:
         self._check(self.lib.nc_get_fields(self.h, _ptr(P), _ptr(T), _ptr(u)))
         return P, T, (u.view(self.ne, 3) if velocity else None)
 
+    def adjoint(self):
+        """The adjoint solution lambda (2N, node-interleaved)."""
+        lam = self._empty(2 * self.nn)
+        self._check(self.lib.nc_get_adjoint(self.h, _ptr(lam)))
+        return lam
+
     def design_fields(self):
         gt, kap, k = self._empty(self.ne), self._empty(self.ne), self._empty(self.ne)
         self._check(self.lib.nc_get_design_fields(self.h, _ptr(gt), _ptr(kap), _ptr(k)))
