@@ -63,6 +63,26 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, dist, device):
+    """The maximum of a per-rank number over all ranks (the identity on one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_design_seeds(rank, count):
+    """Seeds of the designs one rank solves: every replica works on its own designs (weak scaling)."""
+    return [100 * rank + i for i in range(count)]
+
+
+def whole_job_rate(world, steps, seconds):
+    """Solves per second of the whole job: every rank ran `steps` steps in at most `seconds`."""
+    return world * steps / seconds
+
+
 # ------------------------------------------------------------------------------- clocks ------
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
@@ -264,7 +284,7 @@ def run_gpu(args, rank, world, local):
     n = args.n
     E = n ** 3
     ndes = max(1, min(3, args.steps + args.warmup))
-    designs = [filtered_random(n, n, n, seed=100 * rank + i, volfrac=args.volfrac) for i in range(ndes)]
+    designs = [filtered_random(n, n, n, seed=sd, volfrac=args.volfrac) for sd in replica_design_seeds(rank, ndes)]
     rho_dev = [torch.from_numpy(d).to(dev) for d in designs]
     rho_host = [torch.from_numpy(d).pin_memory() for d in designs]
     grad_dev = torch.empty(E, dtype=torch.float64, device=dev)
@@ -314,13 +334,11 @@ def run_gpu(args, rank, world, local):
     l1, _ = pb.counters()
     prof = pb.profile()
     pb.set_profiling(False)
+    ms = max_over_ranks(ms, dist, dev)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-        ms = float(t.item())
     timed_stats = list(stats_log)
-    value = world * args.steps / (ms * 1e-3)
+    value = whole_job_rate(world, args.steps, ms * 1e-3)
 
     # end to end through the C ABI with host buffers (H2D of the design, D2H of f and the gradient)
     e2e = None
@@ -334,11 +352,8 @@ def run_gpu(args, rank, world, local):
             step(i, host=True)
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([wall], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            wall = float(t.item())
-        e2e = {"value": world * args.steps / wall, "unit": UNIT, "h2d_bytes_per_step": 8 * E,
+        wall = max_over_ranks(wall, dist, dev)
+        e2e = {"value": whole_job_rate(world, args.steps, wall), "unit": UNIT, "h2d_bytes_per_step": 8 * E,
                "d2h_bytes_per_step": 8 * E + 8}
 
     # the all-FP64 path on the same workload, for the mixed-vs-FP64 comparison

@@ -95,7 +95,7 @@ typedef struct {
   int mg_levels;        /* 0: coarsen while every dimension is even [0] */
   int nu_pre, nu_post;  /* smoothing sweeps [2, 2] */
   double omega;         /* damping of the block-Jacobi smoother [0.7] */
-  double filter_rtol;   /* relative tolerance of the filter's conjugate gradients [1e-12] */
+  double filter_rtol;   /* relative residual tolerance of the filter solve [1e-12] */
   double timeout_s;     /* wall-clock limit of one call [600] */
   double adjoint_rtol;  /* adjoint stops at ||df/ds - J^T lambda|| <= adjoint_rtol ||df/ds||;
                            <= 0: the state's newton_rtol [0] */
