@@ -379,17 +379,7 @@ class Problem:
     def residual_at_nodes(self, s, nodes):
         """R(s) at the given nodes (P and T rows), from the elements around them only."""
         nodes = np.asarray(nodes)
-        m = self.mesh
-        ijk = m.node_ijk()[nodes]
-        elems = set()
-        for (i, j, k) in ijk:
-            for dk in (-1, 0):
-                for dj in (-1, 0):
-                    for di in (-1, 0):
-                        a, b, c = i + di, j + dj, k + dk
-                        if 0 <= a < m.nx and 0 <= b < m.ny and 0 <= c < m.nz:
-                            elems.add(a + m.nx * (b + m.ny * c))
-        el = np.array(sorted(elems))
+        el = self._elements_around(nodes)
         s2 = s.reshape(-1, 2)
         cn = self.conn[el]
         Qq = np.repeat(self.q_scale * self.Qe[el, None], 8, axis=1)

@@ -89,7 +89,8 @@ struct nc_problem {
   float2 *mat32 = nullptr, *s32 = nullptr, *v32 = nullptr, *y32 = nullptr;
   // Krylov
   int m = 30;
-  double *V = nullptr, *Z = nullptr;
+  double *V = nullptr, *Z = nullptr;      // FP64 basis (NC_PREC_FP64)
+  float *V32 = nullptr, *Z32 = nullptr;   // FP32 basis (mixed precision)
   double *part = nullptr, *dres = nullptr, *hres = nullptr;
   // filter PCG (node vectors)
   double *fx = nullptr, *fb = nullptr, *fr = nullptr, *fq = nullptr, *fdinv = nullptr;
@@ -242,8 +243,8 @@ nc_status check_timeout(nc_problem* pb) {
 }
 
 // ---------------------------------------------------------------- reductions -------
-nc_status dots(nc_problem* pb, const double* V, long long ld, int nvec, const double* w, long long n,
-               double* out) {
+template <typename T>
+nc_status dots(nc_problem* pb, const T* V, long long ld, int nvec, const T* w, long long n, double* out) {
   PCK(NC_PROF_KRYLOV_VEC, launch_multidot(V, ld, nvec, w, n, pb->part, pb->dres, pb->st, &pb->cnt));
   CK(cudaMemcpyAsync(pb->hres, pb->dres, sizeof(double) * nvec, cudaMemcpyDeviceToHost, pb->st));
   CKS(sync(pb, "dot products"));
@@ -463,14 +464,50 @@ nc_status mg_setup_any(nc_problem* pb, bool refactor) {
 }
 
 // ---------------------------------------------------------------- FGMRES ------------
+// Krylov vectors are FP64 on the FP64 path and FP32 on the mixed-precision path, where the operator
+// (J or J^T on the FP32 state copy) and the preconditioner are FP32 as well; the Hessenberg matrix,
+// the Givens rotations and the update of the FP64 solution are FP64 in both.
+
+// z = M^-1 v for FP32 vectors: the V-cycle reads v in place and leaves its result in z.
+nc_status kry_precondition(nc_problem* pb, bool tr, const float* v, float* z) {
+  MGLevelDev<float>& d = pb->mg32.lev[0];
+  float2* const b0 = d.b;
+  float2* const x0 = d.x;
+  float2* const xn0 = d.xn;
+  d.b = (float2*)v;   // level 0 only reads b
+  d.x = (float2*)z;
+  nc_status s = vcycle<float>(pb, 0, tr);
+  if (s == NC_OK && d.x != (float2*)z)
+    CK(cudaMemcpyAsync(z, d.x, sizeof(float2) * pb->g.nn, cudaMemcpyDeviceToDevice, pb->st));
+  d.b = b0;
+  d.x = x0;
+  d.xn = xn0;
+  return s;
+}
+
+nc_status kry_precondition(nc_problem* pb, bool tr, const double* v, double* z) {
+  return precondition(pb, tr, v, z);
+}
+
+nc_status kry_op(nc_problem* pb, bool tr, const float* z, float* w) {
+  PCK(NC_PROF_OUTER_OP32, launch_level0_apply<float>(pb->g, pb->ph, pb->s32, pb->mat32, (const float2*)z, (float2*)w,
+                                                     tr, pb->st, &pb->cnt));
+  return NC_OK;
+}
+
+nc_status kry_op(nc_problem* pb, bool tr, const double* z, double* w) {
+  return outer_op(pb, tr, false, z, w);
+}
+
 // Right-preconditioned flexible GMRES(m) with classical Gram-Schmidt applied twice. Solves
 // op(x) = b on the free DOFs from x = 0; stops when the (Arnoldi) residual is <= rtol ||b||.
-nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x, double rtol, int maxit,
-                 int* its_out, double* relres_out) {
+// b is not modified (it may be any FP64 work vector other than x and R_try).
+template <typename T>
+nc_status fgmres_t(nc_problem* pb, bool tr, T* V, T* Z, const double* b, double* x, double rtol, int maxit,
+                   int* its_out, double* relres_out) {
   const long long n = 2 * pb->g.nn;
   const int m = pb->m;
-  double* V = pb->V;
-  double* Z = pb->Z;
+  const bool fp32 = sizeof(T) == 4;
   CK(cudaMemsetAsync(x, 0, sizeof(double) * n, pb->st));
   double bb;
   CKS(norm2_free(pb, b, &bb));
@@ -491,11 +528,11 @@ nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x,
     bool done = false;
     for (; j < m && total < maxit; ++j, ++total) {
       CKS(check_timeout(pb));
-      double* vj = V + (long long)j * n;
-      double* zj = Z + (long long)j * n;
-      double* wv = V + (long long)(j + 1) * n;
-      CKS(precondition(pb, tr, vj, zj));
-      CKS(outer_op(pb, tr, fp32, zj, wv));
+      T* vj = V + (long long)j * n;
+      T* zj = Z + (long long)j * n;
+      T* wv = V + (long long)(j + 1) * n;
+      CKS(kry_precondition(pb, tr, vj, zj));
+      CKS(kry_op(pb, tr, zj, wv));
       double hn;
       if (j + 1 <= 32) {
         // CGS2 with coefficients kept on the device; one host synchronisation per iteration
@@ -538,7 +575,7 @@ nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x,
         double hn2 = ww - corr;
         if (!std::isfinite(hn2)) return fail(pb, NC_ERR_NAN, "non-finite Krylov vector");
         hn = hn2 > 0.0 ? std::sqrt(hn2) : 0.0;
-        if (hn > 0.0) PCK(NC_PROF_KRYLOV_VEC, launch_scale_copy(wv, wv, 1.0 / hn, n, pb->st, &pb->cnt));
+        if (hn > 0.0) PCK(NC_PROF_KRYLOV_VEC, launch_scale(wv, 1.0 / hn, n, pb->st, &pb->cnt));
       }
       for (int i = 0; i <= j; ++i) H[i * m + j] = h[i];
       H[(j + 1) * m + j] = hn;
@@ -569,19 +606,26 @@ nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x,
     *its_out = total;
     if (done) return NC_OK;
     if (total >= maxit) return NC_OK;   // caller judges the reached residual
-    // restart with the true residual r = b - op(x)
-    double* r = V;
-    CKS(outer_op(pb, tr, fp32, x, pb->w));
-    CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
-    PCK(NC_PROF_KRYLOV_VEC, launch_axpby(r, pb->w, -1.0, 1.0, n, pb->st, &pb->cnt));
+    // restart with the residual r = b - op(x) (op in the path's Krylov precision), in R_try
+    double* r = pb->R_try;
+    CKS(outer_op(pb, tr, fp32, x, r));
+    PCK(NC_PROF_KRYLOV_VEC, launch_axpby(r, b, 1.0, -1.0, n, pb->st, &pb->cnt));
     PCK(NC_PROF_KRYLOV_VEC, launch_zero_dirichlet(pb->g, r, pb->st, &pb->cnt));
     double rr;
     CKS(norm2_free(pb, r, &rr));
     beta = std::sqrt(rr);
     *relres_out = beta / bnorm;
     if (beta <= rtol * bnorm) return NC_OK;
-    PCK(NC_PROF_KRYLOV_VEC, launch_scale_copy(r, r, 1.0 / beta, n, pb->st, &pb->cnt));
+    PCK(NC_PROF_KRYLOV_VEC, launch_scale_copy(V, r, 1.0 / beta, n, pb->st, &pb->cnt));
   }
+}
+
+// FGMRES on the FP64 path (fp32 false) or the mixed-precision path (fp32 true).
+nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x, double rtol, int maxit,
+                 int* its_out, double* relres_out) {
+  if (fp32 != (pb->par.precision != NC_PREC_FP64)) return fail(pb, NC_ERR_ARG, "Krylov precision mismatch");
+  if (fp32) return fgmres_t<float>(pb, tr, pb->V32, pb->Z32, b, x, rtol, maxit, its_out, relres_out);
+  return fgmres_t<double>(pb, tr, pb->V, pb->Z, b, x, rtol, maxit, its_out, relres_out);
 }
 
 // ---------------------------------------------------------------- Newton ------------
@@ -778,7 +822,8 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
   b += 6 * al(16 * nn);                 // R, R_try, dx, w, rhs, R0
   b += 3 * al(8 * ne) + al(24 * ne);    // rho, gamma_t, gsens, u
   b += 2 * al(16 * ne) + al(8 * ne) + 3 * al(8 * nn);   // mat, dmat, mat32, s32, v32, y32
-  b += al(16 * nn * (m + 1)) + al(16 * nn * m);     // V, Z
+  const size_t ks = p->precision == NC_PREC_FP64 ? 8 : 4;   // Krylov basis entry size
+  b += al(2 * ks * nn * (m + 1)) + al(2 * ks * nn * m);     // V, Z
   b += al(8 * 66 * kReduceBlocksMax) + al(8 * 132);
   b += 5 * al(8 * nn) + 5 * al(4 * nn); // filter vectors
   const size_t rs = p->precision == NC_PREC_FP64 ? 8 : 4;
@@ -941,7 +986,11 @@ nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream,
   A(dalloc(pb, &pb->rho, ne)); A(dalloc(pb, &pb->gamma_t, ne)); A(dalloc(pb, &pb->gsens, ne)); A(dalloc(pb, &pb->u, 3 * ne));
   A(dalloc(pb, &pb->mat, ne)); A(dalloc(pb, &pb->dmat, ne)); A(dalloc(pb, &pb->mat32, ne)); A(dalloc(pb, &pb->s32, nn));
   A(dalloc(pb, &pb->v32, nn)); A(dalloc(pb, &pb->y32, nn));
-  A(dalloc(pb, &pb->V, (size_t)2 * nn * (pb->m + 1))); A(dalloc(pb, &pb->Z, (size_t)2 * nn * pb->m));
+  if (p->precision == NC_PREC_FP64) {
+    A(dalloc(pb, &pb->V, (size_t)2 * nn * (pb->m + 1))); A(dalloc(pb, &pb->Z, (size_t)2 * nn * pb->m));
+  } else {
+    A(dalloc(pb, &pb->V32, (size_t)2 * nn * (pb->m + 1))); A(dalloc(pb, &pb->Z32, (size_t)2 * nn * pb->m));
+  }
   A(dalloc(pb, &pb->part, 66 * kReduceBlocksMax)); A(dalloc(pb, &pb->dres, 132));
   A(dalloc(pb, &pb->fx, nn)); A(dalloc(pb, &pb->fb, nn)); A(dalloc(pb, &pb->fr, nn));
   A(dalloc(pb, &pb->fq, nn)); A(dalloc(pb, &pb->fdinv, nn));
@@ -1151,12 +1200,14 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
     CKS(check_timeout(pb));
     int its;
     double lres;
-    // FP32 inner solves: 1e-5 per refinement pass (the first pass reaches a true reduction of about
-    // 1e-3 and prepares the second, which then reaches 1e-8); FP64: one pass to the tolerance
+    // FP32 inner solves: the first pass asks for 1e-5 and reaches a true reduction of about 1e-3
+    // (the FP32 operator's accuracy on the smooth part of the error); later passes ask for what is
+    // left to reach the tolerance (at least 1e-6), so that two passes usually suffice.
+    // FP64: one pass to the tolerance.
     double eta;
     if (fp32) {
       const double first = pb->par.adjoint_eta_first > 0 ? pb->par.adjoint_eta_first : 1e-5;
-      eta = pass == 0 ? first : std::max(1e-5, 0.5 * kAdjointRtol / rel);
+      eta = pass == 0 ? first : std::max(1e-6, 0.3 * kAdjointRtol / rel);
     } else {
       eta = std::max(0.5 * kAdjointRtol / rel, 1e-12);
       if (pass == 0 && pb->par.adjoint_eta_first > 0) eta = pb->par.adjoint_eta_first;

@@ -24,29 +24,36 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// Per-thread accumulation type of the Krylov kernels: FP32 vectors accumulate a thread's few
+// entries in FP32 (products of FP32 numbers, about n / 300k terms per thread) and the block and
+// grid sums are FP64; FP64 vectors accumulate in FP64 throughout.
+template <typename T> struct KAcc { typedef double type; };
+template <> struct KAcc<float> { typedef float type; };
+
 // part[i * gridDim.x + b] = sum over segment b of V_i . w. Register tile of NV >= nvec vectors:
 // every element of w and of each V_i is read once.
-template <int NV>
-__global__ void __launch_bounds__(256) k_multidot_part(const double* __restrict__ V, long long ld, int nvec,
-                                                       const double* __restrict__ w, long long n,
+template <int NV, typename T>
+__global__ void __launch_bounds__(256) k_multidot_part(const T* __restrict__ V, long long ld, int nvec,
+                                                       const T* __restrict__ w, long long n,
                                                        double* __restrict__ part) {
+  typedef typename KAcc<T>::type A;
   __shared__ double sh[32];
-  double acc[NV];
+  A acc[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  for (int i = 0; i < NV; ++i) acc[i] = 0;
   const long long seg = (n + gridDim.x - 1) / gridDim.x;
   const long long lo = seg * blockIdx.x;
   const long long hi = min(n, lo + seg);
   for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
-    const double x = w[t];
+    const A x = w[t];
 #pragma unroll
     for (int i = 0; i < NV; ++i)
-      if (i < nvec) acc[i] += V[(long long)i * ld + t] * x;
+      if (i < nvec) acc[i] += (A)V[(long long)i * ld + t] * x;
   }
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     if (i >= nvec) break;
-    const double r = block_sum(acc[i], sh);
+    const double r = block_sum((double)acc[i], sh);
     if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = r;
   }
 }
@@ -76,43 +83,45 @@ __device__ __forceinline__ bool cgs_fast(const double* __restrict__ d1, int nvec
   return ww - s >= 0.5 * ww;
 }
 
-template <int NV>
-__global__ void __launch_bounds__(256) k_cgs_update(double* __restrict__ w, const double* __restrict__ V, long long ld,
+template <int NV, typename T>
+__global__ void __launch_bounds__(256) k_cgs_update(T* __restrict__ w, const T* __restrict__ V, long long ld,
                                                     int nvec, const double* __restrict__ d1, long long n,
                                                     double* __restrict__ part) {
+  typedef typename KAcc<T>::type A;
   __shared__ double sh[32];
   double sum2, ww;
   const bool fast = cgs_fast(d1, nvec, &sum2, &ww);
-  double cc[NV];
+  A cc[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) cc[i] = i < nvec ? d1[i] : 0.0;
+  for (int i = 0; i < NV; ++i) cc[i] = i < nvec ? (A)d1[i] : (A)0;
   const long long seg = (n + gridDim.x - 1) / gridDim.x;
   const long long lo = seg * blockIdx.x;
   const long long hi = min(n, lo + seg);
   if (fast) {
-    const double inv = 1.0 / sqrt(ww - sum2);
+    const A inv = (A)(1.0 / sqrt(ww - sum2));
     for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
-      double x = w[t];
+      A x = w[t];
 #pragma unroll
       for (int i = 0; i < NV; ++i)
-        if (i < nvec) x -= cc[i] * V[(long long)i * ld + t];
-      w[t] = x * inv;
+        if (i < nvec) x -= cc[i] * (A)V[(long long)i * ld + t];
+      w[t] = (T)(x * inv);
     }
     return;
   }
-  double acc[NV];
+  A acc[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-  double accw = 0.0;
+  for (int i = 0; i < NV; ++i) acc[i] = 0;
+  A accw = 0;
   for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
-    double v[NV];
-    double x = w[t];
+    A v[NV];
+    A x = w[t];
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      v[i] = i < nvec ? V[(long long)i * ld + t] : 0.0;
+      v[i] = i < nvec ? (A)V[(long long)i * ld + t] : (A)0;
       x -= cc[i] * v[i];
     }
-    w[t] = x;
+    w[t] = (T)x;
+    x = (A)(T)x;   // the dots see the stored value
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] += v[i] * x;
     accw += x * x;
@@ -120,10 +129,10 @@ __global__ void __launch_bounds__(256) k_cgs_update(double* __restrict__ w, cons
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     if (i >= nvec) break;
-    const double r = block_sum(acc[i], sh);
+    const double r = block_sum((double)acc[i], sh);
     if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = r;
   }
-  const double r = block_sum(accw, sh);
+  const double r = block_sum((double)accw, sh);
   if (threadIdx.x == 0) part[(long long)nvec * gridDim.x + blockIdx.x] = r;
 }
 
@@ -141,27 +150,29 @@ __global__ void k_cgs_sum(const double* __restrict__ part, int nb, int nvec, con
 }
 
 // Re-orthogonalisation: w <- (w - sum_i d2_i V_i) / sqrt(d2[nvec] - sum d2_i^2) (only if the test failed).
-template <int NV>
-__global__ void __launch_bounds__(256) k_cgs_reorth(double* __restrict__ w, const double* __restrict__ V, long long ld,
+template <int NV, typename T>
+__global__ void __launch_bounds__(256) k_cgs_reorth(T* __restrict__ w, const T* __restrict__ V, long long ld,
                                                     int nvec, const double* __restrict__ d1,
                                                     const double* __restrict__ d2, long long n) {
+  typedef typename KAcc<T>::type A;
   double s1, ww1;
   if (cgs_fast(d1, nvec, &s1, &ww1)) return;
-  double cc[NV];
+  A cc[NV];
   double corr = 0.0;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    cc[i] = i < nvec ? d2[i] : 0.0;
-    corr += cc[i] * cc[i];
+    const double c = i < nvec ? d2[i] : 0.0;
+    cc[i] = (A)c;
+    corr += c * c;
   }
   const double h2 = d2[nvec] - corr;
-  const double inv = h2 > 0.0 ? 1.0 / sqrt(h2) : 0.0;
+  const A inv = (A)(h2 > 0.0 ? 1.0 / sqrt(h2) : 0.0);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    double x = w[t];
+    A x = w[t];
 #pragma unroll
     for (int i = 0; i < NV; ++i)
-      if (i < nvec) x -= cc[i] * V[(long long)i * ld + t];
-    w[t] = x * inv;
+      if (i < nvec) x -= cc[i] * (A)V[(long long)i * ld + t];
+    w[t] = (T)(x * inv);
   }
 }
 
@@ -179,13 +190,16 @@ __global__ void k_norm2_free_part(const double* __restrict__ a, long long nfree2
 
 struct Coef64 { double c[64]; };
 
-__global__ void k_axpy_multi(double* __restrict__ y, const double* __restrict__ V, long long ld, int nvec,
+// y += sum_i c_i V_i; FP32 basis vectors are combined in FP32 and the sum is added to y in y's type.
+template <typename TY, typename T>
+__global__ void k_axpy_multi(TY* __restrict__ y, const T* __restrict__ V, long long ld, int nvec,
                              Coef64 coef, long long n) {
+  typedef typename KAcc<T>::type A;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
-    double acc = y[t];
-    for (int i = 0; i < nvec; ++i) acc += coef.c[i] * V[(long long)i * ld + t];
-    y[t] = acc;
+    A acc = 0;
+    for (int i = 0; i < nvec; ++i) acc += (A)coef.c[i] * (A)V[(long long)i * ld + t];
+    y[t] = y[t] + (TY)acc;
   }
 }
 
@@ -195,10 +209,18 @@ __global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, do
     y[t] = a * x[t] + b * y[t];
 }
 
-__global__ void k_scale_copy(double* __restrict__ y, const double* __restrict__ x, double a, long long n) {
+template <typename T>
+__global__ void k_scale(T* __restrict__ y, double a, long long n) {
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
-    y[t] = a * x[t];
+    y[t] = (T)((typename KAcc<T>::type)a * y[t]);
+}
+
+template <typename T>
+__global__ void k_scale_copy(T* __restrict__ y, const double* __restrict__ x, double a, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = (T)(a * x[t]);
 }
 
 __global__ void k_vmul(double* __restrict__ z, const double* __restrict__ a, const double* __restrict__ b,
@@ -220,13 +242,14 @@ __global__ void k_cast_f2d(double* __restrict__ y, const float* __restrict__ x, 
     y[t] = (double)x[t];
 }
 
-__global__ void k_zero_dirichlet(Grid g, double* __restrict__ a) {
+template <typename T>
+__global__ void k_zero_dirichlet(Grid g, T* __restrict__ a) {
   const long long plane = (long long)g.NX * g.NY;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= plane) return;
   const long long n = (long long)g.nz * plane + t;
-  a[2 * n] = 0.0;
-  a[2 * n + 1] = 0.0;
+  a[2 * n] = (T)0;
+  a[2 * n + 1] = (T)0;
 }
 
 __global__ void k_check_design(const double* __restrict__ rho, long long n, int* flag) {
@@ -402,17 +425,28 @@ int reduce_blocks(long long n) {
   return (int)b;
 }
 
+template <typename T>
+cudaError_t launch_multidot_t(const T* V, long long ld, int nvec, const T* w, long long n,
+                              double* part, double* res, cudaStream_t st, Counters* c) {
+  const int nb = reduce_blocks(n);
+  if (nvec <= 4) k_multidot_part<4, T><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
+  else if (nvec <= 8) k_multidot_part<8, T><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
+  else if (nvec <= 16) k_multidot_part<16, T><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
+  else if (nvec <= 32) k_multidot_part<32, T><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
+  else k_multidot_part<66, T><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
+  k_sum_parts<<<nvec, 256, 0, st>>>(part, nb, nvec, res);
+  if (c) { c->launches += 2; c->bytes += (double)sizeof(T) * n * (nvec + 1); c->flops += 2.0 * n * nvec; }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_multidot(const double* V, long long ld, int nvec, const double* w, long long n,
                             double* part, double* res, cudaStream_t st, Counters* c) {
-  const int nb = reduce_blocks(n);
-  if (nvec <= 4) k_multidot_part<4><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
-  else if (nvec <= 8) k_multidot_part<8><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
-  else if (nvec <= 16) k_multidot_part<16><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
-  else if (nvec <= 32) k_multidot_part<32><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
-  else k_multidot_part<66><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
-  k_sum_parts<<<nvec, 256, 0, st>>>(part, nb, nvec, res);
-  if (c) { c->launches += 2; c->bytes += 8.0 * n * (nvec + 1); c->flops += 2.0 * n * nvec; }
-  return cudaGetLastError();
+  return launch_multidot_t<double>(V, ld, nvec, w, n, part, res, st, c);
+}
+
+cudaError_t launch_multidot(const float* V, long long ld, int nvec, const float* w, long long n,
+                            double* part, double* res, cudaStream_t st, Counters* c) {
+  return launch_multidot_t<float>(V, ld, nvec, w, n, part, res, st, c);
 }
 
 cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, double* res, cudaStream_t st,
@@ -425,15 +459,16 @@ cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_cgs(double* w, const double* V, long long ld, int nvec, const double* d1, double* d2, long long n,
-                      double* part, cudaStream_t st, Counters* cnt) {
+template <typename T>
+cudaError_t launch_cgs_t(T* w, const T* V, long long ld, int nvec, const double* d1, double* d2, long long n,
+                         double* part, cudaStream_t st, Counters* cnt) {
   const int nb = reduce_blocks(n);
   const unsigned ns = stream_blocks(n);
 #define NC_CGS(NV)                                                                     \
   do {                                                                                 \
-    k_cgs_update<NV><<<nb, kRedThreads, 0, st>>>(w, V, ld, nvec, d1, n, part);        \
+    k_cgs_update<NV, T><<<nb, kRedThreads, 0, st>>>(w, V, ld, nvec, d1, n, part);     \
     k_cgs_sum<<<nvec + 1, 256, 0, st>>>(part, nb, nvec, d1, d2);                       \
-    k_cgs_reorth<NV><<<ns, 256, 0, st>>>(w, V, ld, nvec, d1, d2, n);                   \
+    k_cgs_reorth<NV, T><<<ns, 256, 0, st>>>(w, V, ld, nvec, d1, d2, n);                \
   } while (0)
   if (nvec <= 4) NC_CGS(4);
   else if (nvec <= 8) NC_CGS(8);
@@ -441,18 +476,44 @@ cudaError_t launch_cgs(double* w, const double* V, long long ld, int nvec, const
   else if (nvec <= 32) NC_CGS(32);
   else return cudaErrorInvalidValue;
 #undef NC_CGS
-  if (cnt) { cnt->launches += 3; cnt->bytes += 8.0 * n * (nvec + 2); cnt->flops += 2.0 * n * nvec; }
+  if (cnt) { cnt->launches += 3; cnt->bytes += (double)sizeof(T) * n * (nvec + 2); cnt->flops += 2.0 * n * nvec; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cgs(double* w, const double* V, long long ld, int nvec, const double* d1, double* d2, long long n,
+                      double* part, cudaStream_t st, Counters* cnt) {
+  return launch_cgs_t<double>(w, V, ld, nvec, d1, d2, n, part, st, cnt);
+}
+
+cudaError_t launch_cgs(float* w, const float* V, long long ld, int nvec, const double* d1, double* d2, long long n,
+                      double* part, cudaStream_t st, Counters* cnt) {
+  return launch_cgs_t<float>(w, V, ld, nvec, d1, d2, n, part, st, cnt);
+}
+
+template <typename TY, typename T>
+cudaError_t launch_axpy_multi_t(TY* y, const T* V, long long ld, int nvec, const double* coef,
+                                long long n, cudaStream_t st, Counters* c) {
+  if (nvec > 64) return cudaErrorInvalidValue;
+  Coef64 cf;
+  for (int i = 0; i < nvec; ++i) cf.c[i] = coef[i];
+  k_axpy_multi<TY, T><<<stream_blocks(n), 256, 0, st>>>(y, V, ld, nvec, cf, n);
+  if (c) { c->launches += 1; c->bytes += (double)n * (sizeof(T) * nvec + 2 * sizeof(TY)); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_multi(double* y, const double* V, long long ld, int nvec, const double* coef,
                               long long n, cudaStream_t st, Counters* c) {
-  if (nvec > 64) return cudaErrorInvalidValue;
-  Coef64 cf;
-  for (int i = 0; i < nvec; ++i) cf.c[i] = coef[i];
-  k_axpy_multi<<<stream_blocks(n), 256, 0, st>>>(y, V, ld, nvec, cf, n);
-  if (c) { c->launches += 1; c->bytes += 8.0 * n * (nvec + 2); }
-  return cudaGetLastError();
+  return launch_axpy_multi_t<double, double>(y, V, ld, nvec, coef, n, st, c);
+}
+
+cudaError_t launch_axpy_multi(double* y, const float* V, long long ld, int nvec, const double* coef,
+                              long long n, cudaStream_t st, Counters* c) {
+  return launch_axpy_multi_t<double, float>(y, V, ld, nvec, coef, n, st, c);
+}
+
+cudaError_t launch_axpy_multi(float* y, const float* V, long long ld, int nvec, const double* coef,
+                              long long n, cudaStream_t st, Counters* c) {
+  return launch_axpy_multi_t<float, float>(y, V, ld, nvec, coef, n, st, c);
 }
 
 cudaError_t launch_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st,
@@ -464,8 +525,27 @@ cudaError_t launch_axpby(double* y, const double* x, double a, double b, long lo
 
 cudaError_t launch_scale_copy(double* y, const double* x, double a, long long n, cudaStream_t st,
                               Counters* c) {
-  k_scale_copy<<<stream_blocks(n), 256, 0, st>>>(y, x, a, n);
+  k_scale_copy<double><<<stream_blocks(n), 256, 0, st>>>(y, x, a, n);
   if (c) { c->launches += 1; c->bytes += 16.0 * n; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(double* y, double a, long long n, cudaStream_t st, Counters* c) {
+  k_scale<double><<<stream_blocks(n), 256, 0, st>>>(y, a, n);
+  if (c) { c->launches += 1; c->bytes += 16.0 * n; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(float* y, double a, long long n, cudaStream_t st, Counters* c) {
+  k_scale<float><<<stream_blocks(n), 256, 0, st>>>(y, a, n);
+  if (c) { c->launches += 1; c->bytes += 8.0 * n; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(float* y, const double* x, double a, long long n, cudaStream_t st,
+                              Counters* c) {
+  k_scale_copy<float><<<stream_blocks(n), 256, 0, st>>>(y, x, a, n);
+  if (c) { c->launches += 1; c->bytes += 12.0 * n; }
   return cudaGetLastError();
 }
 
@@ -489,6 +569,13 @@ cudaError_t launch_cast_f2d(double* y, const float* x, long long n, cudaStream_t
 }
 
 cudaError_t launch_zero_dirichlet(const Grid& g, double* a, cudaStream_t st, Counters* c) {
+  const long long plane = (long long)g.NX * g.NY;
+  k_zero_dirichlet<<<grid_blocks(plane, 256), 256, 0, st>>>(g, a);
+  if (c) c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_dirichlet(const Grid& g, float* a, cudaStream_t st, Counters* c) {
   const long long plane = (long long)g.NX * g.NY;
   k_zero_dirichlet<<<grid_blocks(plane, 256), 256, 0, st>>>(g, a);
   if (c) c->launches += 1;

@@ -65,8 +65,11 @@ cudaError_t launch_u_centroid(const Grid& g, const Phys& ph, const double2* s, c
 // kReduceBlocksMax blocks (8 per SM, enough loads in flight to stream vectors at full bandwidth).
 const int kReduceBlocksMax = 1216;
 int reduce_blocks(long long n);
-// res[i] = <V_i, w> for i < nvec, V_i = V + i*ld; n doubles each. part: nvec*reduce_blocks(n).
+// res[i] = <V_i, w> for i < nvec, V_i = V + i*ld; n entries each. part: nvec*reduce_blocks(n).
+// FP32 vectors: FP32 products and per-thread sums, FP64 block and grid sums.
 cudaError_t launch_multidot(const double* V, long long ld, int nvec, const double* w, long long n,
+                            double* part, double* res, cudaStream_t st, Counters* c);
+cudaError_t launch_multidot(const float* V, long long ld, int nvec, const float* w, long long n,
                             double* part, double* res, cudaStream_t st, Counters* c);
 // res[0] = sum over free entries (Dirichlet rows excluded) of a^2, for a state vector.
 cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, double* res,
@@ -77,19 +80,31 @@ cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, doub
 // the host repeats the same test on the read-back values.
 cudaError_t launch_cgs(double* w, const double* V, long long ld, int nvec, const double* d1, double* d2, long long n,
                       double* part, cudaStream_t st, Counters* cnt);
-// y += sum_i coef[i] * V_i (nvec <= 64), n doubles.
+cudaError_t launch_cgs(float* w, const float* V, long long ld, int nvec, const double* d1, double* d2, long long n,
+                      double* part, cudaStream_t st, Counters* cnt);
+// y += sum_i coef[i] * V_i (nvec <= 64), n entries.
 cudaError_t launch_axpy_multi(double* y, const double* V, long long ld, int nvec, const double* coef,
+                              long long n, cudaStream_t st, Counters* c);
+cudaError_t launch_axpy_multi(double* y, const float* V, long long ld, int nvec, const double* coef,
+                              long long n, cudaStream_t st, Counters* c);
+cudaError_t launch_axpy_multi(float* y, const float* V, long long ld, int nvec, const double* coef,
                               long long n, cudaStream_t st, Counters* c);
 // y = a*x + b*y
 cudaError_t launch_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st,
                          Counters* c);
+// y = y * a (in place)
+cudaError_t launch_scale(double* y, double a, long long n, cudaStream_t st, Counters* c);
+cudaError_t launch_scale(float* y, double a, long long n, cudaStream_t st, Counters* c);
 // y = x * a
 cudaError_t launch_scale_copy(double* y, const double* x, double a, long long n, cudaStream_t st,
+                              Counters* c);
+cudaError_t launch_scale_copy(float* y, const double* x, double a, long long n, cudaStream_t st,
                               Counters* c);
 cudaError_t launch_cast_d2f(float* y, const double* x, long long n, cudaStream_t st, Counters* c);
 cudaError_t launch_cast_f2d(double* y, const float* x, long long n, cudaStream_t st, Counters* c);
 // Zero the Dirichlet (top plane) entries of a state vector.
 cudaError_t launch_zero_dirichlet(const Grid& g, double* a, cudaStream_t st, Counters* c);
+cudaError_t launch_zero_dirichlet(const Grid& g, float* a, cudaStream_t st, Counters* c);
 // Design check: flag = 1 if any value is NaN or outside [0,1].
 cudaError_t launch_check_design(const double* rho, long long ne, int* flag, cudaStream_t st);
 // Filter pieces (Helmholtz (r^2 K + M) x = T^T gamma, Q1 nodal, element mean out).

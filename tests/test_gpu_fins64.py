@@ -37,9 +37,8 @@ def test_fins_fp64_vs_mixed(nc, alpha):
     nodes = rng.choice(op.mesh.n_nodes, 400, replace=False)
     free = ~op.dir_mask.reshape(-1, 2)[nodes]
     states = {}
-    pb = nc.Problem(N, N, N, 1.0 / N, alpha=alpha, mg_levels=5, newton_rtol=1e-8)
     for prec in (nc.NC_PREC_FP64, nc.NC_PREC_MIXED):
-        pb.set_params(precision=prec)
+        pb = nc.Problem(N, N, N, 1.0 / N, alpha=alpha, mg_levels=5, newton_rtol=1e-8, precision=prec)
         pb.set_design(rho)
         st = pb.solve_state()
         P, T, _ = pb.get_fields(velocity=False)
@@ -51,7 +50,7 @@ def test_fins_fp64_vs_mixed(nc, alpha):
               % (alpha, prec, st["newton_its"], st["krylov_its"], st.get("ramped"), worst))
         assert worst <= 1e-8
         states[prec] = s
-    pb.close()
+        pb.close()
     s64, s32 = states[nc.NC_PREC_FP64], states[nc.NC_PREC_MIXED]
     err = np.linalg.norm(s32 - s64) / np.linalg.norm(s64)
     print("alpha %.0e: mixed vs FP64 state rel L2 %.2e" % (alpha, err))

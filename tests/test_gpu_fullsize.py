@@ -116,15 +116,14 @@ def test_state_adjoint_sensitivities_128(setup):
 
 def test_fp64_path_agrees_128(setup):
     nc, op, pb, rho, nodes = setup
-    pb.set_params(precision=nc.NC_PREC_MIXED)
     pb.set_design(rho)
     pb.solve_state()
     Pm, Tm, _ = pb.get_fields(velocity=False)
-    pb.set_params(precision=nc.NC_PREC_FP64)
-    pb.set_design(rho)
-    st = pb.solve_state()
-    P, T, _ = pb.get_fields(velocity=False)
-    pb.set_params(precision=nc.NC_PREC_MIXED)
+    p64 = nc.Problem(N, N, N, 1.0 / N, alpha=ALPHA, mg_levels=6, precision=nc.NC_PREC_FP64)
+    p64.set_design(rho)
+    st = p64.solve_state()
+    P, T, _ = p64.get_fields(velocity=False)
+    p64.close()
     s = np.empty(2 * op.mesh.n_nodes)
     s[0::2], s[1::2] = P.cpu().numpy(), T.cpu().numpy()
     r0 = op.reference_norm()
