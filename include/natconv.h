@@ -63,6 +63,8 @@ typedef enum {
 } nc_status;
 
 enum { NC_PREC_MIXED = 0, NC_PREC_FP64 = 1 };
+/* Arithmetic of the outer residuals on the mixed-precision path (nc_params.outer_arith). */
+enum { NC_ARITH_DF64 = 0, NC_ARITH_FP64 = 1 };
 enum { NC_OBJ_MEAN_T_HEATED = 0 };
 
 typedef struct nc_problem nc_problem;
@@ -90,11 +92,12 @@ typedef struct {
   double krylov_rtol;   /* upper bound of the FGMRES relative tolerance per Newton step [1e-2] */
   int krylov_maxit;     /* FGMRES iterations per linear solve [300] */
   int restart;          /* FGMRES restart length, <= 64 [30] */
-  int precision;        /* NC_PREC_MIXED (FP32 multigrid and Krylov operator, FP64 residual,
-                           orthogonalisation and coarse solve) or NC_PREC_FP64 [MIXED] */
+  int precision;        /* NC_PREC_MIXED (FP32 multigrid, Krylov operator and Krylov basis; outer
+                           residuals in outer_arith; FP64 Hessenberg, Newton update and coarse
+                           residual) or NC_PREC_FP64 (IEEE FP64 throughout) [MIXED] */
   int mg_levels;        /* 0: coarsen while every dimension is even [0] */
-  int nu_pre, nu_post;  /* smoothing sweeps [2, 2] */
-  double omega;         /* damping of the block-Jacobi smoother [0.7] */
+  int nu_pre, nu_post;  /* smoothing sweeps; the first pre-sweep starts from x = 0 [1, 2] */
+  double omega;         /* damping of the block-Jacobi smoother [0.9] */
   double filter_rtol;   /* relative residual tolerance of the filter solve [1e-12] */
   double timeout_s;     /* wall-clock limit of one call [600] */
   double adjoint_rtol;  /* adjoint stops at ||df/ds - J^T lambda|| <= adjoint_rtol ||df/ds||;
@@ -104,6 +107,13 @@ typedef struct {
   double krylov_eta_min; /* lower bound of the Newton forcing term; <= 0: 1e-12 [0] */
   double adjoint_eta_first; /* FGMRES tolerance of the first adjoint refinement pass; <= 0: 1e-5 with
                                NC_PREC_MIXED, the adjoint tolerance with NC_PREC_FP64 [0] */
+  int mg_tail_nodes;    /* the multigrid levels below the finest with at most this many nodes, down
+                           to the coarsest, run as one fused kernel on a thread-block cluster (the
+                           same arithmetic as separate launches); 0: separate launches [5000] */
+  int outer_arith;      /* NC_PREC_MIXED only: arithmetic of the Newton residual, the adjoint
+                           refinement residual J^T lambda and the sensitivities. NC_ARITH_DF64:
+                           double-float (hi + lo pairs of floats, about 48 significant bits, on the
+                           FP32 units; inputs and outputs FP64); NC_ARITH_FP64: IEEE FP64 [DF64] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */
@@ -181,7 +191,8 @@ nc_status nc_get_design_fields(const nc_problem* pb, double* gamma_tilde, double
  * s, v, w, out are state vectors (2N doubles). Entries on the Dirichlet top face of v and w
  * are ignored; the corresponding outputs are: R_d = s_d (residual), 0 (products). */
 
-/* R(s) (Eq. finalsyseq) and ||R_free(s)||^2 (norm2_free may be NULL). Requires a design. */
+/* R(s) (Eq. finalsyseq) and ||R_free(s)||^2 (norm2_free may be NULL), in the arithmetic of the
+ * Newton residual (FP64 on the FP64 path, outer_arith on the mixed path). Requires a design. */
 nc_status nc_eval_residual(nc_problem* pb, const double* s, double* R, double* norm2_free);
 
 /* Exact Newton Jacobian product J(s) v, including the derivatives of tau and N*, computed in
@@ -189,7 +200,8 @@ nc_status nc_eval_residual(nc_problem* pb, const double* s, double* R, double* n
 nc_status nc_apply_jacobian(nc_problem* pb, const double* s, const double* v, double* out,
                             int precision);
 
-/* Transposed product J(s)^T w in FP64 (the adjoint operator). Requires a design. */
+/* Transposed product J(s)^T w (the adjoint operator) in the arithmetic of the adjoint refinement
+ * residual (FP64 on the FP64 path, outer_arith on the mixed path). Requires a design. */
 nc_status nc_apply_jacobian_transpose(nc_problem* pb, const double* s, const double* w,
                                       double* out);
 
@@ -210,7 +222,8 @@ enum {
   NC_PROF_COARSE_FACTOR = 12,   /* inverse of the coarsest-level matrix */
   NC_PROF_COARSE_SOLVE = 13,    /* coarsest-level solve inside the V-cycle */
   NC_PROF_MG_STENCIL_L1 = 14,   /* stencil operators of multigrid level 1 (the largest stencil level) */
-  NC_PROF_NCLASSES = 15
+  NC_PROF_MG_TAIL = 15,         /* fused V-cycle on the small coarse levels (one cluster kernel) */
+  NC_PROF_NCLASSES = 16
 };
 
 /* Per-launch CUDA-event timing of kernel classes for calls on pb: bit c of class_mask times class

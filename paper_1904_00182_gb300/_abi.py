@@ -9,6 +9,8 @@ LIB_PATH = os.path.join(HERE, "lib", "libnatconv.so")
 NC_OK = 0
 NC_PREC_MIXED = 0
 NC_PREC_FP64 = 1
+NC_ARITH_DF64 = 0
+NC_ARITH_FP64 = 1
 NC_OBJ_MEAN_T_HEATED = 0
 
 STATUS_NAMES = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_OOM", 3: "NC_ERR_CUDA", 4: "NC_ERR_DIVERGED",
@@ -23,7 +25,7 @@ EXPORTS = ("nc_default_params", "nc_create_problem", "nc_destroy_problem", "nc_f
 
 PROF_CLASSES = ("residual", "outer_op64", "outer_op32", "mg_op0", "mg_stencil", "mg_setup_fine", "smooth",
                 "krylov_vec", "filter", "sens", "other", "mg_setup_coarse", "coarse_factor", "coarse_solve",
-                "mg_stencil_l1")
+                "mg_stencil_l1", "mg_tail")
 
 
 class NatConvError(RuntimeError):
@@ -50,6 +52,7 @@ class Params(ctypes.Structure):
         ("nu_post", ctypes.c_int), ("omega", ctypes.c_double), ("filter_rtol", ctypes.c_double),
         ("timeout_s", ctypes.c_double), ("adjoint_rtol", ctypes.c_double), ("coarse_refactor", ctypes.c_int),
         ("krylov_eta_min", ctypes.c_double), ("adjoint_eta_first", ctypes.c_double),
+        ("mg_tail_nodes", ctypes.c_int), ("outer_arith", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -87,6 +87,8 @@ struct nc_problem {
   double *rho = nullptr, *gamma_t = nullptr, *gsens = nullptr, *u = nullptr;
   double2 *mat = nullptr, *dmat = nullptr;
   float2 *mat32 = nullptr, *s32 = nullptr, *v32 = nullptr, *y32 = nullptr;
+  // double-float copies (mixed path with NC_ARITH_DF64): materials per element, split scratch per node
+  float4 *mat_df = nullptr, *s_df = nullptr, *w_df = nullptr;
   // Krylov
   int m = 30;
   double *V = nullptr, *Z = nullptr;      // FP64 basis (NC_PREC_FP64)
@@ -301,8 +303,25 @@ nc_status filter_solve(nc_problem* pb) {
 }
 
 // ---------------------------------------------------------------- operators --------
+// Outer residuals (Newton residual, adjoint refinement residual, sensitivities) in double-float?
+bool outer_df(const nc_problem* pb) {
+  return pb->par.precision != NC_PREC_FP64 && pb->par.outer_arith == NC_ARITH_DF64;
+}
+
+// J(s)^T w in the arithmetic of the outer residuals.
+nc_status outer_jtv(nc_problem* pb, int cls, const double2* s, const double2* w, double* out) {
+  if (outer_df(pb))
+    PCK(cls, launch_jtv_df(pb->g, pb->ph, s, pb->mat_df, pb->s_df, w, pb->w_df, out, pb->st, &pb->cnt));
+  else
+    PCK(cls, launch_jtv_f64(pb->g, pb->ph, s, pb->mat, w, out, pb->st, &pb->cnt));
+  return NC_OK;
+}
+
 nc_status residual(nc_problem* pb, const double2* s, double* R, double* phi) {
-  PCK(NC_PROF_RESIDUAL, launch_residual(pb->g, pb->ph, s, pb->mat, R, pb->st, &pb->cnt));
+  if (outer_df(pb))
+    PCK(NC_PROF_RESIDUAL, launch_residual_df(pb->g, pb->ph, s, pb->mat_df, pb->s_df, R, pb->st, &pb->cnt));
+  else
+    PCK(NC_PROF_RESIDUAL, launch_residual(pb->g, pb->ph, s, pb->mat, R, pb->st, &pb->cnt));
   CKS(norm2_free(pb, R, phi));
   if (!std::isfinite(*phi)) return fail(pb, NC_ERR_NAN, "non-finite residual");
   return NC_OK;
@@ -400,6 +419,16 @@ nc_status level_apply(nc_problem* pb, int l, bool tr, const typename Vec2<R>::ty
   return NC_OK;
 }
 
+// First level of the fused multigrid tail (levels with at most mg_tail_nodes nodes, below the
+// finest, with at least one level above the coarsest), or 0 if there is none.
+int tail_level(const nc_problem* pb) {
+  const int L = (int)pb->lv.g.size();
+  if (pb->par.mg_tail_nodes <= 0) return 0;
+  for (int l = 1; l < L - 1; ++l)
+    if (pb->lv.g[l].nn <= pb->par.mg_tail_nodes) return (L - l <= kTailMaxLevels) ? l : 0;
+  return 0;
+}
+
 // V-cycle on level l: solves approximately A_l x_l = b_l; the result is left in lev[l].x.
 // Level 0 applies the matrix-free Jacobian and updates separately; coarser levels fuse the
 // stencil product with the Jacobi update or the residual.
@@ -414,6 +443,21 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
   }
   const R om = (R)pb->par.omega;
   const int nu1 = std::max(1, pb->par.nu_pre), nu2 = std::max(0, pb->par.nu_post);
+  if (l > 0 && l == tail_level(pb)) {
+    // levels l .. L-1 in one cluster kernel; the host pointers follow its x / xn swaps
+    TailArgs<R> a;
+    for (int q = l; q < L; ++q) {
+      TailLevel<R>& tl = a.lev[q - l];
+      const MGLevelDev<R>& dq = mg.lev[q];
+      tl.g = dq.g; tl.S = dq.S; tl.dinv = dq.dinv; tl.x = dq.x; tl.xn = dq.xn; tl.b = dq.b;
+    }
+    a.nlev = L - l; a.Ac = mg.Ac; a.Ainv32 = mg.Ainv32; a.cw = mg.cw; a.nf = mg.nf;
+    a.omega = om; a.nu1 = nu1; a.nu2 = nu2;
+    PCK(NC_PROF_MG_TAIL, launch_mg_tail<R>(a, tr, pb->st, &pb->cnt));
+    for (int q = l; q < L - 1; ++q)
+      for (int sw = 0; sw < (nu1 - 1) + nu2; ++sw) std::swap(mg.lev[q].x, mg.lev[q].xn);
+    return NC_OK;
+  }
   auto sweep = [&]() -> nc_status {
     if (l == 0) {
       CKS(level_apply<R>(pb, l, tr, d.x, d.y));
@@ -803,6 +847,8 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (p->alpha < 0 || p->g < 0 || p->q_c < 0 || p->q_p < 0) { *why = "alpha, g, q_c, q_p must be >= 0"; return NC_ERR_ARG; }
   if (p->restart < 1 || p->restart > kMaxRestart) { *why = "restart must be in [1, 64]"; return NC_ERR_ARG; }
   if (p->precision != NC_PREC_MIXED && p->precision != NC_PREC_FP64) { *why = "unknown precision"; return NC_ERR_ARG; }
+  if (p->outer_arith != NC_ARITH_DF64 && p->outer_arith != NC_ARITH_FP64) { *why = "unknown outer_arith"; return NC_ERR_ARG; }
+  if (p->mg_tail_nodes < 0) { *why = "mg_tail_nodes must be >= 0"; return NC_ERR_ARG; }
   if (!(p->newton_rtol > 0) || p->newton_maxit < 0 || p->krylov_maxit < 1) { *why = "bad tolerances"; return NC_ERR_ARG; }
   if (!(p->filter_radius >= 0) || !(p->filter_rtol > 0)) { *why = "bad filter parameters"; return NC_ERR_ARG; }
   Grid g0 = make_grid(g->nx, g->ny, g->nz, g->h);
@@ -824,6 +870,7 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
   b += 2 * al(16 * ne) + al(8 * ne) + 3 * al(8 * nn);   // mat, dmat, mat32, s32, v32, y32
   const size_t ks = p->precision == NC_PREC_FP64 ? 8 : 4;   // Krylov basis entry size
   b += al(2 * ks * nn * (m + 1)) + al(2 * ks * nn * m);     // V, Z
+  if (p->precision != NC_PREC_FP64) b += al(16 * ne) + 2 * al(16 * nn);   // mat_df, s_df, w_df
   b += al(8 * 66 * kReduceBlocksMax) + al(8 * 132);
   b += 5 * al(8 * nn) + 5 * al(4 * nn); // filter vectors
   const size_t rs = p->precision == NC_PREC_FP64 ? 8 : 4;
@@ -936,15 +983,17 @@ nc_status nc_default_params(nc_params* p) {
   p->restart = 30;
   p->precision = NC_PREC_MIXED;
   p->mg_levels = 0;
-  p->nu_pre = 2;
+  p->nu_pre = 1;
   p->nu_post = 2;
-  p->omega = 0.7;
+  p->omega = 0.9;
   p->filter_rtol = 1e-12;
   p->timeout_s = 600.0;
   p->adjoint_rtol = 0.0;
   p->coarse_refactor = 0;
   p->krylov_eta_min = 0.0;
   p->adjoint_eta_first = 0.0;
+  p->outer_arith = NC_ARITH_DF64;
+  p->mg_tail_nodes = 5000;
   return NC_OK;
 }
 
@@ -990,6 +1039,7 @@ nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream,
     A(dalloc(pb, &pb->V, (size_t)2 * nn * (pb->m + 1))); A(dalloc(pb, &pb->Z, (size_t)2 * nn * pb->m));
   } else {
     A(dalloc(pb, &pb->V32, (size_t)2 * nn * (pb->m + 1))); A(dalloc(pb, &pb->Z32, (size_t)2 * nn * pb->m));
+    A(dalloc(pb, &pb->mat_df, ne)); A(dalloc(pb, &pb->s_df, nn)); A(dalloc(pb, &pb->w_df, nn));
   }
   A(dalloc(pb, &pb->part, 66 * kReduceBlocksMax)); A(dalloc(pb, &pb->dres, 132));
   A(dalloc(pb, &pb->fx, nn)); A(dalloc(pb, &pb->fb, nn)); A(dalloc(pb, &pb->fr, nn));
@@ -1069,6 +1119,7 @@ nc_status nc_set_design(nc_problem* pb, const double* rho) {
   PCK(NC_PROF_FILTER, launch_elem_from_nodes(g, pb->fx, 0.125, pb->par.heated_layers, 1.0, pb->gamma_t, pb->st, &pb->cnt));
   RampConst rc{pb->kappa_f, pb->kappa_s, pb->par.k_f, pb->par.k_s, pb->par.q_c, pb->par.q_p};
   PCK(NC_PROF_OTHER, launch_ramp(pb->gamma_t, g.ne, rc, pb->mat, pb->dmat, pb->mat32, pb->st, &pb->cnt));
+  if (pb->mat_df) PCK(NC_PROF_OTHER, launch_split2(pb->mat, pb->mat_df, g.ne, pb->st, &pb->cnt));
   CK(cudaMemsetAsync(pb->s, 0, sizeof(double2) * g.nn, pb->st));
   CK(cudaMemsetAsync(pb->s_start, 0, sizeof(double2) * g.nn, pb->st));
   CKS(reference_norm(pb));
@@ -1184,7 +1235,7 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
       CK(cudaMemcpyAsync(pb->w, pb->rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
       rr = bb;
     } else {
-      PCK(NC_PROF_OUTER_OP64, launch_jtv_f64(g, pb->ph, pb->s, pb->mat, pb->lam, pb->w, pb->st, &pb->cnt));
+      CKS(outer_jtv(pb, NC_PROF_OUTER_OP64, pb->s, pb->lam, pb->w));
       PCK(NC_PROF_OTHER, launch_axpby(pb->w, pb->rhs, 1.0, -1.0, n, pb->st, &pb->cnt));
       PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->w, pb->st, &pb->cnt));
       CKS(norm2_free(pb, pb->w, &rr));
@@ -1240,7 +1291,11 @@ nc_status nc_sensitivities(nc_problem* pb, double* dfdrho) {
   pb->t_start = now_s();
   const Grid& g = pb->g;
   set_q_scale(pb, 1.0);
-  PCK(NC_PROF_SENS, launch_sens_elem(g, pb->ph, pb->s, pb->lam, pb->mat, pb->dmat, pb->gsens, pb->st, &pb->cnt));
+  if (outer_df(pb))
+    PCK(NC_PROF_SENS, launch_sens_df(g, pb->ph, pb->s, pb->lam, pb->mat_df, pb->dmat, pb->s_df, pb->w_df, pb->gsens,
+                                     pb->st, &pb->cnt));
+  else
+    PCK(NC_PROF_SENS, launch_sens_elem(g, pb->ph, pb->s, pb->lam, pb->mat, pb->dmat, pb->gsens, pb->st, &pb->cnt));
   // filter transpose: gamma~_e = (1/8) sum_a x_a, x = A^-1 T^T gamma  =>  df/dgamma = T A^-1 (1/8 sum)
   PCK(NC_PROF_FILTER, launch_filter_rhs(g, pb->gsens, 0, 0.125, pb->fb, pb->st, &pb->cnt));
   CKS(filter_solve(pb));
@@ -1319,7 +1374,7 @@ static nc_status apply_generic(nc_problem* pb, const double* s, const double* v,
     PCK(NC_PROF_OTHER, launch_cast_d2f((float*)pb->s32, (const double*)pb->s_try, n, pb->st, &pb->cnt));
     CKS(outer_op(pb, tr, true, pb->w, pb->R_try));
   } else {
-    if (tr) PCK(NC_PROF_OTHER, launch_jtv_f64(g, pb->ph, pb->s_try, pb->mat, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
+    if (tr) CKS(outer_jtv(pb, NC_PROF_OTHER, pb->s_try, (const double2*)pb->w, pb->R_try));
     else PCK(NC_PROF_OTHER, launch_jv_f64(g, pb->ph, pb->s_try, pb->mat, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
   }
   CKS(copy_out(pb, out, pb->R_try, sizeof(double) * n));

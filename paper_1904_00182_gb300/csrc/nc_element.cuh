@@ -1,5 +1,5 @@
 // Element-level arithmetic of the stabilised Darcy-Boussinesq weak form (App. A of the paper),
-// written once, templated on the arithmetic type (double or float).
+// written once, templated on the arithmetic type (double, float or double-float df64).
 //
 // Weak form (Eq. weakstable), per element with permeability kappa, conductivity k, source Q:
 //   R^P_a = sum_q w ( -grad N_a . u_q )                                 (continuity rows)
@@ -19,6 +19,7 @@
 #pragma once
 
 #include "nc_common.cuh"
+#include "nc_df64.cuh"
 
 namespace nc {
 
@@ -152,6 +153,7 @@ __device__ __forceinline__ void q1_test(const R* A, const R Bx[8], const R By[8]
 template <typename R> __device__ __forceinline__ R nc_rsqrt(R x);
 template <> __device__ __forceinline__ double nc_rsqrt<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ float nc_rsqrt<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ df64 nc_rsqrt<df64>(df64 x) { return df_rsqrt(x); }
 
 // Gauss-point state of an element: V_q = grad P_q - beta T_q e_z (so u_q = -c V_q, c = kappa/mu),
 // grad T_q, S_q = rho0 c_p u_q . grad T_q - Q, centroid velocity u0 and tau.

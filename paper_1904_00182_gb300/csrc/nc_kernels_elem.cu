@@ -127,7 +127,132 @@ __global__ void k_u_centroid(Grid g, Phys ph, ElemConst<double> C, const double2
   u[3 * e + 2] = st.u0z;
 }
 
+// ---- double-float variants (mixed-precision path) ----
+// Minimum resident blocks of 128 threads per SM (register budget) of the double-float kernels.
+#ifndef NC_LB_RESIDUAL_DF
+#define NC_LB_RESIDUAL_DF 4
+#endif
+#ifndef NC_LB_JTV_DF
+#define NC_LB_JTV_DF 4
+#endif
+#ifndef NC_LB_SENS_DF
+#define NC_LB_SENS_DF 2
+#endif
+// Inputs arrive split once per call: state and direction as float4 (P.hi, P.lo, T.hi, T.lo) per
+// node, materials as float4 (kappa.hi, kappa.lo, k.hi, k.lo) per element. Outputs are converted to
+// FP64 (hi + lo) and accumulated with FP64 atomics, as in the FP64 kernels.
+
+__global__ void k_split2(const double2* __restrict__ x, float4* __restrict__ y, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double2 v = x[t];
+    const df64 a = df_from_double(v.x), b = df_from_double(v.y);
+    y[t] = make_float4(a.hi, a.lo, b.hi, b.lo);
+  }
+}
+
+__device__ __forceinline__ void gather_df(const Grid& g, const float4* __restrict__ s, int n0, bool zero_top,
+                                          df64 p[8], df64 t[8]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    if (zero_top && (a >> 2)) { p[a] = df64(0.0f, 0.0f); t[a] = df64(0.0f, 0.0f); continue; }
+    const float4 v = s[n0 + corner_off(g, a)];
+    p[a] = df64(v.x, v.y);
+    t[a] = df64(v.z, v.w);
+  }
+}
+
+__global__ void __launch_bounds__(128, NC_LB_RESIDUAL_DF) k_residual_df(Grid g, Phys ph, ElemConst<df64> C, df64 Qh, const float4* __restrict__ s,
+                              const float4* __restrict__ mat, double* __restrict__ out) {
+  NC_ELEM_PROLOGUE();
+  df64 p[8], t[8];
+  gather_df(g, s, n0, false, p, t);
+  const float4 m = mat[e];
+  const df64 Q = k < ph.heated_layers ? Qh : df64(0.0f, 0.0f);
+  df64 RP[8], RT[8];
+  elem_residual<df64>(C, p, t, df64(m.x, m.y), df64(m.z, m.w), Q, RP, RT);
+  scatter_add(g, out, n0, top, RP, RT);
+}
+
+__global__ void __launch_bounds__(128, NC_LB_JTV_DF) k_jtv_df(Grid g, Phys ph, ElemConst<df64> C, df64 Qh, const float4* __restrict__ s,
+                         const float4* __restrict__ mat, const float4* __restrict__ w, double* __restrict__ out) {
+  NC_ELEM_PROLOGUE();
+  df64 p[8], t[8], lp[8], lt[8];
+  gather_df(g, s, n0, false, p, t);
+  gather_df(g, w, n0, top, lp, lt);
+  const float4 m = mat[e];
+  ElemState<df64> st;
+  elem_state(C, p, t, df64(m.x, m.y), k < ph.heated_layers ? Qh : df64(0.0f, 0.0f), st);
+  df64 oP[8], oT[8];
+  elem_jtv<df64, false>(C, st, df64(m.z, m.w), lp, lt, oP, oT, nullptr, nullptr);
+  scatter_add(g, out, n0, top, oP, oT);
+}
+
+__global__ void __launch_bounds__(128, NC_LB_SENS_DF) k_sens_df(Grid g, Phys ph, ElemConst<df64> C, const float4* __restrict__ s,
+                          const float4* __restrict__ lam, const float4* __restrict__ mat,
+                          const double2* __restrict__ dmat, double* __restrict__ out) {
+  NC_ELEM_PROLOGUE();
+  if (k < ph.heated_layers) { out[e] = 0.0; return; }
+  df64 p[8], t[8], lp[8], lt[8];
+  gather_df(g, s, n0, false, p, t);
+  gather_df(g, lam, n0, top, lp, lt);
+  const float4 m = mat[e];
+  ElemState<df64> st;
+  elem_state(C, p, t, df64(m.x, m.y), df64(0.0f, 0.0f), st);
+  df64 oP[8], oT[8], dkap, dk;
+  elem_jtv<df64, true>(C, st, df64(m.z, m.w), lp, lt, oP, oT, &dkap, &dk);
+  const double2 d = dmat[e];
+  out[e] = -((double)dkap * d.x + (double)dk * d.y);
+}
+
 }  // namespace
+
+cudaError_t launch_split2(const double2* x, float4* y, long long n, cudaStream_t st, Counters* c) {
+  k_split2<<<grid_blocks(n, 256, 152 * 16), 256, 0, st>>>(x, y, n);
+  if (c) { c->launches += 1; c->bytes += 32.0 * n; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_df(const Grid& g, const Phys& ph, const double2* s, const float4* mat_df,
+                               float4* s_df, double* out, cudaStream_t st, Counters* c) {
+  cudaError_t err = cudaMemsetAsync(out, 0, sizeof(double) * 2 * g.nn, st);
+  if (err != cudaSuccess) return err;
+  err = launch_split2(s, s_df, g.nn, st, c);
+  if (err != cudaSuccess) return err;
+  const Launch3 L = launch_elems(g);
+  k_residual_df<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<df64>(ph), df64(ph.Q), s_df, mat_df, out);
+  const long long plane = (long long)g.NX * g.NY;
+  k_residual_bc<<<grid_blocks(plane, 256), 256, 0, st>>>(g, s, out);
+  if (c) { c->launches += 2; c->bytes += 16.0 * g.nn * 2 + 16.0 * g.ne; c->flops += kFlopsResidualDF * g.ne; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jtv_df(const Grid& g, const Phys& ph, const double2* s, const float4* mat_df, float4* s_df,
+                          const double2* w, float4* w_df, double* out, cudaStream_t st, Counters* c) {
+  cudaError_t err = cudaMemsetAsync(out, 0, sizeof(double) * 2 * g.nn, st);
+  if (err != cudaSuccess) return err;
+  if ((err = launch_split2(s, s_df, g.nn, st, c)) != cudaSuccess) return err;
+  if ((err = launch_split2(w, w_df, g.nn, st, c)) != cudaSuccess) return err;
+  const Launch3 L = launch_elems(g);
+  k_jtv_df<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<df64>(ph), df64(ph.Q), s_df, mat_df, w_df, out);
+  if (c) {
+    c->launches += 1;
+    c->bytes += (32.0 + 16.0) * g.nn + 16.0 * g.ne;
+    c->flops += (kFlopsStateDF + kFlopsJtvDF) * g.ne;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sens_df(const Grid& g, const Phys& ph, const double2* s, const double2* lam, const float4* mat_df,
+                           const double2* dmat, float4* s_df, float4* l_df, double* out, cudaStream_t st, Counters* c) {
+  cudaError_t err;
+  if ((err = launch_split2(s, s_df, g.nn, st, c)) != cudaSuccess) return err;
+  if ((err = launch_split2(lam, l_df, g.nn, st, c)) != cudaSuccess) return err;
+  const Launch3 L = launch_elems(g);
+  k_sens_df<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<df64>(ph), s_df, l_df, mat_df, dmat, out);
+  if (c) { c->launches += 1; c->bytes += 32.0 * g.nn + 40.0 * g.ne; c->flops += (kFlopsStateDF + kFlopsSensDF) * g.ne; }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_residual(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
                             double* out, cudaStream_t st, Counters* c) {

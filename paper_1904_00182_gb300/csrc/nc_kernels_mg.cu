@@ -11,11 +11,22 @@
 // node, no atomics). The smoother is damped 2x2 node-block Jacobi; the coarsest level is solved with
 // an FP32 Gauss-Jordan inverse (partial pivoting) and one step of FP64 iterative refinement (the
 // coarse residual is computed in FP64 against the FP64 Galerkin matrix).
+#include <cooperative_groups.h>
+
 #include "nc_launch.h"
 
 namespace nc {
 
 namespace {
+
+// Loads of the node bodies of the transfer and stencil operators: plain (separate launches; read-only data may take the
+// non-coherent path) or L2-coherent (the fused tail kernel, whose vectors change between its steps).
+struct LdPlain {
+  template <typename T> __device__ __forceinline__ T operator()(const T* p) const { return *p; }
+};
+struct LdCG {
+  template <typename T> __device__ __forceinline__ T operator()(const T* p) const { return __ldcg(p); }
+};
 
 // out[A] = sum_l P_c[l][A] in[l]: transpose of the trilinear interpolation from the parent's 8
 // corners A to the 8 nodes l of child c, applied as three 1D stages. Along an axis where the child
@@ -239,17 +250,13 @@ __global__ void k_sub(long long nn, const typename Vec2<R>::type* __restrict__ b
   r[n] = mk2<R>(bb.x - yy.x, bb.y - yy.y);
 }
 
-template <typename R>
-__global__ void k_restrict(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ rf,
-                           typename Vec2<R>::type* __restrict__ bc) {
-  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pidx >= gc.NXY) return;
-  const int K = blockIdx.y;
-  const int J = pidx / gc.NX;
-  const int I = pidx - J * gc.NX;
-  const int n = pidx + gc.NXY * K;
+// Full weighting (R = P^T) at coarse node (I, J, K): the fine residual rf at the 27 fine nodes
+// around it, weights 1, 1/2, 1/4, 1/8 by distance; the top (Dirichlet) plane gets 0.
+template <typename R, typename LD>
+__device__ __forceinline__ typename Vec2<R>::type restrict_node(const Grid& gf, const typename Vec2<R>::type* rf,
+                                                                int I, int J, int K, bool top, LD ld) {
   R a0 = R(0), a1 = R(0);
-  if (K < gc.nz) {
+  if (!top) {
 #pragma unroll
     for (int dk = -1; dk <= 1; ++dk) {
       const int k = 2 * K + dk;
@@ -266,22 +273,31 @@ __global__ void k_restrict(Grid gf, Grid gc, const typename Vec2<R>::type* __res
           const int i = 2 * I + di;
           if (i < 0 || i > gf.nx) continue;
           const R w = wj * (di ? R(0.5) : R(1));
-          const typename Vec2<R>::type v = rf[row + i];
+          const typename Vec2<R>::type v = ld(rf + row + i);
           a0 += w * v.x;
           a1 += w * v.y;
         }
       }
     }
   }
-  bc[n] = mk2<R>(a0, a1);
+  return mk2<R>(a0, a1);
 }
 
 template <typename R>
-__global__ void k_prolong_add(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ xc,
-                              typename Vec2<R>::type* __restrict__ xf) {
-  NC_NODE_FLAT(gf);
-  if (k == gf.nz) return;
-  const int n = pidx + gf.NXY * k;
+__global__ void k_restrict(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ rf,
+                           typename Vec2<R>::type* __restrict__ bc) {
+  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pidx >= gc.NXY) return;
+  const int K = blockIdx.y;
+  const int J = pidx / gc.NX;
+  const int I = pidx - J * gc.NX;
+  bc[pidx + gc.NXY * K] = restrict_node<R>(gf, rf, I, J, K, K >= gc.nz, LdPlain());
+}
+
+// Trilinear interpolation of the coarse correction at fine node (i, j, k), added to xf.
+template <typename R, typename LD>
+__device__ __forceinline__ void prolong_node(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* xc,
+                                             typename Vec2<R>::type* xf, int n, int i, int j, int k, LD ld) {
   const int ci = i >> 1, cj = j >> 1, ck = k >> 1;
   const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
   const R wi = (i & 1) ? R(0.5) : R(1), wj = (j & 1) ? R(0.5) : R(1), wk = (k & 1) ? R(0.5) : R(1);
@@ -291,15 +307,23 @@ __global__ void k_prolong_add(Grid gf, Grid gc, const typename Vec2<R>::type* __
     for (int b = 0; b < nj; ++b) {
       const int row = gc.NX * (cj + b) + gc.NXY * (ck + c) + ci;
       for (int a = 0; a < ni; ++a) {
-        const typename Vec2<R>::type v = xc[row + a];
+        const typename Vec2<R>::type v = ld(xc + row + a);
         a0 += v.x;
         a1 += v.y;
       }
     }
-  typename Vec2<R>::type o = xf[n];
+  typename Vec2<R>::type o = ld(xf + n);
   o.x += w * a0;
   o.y += w * a1;
   xf[n] = o;
+}
+
+template <typename R>
+__global__ void k_prolong_add(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ xc,
+                              typename Vec2<R>::type* __restrict__ xf) {
+  NC_NODE_FLAT(gf);
+  if (k == gf.nz) return;
+  prolong_node<R>(gf, gc, xc, xf, pidx + gf.NXY * k, i, j, k, LdPlain());
 }
 
 template <typename R>
@@ -336,7 +360,9 @@ __global__ void k_from_mg(const typename Vec2<R>::type* __restrict__ x, double2*
 
 // ---- assembled 27-point block stencils of the coarse levels ----------------------------------
 // Slot of offset (oi,oj,ok) in {-1,0,1}^3 and block entry (f,g): ((o * 4) + 2 f + g), o = (oi+1) +
-// 3 (oj+1) + 9 (ok+1). Storage is structure-of-arrays: S[slot * nn + node], 108 slots.
+// 3 (oj+1) + 9 (ok+1). Storage: one 2x2 block per (offset, node), blocks of an offset contiguous over
+// the nodes: S[(o * nn + node) * 4 + 2 f + g] (27 planes of 4-vectors; a warp's loads of one offset
+// are contiguous 16-byte vectors).
 
 template <typename R>
 __global__ void k_stencil_build(Grid g, const R* __restrict__ ebe, R* __restrict__ S) {
@@ -375,11 +401,68 @@ __global__ void k_stencil_build(Grid g, const R* __restrict__ ebe, R* __restrict
     }
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) S[(long long)(o * 4 + q) * g.nn + n] = acc[q];
+  for (int q = 0; q < 4; ++q) S[((long long)o * g.nn + n) * 4 + q] = acc[q];
+}
+
+// One 2x2 stencil block (entries (0,0), (0,1), (1,0), (1,1)); read-only data.
+template <typename R> struct Blk4 { R a00, a01, a10, a11; };
+__device__ __forceinline__ Blk4<float> ld_blk(const float* __restrict__ S, int idx) {
+  const float4 v = reinterpret_cast<const float4*>(S)[idx];
+  return Blk4<float>{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Blk4<double> ld_blk(const double* __restrict__ S, int idx) {
+  const double2 u = reinterpret_cast<const double2*>(S)[2 * idx];
+  const double2 v = reinterpret_cast<const double2*>(S)[2 * idx + 1];
+  return Blk4<double>{u.x, u.y, v.x, v.y};
 }
 
 // y = A x (MODE 0), r = b - A x (MODE 1) or x_new = x + omega D^-1 (b - A x) (MODE 2), with A the
-// assembled stencil or (TR) its transpose. One thread per node, gathers its 27 neighbours.
+// assembled stencil or (TR) its transpose, at node n = (i, j, k) below the top plane: gathers the
+// 27 neighbours. A neighbour outside the grid is read at the node itself (always in range) and its
+// value replaced by zero, so the loop has no branches and all 54 loads can be in flight together.
+// S and dinv are read-only; x and b go through the load policy.
+template <typename R, bool TR, int MODE, typename LD>
+__device__ __forceinline__ void stencil_node(const Grid& g, const R* __restrict__ S,
+                                             const typename Vec2<R>::type* x, const typename Vec2<R>::type* b,
+                                             const R* __restrict__ dinv, R omega, typename Vec2<R>::type* out,
+                                             int n, int i, int j, int k, LD ld) {
+  const int nn = (int)g.nn;
+  typename Vec2<R>::type xv[27];
+  Blk4<R> c[27];
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    const int oi = o % 3 - 1, oj = (o / 3) % 3 - 1, ok = o / 9 - 1;
+    const bool inside = !((oi < 0 && i == 0) || (oi > 0 && i == g.nx) || (oj < 0 && j == 0) ||
+                          (oj > 0 && j == g.ny) || (ok < 0 && k == 0));
+    const int m = inside ? n + oi + g.NX * oj + g.NXY * ok : n;
+    xv[o] = ld(x + m);
+    c[o] = TR ? ld_blk(S, (26 - o) * nn + m) : ld_blk(S, o * nn + n);   // TR: offset -o seen from m
+    if (!inside) { xv[o].x = R(0); xv[o].y = R(0); }
+  }
+  R y0 = R(0), y1 = R(0);
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    if (!TR) {
+      y0 += c[o].a00 * xv[o].x + c[o].a01 * xv[o].y;
+      y1 += c[o].a10 * xv[o].x + c[o].a11 * xv[o].y;
+    } else {
+      y0 += c[o].a00 * xv[o].x + c[o].a10 * xv[o].y;
+      y1 += c[o].a01 * xv[o].x + c[o].a11 * xv[o].y;
+    }
+  }
+  if (MODE == 0) { out[n] = mk2<R>(y0, y1); return; }
+  const typename Vec2<R>::type bb = ld(b + n);
+  const R r0 = bb.x - y0, r1 = bb.y - y1;
+  if (MODE == 1) { out[n] = mk2<R>(r0, r1); return; }
+  const R* d = dinv + 4 * n;
+  R z0, z1;
+  if (TR) { z0 = d[0] * r0 + d[2] * r1; z1 = d[1] * r0 + d[3] * r1; }
+  else { z0 = d[0] * r0 + d[1] * r1; z1 = d[2] * r0 + d[3] * r1; }
+  const typename Vec2<R>::type xs = ld(x + n);
+  out[n] = mk2<R>(xs.x + omega * z0, xs.y + omega * z1);
+}
+
+// One thread per node (flat z-plane launch); the top (Dirichlet) plane gets 0.
 template <typename R, bool TR, int MODE>
 __global__ void __launch_bounds__(128) k_stencil_apply(Grid g, const R* __restrict__ S,
                                                        const typename Vec2<R>::type* __restrict__ x,
@@ -389,35 +472,7 @@ __global__ void __launch_bounds__(128) k_stencil_apply(Grid g, const R* __restri
   NC_NODE_FLAT(g);
   const int n = pidx + g.NXY * k;
   if (k == g.nz) { out[n] = mk2<R>(R(0), R(0)); return; }
-  const int nn = (int)g.nn;
-  R y0 = R(0), y1 = R(0);
-#pragma unroll
-  for (int o = 0; o < 27; ++o) {
-    const int oi = o % 3 - 1, oj = (o / 3) % 3 - 1, ok = o / 9 - 1;
-    if ((oi < 0 && i == 0) || (oi > 0 && i == g.nx) || (oj < 0 && j == 0) || (oj > 0 && j == g.ny) ||
-        (ok < 0 && k == 0))
-      continue;
-    const int m = n + oi + g.NX * oj + g.NXY * ok;
-    const typename Vec2<R>::type xv = x[m];
-    if (!TR) {
-      y0 += S[(o * 4 + 0) * nn + n] * xv.x + S[(o * 4 + 1) * nn + n] * xv.y;
-      y1 += S[(o * 4 + 2) * nn + n] * xv.x + S[(o * 4 + 3) * nn + n] * xv.y;
-    } else {
-      const int ro = 26 - o;   // offset -o seen from the neighbour
-      y0 += S[(ro * 4 + 0) * nn + m] * xv.x + S[(ro * 4 + 2) * nn + m] * xv.y;
-      y1 += S[(ro * 4 + 1) * nn + m] * xv.x + S[(ro * 4 + 3) * nn + m] * xv.y;
-    }
-  }
-  if (MODE == 0) { out[n] = mk2<R>(y0, y1); return; }
-  const typename Vec2<R>::type bb = b[n];
-  const R r0 = bb.x - y0, r1 = bb.y - y1;
-  if (MODE == 1) { out[n] = mk2<R>(r0, r1); return; }
-  const R* d = dinv + 4 * n;
-  R z0, z1;
-  if (TR) { z0 = d[0] * r0 + d[2] * r1; z1 = d[1] * r0 + d[3] * r1; }
-  else { z0 = d[0] * r0 + d[1] * r1; z1 = d[2] * r0 + d[3] * r1; }
-  const typename Vec2<R>::type xv = x[n];
-  out[n] = mk2<R>(xv.x + omega * z0, xv.y + omega * z1);
+  stencil_node<R, TR, MODE>(g, S, x, b, dinv, omega, out, n, i, j, k, LdPlain());
 }
 
 // ---- coarsest level: FP32 Gauss-Jordan inverse with partial pivoting (one block) ------------------
@@ -623,6 +678,114 @@ __global__ void __launch_bounds__(256) k_coarse_fix(const float* __restrict__ Ai
   for (int q = nf + blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += gridDim.x * blockDim.x) x[q] = R(0);
 }
 
+// ---- fused multigrid tail (one thread-block cluster) ---------------------------------------------
+// The steps of vcycle() on levels l0 .. L-1 in launch order; every step is a grid-stride loop over
+// the cluster's threads followed by a cluster barrier (release/acquire at cluster scope, after a
+// fence). Vectors written inside the kernel are read through L2 (LdCG).
+template <typename R, bool TR>
+__global__ void __launch_bounds__(1024, 1) k_mg_tail(const TailArgs<R> A) {
+  typedef typename Vec2<R>::type V;
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  const int T = blockDim.x * gridDim.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const LdCG ld;
+  const int L = A.nlev;
+  V* x[kTailMaxLevels];
+  V* xn[kTailMaxLevels];
+#pragma unroll
+  for (int l = 0; l < kTailMaxLevels; ++l) {
+    x[l] = l < L ? A.lev[l].x : nullptr;
+    xn[l] = l < L ? A.lev[l].xn : nullptr;
+  }
+  auto barrier = [&]() { __threadfence(); cl.sync(); };
+  auto smooth = [&](int l) {   // xn = x + omega D^-1 (b - A x), then swap
+    const TailLevel<R>& d = A.lev[l];
+    for (int n = t; n < (int)d.g.nn; n += T) {
+      const int i = n % d.g.NX, j = (n / d.g.NX) % d.g.NY, k = n / d.g.NXY;
+      if (k == d.g.nz) xn[l][n] = mk2<R>(R(0), R(0));
+      else stencil_node<R, TR, 2>(d.g, d.S, x[l], d.b, d.dinv, A.omega, xn[l], n, i, j, k, ld);
+    }
+    barrier();
+    V* tmp = x[l]; x[l] = xn[l]; xn[l] = tmp;
+  };
+  // descent: pre-smoothing, residual, restriction
+  for (int l = 0; l < L - 1; ++l) {
+    const TailLevel<R>& d = A.lev[l];
+    for (int n = t; n < (int)d.g.nn; n += T) {   // first sweep from x = 0: x = omega D^-1 b
+      const V bb = ld(d.b + n);
+      const R* dd = d.dinv + 4 * n;
+      const R z0 = TR ? dd[0] * bb.x + dd[2] * bb.y : dd[0] * bb.x + dd[1] * bb.y;
+      const R z1 = TR ? dd[1] * bb.x + dd[3] * bb.y : dd[2] * bb.x + dd[3] * bb.y;
+      x[l][n] = mk2<R>(A.omega * z0, A.omega * z1);
+    }
+    barrier();
+    for (int it = 1; it < A.nu1; ++it) smooth(l);
+    for (int n = t; n < (int)d.g.nn; n += T) {   // residual into xn
+      const int i = n % d.g.NX, j = (n / d.g.NX) % d.g.NY, k = n / d.g.NXY;
+      if (k == d.g.nz) xn[l][n] = mk2<R>(R(0), R(0));
+      else stencil_node<R, TR, 1>(d.g, d.S, x[l], d.b, d.dinv, A.omega, xn[l], n, i, j, k, ld);
+    }
+    barrier();
+    const Grid& gc = A.lev[l + 1].g;
+    for (int n = t; n < (int)gc.nn; n += T) {
+      const int I = n % gc.NX, J = (n / gc.NX) % gc.NY, K = n / gc.NXY;
+      A.lev[l + 1].b[n] = restrict_node<R>(d.g, xn[l], I, J, K, K >= gc.nz, ld);
+    }
+    barrier();
+  }
+  // coarsest level: x0 = Ainv32 b (FP32), r = b - A x0 (FP64), x = x0 + Ainv32 r (FP32)
+  {
+    const int nf = A.nf;
+    double* bd = A.cw;
+    double* x0 = A.cw + nf;
+    double* rd = A.cw + 2 * nf;
+    const R* bc = (const R*)A.lev[L - 1].b;
+    R* xc = (R*)x[L - 1];
+    const int lane = t & 31, gw = t >> 5, W = T >> 5;
+    for (int c = t; c < nf; c += T) bd[c] = (double)ld(bc + c);
+    barrier();
+    for (int r = gw; r < nf; r += W) {
+      float acc = 0.f;
+      for (int c = lane; c < nf; c += 32)
+        acc += (TR ? A.Ainv32[(long long)c * nf + r] : A.Ainv32[(long long)r * nf + c]) * (float)ld(bd + c);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) x0[r] = (double)acc;
+    }
+    barrier();
+    for (int r = gw; r < nf; r += W) {
+      double acc = 0.0;
+      for (int c = lane; c < nf; c += 32)
+        acc += (TR ? A.Ac[(long long)c * nf + r] : A.Ac[(long long)r * nf + c]) * ld(x0 + c);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) rd[r] = ld(bd + r) - acc;
+    }
+    barrier();
+    for (int r = gw; r < nf; r += W) {
+      float acc = 0.f;
+      for (int c = lane; c < nf; c += 32)
+        acc += (TR ? A.Ainv32[(long long)c * nf + r] : A.Ainv32[(long long)r * nf + c]) * (float)ld(rd + c);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) xc[r] = (R)(ld(x0 + r) + (double)acc);
+    }
+    const int n2 = (int)(2 * A.lev[L - 1].g.nn);
+    for (int q = nf + t; q < n2; q += T) xc[q] = R(0);
+    barrier();
+  }
+  // ascent: prolongation and post-smoothing
+  for (int l = L - 2; l >= 0; --l) {
+    const TailLevel<R>& d = A.lev[l];
+    for (int n = t; n < (int)d.g.nn; n += T) {
+      const int i = n % d.g.NX, j = (n / d.g.NX) % d.g.NY, k = n / d.g.NXY;
+      if (k < d.g.nz) prolong_node<R>(d.g, A.lev[l + 1].g, x[l + 1], x[l], n, i, j, k, ld);
+    }
+    barrier();
+    for (int it = 0; it < A.nu2; ++it) smooth(l);
+  }
+}
+
 }  // namespace
 
 template <typename R>
@@ -809,6 +972,54 @@ cudaError_t launch_from_mg(const typename Vec2<R>::type* x, double* z, long long
   return cudaGetLastError();
 }
 
+// Cluster size of the tail kernel: 16 (non-portable) where the device schedules it, else 8.
+template <typename R, bool TR>
+static int tail_cluster_size() {
+  static int cs = 0;
+  if (cs) return cs;
+  cs = 8;
+  if (cudaFuncSetAttribute(k_mg_tail<R, TR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(1024);
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_mg_tail<R, TR>, &cfg) == cudaSuccess && nclusters > 0) cs = 16;
+  }
+  cudaGetLastError();
+  return cs;
+}
+
+template <typename R>
+cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st, Counters* c) {
+  if (a.nlev < 2 || a.nlev > kTailMaxLevels || a.nf > 1024) return cudaErrorInvalidValue;
+  const int cs = transpose ? tail_cluster_size<R, true>() : tail_cluster_size<R, false>();
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(1024);
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = transpose ? cudaLaunchKernelEx(&cfg, k_mg_tail<R, true>, a) : cudaLaunchKernelEx(&cfg, k_mg_tail<R, false>, a);
+  if (c) {
+    c->launches += 1;
+    for (int l = 0; l + 1 < a.nlev; ++l)   // stencil sweeps: 108 coefficients + x, b, out per node
+      c->bytes += sizeof(R) * 114.0 * a.lev[l].g.nn * (a.nu1 + a.nu2 + 1);
+  }
+  return e;
+}
+
 #define NC_INSTANTIATE_MG(R)                                                                                    \
   template cudaError_t launch_galerkin_fine<R>(const Grid&, const Grid&, const Phys&, const Vec2<R>::type*,   \
                                                const Vec2<R>::type*, R*, R*, cudaStream_t, Counters*);         \
@@ -835,7 +1046,8 @@ cudaError_t launch_from_mg(const typename Vec2<R>::type* x, double* z, long long
   template cudaError_t launch_stencil_build<R>(const Grid&, const R*, R*, cudaStream_t, Counters*);           \
   template cudaError_t launch_stencil_apply<R>(const Grid&, const R*, const Vec2<R>::type*,                  \
                                                const Vec2<R>::type*, const R*, R, Vec2<R>::type*, bool, int, \
-                                               cudaStream_t, Counters*);
+                                               cudaStream_t, Counters*);                                       \
+  template cudaError_t launch_mg_tail<R>(const TailArgs<R>&, bool, cudaStream_t, Counters*);
 
 NC_INSTANTIATE_MG(float)
 NC_INSTANTIATE_MG(double)

@@ -41,6 +41,13 @@ struct Counters {
 // J^T w with design derivatives; one element-Jacobian column.
 const double kFlopsResidual = 801.0, kFlopsState = 375.0, kFlopsJv = 928.0, kFlopsJtv = 953.0,
              kFlopsSens = 1058.0, kFlopsJacColumn = 696.0;
+// The same element code in double-float arithmetic, in FP32 flops: a double-float sum is 11 FP32
+// additions, a product 1 multiplication + 3 FMAs + 3 additions (10 flops). Adds / multiplies per
+// element: residual 323 / 478, element state 155 / 220, J^T w part 371 / 582, with design
+// derivatives 419 / 639.
+const double kDfAdd = 11.0, kDfMul = 10.0;
+const double kFlopsResidualDF = 323 * kDfAdd + 478 * kDfMul, kFlopsStateDF = 155 * kDfAdd + 220 * kDfMul,
+             kFlopsJtvDF = 371 * kDfAdd + 582 * kDfMul, kFlopsSensDF = 419 * kDfAdd + 639 * kDfMul;
 
 // ---------------- element operators (nc_kernels_elem.cu) ----------------
 // out (2N doubles) = R(s); Dirichlet rows = s. s: double2 per node; mat: (kappa, k) per element.
@@ -56,6 +63,16 @@ cudaError_t launch_jtv_f64(const Grid& g, const Phys& ph, const double2* s, cons
 cudaError_t launch_sens_elem(const Grid& g, const Phys& ph, const double2* s, const double2* lam,
                              const double2* mat, const double2* dmat, double* out, cudaStream_t st,
                              Counters* c);
+// Double-float (df64, about 48-bit) variants of the residual, J^T w and the sensitivities for the
+// mixed-precision path: FP64 inputs are split into float4 (hi, lo) scratch arrays (s_df, w_df,
+// l_df: one per node) and the materials come pre-split (mat_df: one per element); outputs are FP64.
+cudaError_t launch_split2(const double2* x, float4* y, long long n, cudaStream_t st, Counters* c);
+cudaError_t launch_residual_df(const Grid& g, const Phys& ph, const double2* s, const float4* mat_df,
+                               float4* s_df, double* out, cudaStream_t st, Counters* c);
+cudaError_t launch_jtv_df(const Grid& g, const Phys& ph, const double2* s, const float4* mat_df, float4* s_df,
+                          const double2* w, float4* w_df, double* out, cudaStream_t st, Counters* c);
+cudaError_t launch_sens_df(const Grid& g, const Phys& ph, const double2* s, const double2* lam, const float4* mat_df,
+                           const double2* dmat, float4* s_df, float4* l_df, double* out, cudaStream_t st, Counters* c);
 // Centroid Darcy velocity (3 per element).
 cudaError_t launch_u_centroid(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
                               double* u, cudaStream_t st, Counters* c);
@@ -147,9 +164,36 @@ template <typename R> struct MGLevelDev {
   typename Vec2<R>::type* b;
   typename Vec2<R>::type* y;
   R* ebe;       // 256 per element (levels >= 1)
-  R* S;         // assembled 27-point 2x2-block stencil, 108 per node, SoA (levels 1 .. L-2)
+  R* S;         // assembled 27-point 2x2-block stencil, 108 per node, 27 planes of 2x2 blocks (levels 1 .. L-2)
   R* dinv;      // 4 per node (2x2 block-diagonal inverse, row major), 0 on Dirichlet nodes
 };
+
+// Fused multigrid tail: the part of a V-cycle on levels l0 .. L-1 (the small coarse grids) run by
+// one thread-block cluster, its steps separated by cluster barriers instead of kernel launches.
+// lev[0] is level l0, lev[nlev-1] the coarsest (solved with Ainv32 / Ac as launch_coarse_solve).
+// The kernel swaps x and xn of each non-coarsest level (nu1 - 1 + nu2) times, like the launch
+// sequence; the caller applies the same swaps to its pointers.
+const int kTailMaxLevels = 8;
+template <typename R> struct TailLevel {
+  Grid g;
+  const R* S;
+  const R* dinv;
+  typename Vec2<R>::type* x;
+  typename Vec2<R>::type* xn;
+  typename Vec2<R>::type* b;
+};
+template <typename R> struct TailArgs {
+  TailLevel<R> lev[kTailMaxLevels];
+  int nlev;
+  const double* Ac;
+  const float* Ainv32;
+  double* cw;   // 3 nf
+  int nf;
+  R omega;
+  int nu1, nu2;
+};
+template <typename R>
+cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st, Counters* c);
 
 // Level-0 set-up: element Jacobians of J(s) (R arithmetic) -> block diagonal of level 0 and
 // Galerkin element matrices of level 1 (P^T J P with trilinear P).

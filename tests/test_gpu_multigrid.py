@@ -1,0 +1,40 @@
+"""The fused multigrid tail (the small coarse levels of a V-cycle in one thread-block cluster
+kernel) performs the steps of the separate launches in the same order with the same node formulas;
+only the compiler's fusion of multiply-adds may differ between the two kernels. So the preconditioner
+agrees to FP32 rounding, the solver takes the same iterations (within one) and the state, adjoint and
+sensitivities agree far inside the solver tolerance, for the V-cycle and its transpose."""
+
+import numpy as np
+import pytest
+
+from synthetic import filtered_random
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nc():
+    from paper_1904_00182_gb300 import build
+    build.build()
+    import paper_1904_00182_gb300
+    return paper_1904_00182_gb300
+
+
+@pytest.mark.parametrize("shape,levels", [((32, 32, 32), 0), ((48, 40, 32), 4)])
+def test_fused_tail_matches_launches(nc, shape, levels):
+    nx, ny, nz = shape
+    rho = filtered_random(nx, ny, nz, seed=9, volfrac=0.2)
+    out = {}
+    for tail in (0, 1 << 30):
+        pb = nc.Problem(nx, ny, nz, 1.0 / nz, alpha=1e4, mg_levels=levels, mg_tail_nodes=tail)
+        pb.set_design(rho)
+        st = pb.solve_state()
+        P, T, _ = pb.get_fields(velocity=False)
+        f, ast = pb.solve_adjoint()
+        g = pb.sensitivities()
+        out[tail] = (P.cpu().numpy(), T.cpu().numpy(), g.cpu().numpy(), st["krylov_its"], ast["krylov_its"])
+        pb.close()
+    a, b = out[0], out[1 << 30]
+    assert abs(a[3] - b[3]) <= 1 and abs(a[4] - b[4]) <= 1
+    for x, y, tol in zip(a[:3], b[:3], (1e-8, 1e-8, 1e-6)):
+        assert np.linalg.norm(x - y) <= tol * np.linalg.norm(y)

@@ -103,6 +103,32 @@ def test_jacobian_products(lib, shape, alpha, seed):
 
 
 @pytest.mark.parametrize("shape,alpha,seed", CASES)
+def test_double_float_outer_operators(lib, shape, alpha, seed):
+    """Mixed path, outer arithmetic double-float: R(s) and J(s)^T w against the FP64 oracle.
+    A double-float sum errs by at most about 2 u^2 (|a| + |b|) with u = 2^-24, 64 times the FP64
+    unit roundoff, so the FP64 operator bound (1e-12, summation order only) widens to 1e-11."""
+    gp, op, _ = make_pair(lib, shape, alpha, seed, precision=lib.NC_PREC_MIXED)
+    assert gp.params.outer_arith == lib.NC_ARITH_DF64
+    for trial in range(2):
+        s = random_state(op, 20 + trial)
+        R, n2 = gp.eval_residual(s)
+        Ro = op.residual(s)
+        assert rel(R.cpu().numpy(), Ro) < 1e-11
+        assert n2 == pytest.approx(np.dot(Ro[op.free], Ro[op.free]), rel=1e-11)
+    s = random_state(op, 5)
+    rng = np.random.default_rng(6)
+    w = rng.standard_normal(s.shape)
+    w[op.dir_mask] = 0.0
+    J = op.jacobian_full(s)
+    f = op.free
+    jt_expect = np.zeros_like(w)
+    jt_expect[f] = J[f][:, f].T @ w[f]
+    jt = gp.apply_jacobian_transpose(s, w).cpu().numpy()
+    assert rel(jt, jt_expect) < 1e-11
+    gp.close()
+
+
+@pytest.mark.parametrize("shape,alpha,seed", CASES)
 @pytest.mark.parametrize("precision,tol", [(1, 1e-8), (0, 1e-6)])
 def test_state_adjoint_sensitivities(lib, shape, alpha, seed, precision, tol):
     gp, op, rho = make_pair(lib, shape, alpha, seed, precision=precision)
