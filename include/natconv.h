@@ -110,6 +110,9 @@ typedef struct {
   int mg_tail_nodes;    /* the multigrid levels below the finest with at most this many nodes, down
                            to the coarsest, run as one fused kernel on a thread-block cluster (the
                            same arithmetic as separate launches); 0: separate launches [5000] */
+  double mg_reuse_below; /* a Newton step whose relative residual is at most this keeps the multigrid
+                            hierarchy of the previous step (lagged preconditioner); 0: rebuild at
+                            every step [1e-4] */
   int outer_arith;      /* NC_PREC_MIXED only: arithmetic of the Newton residual, the adjoint
                            refinement residual J^T lambda and the sensitivities. NC_ARITH_DF64:
                            double-float (hi + lo pairs of floats, about 48 significant bits, on the
@@ -130,6 +133,7 @@ typedef struct {
   double t_total_ms;     /* wall time of the call */
   double alg_bytes;      /* algorithmic bytes of the operator kernels launched */
   long long kernel_launches; /* library kernels launched by the call */
+  int mg_setups;         /* multigrid hierarchies built by the call */
 } nc_stats;
 
 /* Fill *p with the defaults. Returns NC_ERR_ARG if p is NULL. */

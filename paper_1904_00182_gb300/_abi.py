@@ -52,7 +52,7 @@ class Params(ctypes.Structure):
         ("nu_post", ctypes.c_int), ("omega", ctypes.c_double), ("filter_rtol", ctypes.c_double),
         ("timeout_s", ctypes.c_double), ("adjoint_rtol", ctypes.c_double), ("coarse_refactor", ctypes.c_int),
         ("krylov_eta_min", ctypes.c_double), ("adjoint_eta_first", ctypes.c_double),
-        ("mg_tail_nodes", ctypes.c_int), ("outer_arith", ctypes.c_int),
+        ("mg_tail_nodes", ctypes.c_int), ("mg_reuse_below", ctypes.c_double), ("outer_arith", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -65,6 +65,7 @@ class Stats(ctypes.Structure):
         ("ramped", ctypes.c_int), ("rel_residual", ctypes.c_double), ("res_hist", ctypes.c_double * 64),
         ("krylov_hist", ctypes.c_int * 64), ("t_setup_ms", ctypes.c_double), ("t_krylov_ms", ctypes.c_double),
         ("t_total_ms", ctypes.c_double), ("alg_bytes", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
+        ("mg_setups", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -73,7 +74,7 @@ class Stats(ctypes.Structure):
                     ramped=bool(self.ramped), rel_residual=self.rel_residual,
                     res_hist=list(self.res_hist[:n]), krylov_hist=list(self.krylov_hist[:n]),
                     t_setup_ms=self.t_setup_ms, t_krylov_ms=self.t_krylov_ms, t_total_ms=self.t_total_ms,
-                    alg_bytes=self.alg_bytes, kernel_launches=self.kernel_launches)
+                    alg_bytes=self.alg_bytes, kernel_launches=self.kernel_launches, mg_setups=self.mg_setups)
 
 
 _lib = None

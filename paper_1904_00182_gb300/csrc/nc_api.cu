@@ -764,9 +764,17 @@ nc_status newton(nc_problem* pb, double rtol, double ref, nc_stats* stats, bool*
     const double eta_min = pb->par.krylov_eta_min > 0 ? pb->par.krylov_eta_min : 1e-12;
     eta = std::max(std::min(eta, pb->par.krylov_rtol), eta_min);
     double t0 = now_s();
-    CKS(mg_setup_any(pb, pb->first_setup));
-    pb->first_setup = false;
-    pb->mg_ready = true;
+    // lagged preconditioner: once the residual is below mg_reuse_below, the hierarchy of the previous
+    // Newton step is kept (the state changes little; FGMRES absorbs the difference)
+    if (!pb->mg_ready || rel > pb->par.mg_reuse_below) {
+      CKS(mg_setup_any(pb, pb->first_setup));
+      pb->first_setup = false;
+      pb->mg_ready = true;
+      if (stats) stats->mg_setups++;
+    } else if (pb->par.precision != NC_PREC_FP64) {
+      // the Krylov operator and the finest multigrid level use the current state
+      PCK(NC_PROF_MG_COARSE_SETUP, launch_cast_d2f((float*)pb->s32, (const double*)pb->s, 2 * pb->g.nn, pb->st, &pb->cnt));
+    }
     double t1 = now_s();
     PCK(NC_PROF_OTHER, launch_scale_copy(pb->rhs, pb->R, -1.0, n, pb->st, &pb->cnt));
     PCK(NC_PROF_OTHER, launch_zero_dirichlet(pb->g, pb->rhs, pb->st, &pb->cnt));
@@ -849,6 +857,7 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (p->precision != NC_PREC_MIXED && p->precision != NC_PREC_FP64) { *why = "unknown precision"; return NC_ERR_ARG; }
   if (p->outer_arith != NC_ARITH_DF64 && p->outer_arith != NC_ARITH_FP64) { *why = "unknown outer_arith"; return NC_ERR_ARG; }
   if (p->mg_tail_nodes < 0) { *why = "mg_tail_nodes must be >= 0"; return NC_ERR_ARG; }
+  if (!(p->mg_reuse_below >= 0.0)) { *why = "mg_reuse_below must be >= 0"; return NC_ERR_ARG; }
   if (!(p->newton_rtol > 0) || p->newton_maxit < 0 || p->krylov_maxit < 1) { *why = "bad tolerances"; return NC_ERR_ARG; }
   if (!(p->filter_radius >= 0) || !(p->filter_rtol > 0)) { *why = "bad filter parameters"; return NC_ERR_ARG; }
   Grid g0 = make_grid(g->nx, g->ny, g->nz, g->h);
@@ -994,6 +1003,7 @@ nc_status nc_default_params(nc_params* p) {
   p->adjoint_eta_first = 0.0;
   p->outer_arith = NC_ARITH_DF64;
   p->mg_tail_nodes = 5000;
+  p->mg_reuse_below = 1e-4;
   return NC_OK;
 }
 
