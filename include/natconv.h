@@ -65,6 +65,8 @@ typedef enum {
 enum { NC_PREC_MIXED = 0, NC_PREC_FP64 = 1 };
 /* Arithmetic of the outer residuals on the mixed-precision path (nc_params.outer_arith). */
 enum { NC_ARITH_DF64 = 0, NC_ARITH_FP64 = 1 };
+/* Krylov basis storage on the mixed-precision path (nc_params.krylov_basis). */
+enum { NC_BASIS_FP64 = 0, NC_BASIS_FP32 = 1 };
 enum { NC_OBJ_MEAN_T_HEATED = 0 };
 
 typedef struct nc_problem nc_problem;
@@ -92,9 +94,10 @@ typedef struct {
   double krylov_rtol;   /* upper bound of the FGMRES relative tolerance per Newton step [1e-2] */
   int krylov_maxit;     /* FGMRES iterations per linear solve [300] */
   int restart;          /* FGMRES restart length, <= 64 [30] */
-  int precision;        /* NC_PREC_MIXED (FP32 multigrid, Krylov operator and Krylov basis; outer
-                           residuals in outer_arith; FP64 Hessenberg, Newton update and coarse
-                           residual) or NC_PREC_FP64 (IEEE FP64 throughout) [MIXED] */
+  int precision;        /* NC_PREC_MIXED (FP32 multigrid preconditioner and Krylov operator; Newton
+                           residual, adjoint residual and sensitivities in outer_arith, Krylov
+                           orthogonalisation in krylov_basis, coarse-grid residual, Hessenberg and
+                           Newton update in FP64) or NC_PREC_FP64 (IEEE FP64 throughout) [MIXED] */
   int mg_levels;        /* 0: coarsen while every dimension is even [0] */
   int nu_pre, nu_post;  /* smoothing sweeps; the first pre-sweep starts from x = 0 [1, 2] */
   double omega;         /* damping of the block-Jacobi smoother [0.9] */
@@ -114,9 +117,15 @@ typedef struct {
                             hierarchy of the previous step (lagged preconditioner); 0: rebuild at
                             every step [1e-4] */
   int outer_arith;      /* NC_PREC_MIXED only: arithmetic of the Newton residual, the adjoint
-                           refinement residual J^T lambda and the sensitivities. NC_ARITH_DF64:
-                           double-float (hi + lo pairs of floats, about 48 significant bits, on the
-                           FP32 units; inputs and outputs FP64); NC_ARITH_FP64: IEEE FP64 [DF64] */
+                           refinement residual J^T lambda and the sensitivities. NC_ARITH_FP64: IEEE
+                           FP64; NC_ARITH_DF64: double-float (hi + lo pairs of floats, about 48
+                           significant bits, on the FP32 units; inputs and outputs FP64) [FP64] */
+  int krylov_basis;     /* NC_PREC_MIXED only, fixed at creation: FGMRES basis vectors and their
+                           Gram-Schmidt in NC_BASIS_FP64 or NC_BASIS_FP32 (FP32 products, FP64 sums
+                           across threads) [FP64] */
+  double krylov_reorth; /* classical Gram-Schmidt takes a second pass when the first kept less than
+                           this fraction of ||w||^2 (1/2: the DGKS test; 1: always); <= 0: the
+                           default of the basis type [0] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */

@@ -11,6 +11,8 @@ NC_PREC_MIXED = 0
 NC_PREC_FP64 = 1
 NC_ARITH_DF64 = 0
 NC_ARITH_FP64 = 1
+NC_BASIS_FP64 = 0
+NC_BASIS_FP32 = 1
 NC_OBJ_MEAN_T_HEATED = 0
 
 STATUS_NAMES = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_OOM", 3: "NC_ERR_CUDA", 4: "NC_ERR_DIVERGED",
@@ -53,6 +55,7 @@ class Params(ctypes.Structure):
         ("timeout_s", ctypes.c_double), ("adjoint_rtol", ctypes.c_double), ("coarse_refactor", ctypes.c_int),
         ("krylov_eta_min", ctypes.c_double), ("adjoint_eta_first", ctypes.c_double),
         ("mg_tail_nodes", ctypes.c_int), ("mg_reuse_below", ctypes.c_double), ("outer_arith", ctypes.c_int),
+        ("krylov_basis", ctypes.c_int), ("krylov_reorth", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -508,9 +508,10 @@ nc_status mg_setup_any(nc_problem* pb, bool refactor) {
 }
 
 // ---------------------------------------------------------------- FGMRES ------------
-// Krylov vectors are FP64 on the FP64 path and FP32 on the mixed-precision path, where the operator
-// (J or J^T on the FP32 state copy) and the preconditioner are FP32 as well; the Hessenberg matrix,
-// the Givens rotations and the update of the FP64 solution are FP64 in both.
+// Krylov vectors are FP64 (FP64 path; mixed path with NC_BASIS_FP64) or FP32 (mixed path with
+// NC_BASIS_FP32, where the operator J or J^T on the FP32 state copy and the preconditioner are FP32
+// as well). The Hessenberg matrix, the Givens rotations and the update of the FP64 solution are FP64
+// in every case.
 
 // z = M^-1 v for FP32 vectors: the V-cycle reads v in place and leaves its result in z.
 nc_status kry_precondition(nc_problem* pb, bool tr, const float* v, float* z) {
@@ -533,25 +534,31 @@ nc_status kry_precondition(nc_problem* pb, bool tr, const double* v, double* z) 
   return precondition(pb, tr, v, z);
 }
 
-nc_status kry_op(nc_problem* pb, bool tr, const float* z, float* w) {
+nc_status kry_op(nc_problem* pb, bool tr, bool fp32, const float* z, float* w) {
+  (void)fp32;
   PCK(NC_PROF_OUTER_OP32, launch_level0_apply<float>(pb->g, pb->ph, pb->s32, pb->mat32, (const float2*)z, (float2*)w,
                                                      tr, pb->st, &pb->cnt));
   return NC_OK;
 }
 
-nc_status kry_op(nc_problem* pb, bool tr, const double* z, double* w) {
-  return outer_op(pb, tr, false, z, w);
+nc_status kry_op(nc_problem* pb, bool tr, bool fp32, const double* z, double* w) {
+  return outer_op(pb, tr, fp32, z, w);
 }
+
+// Default re-orthogonalisation threshold of FP64 bases: a second pass only when the first cancelled
+// more than 99 % of the norm (two digits of the 16); an FP32 basis uses the DGKS value 1/2.
+const double kReorthFP64 = 1e-2;
 
 // Right-preconditioned flexible GMRES(m) with classical Gram-Schmidt applied twice. Solves
 // op(x) = b on the free DOFs from x = 0; stops when the (Arnoldi) residual is <= rtol ||b||.
 // b is not modified (it may be any FP64 work vector other than x and R_try).
 template <typename T>
-nc_status fgmres_t(nc_problem* pb, bool tr, T* V, T* Z, const double* b, double* x, double rtol, int maxit,
-                   int* its_out, double* relres_out) {
+nc_status fgmres_t(nc_problem* pb, bool tr, bool fp32, T* V, T* Z, const double* b, double* x, double rtol,
+                   int maxit, int* its_out, double* relres_out) {
   const long long n = 2 * pb->g.nn;
   const int m = pb->m;
-  const bool fp32 = sizeof(T) == 4;
+  // second Gram-Schmidt pass when the first kept less than this fraction of ||w||^2
+  const double thr = pb->par.krylov_reorth > 0 ? pb->par.krylov_reorth : (sizeof(T) == 4 ? 0.5 : kReorthFP64);
   CK(cudaMemsetAsync(x, 0, sizeof(double) * n, pb->st));
   double bb;
   CKS(norm2_free(pb, b, &bb));
@@ -576,7 +583,7 @@ nc_status fgmres_t(nc_problem* pb, bool tr, T* V, T* Z, const double* b, double*
       T* zj = Z + (long long)j * n;
       T* wv = V + (long long)(j + 1) * n;
       CKS(kry_precondition(pb, tr, vj, zj));
-      CKS(kry_op(pb, tr, zj, wv));
+      CKS(kry_op(pb, tr, fp32, zj, wv));
       double hn;
       if (j + 1 <= 32) {
         // CGS2 with coefficients kept on the device; one host synchronisation per iteration
@@ -584,14 +591,14 @@ nc_status fgmres_t(nc_problem* pb, bool tr, T* V, T* Z, const double* b, double*
         double* d2 = pb->dres + 66;
         // d1: V_i . w (i <= j) and w . w (w is V_{j+1}); d2: second-pass dots when re-orthogonalising
         PCK(NC_PROF_KRYLOV_VEC, launch_multidot(V, n, j + 2, wv, n, pb->part, d1, pb->st, &pb->cnt));
-        PCK(NC_PROF_KRYLOV_VEC, launch_cgs(wv, V, n, j + 1, d1, d2, n, pb->part, pb->st, &pb->cnt));
+        PCK(NC_PROF_KRYLOV_VEC, launch_cgs(wv, V, n, j + 1, d1, d2, n, thr, pb->part, pb->st, &pb->cnt));
         CK(cudaMemcpyAsync(pb->hres, pb->dres, sizeof(double) * 132, cudaMemcpyDeviceToHost, pb->st));
         CKS(sync(pb, "Gram-Schmidt"));
         // the device's test (DGKS on the Pythagorean norm) repeated on the same values
         double s1 = 0.0;
         for (int i = 0; i <= j; ++i) s1 += pb->hres[i] * pb->hres[i];
         const double ww = pb->hres[j + 1];
-        const bool fast = ww - s1 >= 0.5 * ww;
+        const bool fast = ww - s1 >= thr * ww;
         double hn2;
         if (fast) {
           for (int i = 0; i <= j; ++i) h[i] = pb->hres[i];
@@ -664,12 +671,13 @@ nc_status fgmres_t(nc_problem* pb, bool tr, T* V, T* Z, const double* b, double*
   }
 }
 
-// FGMRES on the FP64 path (fp32 false) or the mixed-precision path (fp32 true).
+// FGMRES on the FP64 path (fp32 false) or the mixed-precision path (fp32 true: FP32 operator and
+// preconditioner; basis as nc_params.krylov_basis).
 nc_status fgmres(nc_problem* pb, bool tr, bool fp32, const double* b, double* x, double rtol, int maxit,
                  int* its_out, double* relres_out) {
   if (fp32 != (pb->par.precision != NC_PREC_FP64)) return fail(pb, NC_ERR_ARG, "Krylov precision mismatch");
-  if (fp32) return fgmres_t<float>(pb, tr, pb->V32, pb->Z32, b, x, rtol, maxit, its_out, relres_out);
-  return fgmres_t<double>(pb, tr, pb->V, pb->Z, b, x, rtol, maxit, its_out, relres_out);
+  if (pb->V32) return fgmres_t<float>(pb, tr, fp32, pb->V32, pb->Z32, b, x, rtol, maxit, its_out, relres_out);
+  return fgmres_t<double>(pb, tr, fp32, pb->V, pb->Z, b, x, rtol, maxit, its_out, relres_out);
 }
 
 // ---------------------------------------------------------------- Newton ------------
@@ -856,6 +864,8 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (p->restart < 1 || p->restart > kMaxRestart) { *why = "restart must be in [1, 64]"; return NC_ERR_ARG; }
   if (p->precision != NC_PREC_MIXED && p->precision != NC_PREC_FP64) { *why = "unknown precision"; return NC_ERR_ARG; }
   if (p->outer_arith != NC_ARITH_DF64 && p->outer_arith != NC_ARITH_FP64) { *why = "unknown outer_arith"; return NC_ERR_ARG; }
+  if (p->krylov_basis != NC_BASIS_FP32 && p->krylov_basis != NC_BASIS_FP64) { *why = "unknown krylov_basis"; return NC_ERR_ARG; }
+  if (!(p->krylov_reorth <= 1.0)) { *why = "krylov_reorth must be <= 1"; return NC_ERR_ARG; }
   if (p->mg_tail_nodes < 0) { *why = "mg_tail_nodes must be >= 0"; return NC_ERR_ARG; }
   if (!(p->mg_reuse_below >= 0.0)) { *why = "mg_reuse_below must be >= 0"; return NC_ERR_ARG; }
   if (!(p->newton_rtol > 0) || p->newton_maxit < 0 || p->krylov_maxit < 1) { *why = "bad tolerances"; return NC_ERR_ARG; }
@@ -877,7 +887,7 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
   b += 6 * al(16 * nn);                 // R, R_try, dx, w, rhs, R0
   b += 3 * al(8 * ne) + al(24 * ne);    // rho, gamma_t, gsens, u
   b += 2 * al(16 * ne) + al(8 * ne) + 3 * al(8 * nn);   // mat, dmat, mat32, s32, v32, y32
-  const size_t ks = p->precision == NC_PREC_FP64 ? 8 : 4;   // Krylov basis entry size
+  const size_t ks = (p->precision == NC_PREC_FP64 || p->krylov_basis == NC_BASIS_FP64) ? 8 : 4;   // basis entry
   b += al(2 * ks * nn * (m + 1)) + al(2 * ks * nn * m);     // V, Z
   if (p->precision != NC_PREC_FP64) b += al(16 * ne) + 2 * al(16 * nn);   // mat_df, s_df, w_df
   b += al(8 * 66 * kReduceBlocksMax) + al(8 * 132);
@@ -1001,7 +1011,9 @@ nc_status nc_default_params(nc_params* p) {
   p->coarse_refactor = 0;
   p->krylov_eta_min = 0.0;
   p->adjoint_eta_first = 0.0;
-  p->outer_arith = NC_ARITH_DF64;
+  p->outer_arith = NC_ARITH_FP64;
+  p->krylov_basis = NC_BASIS_FP64;
+  p->krylov_reorth = 0.0;
   p->mg_tail_nodes = 5000;
   p->mg_reuse_below = 1e-4;
   return NC_OK;
@@ -1045,10 +1057,12 @@ nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream,
   A(dalloc(pb, &pb->rho, ne)); A(dalloc(pb, &pb->gamma_t, ne)); A(dalloc(pb, &pb->gsens, ne)); A(dalloc(pb, &pb->u, 3 * ne));
   A(dalloc(pb, &pb->mat, ne)); A(dalloc(pb, &pb->dmat, ne)); A(dalloc(pb, &pb->mat32, ne)); A(dalloc(pb, &pb->s32, nn));
   A(dalloc(pb, &pb->v32, nn)); A(dalloc(pb, &pb->y32, nn));
-  if (p->precision == NC_PREC_FP64) {
+  if (p->precision == NC_PREC_FP64 || p->krylov_basis == NC_BASIS_FP64) {
     A(dalloc(pb, &pb->V, (size_t)2 * nn * (pb->m + 1))); A(dalloc(pb, &pb->Z, (size_t)2 * nn * pb->m));
   } else {
     A(dalloc(pb, &pb->V32, (size_t)2 * nn * (pb->m + 1))); A(dalloc(pb, &pb->Z32, (size_t)2 * nn * pb->m));
+  }
+  if (p->precision != NC_PREC_FP64) {
     A(dalloc(pb, &pb->mat_df, ne)); A(dalloc(pb, &pb->s_df, nn)); A(dalloc(pb, &pb->w_df, nn));
   }
   A(dalloc(pb, &pb->part, 66 * kReduceBlocksMax)); A(dalloc(pb, &pb->dres, 132));
@@ -1099,8 +1113,9 @@ nc_status nc_set_params(nc_problem* pb, const nc_params* p) {
   std::string why;
   nc_status vs = validate(&gr, p, &why);
   if (vs != NC_OK) return fail(pb, vs, why);
-  if (p->precision != pb->par.precision || p->mg_levels != pb->par.mg_levels || p->restart != pb->par.restart)
-    return fail(pb, NC_ERR_ARG, "precision, mg_levels and restart are fixed at creation");
+  if (p->precision != pb->par.precision || p->mg_levels != pb->par.mg_levels || p->restart != pb->par.restart ||
+      p->krylov_basis != pb->par.krylov_basis)
+    return fail(pb, NC_ERR_ARG, "precision, mg_levels, restart and krylov_basis are fixed at creation");
   DeviceGuard dg(pb->device);
   CKS(sync(pb, "set_params"));
   apply_params(pb, p);

@@ -74,23 +74,24 @@ __global__ void k_sum_parts(const double* __restrict__ part, int nb, int nvec, d
 // pass writes the normalised vector (w - V d1) / sqrt(ww - s) and computes nothing else; otherwise
 // it writes w - V d1 and the partial sums of the second-pass dots (V_i . w', w' . w') for a
 // re-orthogonalisation. The test reads the same device values in every kernel and on the host.
-__device__ __forceinline__ bool cgs_fast(const double* __restrict__ d1, int nvec, double* s_out, double* ww_out) {
+__device__ __forceinline__ bool cgs_fast(const double* __restrict__ d1, int nvec, double thr, double* s_out,
+                                         double* ww_out) {
   double s = 0.0;
   for (int i = 0; i < nvec; ++i) s += d1[i] * d1[i];
   const double ww = d1[nvec];
   *s_out = s;
   *ww_out = ww;
-  return ww - s >= 0.5 * ww;
+  return ww - s >= thr * ww;
 }
 
 template <int NV, typename T>
 __global__ void __launch_bounds__(256) k_cgs_update(T* __restrict__ w, const T* __restrict__ V, long long ld,
-                                                    int nvec, const double* __restrict__ d1, long long n,
-                                                    double* __restrict__ part) {
+                                                    int nvec, const double* __restrict__ d1, double thr,
+                                                    long long n, double* __restrict__ part) {
   typedef typename KAcc<T>::type A;
   __shared__ double sh[32];
   double sum2, ww;
-  const bool fast = cgs_fast(d1, nvec, &sum2, &ww);
+  const bool fast = cgs_fast(d1, nvec, thr, &sum2, &ww);
   A cc[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) cc[i] = i < nvec ? (A)d1[i] : (A)0;
@@ -138,9 +139,9 @@ __global__ void __launch_bounds__(256) k_cgs_update(T* __restrict__ w, const T* 
 
 // Sum of the second-pass partials (re-orthogonalisation only).
 __global__ void k_cgs_sum(const double* __restrict__ part, int nb, int nvec, const double* __restrict__ d1,
-                          double* __restrict__ d2) {
+                          double thr, double* __restrict__ d2) {
   double s, ww;
-  if (cgs_fast(d1, nvec, &s, &ww)) return;
+  if (cgs_fast(d1, nvec, thr, &s, &ww)) return;
   __shared__ double sh[32];
   const int i = blockIdx.x;
   double acc = 0.0;
@@ -152,11 +153,11 @@ __global__ void k_cgs_sum(const double* __restrict__ part, int nb, int nvec, con
 // Re-orthogonalisation: w <- (w - sum_i d2_i V_i) / sqrt(d2[nvec] - sum d2_i^2) (only if the test failed).
 template <int NV, typename T>
 __global__ void __launch_bounds__(256) k_cgs_reorth(T* __restrict__ w, const T* __restrict__ V, long long ld,
-                                                    int nvec, const double* __restrict__ d1,
+                                                    int nvec, const double* __restrict__ d1, double thr,
                                                     const double* __restrict__ d2, long long n) {
   typedef typename KAcc<T>::type A;
   double s1, ww1;
-  if (cgs_fast(d1, nvec, &s1, &ww1)) return;
+  if (cgs_fast(d1, nvec, thr, &s1, &ww1)) return;
   A cc[NV];
   double corr = 0.0;
 #pragma unroll
@@ -461,14 +462,14 @@ cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, doub
 
 template <typename T>
 cudaError_t launch_cgs_t(T* w, const T* V, long long ld, int nvec, const double* d1, double* d2, long long n,
-                         double* part, cudaStream_t st, Counters* cnt) {
+                         double thr, double* part, cudaStream_t st, Counters* cnt) {
   const int nb = reduce_blocks(n);
   const unsigned ns = stream_blocks(n);
 #define NC_CGS(NV)                                                                     \
   do {                                                                                 \
-    k_cgs_update<NV, T><<<nb, kRedThreads, 0, st>>>(w, V, ld, nvec, d1, n, part);     \
-    k_cgs_sum<<<nvec + 1, 256, 0, st>>>(part, nb, nvec, d1, d2);                       \
-    k_cgs_reorth<NV, T><<<ns, 256, 0, st>>>(w, V, ld, nvec, d1, d2, n);                \
+    k_cgs_update<NV, T><<<nb, kRedThreads, 0, st>>>(w, V, ld, nvec, d1, thr, n, part); \
+    k_cgs_sum<<<nvec + 1, 256, 0, st>>>(part, nb, nvec, d1, thr, d2);                  \
+    k_cgs_reorth<NV, T><<<ns, 256, 0, st>>>(w, V, ld, nvec, d1, thr, d2, n);           \
   } while (0)
   if (nvec <= 4) NC_CGS(4);
   else if (nvec <= 8) NC_CGS(8);
@@ -481,13 +482,13 @@ cudaError_t launch_cgs_t(T* w, const T* V, long long ld, int nvec, const double*
 }
 
 cudaError_t launch_cgs(double* w, const double* V, long long ld, int nvec, const double* d1, double* d2, long long n,
-                      double* part, cudaStream_t st, Counters* cnt) {
-  return launch_cgs_t<double>(w, V, ld, nvec, d1, d2, n, part, st, cnt);
+                      double thr, double* part, cudaStream_t st, Counters* cnt) {
+  return launch_cgs_t<double>(w, V, ld, nvec, d1, d2, n, thr, part, st, cnt);
 }
 
 cudaError_t launch_cgs(float* w, const float* V, long long ld, int nvec, const double* d1, double* d2, long long n,
-                      double* part, cudaStream_t st, Counters* cnt) {
-  return launch_cgs_t<float>(w, V, ld, nvec, d1, d2, n, part, st, cnt);
+                      double thr, double* part, cudaStream_t st, Counters* cnt) {
+  return launch_cgs_t<float>(w, V, ld, nvec, d1, d2, n, thr, part, st, cnt);
 }
 
 template <typename TY, typename T>

@@ -92,13 +92,14 @@ cudaError_t launch_multidot(const float* V, long long ld, int nvec, const float*
 cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, double* res,
                               cudaStream_t st, Counters* c);
 // Gram-Schmidt step of FGMRES (nvec <= 32) from the first-pass dots d1 (device: V_i . w, then w . w):
-// w <- (w - V d1) / sqrt(ww - |d1|^2) when ww - |d1|^2 >= ww / 2; otherwise classical Gram-Schmidt is
-// applied twice and d2 receives the second-pass dots and ||w'||^2. The branch is taken on the device;
-// the host repeats the same test on the read-back values.
+// w <- (w - V d1) / sqrt(ww - |d1|^2) when ww - |d1|^2 >= thr ww (the projection kept at least the
+// fraction thr of ||w||^2; thr = 1/2 is the Daniel-Gragg-Kaufman-Stewart test); otherwise classical
+// Gram-Schmidt is applied twice and d2 receives the second-pass dots and ||w'||^2. The branch is
+// taken on the device; the host repeats the same test on the read-back values.
 cudaError_t launch_cgs(double* w, const double* V, long long ld, int nvec, const double* d1, double* d2, long long n,
-                      double* part, cudaStream_t st, Counters* cnt);
+                      double thr, double* part, cudaStream_t st, Counters* cnt);
 cudaError_t launch_cgs(float* w, const float* V, long long ld, int nvec, const double* d1, double* d2, long long n,
-                      double* part, cudaStream_t st, Counters* cnt);
+                      double thr, double* part, cudaStream_t st, Counters* cnt);
 // y += sum_i coef[i] * V_i (nvec <= 64), n entries.
 cudaError_t launch_axpy_multi(double* y, const double* V, long long ld, int nvec, const double* coef,
                               long long n, cudaStream_t st, Counters* c);

@@ -39,8 +39,8 @@ def test_default_params_and_footprint(lib):
     p = default_params()
     assert p.alpha == 1e3 and p.k_s == 100.0 and p.q_c == pytest.approx(8.81)
     assert p.newton_rtol == 1e-8 and p.restart == 30
-    from paper_1904_00182_gb300 import NC_ARITH_DF64, NC_PREC_MIXED
-    assert p.precision == NC_PREC_MIXED and p.outer_arith == NC_ARITH_DF64
+    from paper_1904_00182_gb300 import NC_ARITH_FP64, NC_BASIS_FP64, NC_PREC_MIXED
+    assert p.precision == NC_PREC_MIXED and p.outer_arith == NC_ARITH_FP64 and p.krylov_basis == NC_BASIS_FP64
     b16 = footprint_bytes(Grid(16, 16, 16, 1 / 16), p)
     b32 = footprint_bytes(Grid(32, 32, 32, 1 / 32), p)
     assert 0 < b16 < b32
@@ -66,6 +66,10 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
         footprint_bytes(Grid(16, 16, 16, 1 / 16), p)
     p = default_params()
     p.outer_arith = 2
+    with pytest.raises(NatConvError):
+        footprint_bytes(Grid(16, 16, 16, 1 / 16), p)
+    p = default_params()
+    p.krylov_basis = 2
     with pytest.raises(NatConvError):
         footprint_bytes(Grid(16, 16, 16, 1 / 16), p)
 

@@ -3,7 +3,9 @@
 Sizes the oracle finishes in seconds: 16^3 (4096 elements, 32 blocks of the element kernels) and
 a ragged 12 x 10 x 6 box. Tolerances: FP64 operators 1e-12 relative (only the summation order
 differs), FP32 operators 1e-4, solved fields 1e-8 (FP64 path) / 1e-6 (mixed path) relative L2,
-sensitivities 1e-6 relative L2 (the targets stated for this method's GPU path).
+sensitivities 1e-6 relative L2 (the targets stated for this method's GPU path). The mixed path is
+checked with its default precision assignment and with the fast one (double-float outer residuals,
+FP32 Krylov basis); double-float operators are held to 1e-11.
 """
 
 import numpy as np
@@ -31,11 +33,11 @@ def lib():
     return nc
 
 
-def make_pair(nc, shape, alpha, seed, precision=1, volfrac=0.2, rtol=1e-10):
+def make_pair(nc, shape, alpha, seed, precision=1, volfrac=0.2, rtol=1e-10, **kw):
     nx, ny, nz = shape
     h = 1.0 / nz
     rho = filtered_random(nx, ny, nz, seed, volfrac=volfrac)
-    gp = nc.Problem(nx, ny, nz, h, alpha=alpha, precision=precision, newton_rtol=rtol)
+    gp = nc.Problem(nx, ny, nz, h, alpha=alpha, precision=precision, newton_rtol=rtol, **kw)
     gp.set_design(rho)
     op = oracle.Problem(oracle.Mesh(nx, ny, nz, h), oracle.Params(alpha=alpha, newton_rtol=rtol))
     op.set_design(rho)
@@ -107,8 +109,7 @@ def test_double_float_outer_operators(lib, shape, alpha, seed):
     """Mixed path, outer arithmetic double-float: R(s) and J(s)^T w against the FP64 oracle.
     A double-float sum errs by at most about 2 u^2 (|a| + |b|) with u = 2^-24, 64 times the FP64
     unit roundoff, so the FP64 operator bound (1e-12, summation order only) widens to 1e-11."""
-    gp, op, _ = make_pair(lib, shape, alpha, seed, precision=lib.NC_PREC_MIXED)
-    assert gp.params.outer_arith == lib.NC_ARITH_DF64
+    gp, op, _ = make_pair(lib, shape, alpha, seed, precision=lib.NC_PREC_MIXED, outer_arith=lib.NC_ARITH_DF64)
     for trial in range(2):
         s = random_state(op, 20 + trial)
         R, n2 = gp.eval_residual(s)
@@ -128,10 +129,17 @@ def test_double_float_outer_operators(lib, shape, alpha, seed):
     gp.close()
 
 
+# mixed path variants: the default (IEEE FP64 outer residuals and Krylov basis) and the fast one
+# (double-float outer residuals, FP32 Krylov basis)
+VARIANTS = {"fp64": (1, 1e-8, {}), "mixed": (0, 1e-6, {}),
+            "mixed_fast": (0, 1e-6, {"outer_arith": 0, "krylov_basis": 1})}
+
+
 @pytest.mark.parametrize("shape,alpha,seed", CASES)
-@pytest.mark.parametrize("precision,tol", [(1, 1e-8), (0, 1e-6)])
-def test_state_adjoint_sensitivities(lib, shape, alpha, seed, precision, tol):
-    gp, op, rho = make_pair(lib, shape, alpha, seed, precision=precision)
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_state_adjoint_sensitivities(lib, shape, alpha, seed, variant):
+    precision, tol, kw = VARIANTS[variant]
+    gp, op, rho = make_pair(lib, shape, alpha, seed, precision=precision, **kw)
     stats = gp.solve_state()
     assert stats["rel_residual"] <= 1e-10
     op.solve_state()
