@@ -146,3 +146,28 @@ def test_fp64_path_agrees_128(setup):
     print("128^3 FP64 path: %d Newton, %d Krylov; mixed vs FP64 state rel L2 %.2e"
           % (st["newton_its"], st["krylov_its"], err))
     assert err <= 1e-6
+
+
+def test_state_256x128x128(base):
+    """The workload's larger grid, 256 x 128 x 128 (4.2M elements), volume fraction 0.3, 6 levels
+    (coarsest 8 x 4 x 4 elements, 360 DOFs): the oracle's residual at the GPU state on sampled rows
+    is below the stopping tolerance."""
+    nc = base[0]
+    nx, ny, nz = 256, 128, 128
+    rho = filtered_random(nx, ny, nz, seed=3, volfrac=0.3)
+    op = oracle.Problem(oracle.Mesh(nx, ny, nz, 1.0 / nz), oracle.Params(alpha=ALPHA))
+    op.set_design(rho)
+    pb = nc.Problem(nx, ny, nz, 1.0 / nz, alpha=ALPHA, mg_levels=6)
+    pb.set_design(rho)
+    st = pb.solve_state()
+    P, T, _ = pb.get_fields(velocity=False)
+    pb.close()
+    s = np.empty(2 * op.mesh.n_nodes)
+    s[0::2], s[1::2] = P.cpu().numpy(), T.cpu().numpy()
+    rng = np.random.default_rng(5)
+    nodes = rng.choice(op.mesh.n_nodes, 400, replace=False)
+    Rs = op.residual_at_nodes(s, nodes)
+    worst = np.abs(Rs[_free_rows(op, nodes)]).max() / op.reference_norm()
+    print("256x128x128: %d Newton, %d Krylov, %.1f ms; sampled |R_free| / ||R_free(0)|| = %.2e"
+          % (st["newton_its"], st["krylov_its"], st["t_total_ms"], worst))
+    assert worst <= 1e-8
