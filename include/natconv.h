@@ -197,6 +197,10 @@ nc_status nc_get_fields(const nc_problem* pb, double* P, double* T, double* u);
  * the Dirichlet rows). Requires a solved adjoint. */
 nc_status nc_get_adjoint(const nc_problem* pb, double* lam);
 
+/* The resolved fluid and solid permeabilities kappa_f (Eq. nusselt5 when params.kappa_f <= 0) and
+ * kappa_s = kappa_ratio * kappa_f (Eq. permRAMP). Either pointer may be NULL. */
+nc_status nc_get_permeabilities(const nc_problem* pb, double* kappa_f, double* kappa_s);
+
 /* Filtered design gamma~, kappa_e and k_e (E values each; any may be NULL). */
 nc_status nc_get_design_fields(const nc_problem* pb, double* gamma_tilde, double* kappa, double* k);
 

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_OOM", 3: "NC_ERR_CUDA", 
 # Every exported symbol of include/natconv.h.
 EXPORTS = ("nc_default_params", "nc_create_problem", "nc_destroy_problem", "nc_footprint_bytes", "nc_set_params",
            "nc_set_design", "nc_set_state", "nc_solve_state", "nc_objective", "nc_solve_adjoint",
-           "nc_sensitivities", "nc_get_fields", "nc_get_adjoint", "nc_get_design_fields", "nc_eval_residual",
+           "nc_sensitivities", "nc_get_fields", "nc_get_adjoint", "nc_get_permeabilities", "nc_get_design_fields", "nc_eval_residual",
            "nc_apply_jacobian", "nc_apply_jacobian_transpose", "nc_set_profiling", "nc_get_profile",
            "nc_counters", "nc_norm2_free_noalloc", "nc_last_error")
 
@@ -108,6 +108,7 @@ def load_library(path=None):
         "nc_sensitivities": ([vp, vp], i),
         "nc_get_fields": ([vp, vp, vp, vp], i),
         "nc_get_adjoint": ([vp, vp], i),
+        "nc_get_permeabilities": ([vp, dp, dp], i),
         "nc_get_design_fields": ([vp, vp, vp, vp], i),
         "nc_eval_residual": ([vp, vp, vp, dp], i),
         "nc_apply_jacobian": ([vp, vp, vp, vp, i], i),

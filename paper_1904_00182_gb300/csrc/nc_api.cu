@@ -1346,6 +1346,13 @@ nc_status nc_get_fields(const nc_problem* cpb, double* P, double* T, double* u) 
   return NC_OK;
 }
 
+nc_status nc_get_permeabilities(const nc_problem* pb, double* kappa_f, double* kappa_s) {
+  if (!pb) return NC_ERR_ARG;
+  if (kappa_f) *kappa_f = pb->kappa_f;
+  if (kappa_s) *kappa_s = pb->kappa_s;
+  return NC_OK;
+}
+
 nc_status nc_get_adjoint(const nc_problem* cpb, double* lam) {
   nc_problem* pb = const_cast<nc_problem*>(cpb);
   if (!pb || !lam) return NC_ERR_ARG;

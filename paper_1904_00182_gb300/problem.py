@@ -144,6 +144,12 @@ class Problem:
         self._check(self.lib.nc_get_adjoint(self.h, _ptr(lam)))
         return lam
 
+    def permeabilities(self):
+        """(kappa_f, kappa_s) as resolved by the library."""
+        kf, ks = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.nc_get_permeabilities(self.h, ctypes.byref(kf), ctypes.byref(ks)))
+        return kf.value, ks.value
+
     def design_fields(self):
         gt, kap, k = self._empty(self.ne), self._empty(self.ne), self._empty(self.ne)
         self._check(self.lib.nc_get_design_fields(self.h, _ptr(gt), _ptr(kap), _ptr(k)))
