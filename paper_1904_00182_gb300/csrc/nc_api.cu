@@ -86,6 +86,8 @@ struct nc_problem {
   double *R = nullptr, *R_try = nullptr, *dx = nullptr, *w = nullptr, *rhs = nullptr;
   double *rho = nullptr, *gamma_t = nullptr, *gsens = nullptr, *u = nullptr;
   double2 *mat = nullptr, *dmat = nullptr;
+  double2* dl = nullptr;   // element (dL/dkappa, dL/dk) at the adjoint solution (see dl_ready)
+  bool dl_ready = false;   // dl holds the derivatives of the current lambda
   float2 *mat32 = nullptr, *s32 = nullptr, *v32 = nullptr, *y32 = nullptr;
   // double-float copies (mixed path with NC_ARITH_DF64): materials per element, split scratch per node
   float4 *mat_df = nullptr, *s_df = nullptr, *w_df = nullptr;
@@ -308,12 +310,13 @@ bool outer_df(const nc_problem* pb) {
   return pb->par.precision != NC_PREC_FP64 && pb->par.outer_arith == NC_ARITH_DF64;
 }
 
-// J(s)^T w in the arithmetic of the outer residuals.
-nc_status outer_jtv(nc_problem* pb, int cls, const double2* s, const double2* w, double* out) {
+// J(s)^T w in the arithmetic of the outer residuals; dl (nullable): element design derivatives of
+// w . R stored by the same pass.
+nc_status outer_jtv(nc_problem* pb, int cls, const double2* s, const double2* w, double* out, double2* dl = nullptr) {
   if (outer_df(pb))
-    PCK(cls, launch_jtv_df(pb->g, pb->ph, s, pb->mat_df, pb->s_df, w, pb->w_df, out, pb->st, &pb->cnt));
+    PCK(cls, launch_jtv_df(pb->g, pb->ph, s, pb->mat_df, pb->s_df, w, pb->w_df, out, dl, pb->st, &pb->cnt));
   else
-    PCK(cls, launch_jtv_f64(pb->g, pb->ph, s, pb->mat, w, out, pb->st, &pb->cnt));
+    PCK(cls, launch_jtv_f64(pb->g, pb->ph, s, pb->mat, w, out, dl, pb->st, &pb->cnt));
   return NC_OK;
 }
 
@@ -338,7 +341,7 @@ nc_status outer_op(nc_problem* pb, bool transpose, bool fp32, const double* x, d
                                                        pb->st, &pb->cnt));
     PCK(NC_PROF_OUTER_OP32, launch_cast_f2d(y, (const float*)pb->y32, 2 * g.nn, pb->st, &pb->cnt));
   } else {
-    if (transpose) PCK(NC_PROF_OUTER_OP64, launch_jtv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, pb->st, &pb->cnt));
+    if (transpose) PCK(NC_PROF_OUTER_OP64, launch_jtv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, nullptr, pb->st, &pb->cnt));
     else PCK(NC_PROF_OUTER_OP64, launch_jv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, pb->st, &pb->cnt));
   }
   return NC_OK;
@@ -886,7 +889,7 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
   b += 4 * al(16 * nn);                 // s, s_try, lam, s_start
   b += 6 * al(16 * nn);                 // R, R_try, dx, w, rhs, R0
   b += 3 * al(8 * ne) + al(24 * ne);    // rho, gamma_t, gsens, u
-  b += 2 * al(16 * ne) + al(8 * ne) + 3 * al(8 * nn);   // mat, dmat, mat32, s32, v32, y32
+  b += 3 * al(16 * ne) + al(8 * ne) + 3 * al(8 * nn);   // mat, dmat, dl, mat32, s32, v32, y32
   const size_t ks = (p->precision == NC_PREC_FP64 || p->krylov_basis == NC_BASIS_FP64) ? 8 : 4;   // basis entry
   b += al(2 * ks * nn * (m + 1)) + al(2 * ks * nn * m);     // V, Z
   if (p->precision != NC_PREC_FP64) b += al(16 * ne) + 2 * al(16 * nn);   // mat_df, s_df, w_df
@@ -1055,7 +1058,7 @@ nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream,
   A(dalloc(pb, &pb->R, 2 * nn)); A(dalloc(pb, &pb->R_try, 2 * nn)); A(dalloc(pb, &pb->dx, 2 * nn));
   A(dalloc(pb, &pb->w, 2 * nn)); A(dalloc(pb, &pb->rhs, 2 * nn)); A(dalloc(pb, &pb->R0, 2 * nn));
   A(dalloc(pb, &pb->rho, ne)); A(dalloc(pb, &pb->gamma_t, ne)); A(dalloc(pb, &pb->gsens, ne)); A(dalloc(pb, &pb->u, 3 * ne));
-  A(dalloc(pb, &pb->mat, ne)); A(dalloc(pb, &pb->dmat, ne)); A(dalloc(pb, &pb->mat32, ne)); A(dalloc(pb, &pb->s32, nn));
+  A(dalloc(pb, &pb->mat, ne)); A(dalloc(pb, &pb->dmat, ne)); A(dalloc(pb, &pb->dl, ne)); A(dalloc(pb, &pb->mat32, ne)); A(dalloc(pb, &pb->s32, nn));
   A(dalloc(pb, &pb->v32, nn)); A(dalloc(pb, &pb->y32, nn));
   if (p->precision == NC_PREC_FP64 || p->krylov_basis == NC_BASIS_FP64) {
     A(dalloc(pb, &pb->V, (size_t)2 * nn * (pb->m + 1))); A(dalloc(pb, &pb->Z, (size_t)2 * nn * pb->m));
@@ -1250,6 +1253,7 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
   CKS(norm2_free(pb, pb->rhs, &bb));
   const double bnorm = std::sqrt(bb);
   CK(cudaMemsetAsync(pb->lam, 0, sizeof(double) * n, pb->st));
+  pb->dl_ready = false;
   if (bnorm == 0.0) { pb->stage = 3; return NC_OK; }
   const bool fp32 = pb->par.precision != NC_PREC_FP64;
   const double kAdjointRtol = pb->par.adjoint_rtol > 0 ? pb->par.adjoint_rtol : pb->par.newton_rtol;
@@ -1260,7 +1264,9 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
       CK(cudaMemcpyAsync(pb->w, pb->rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
       rr = bb;
     } else {
-      CKS(outer_jtv(pb, NC_PROF_OUTER_OP64, pb->s, pb->lam, pb->w));
+      // the same pass stores the element design derivatives at this lambda; if it is the last
+      // (converged) one, the sensitivities need no element sweep of their own
+      CKS(outer_jtv(pb, NC_PROF_OUTER_OP64, pb->s, pb->lam, pb->w, pb->dl));
       PCK(NC_PROF_OTHER, launch_axpby(pb->w, pb->rhs, 1.0, -1.0, n, pb->st, &pb->cnt));
       PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->w, pb->st, &pb->cnt));
       CKS(norm2_free(pb, pb->w, &rr));
@@ -1271,7 +1277,10 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
       if (pass < 64) stats->res_hist[pass] = rel;
     }
     if (!std::isfinite(rel)) return fail(pb, NC_ERR_NAN, "non-finite adjoint residual");
-    if (rel <= kAdjointRtol) break;
+    if (rel <= kAdjointRtol) {
+      pb->dl_ready = pass > 0;   // the last J^T pass was at this (final) lambda
+      break;
+    }
     if (pass >= 30) return fail(pb, NC_ERR_MAXIT, "adjoint refinement did not converge");
     CKS(check_timeout(pb));
     int its;
@@ -1316,7 +1325,9 @@ nc_status nc_sensitivities(nc_problem* pb, double* dfdrho) {
   pb->t_start = now_s();
   const Grid& g = pb->g;
   set_q_scale(pb, 1.0);
-  if (outer_df(pb))
+  if (pb->dl_ready)
+    PCK(NC_PROF_SENS, launch_sens_from_dl(g, pb->par.heated_layers, pb->dl, pb->dmat, pb->gsens, pb->st, &pb->cnt));
+  else if (outer_df(pb))
     PCK(NC_PROF_SENS, launch_sens_df(g, pb->ph, pb->s, pb->lam, pb->mat_df, pb->dmat, pb->s_df, pb->w_df, pb->gsens,
                                      pb->st, &pb->cnt));
   else

@@ -78,10 +78,12 @@ __global__ void k_residual_bc(Grid g, const double2* __restrict__ s, double* __r
   out[2 * n + 1] = s[n].y;
 }
 
-template <typename R, typename SV, typename O, bool TRANSPOSE>
+// J v or J^T w. With DL (transpose only), the pass also stores the element derivatives
+// (dL/dkappa_e, dL/dk_e) of L = w . R_e, the design derivatives the sensitivities need at this w.
+template <typename R, typename SV, typename O, bool TRANSPOSE, bool DL = false>
 __global__ void k_jprod(Grid g, Phys ph, ElemConst<R> C, const SV* __restrict__ s,
                         const typename Vec2<R>::type* __restrict__ mat, const double2* __restrict__ v,
-                        O* __restrict__ out) {
+                        O* __restrict__ out, double2* __restrict__ dl) {
   NC_ELEM_PROLOGUE();
   R p[8], t[8], dp[8], dt[8];
   gather_state<R>(g, s, n0, p, t);
@@ -90,11 +92,25 @@ __global__ void k_jprod(Grid g, Phys ph, ElemConst<R> C, const SV* __restrict__ 
   ElemState<R> st;
   elem_state(C, p, t, m.x, elem_source<R>(ph, k), st);
   R oP[8], oT[8];
-  if (TRANSPOSE)
+  if (TRANSPOSE && DL) {
+    R dkap, dk;
+    elem_jtv<R, true>(C, st, m.y, dp, dt, oP, oT, &dkap, &dk);
+    dl[e] = make_double2((double)dkap, (double)dk);
+  } else if (TRANSPOSE) {
     elem_jtv<R, false>(C, st, m.y, dp, dt, oP, oT, nullptr, nullptr);
-  else
+  } else {
     elem_jv_dir<R>(C, st, m.y, dp, dt, oP, oT);
+  }
   scatter_add(g, out, n0, top, oP, oT);
+}
+
+// df/dgamma~_e = -(dL/dkappa kappa' + dL/dk k') from stored element derivatives; 0 on heated elements.
+__global__ void k_sens_from_dl(long long ne, long long heated, const double2* __restrict__ dl,
+                               const double2* __restrict__ dmat, double* __restrict__ out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+    const double2 a = dl[e], d = dmat[e];
+    out[e] = e < heated ? 0.0 : -(a.x * d.x + a.y * d.y);
+  }
 }
 
 __global__ void k_sens(Grid g, Phys ph, ElemConst<double> C, const double2* __restrict__ s,
@@ -174,8 +190,10 @@ __global__ void __launch_bounds__(128, NC_LB_RESIDUAL_DF) k_residual_df(Grid g, 
   scatter_add(g, out, n0, top, RP, RT);
 }
 
+template <bool DL>
 __global__ void __launch_bounds__(128, NC_LB_JTV_DF) k_jtv_df(Grid g, Phys ph, ElemConst<df64> C, df64 Qh, const float4* __restrict__ s,
-                         const float4* __restrict__ mat, const float4* __restrict__ w, double* __restrict__ out) {
+                         const float4* __restrict__ mat, const float4* __restrict__ w, double* __restrict__ out,
+                         double2* __restrict__ dl) {
   NC_ELEM_PROLOGUE();
   df64 p[8], t[8], lp[8], lt[8];
   gather_df(g, s, n0, false, p, t);
@@ -184,7 +202,13 @@ __global__ void __launch_bounds__(128, NC_LB_JTV_DF) k_jtv_df(Grid g, Phys ph, E
   ElemState<df64> st;
   elem_state(C, p, t, df64(m.x, m.y), k < ph.heated_layers ? Qh : df64(0.0f, 0.0f), st);
   df64 oP[8], oT[8];
-  elem_jtv<df64, false>(C, st, df64(m.z, m.w), lp, lt, oP, oT, nullptr, nullptr);
+  if (DL) {
+    df64 dkap, dk;
+    elem_jtv<df64, true>(C, st, df64(m.z, m.w), lp, lt, oP, oT, &dkap, &dk);
+    dl[e] = make_double2((double)dkap, (double)dk);
+  } else {
+    elem_jtv<df64, false>(C, st, df64(m.z, m.w), lp, lt, oP, oT, nullptr, nullptr);
+  }
   scatter_add(g, out, n0, top, oP, oT);
 }
 
@@ -228,17 +252,18 @@ cudaError_t launch_residual_df(const Grid& g, const Phys& ph, const double2* s, 
 }
 
 cudaError_t launch_jtv_df(const Grid& g, const Phys& ph, const double2* s, const float4* mat_df, float4* s_df,
-                          const double2* w, float4* w_df, double* out, cudaStream_t st, Counters* c) {
+                          const double2* w, float4* w_df, double* out, double2* dl, cudaStream_t st, Counters* c) {
   cudaError_t err = cudaMemsetAsync(out, 0, sizeof(double) * 2 * g.nn, st);
   if (err != cudaSuccess) return err;
   if ((err = launch_split2(s, s_df, g.nn, st, c)) != cudaSuccess) return err;
   if ((err = launch_split2(w, w_df, g.nn, st, c)) != cudaSuccess) return err;
   const Launch3 L = launch_elems(g);
-  k_jtv_df<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<df64>(ph), df64(ph.Q), s_df, mat_df, w_df, out);
+  if (dl) k_jtv_df<true><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<df64>(ph), df64(ph.Q), s_df, mat_df, w_df, out, dl);
+  else k_jtv_df<false><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<df64>(ph), df64(ph.Q), s_df, mat_df, w_df, out, dl);
   if (c) {
     c->launches += 1;
     c->bytes += (32.0 + 16.0) * g.nn + 16.0 * g.ne;
-    c->flops += (kFlopsStateDF + kFlopsJtvDF) * g.ne;
+    c->flops += (kFlopsStateDF + (dl ? kFlopsSensDF : kFlopsJtvDF)) * g.ne;
   }
   return cudaGetLastError();
 }
@@ -268,26 +293,39 @@ cudaError_t launch_residual(const Grid& g, const Phys& ph, const double2* s, con
 
 template <typename R, typename SV, bool TR>
 static cudaError_t jprod(const Grid& g, const Phys& ph, const SV* s, const typename Vec2<R>::type* mat,
-                         const double2* v, double* out, cudaStream_t st, Counters* c) {
+                         const double2* v, double* out, double2* dl, cudaStream_t st, Counters* c) {
   cudaError_t err = cudaMemsetAsync(out, 0, sizeof(double) * 2 * g.nn, st);
   if (err != cudaSuccess) return err;
   const Launch3 L = launch_elems(g);
-  k_jprod<R, SV, double, TR><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, v, out);
+  if constexpr (TR) {
+    if (dl) k_jprod<R, SV, double, true, true><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, v, out, dl);
+    else k_jprod<R, SV, double, true, false><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, v, out, dl);
+  } else {
+    k_jprod<R, SV, double, false, false><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, v, out, dl);
+  }
   if (c) {
     c->launches += 1;
-    c->bytes += (2.0 * sizeof(SV) + 32.0) * g.nn + 2.0 * sizeof(R) * g.ne;
-    c->flops += (kFlopsState + (TR ? kFlopsJtv : kFlopsJv)) * g.ne;
+    c->bytes += (2.0 * sizeof(SV) + 32.0) * g.nn + 2.0 * sizeof(R) * g.ne + (dl ? 16.0 * g.ne : 0.0);
+    c->flops += (kFlopsState + (TR ? (dl ? kFlopsSens : kFlopsJtv) : kFlopsJv)) * g.ne;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_jv_f64(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
                           const double2* v, double* out, cudaStream_t st, Counters* c) {
-  return jprod<double, double2, false>(g, ph, s, mat, v, out, st, c);
+  return jprod<double, double2, false>(g, ph, s, mat, v, out, nullptr, st, c);
 }
 cudaError_t launch_jtv_f64(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
-                           const double2* w, double* out, cudaStream_t st, Counters* c) {
-  return jprod<double, double2, true>(g, ph, s, mat, w, out, st, c);
+                           const double2* w, double* out, double2* dl, cudaStream_t st, Counters* c) {
+  return jprod<double, double2, true>(g, ph, s, mat, w, out, dl, st, c);
+}
+
+cudaError_t launch_sens_from_dl(const Grid& g, int heated_layers, const double2* dl, const double2* dmat, double* out,
+                                cudaStream_t st, Counters* c) {
+  const long long heated = (long long)heated_layers * g.nx * g.ny;
+  k_sens_from_dl<<<grid_blocks(g.ne, 256, 152 * 16), 256, 0, st>>>(g.ne, heated, dl, dmat, out);
+  if (c) { c->launches += 1; c->bytes += 40.0 * g.ne; }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sens_elem(const Grid& g, const Phys& ph, const double2* s, const double2* lam,

@@ -56,9 +56,13 @@ cudaError_t launch_residual(const Grid& g, const Phys& ph, const double2* s, con
 // out = J(s) v (projected: Dirichlet inputs ignored, Dirichlet outputs 0); FP64 arithmetic.
 cudaError_t launch_jv_f64(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
                           const double2* v, double* out, cudaStream_t st, Counters* c);
-// out = J(s)^T w (projected), FP64.
+// out = J(s)^T w (projected), FP64. dl (nullable, E): element derivatives (dL/dkappa, dL/dk) of
+// L = w . R_e, stored by the same pass.
 cudaError_t launch_jtv_f64(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
-                           const double2* w, double* out, cudaStream_t st, Counters* c);
+                           const double2* w, double* out, double2* dl, cudaStream_t st, Counters* c);
+// df/dgamma~ = -(dL/dkappa kappa' + dL/dk k') from stored dl; 0 on the heated layers.
+cudaError_t launch_sens_from_dl(const Grid& g, int heated_layers, const double2* dl, const double2* dmat, double* out,
+                                cudaStream_t st, Counters* c);
 // d f / d gamma~_e = -(dL/dkappa kappa' + dL/dk k'), 0 on heated elements; dmat: (kappa', k').
 cudaError_t launch_sens_elem(const Grid& g, const Phys& ph, const double2* s, const double2* lam,
                              const double2* mat, const double2* dmat, double* out, cudaStream_t st,
@@ -70,7 +74,7 @@ cudaError_t launch_split2(const double2* x, float4* y, long long n, cudaStream_t
 cudaError_t launch_residual_df(const Grid& g, const Phys& ph, const double2* s, const float4* mat_df,
                                float4* s_df, double* out, cudaStream_t st, Counters* c);
 cudaError_t launch_jtv_df(const Grid& g, const Phys& ph, const double2* s, const float4* mat_df, float4* s_df,
-                          const double2* w, float4* w_df, double* out, cudaStream_t st, Counters* c);
+                          const double2* w, float4* w_df, double* out, double2* dl, cudaStream_t st, Counters* c);
 cudaError_t launch_sens_df(const Grid& g, const Phys& ph, const double2* s, const double2* lam, const float4* mat_df,
                            const double2* dmat, float4* s_df, float4* l_df, double* out, cudaStream_t st, Counters* c);
 // Centroid Darcy velocity (3 per element).
