@@ -36,6 +36,7 @@ template <int NV, typename T>
 __global__ void __launch_bounds__(256) k_multidot_part(const T* __restrict__ V, long long ld, int nvec,
                                                        const T* __restrict__ w, long long n,
                                                        double* __restrict__ part) {
+  const int nv = NV <= 8 ? NV : nvec;   // exact tile for small counts: no guarded slots
   typedef typename KAcc<T>::type A;
   __shared__ double sh[32];
   A acc[NV];
@@ -48,11 +49,11 @@ __global__ void __launch_bounds__(256) k_multidot_part(const T* __restrict__ V, 
     const A x = w[t];
 #pragma unroll
     for (int i = 0; i < NV; ++i)
-      if (i < nvec) acc[i] += (A)V[(long long)i * ld + t] * x;
+      if (i < nv) acc[i] += (A)V[(long long)i * ld + t] * x;
   }
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    if (i >= nvec) break;
+    if (i >= nv) break;
     const double r = block_sum((double)acc[i], sh);
     if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = r;
   }
@@ -88,13 +89,14 @@ template <int NV, typename T>
 __global__ void __launch_bounds__(256) k_cgs_update(T* __restrict__ w, const T* __restrict__ V, long long ld,
                                                     int nvec, const double* __restrict__ d1, double thr,
                                                     long long n, double* __restrict__ part) {
+  const int nv = NV <= 8 ? NV : nvec;   // exact tile for small counts: no guarded slots
   typedef typename KAcc<T>::type A;
   __shared__ double sh[32];
   double sum2, ww;
-  const bool fast = cgs_fast(d1, nvec, thr, &sum2, &ww);
+  const bool fast = cgs_fast(d1, nv, thr, &sum2, &ww);
   A cc[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) cc[i] = i < nvec ? (A)d1[i] : (A)0;
+  for (int i = 0; i < NV; ++i) cc[i] = i < nv ? (A)d1[i] : (A)0;
   const long long seg = (n + gridDim.x - 1) / gridDim.x;
   const long long lo = seg * blockIdx.x;
   const long long hi = min(n, lo + seg);
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(256) k_cgs_update(T* __restrict__ w, const T* 
       A x = w[t];
 #pragma unroll
       for (int i = 0; i < NV; ++i)
-        if (i < nvec) x -= cc[i] * (A)V[(long long)i * ld + t];
+        if (i < nv) x -= cc[i] * (A)V[(long long)i * ld + t];
       w[t] = (T)(x * inv);
     }
     return;
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(256) k_cgs_update(T* __restrict__ w, const T* 
     A x = w[t];
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      v[i] = i < nvec ? (A)V[(long long)i * ld + t] : (A)0;
+      v[i] = i < nv ? (A)V[(long long)i * ld + t] : (A)0;
       x -= cc[i] * v[i];
     }
     w[t] = (T)x;
@@ -129,12 +131,12 @@ __global__ void __launch_bounds__(256) k_cgs_update(T* __restrict__ w, const T* 
   }
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    if (i >= nvec) break;
+    if (i >= nv) break;
     const double r = block_sum((double)acc[i], sh);
     if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = r;
   }
   const double r = block_sum((double)accw, sh);
-  if (threadIdx.x == 0) part[(long long)nvec * gridDim.x + blockIdx.x] = r;
+  if (threadIdx.x == 0) part[(long long)nv * gridDim.x + blockIdx.x] = r;
 }
 
 // Sum of the second-pass partials (re-orthogonalisation only).
@@ -155,24 +157,25 @@ template <int NV, typename T>
 __global__ void __launch_bounds__(256) k_cgs_reorth(T* __restrict__ w, const T* __restrict__ V, long long ld,
                                                     int nvec, const double* __restrict__ d1, double thr,
                                                     const double* __restrict__ d2, long long n) {
+  const int nv = NV <= 8 ? NV : nvec;   // exact tile for small counts: no guarded slots
   typedef typename KAcc<T>::type A;
   double s1, ww1;
-  if (cgs_fast(d1, nvec, thr, &s1, &ww1)) return;
+  if (cgs_fast(d1, nv, thr, &s1, &ww1)) return;
   A cc[NV];
   double corr = 0.0;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    const double c = i < nvec ? d2[i] : 0.0;
+    const double c = i < nv ? d2[i] : 0.0;
     cc[i] = (A)c;
     corr += c * c;
   }
-  const double h2 = d2[nvec] - corr;
+  const double h2 = d2[nv] - corr;
   const A inv = (A)(h2 > 0.0 ? 1.0 / sqrt(h2) : 0.0);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     A x = w[t];
 #pragma unroll
     for (int i = 0; i < NV; ++i)
-      if (i < nvec) x -= cc[i] * (A)V[(long long)i * ld + t];
+      if (i < nv) x -= cc[i] * (A)V[(long long)i * ld + t];
     w[t] = (T)(x * inv);
   }
 }
@@ -430,11 +433,22 @@ template <typename T>
 cudaError_t launch_multidot_t(const T* V, long long ld, int nvec, const T* w, long long n,
                               double* part, double* res, cudaStream_t st, Counters* c) {
   const int nb = reduce_blocks(n);
-  if (nvec <= 4) k_multidot_part<4, T><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
-  else if (nvec <= 8) k_multidot_part<8, T><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
-  else if (nvec <= 16) k_multidot_part<16, T><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
-  else if (nvec <= 32) k_multidot_part<32, T><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
-  else k_multidot_part<66, T><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part);
+#define NC_MD(NV) k_multidot_part<NV, T><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part)
+  switch (nvec) {   // exact tiles up to 8 vectors, rounded-up tiles beyond
+    case 1: NC_MD(1); break;
+    case 2: NC_MD(2); break;
+    case 3: NC_MD(3); break;
+    case 4: NC_MD(4); break;
+    case 5: NC_MD(5); break;
+    case 6: NC_MD(6); break;
+    case 7: NC_MD(7); break;
+    case 8: NC_MD(8); break;
+    default:
+      if (nvec <= 16) NC_MD(16);
+      else if (nvec <= 32) NC_MD(32);
+      else NC_MD(66);
+  }
+#undef NC_MD
   k_sum_parts<<<nvec, 256, 0, st>>>(part, nb, nvec, res);
   if (c) { c->launches += 2; c->bytes += (double)sizeof(T) * n * (nvec + 1); c->flops += 2.0 * n * nvec; }
   return cudaGetLastError();
@@ -471,9 +485,18 @@ cudaError_t launch_cgs_t(T* w, const T* V, long long ld, int nvec, const double*
     k_cgs_sum<<<nvec + 1, 256, 0, st>>>(part, nb, nvec, d1, thr, d2);                  \
     k_cgs_reorth<NV, T><<<ns, 256, 0, st>>>(w, V, ld, nvec, d1, thr, d2, n);           \
   } while (0)
-  if (nvec <= 4) NC_CGS(4);
-  else if (nvec <= 8) NC_CGS(8);
-  else if (nvec <= 16) NC_CGS(16);
+  if (nvec <= 8) {   // exact tiles up to 8 vectors
+    switch (nvec) {
+      case 1: NC_CGS(1); break;
+      case 2: NC_CGS(2); break;
+      case 3: NC_CGS(3); break;
+      case 4: NC_CGS(4); break;
+      case 5: NC_CGS(5); break;
+      case 6: NC_CGS(6); break;
+      case 7: NC_CGS(7); break;
+      default: NC_CGS(8); break;
+    }
+  } else if (nvec <= 16) NC_CGS(16);
   else if (nvec <= 32) NC_CGS(32);
   else return cudaErrorInvalidValue;
 #undef NC_CGS
