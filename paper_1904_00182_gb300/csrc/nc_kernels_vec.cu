@@ -36,7 +36,7 @@ template <int NV, typename T>
 __global__ void __launch_bounds__(256) k_multidot_part(const T* __restrict__ V, long long ld, int nvec,
                                                        const T* __restrict__ w, long long n,
                                                        double* __restrict__ part) {
-  const int nv = NV <= 8 ? NV : nvec;   // exact tile for small counts: no guarded slots
+  const int nv = NV <= 12 ? NV : nvec;   // exact tile for small counts: no guarded slots
   typedef typename KAcc<T>::type A;
   __shared__ double sh[32];
   A acc[NV];
@@ -89,7 +89,7 @@ template <int NV, typename T>
 __global__ void __launch_bounds__(256) k_cgs_update(T* __restrict__ w, const T* __restrict__ V, long long ld,
                                                     int nvec, const double* __restrict__ d1, double thr,
                                                     long long n, double* __restrict__ part) {
-  const int nv = NV <= 8 ? NV : nvec;   // exact tile for small counts: no guarded slots
+  const int nv = NV <= 12 ? NV : nvec;   // exact tile for small counts: no guarded slots
   typedef typename KAcc<T>::type A;
   __shared__ double sh[32];
   double sum2, ww;
@@ -157,7 +157,7 @@ template <int NV, typename T>
 __global__ void __launch_bounds__(256) k_cgs_reorth(T* __restrict__ w, const T* __restrict__ V, long long ld,
                                                     int nvec, const double* __restrict__ d1, double thr,
                                                     const double* __restrict__ d2, long long n) {
-  const int nv = NV <= 8 ? NV : nvec;   // exact tile for small counts: no guarded slots
+  const int nv = NV <= 12 ? NV : nvec;   // exact tile for small counts: no guarded slots
   typedef typename KAcc<T>::type A;
   double s1, ww1;
   if (cgs_fast(d1, nv, thr, &s1, &ww1)) return;
@@ -434,7 +434,7 @@ cudaError_t launch_multidot_t(const T* V, long long ld, int nvec, const T* w, lo
                               double* part, double* res, cudaStream_t st, Counters* c) {
   const int nb = reduce_blocks(n);
 #define NC_MD(NV) k_multidot_part<NV, T><<<nb, kRedThreads, 0, st>>>(V, ld, nvec, w, n, part)
-  switch (nvec) {   // exact tiles up to 8 vectors, rounded-up tiles beyond
+  switch (nvec) {   // exact tiles up to 12 vectors, rounded-up tiles beyond
     case 1: NC_MD(1); break;
     case 2: NC_MD(2); break;
     case 3: NC_MD(3); break;
@@ -443,6 +443,10 @@ cudaError_t launch_multidot_t(const T* V, long long ld, int nvec, const T* w, lo
     case 6: NC_MD(6); break;
     case 7: NC_MD(7); break;
     case 8: NC_MD(8); break;
+    case 9: NC_MD(9); break;
+    case 10: NC_MD(10); break;
+    case 11: NC_MD(11); break;
+    case 12: NC_MD(12); break;
     default:
       if (nvec <= 16) NC_MD(16);
       else if (nvec <= 32) NC_MD(32);
@@ -485,7 +489,7 @@ cudaError_t launch_cgs_t(T* w, const T* V, long long ld, int nvec, const double*
     k_cgs_sum<<<nvec + 1, 256, 0, st>>>(part, nb, nvec, d1, thr, d2);                  \
     k_cgs_reorth<NV, T><<<ns, 256, 0, st>>>(w, V, ld, nvec, d1, thr, d2, n);           \
   } while (0)
-  if (nvec <= 8) {   // exact tiles up to 8 vectors
+  if (nvec <= 12) {   // exact tiles up to 12 vectors
     switch (nvec) {
       case 1: NC_CGS(1); break;
       case 2: NC_CGS(2); break;
@@ -494,7 +498,11 @@ cudaError_t launch_cgs_t(T* w, const T* V, long long ld, int nvec, const double*
       case 5: NC_CGS(5); break;
       case 6: NC_CGS(6); break;
       case 7: NC_CGS(7); break;
-      default: NC_CGS(8); break;
+      case 8: NC_CGS(8); break;
+      case 9: NC_CGS(9); break;
+      case 10: NC_CGS(10); break;
+      case 11: NC_CGS(11); break;
+      default: NC_CGS(12); break;
     }
   } else if (nvec <= 16) NC_CGS(16);
   else if (nvec <= 32) NC_CGS(32);
