@@ -255,6 +255,15 @@ DF64_CLASSES = ("residual", "outer_op64", "sens")
 ALU_PEAK_TFLOPS = {"fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "fp64": 152 * 2 * 2 * 2.07e9 / 1e12}
 
 
+# DRAM bytes per launch (dram__bytes read + write) of the kernel behind a class at 128^3, default
+# mixed precision, from one ncu capture of the unchanged kernel (summaries under profiles/).
+NCU_TRAFFIC_128 = {
+    "outer_op64": (172.4e6, "profiles/k_jprod_transpose_fp64_128cubed.md"),
+    "residual": (107.5e6, "profiles/k_residual_fp64_128cubed.md"),
+    "mg_op0": (69.1e6, "profiles/k_level0_apply_float_128cubed.md"),
+}
+
+
 def roofline_entry(name, v, peaks, df64=False):
     ms, n, nbytes, flops = v
     per_launch_s = ms * 1e-3 / n
@@ -422,6 +431,8 @@ def run_gpu(args, rank, world, local):
         peaks = json.load(fh)
     df64 = pb_params["precision"] == nc.NC_PREC_MIXED and pb_params["outer_arith"] == nc.NC_ARITH_DF64
     roof = roofline_entry(dom, prof[dom], peaks, df64) if prof[dom][1] > 0 else None
+    if roof and n == 128 and not df64 and dom in NCU_TRAFFIC_128:
+        roof["traffic"], roof["traffic_source"] = NCU_TRAFFIC_128[dom]
     if roof:
         roof["timed"] = "live, CUDA events on the library stream around every launch of this class in the timed region"
     # breakdown and per-class rooflines from the profiled warm-up steps (all classes timed)
