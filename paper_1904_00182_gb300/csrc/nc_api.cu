@@ -474,15 +474,16 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
   };
   PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.x, om, tr, true, pb->st, &pb->cnt));
   for (int it = 1; it < nu1; ++it) CKS(sweep());
+  MGLevelDev<R>& c = mg.lev[l + 1];
   if (l == 0) {
+    // residual b - A x restricted directly, without storing it
     CKS(level_apply<R>(pb, l, tr, d.x, d.y));
-    PCK(NC_PROF_SMOOTH, launch_sub<R>(d.g, d.b, d.y, d.xn, pb->st, &pb->cnt));
+    PCK(NC_PROF_SMOOTH, launch_restrict_residual<R>(d.g, c.g, d.b, d.y, c.b, pb->st, &pb->cnt));
   } else {
     PCK(l == 1 ? NC_PROF_MG_STENCIL_L1 : NC_PROF_MG_STENCIL,
         launch_stencil_apply<R>(d.g, d.S, d.x, d.b, d.dinv, om, d.xn, tr, 1, pb->st, &pb->cnt));
+    PCK(NC_PROF_SMOOTH, launch_restrict<R>(d.g, c.g, d.xn, c.b, pb->st, &pb->cnt));
   }
-  MGLevelDev<R>& c = mg.lev[l + 1];
-  PCK(NC_PROF_SMOOTH, launch_restrict<R>(d.g, c.g, d.xn, c.b, pb->st, &pb->cnt));
   CKS(vcycle<R>(pb, l + 1, tr));
   PCK(NC_PROF_SMOOTH, launch_prolong_add<R>(d.g, c.g, c.x, d.x, pb->st, &pb->cnt));
   for (int it = 0; it < nu2; ++it) CKS(sweep());

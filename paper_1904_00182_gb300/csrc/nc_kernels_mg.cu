@@ -252,9 +252,9 @@ __global__ void k_sub(long long nn, const typename Vec2<R>::type* __restrict__ b
 
 // Full weighting (R = P^T) at coarse node (I, J, K): the fine residual rf at the 27 fine nodes
 // around it, weights 1, 1/2, 1/4, 1/8 by distance; the top (Dirichlet) plane gets 0.
-template <typename R, typename LD>
-__device__ __forceinline__ typename Vec2<R>::type restrict_node(const Grid& gf, const typename Vec2<R>::type* rf,
-                                                                int I, int J, int K, bool top, LD ld) {
+template <typename R, typename FETCH>
+__device__ __forceinline__ typename Vec2<R>::type restrict_node_f(const Grid& gf, int I, int J, int K, bool top,
+                                                                  FETCH fetch) {
   R a0 = R(0), a1 = R(0);
   if (!top) {
 #pragma unroll
@@ -273,7 +273,7 @@ __device__ __forceinline__ typename Vec2<R>::type restrict_node(const Grid& gf, 
           const int i = 2 * I + di;
           if (i < 0 || i > gf.nx) continue;
           const R w = wj * (di ? R(0.5) : R(1));
-          const typename Vec2<R>::type v = ld(rf + row + i);
+          const typename Vec2<R>::type v = fetch(row + i);
           a0 += w * v.x;
           a1 += w * v.y;
         }
@@ -281,6 +281,27 @@ __device__ __forceinline__ typename Vec2<R>::type restrict_node(const Grid& gf, 
     }
   }
   return mk2<R>(a0, a1);
+}
+
+template <typename R, typename LD>
+__device__ __forceinline__ typename Vec2<R>::type restrict_node(const Grid& gf, const typename Vec2<R>::type* rf,
+                                                                int I, int J, int K, bool top, LD ld) {
+  return restrict_node_f<R>(gf, I, J, K, top, [&](int m) { return ld(rf + m); });
+}
+
+// Full weighting of the fine residual r = b - y formed on the fly (no stored residual vector).
+template <typename R>
+__global__ void k_restrict_res(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ b,
+                               const typename Vec2<R>::type* __restrict__ y, typename Vec2<R>::type* __restrict__ bc) {
+  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pidx >= gc.NXY) return;
+  const int K = blockIdx.y;
+  const int J = pidx / gc.NX;
+  const int I = pidx - J * gc.NX;
+  bc[pidx + gc.NXY * K] = restrict_node_f<R>(gf, I, J, K, K >= gc.nz, [&](int m) {
+    const typename Vec2<R>::type bb = b[m], yy = y[m];
+    return mk2<R>(bb.x - yy.x, bb.y - yy.y);
+  });
 }
 
 template <typename R>
@@ -680,8 +701,8 @@ __global__ void __launch_bounds__(256) k_coarse_fix(const float* __restrict__ Ai
 
 // ---- fused multigrid tail (one thread-block cluster) ---------------------------------------------
 // The steps of vcycle() on levels l0 .. L-1 in launch order; every step is a grid-stride loop over
-// the cluster's threads followed by a cluster barrier (release/acquire at cluster scope, after a
-// fence). Vectors written inside the kernel are read through L2 (LdCG).
+// the cluster's threads followed by a cluster barrier (release/acquire at cluster scope). Vectors
+// written inside the kernel are read through L2 (LdCG).
 template <typename R, bool TR>
 __global__ void __launch_bounds__(1024, 1) k_mg_tail(const TailArgs<R> A) {
   typedef typename Vec2<R>::type V;
@@ -697,7 +718,9 @@ __global__ void __launch_bounds__(1024, 1) k_mg_tail(const TailArgs<R> A) {
     x[l] = l < L ? A.lev[l].x : nullptr;
     xn[l] = l < L ? A.lev[l].xn : nullptr;
   }
-  auto barrier = [&]() { __threadfence(); cl.sync(); };
+  // cluster barrier: arrive has release and wait acquire semantics at cluster scope, which orders
+  // the global-memory writes of one step before the reads of the next in every CTA of the cluster
+  auto barrier = [&]() { cl.sync(); };
   auto smooth = [&](int l) {   // xn = x + omega D^-1 (b - A x), then swap
     const TailLevel<R>& d = A.lev[l];
     for (int n = t; n < (int)d.g.nn; n += T) {
@@ -870,6 +893,16 @@ cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const typename Vec2<
 }
 
 template <typename R>
+cudaError_t launch_restrict_residual(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* b,
+                                     const typename Vec2<R>::type* y, typename Vec2<R>::type* bc, cudaStream_t st,
+                                     Counters* c) {
+  const Launch3 L = launch_nodes_flat(gc);
+  k_restrict_res<R><<<L.grid, L.block, 0, st>>>(gf, gc, b, y, bc);
+  if (c) { c->launches += 1; c->bytes += sizeof(R) * 2.0 * (2.0 * gf.nn + gc.nn); }
+  return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_prolong_add(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* xc,
                                typename Vec2<R>::type* xf, cudaStream_t st, Counters* c) {
   const Launch3 L = launch_nodes_flat(gf);
@@ -1036,6 +1069,8 @@ cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st
                                      cudaStream_t, Counters*);                                                 \
   template cudaError_t launch_restrict<R>(const Grid&, const Grid&, const Vec2<R>::type*, Vec2<R>::type*,     \
                                           cudaStream_t, Counters*);                                            \
+  template cudaError_t launch_restrict_residual<R>(const Grid&, const Grid&, const Vec2<R>::type*,            \
+                                                   const Vec2<R>::type*, Vec2<R>::type*, cudaStream_t, Counters*); \
   template cudaError_t launch_prolong_add<R>(const Grid&, const Grid&, const Vec2<R>::type*, Vec2<R>::type*,  \
                                              cudaStream_t, Counters*);                                         \
   template cudaError_t launch_dense_assemble<R>(const Grid&, const R*, double*, int, cudaStream_t, Counters*);\

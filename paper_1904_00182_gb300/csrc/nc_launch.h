@@ -232,6 +232,11 @@ cudaError_t launch_sub(const Grid& g, const typename Vec2<R>::type* b, const typ
 template <typename R>
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* rf,
                             typename Vec2<R>::type* bc, cudaStream_t st, Counters* c);
+// Restriction of the residual b - y formed on the fly (level 0: no residual vector is stored).
+template <typename R>
+cudaError_t launch_restrict_residual(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* b,
+                                     const typename Vec2<R>::type* y, typename Vec2<R>::type* bc, cudaStream_t st,
+                                     Counters* c);
 // x_f += P x_c
 template <typename R>
 cudaError_t launch_prolong_add(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* xc,
