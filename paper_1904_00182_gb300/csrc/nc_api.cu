@@ -546,7 +546,16 @@ nc_status kry_op(nc_problem* pb, bool tr, bool fp32, const float* z, float* w) {
 }
 
 nc_status kry_op(nc_problem* pb, bool tr, bool fp32, const double* z, double* w) {
-  return outer_op(pb, tr, fp32, z, w);
+  if (fp32) {
+    // z was just produced by the FP32 preconditioner: its FP32 copy (z rounded to FP32, exactly the
+    // finest level's x) is still in the hierarchy, so the operator reads it without a cast
+    const Grid& g = pb->g;
+    PCK(NC_PROF_OUTER_OP32, launch_level0_apply<float>(g, pb->ph, pb->s32, pb->mat32, pb->mg32.lev[0].x, pb->y32, tr,
+                                                       pb->st, &pb->cnt));
+    PCK(NC_PROF_OUTER_OP32, launch_cast_f2d(w, (const float*)pb->y32, 2 * g.nn, pb->st, &pb->cnt));
+    return NC_OK;
+  }
+  return outer_op(pb, tr, false, z, w);
 }
 
 // Default re-orthogonalisation threshold of FP64 bases: a second pass only when the first cancelled
