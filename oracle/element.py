@@ -107,6 +107,12 @@ class ElementModel:
         RT += w * k[:, None] * np.einsum("qai,eqi->ea", D, st["Hq"])
         return RP, RT
 
+    def supg_load(self, pe, te, kappa, Qq):
+        """f_tQ,e of Eq. objdiscr: sum_q w Q_q N*_a(q), (E, 8); depends on the state through u0, tau."""
+        st = self.gauss_state(pe, te, kappa)
+        Nstar = self.N[None] + st["tau"][:, None, None] * np.einsum("ei,qai->eqa", st["u0"], self.D)
+        return self.w * np.einsum("eqa,eq->ea", Nstar, Qq)
+
     # ---- directional derivative -------------------------------------------------------------
     def _dres(self, st, k, Qq, duq, du0, dHq, dk):
         """Linearised residual for given perturbations of u_q, u0, grad T_q and k."""

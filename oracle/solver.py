@@ -10,7 +10,10 @@
   in the design doc (full step if it reduces phi = ||R||^2 by 1e-4 phi0, else the best of a
   parabola through phi(0), phi(1/2), phi(1) and those two points, else halving).
 * Objective: the mean temperature over the heated region (Galerkin weights), the
-  normalised thermal compliance of Eq. objfunc for a uniform source.
+  normalised thermal compliance of Eq. objfunc for a uniform source; and the discrete thermal
+  compliance of Eq. objdiscr, sum_e f_tQ,e^T t_e with the SUPG-weighted source load (its state
+  derivative by complex step; no explicit design derivative, since the source lies in the passive
+  heated region).
 * Adjoint: J^T lambda = df/ds on the free DOFs; sensitivities
   df/dgamma~_e = -lambda_e^T dR_e/dgamma~_e (Sec. 5.1 "adjoint sensitivity analysis"),
   then the filter transpose.
@@ -314,10 +317,42 @@ class Problem:
         s = self.s if s is None else s
         return float(self.objective_weights() @ s)
 
-    def solve_adjoint(self):
+    # ---- thermal compliance of Eq. objdiscr (SUPG-weighted source) --------------------------
+    def _supg_elems(self, s, sl, cplx_dof=None, h=1e-30):
+        """Element values f_e = f_tQ,e . t_e of the heated elements sl; with cplx_dof = d (0..15)
+        the d-th element DOF gets the imaginary step i h (complex-step derivative)."""
+        pe, te = self.gather(s, sl)
+        if cplx_dof is not None:
+            pe, te = pe.astype(complex), te.astype(complex)
+            (pe if cplx_dof < 8 else te)[:, cplx_dof % 8] += 1j * h
+        Qq = np.repeat(self.q_scale * self.Qe[sl, None], 8, axis=1)
+        return np.sum(self.em.supg_load(pe, te, self.kappa[sl], Qq) * te, axis=1)
+
+    def supg_compliance(self, s=None):
+        """f = sum_e f_tQ,e^T t_e (Eq. objdiscr), over the elements with a source."""
+        s = self.s if s is None else s
+        el = np.flatnonzero(self.Qe != 0.0)
+        return float(np.sum(self._supg_elems(s, el)))
+
+    def supg_compliance_weights(self, s=None):
+        """df/ds of supg_compliance by complex-step differentiation of the element values."""
+        s = self.s if s is None else s
+        el = np.flatnonzero(self.Qe != 0.0)
+        cn = self.conn[el]
+        d = np.zeros(2 * self.mesh.n_nodes)
+        h = 1e-30
+        for dof in range(16):
+            g = np.imag(self._supg_elems(s, el, dof, h)) / h
+            d += np.bincount(2 * cn[:, dof % 8] + (1 if dof >= 8 else 0), g, minlength=d.size)
+        d[self.dir_mask] = 0.0
+        return d
+
+    def solve_adjoint(self, objective="mean_T"):
+        """J^T lambda = df/ds on the free DOFs; objective "mean_T" (default) or "supg_compliance"."""
         J = self.jacobian_full(self.s)
         Jf = J[self.free][:, self.free]
-        rhs = self.objective_weights()[self.free]
+        w = self.objective_weights() if objective == "mean_T" else self.supg_compliance_weights()
+        rhs = w[self.free]
         lam = np.zeros(2 * self.mesh.n_nodes)
         lam[self.free] = spla.spsolve(Jf.T.tocsc(), rhs)
         self.lam = lam
