@@ -67,7 +67,10 @@ enum { NC_PREC_MIXED = 0, NC_PREC_FP64 = 1 };
 enum { NC_ARITH_DF64 = 0, NC_ARITH_FP64 = 1 };
 /* Krylov basis storage on the mixed-precision path (nc_params.krylov_basis). */
 enum { NC_BASIS_FP64 = 0, NC_BASIS_FP32 = 1 };
-enum { NC_OBJ_MEAN_T_HEATED = 0 };
+/* Objectives: the mean temperature over the heated region (Galerkin weights; equal to the thermal
+ * compliance of Eq. objfunc when the total power is 1), or the discrete thermal compliance of
+ * Eq. objdiscr, sum_e f_tQ,e^T t_e, whose SUPG-weighted source load depends on the state. */
+enum { NC_OBJ_MEAN_T_HEATED = 0, NC_OBJ_SUPG_COMPLIANCE = 1 };
 
 typedef struct nc_problem nc_problem;
 

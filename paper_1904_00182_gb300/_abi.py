@@ -14,6 +14,7 @@ NC_ARITH_FP64 = 1
 NC_BASIS_FP64 = 0
 NC_BASIS_FP32 = 1
 NC_OBJ_MEAN_T_HEATED = 0
+NC_OBJ_SUPG_COMPLIANCE = 1
 
 STATUS_NAMES = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_OOM", 3: "NC_ERR_CUDA", 4: "NC_ERR_DIVERGED",
                 5: "NC_ERR_MAXIT", 6: "NC_ERR_NAN", 7: "NC_ERR_TIMEOUT", 8: "NC_ERR_STATE"}

@@ -1223,10 +1223,21 @@ nc_status nc_solve_state(nc_problem* pb, nc_stats* stats) {
 
 nc_status nc_objective(nc_problem* pb, int objective, double* f) {
   if (!pb || !f) return NC_ERR_ARG;
-  if (objective != NC_OBJ_MEAN_T_HEATED) return fail(pb, NC_ERR_ARG, "unknown objective");
+  if (objective != NC_OBJ_MEAN_T_HEATED && objective != NC_OBJ_SUPG_COMPLIANCE)
+    return fail(pb, NC_ERR_ARG, "unknown objective");
   if (pb->stage < 2) return fail(pb, NC_ERR_STATE, "objective needs a solved state");
   DeviceGuard dg(pb->device);
   const Grid& g = pb->g;
+  if (objective == NC_OBJ_SUPG_COMPLIANCE) {
+    set_q_scale(pb, 1.0);
+    const long long nh = (long long)g.nx * g.ny * pb->par.heated_layers;
+    PCK(NC_PROF_OTHER, launch_obj_supg(g, pb->ph, pb->s, pb->mat, pb->gsens, pb->rhs, pb->st, &pb->cnt));
+    PCK(NC_PROF_OTHER, launch_sum(pb->gsens, nh, pb->part, pb->dres, pb->st, &pb->cnt));
+    CK(cudaMemcpyAsync(pb->hres, pb->dres, sizeof(double), cudaMemcpyDeviceToHost, pb->st));
+    CKS(sync(pb, "objective"));
+    *f = pb->hres[0];
+    return NC_OK;
+  }
   PCK(NC_PROF_OTHER, launch_dfds(g, pb->par.heated_layers, g.h * g.h * g.h / 8.0 / pb->vol_h, pb->rhs, pb->st, &pb->cnt));
   CKS(dots(pb, pb->rhs, 0, 1, (const double*)pb->s, 2 * g.nn, f));
   return NC_OK;

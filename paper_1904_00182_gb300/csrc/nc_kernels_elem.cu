@@ -143,6 +143,45 @@ __global__ void k_u_centroid(Grid g, Phys ph, ElemConst<double> C, const double2
   u[3 * e + 2] = st.u0z;
 }
 
+// Thermal compliance of Eq. objdiscr on one heated element, f_e = f_tQ,e . t_e with the SUPG-weighted
+// source load f_tQ,e,a = sum_q w Q N*_a(q), N* = N + tau u0 . grad N. With sum_q N_a(q) = 1 on the
+// 2x2x2 rule: f_e = Q w (sum_a t_a + tau u0 . G), G = sum_q grad T_q. Its state derivative (the
+// adjoint load) follows from du0 = -(c/8) sum_q (grad dP_q - beta dT_q e_z) and
+// dtau = -tau^3 (4/h_e^2) u0 . du0:
+//   df_e = Q w [ sum_q dT_q + tau u0 . sum_q grad dT_q + A . du0 ],  A = tau G - tau^3 (4/h_e^2)(u0 . G) u0,
+// i.e. test-function sums with constant coefficients: T rows N-part Q w (1 + (c/8) beta A_z) and
+// gradient part Q w tau u0; P rows gradient part -Q w (c/8) A.
+__global__ void k_obj_supg(Grid g, Phys ph, ElemConst<double> C, const double2* __restrict__ s,
+                           const double2* __restrict__ mat, double* __restrict__ fe, double* __restrict__ d) {
+  NC_ELEM_PROLOGUE();
+  double p[8], t[8];
+  gather_state<double>(g, s, n0, p, t);
+  const double2 m = mat[e];
+  const double Q = elem_source<double>(ph, k);
+  ElemState<double> st;
+  elem_state(C, p, t, m.x, Q, st);
+  double Gx = 0, Gy = 0, Gz = 0, tsum = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { Gx += st.hx[q]; Gy += st.hy[q]; Gz += st.hz[q]; tsum += t[q]; }
+  const double Qw = Q * C.w;
+  const double u0G = st.u0x * Gx + st.u0y * Gy + st.u0z * Gz;
+  fe[e] = Qw * (tsum + st.tau * u0G);
+  const double t3 = st.tau * st.tau * st.tau * C.c4he2 * u0G;
+  const double Ax = st.tau * Gx - t3 * st.u0x, Ay = st.tau * Gy - t3 * st.u0y, Az = st.tau * Gz - t3 * st.u0z;
+  const double cb = 0.125 * st.c;
+  double An[8], Bx[8], By[8], Bz[8], oP[8], oT[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    An[q] = Qw * (1.0 + cb * C.beta * Az);
+    Bx[q] = Qw * st.tau * st.u0x; By[q] = Qw * st.tau * st.u0y; Bz[q] = Qw * st.tau * st.u0z;
+  }
+  q1_test<double, true>(An, Bx, By, Bz, C.cp, C.cm, C.ih, oT);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { Bx[q] = -Qw * cb * Ax; By[q] = -Qw * cb * Ay; Bz[q] = -Qw * cb * Az; }
+  q1_test<double, false>(nullptr, Bx, By, Bz, C.cp, C.cm, C.ih, oP);
+  scatter_add(g, d, n0, top, oP, oT);
+}
+
 // ---- double-float variants (mixed-precision path) ----
 // Minimum resident blocks of 128 threads per SM (register budget) of the double-float kernels.
 #ifndef NC_LB_RESIDUAL_DF
@@ -230,6 +269,17 @@ __global__ void __launch_bounds__(128, NC_LB_SENS_DF) k_sens_df(Grid g, Phys ph,
 }
 
 }  // namespace
+
+cudaError_t launch_obj_supg(const Grid& g, const Phys& ph, const double2* s, const double2* mat, double* fe,
+                            double* d, cudaStream_t st, Counters* c) {
+  cudaError_t err = cudaMemsetAsync(d, 0, sizeof(double) * 2 * g.nn, st);
+  if (err != cudaSuccess) return err;
+  Launch3 L = launch_elems(g);
+  L.grid.z = (unsigned)ph.heated_layers;   // the source lies in the heated layers only
+  k_obj_supg<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<double>(ph), s, mat, fe, d);
+  if (c) { c->launches += 1; c->bytes += 16.0 * g.nn + 24.0 * g.nx * g.ny * ph.heated_layers; }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_split2(const double2* x, float4* y, long long n, cudaStream_t st, Counters* c) {
   k_split2<<<grid_blocks(n, 256, 152 * 16), 256, 0, st>>>(x, y, n);

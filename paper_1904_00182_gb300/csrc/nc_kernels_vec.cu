@@ -192,6 +192,18 @@ __global__ void k_norm2_free_part(const double* __restrict__ a, long long nfree2
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// Plain sum of a vector (segment per block).
+__global__ void k_sum_part(const double* __restrict__ a, long long n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const long long seg = (n + gridDim.x - 1) / gridDim.x;
+  const long long lo = seg * blockIdx.x;
+  const long long hi = min(n, lo + seg);
+  double acc = 0.0;
+  for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) acc += a[t];
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
 struct Coef64 { double c[64]; };
 
 // y += sum_i c_i V_i; FP32 basis vectors are combined in FP32 and the sum is added to y in y's type.
@@ -466,6 +478,14 @@ cudaError_t launch_multidot(const double* V, long long ld, int nvec, const doubl
 cudaError_t launch_multidot(const float* V, long long ld, int nvec, const float* w, long long n,
                             double* part, double* res, cudaStream_t st, Counters* c) {
   return launch_multidot_t<float>(V, ld, nvec, w, n, part, res, st, c);
+}
+
+cudaError_t launch_sum(const double* a, long long n, double* part, double* res, cudaStream_t st, Counters* c) {
+  const int nb = reduce_blocks(n);
+  k_sum_part<<<nb, kRedThreads, 0, st>>>(a, n, part);
+  k_sum_parts<<<1, 256, 0, st>>>(part, nb, 1, res);
+  if (c) { c->launches += 2; c->bytes += 8.0 * n; }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, double* res, cudaStream_t st,

@@ -77,6 +77,10 @@ cudaError_t launch_jtv_df(const Grid& g, const Phys& ph, const double2* s, const
                           const double2* w, float4* w_df, double* out, double2* dl, cudaStream_t st, Counters* c);
 cudaError_t launch_sens_df(const Grid& g, const Phys& ph, const double2* s, const double2* lam, const float4* mat_df,
                            const double2* dmat, float4* s_df, float4* l_df, double* out, cudaStream_t st, Counters* c);
+// Thermal compliance of Eq. objdiscr on the heated elements: fe[e] = f_tQ,e . t_e for e in the heated
+// layers (other entries untouched) and d = its state derivative (2N, zeroed first).
+cudaError_t launch_obj_supg(const Grid& g, const Phys& ph, const double2* s, const double2* mat, double* fe,
+                            double* d, cudaStream_t st, Counters* c);
 // Centroid Darcy velocity (3 per element).
 cudaError_t launch_u_centroid(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
                               double* u, cudaStream_t st, Counters* c);
@@ -92,6 +96,8 @@ cudaError_t launch_multidot(const double* V, long long ld, int nvec, const doubl
                             double* part, double* res, cudaStream_t st, Counters* c);
 cudaError_t launch_multidot(const float* V, long long ld, int nvec, const float* w, long long n,
                             double* part, double* res, cudaStream_t st, Counters* c);
+// res[0] = sum of a[0..n) (deterministic two-stage reduction).
+cudaError_t launch_sum(const double* a, long long n, double* part, double* res, cudaStream_t st, Counters* c);
 // res[0] = sum over free entries (Dirichlet rows excluded) of a^2, for a state vector.
 cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, double* res,
                               cudaStream_t st, Counters* c);

@@ -155,3 +155,33 @@ def test_state_adjoint_sensitivities(lib, shape, alpha, seed, variant):
     go = op.sensitivities()
     assert rel(g, go) < 1e-6
     gp.close()
+
+
+@pytest.mark.parametrize("shape,alpha,seed", CASES)
+@pytest.mark.parametrize("precision,tol", [(1, 1e-8), (0, 1e-6)])
+def test_supg_compliance_objective(lib, shape, alpha, seed, precision, tol):
+    """Thermal compliance of Eq. objdiscr (SUPG-weighted source): value at the GPU state against the
+    oracle (1e-12), and the objective, adjoint and sensitivities of the solved problem against the
+    oracle's. The heated region gets the fluid permeability (kappa_s = kappa_f) so that its Darcy
+    velocity, which the SUPG weights see, is not negligible."""
+    nx, ny, nz = shape
+    h = 1.0 / nz
+    rho = filtered_random(nx, ny, nz, seed, volfrac=0.2)
+    gp = lib.Problem(nx, ny, nz, h, alpha=alpha, precision=precision, newton_rtol=1e-10, kappa_ratio=1.0)
+    op = oracle.Problem(oracle.Mesh(nx, ny, nz, h), oracle.Params(alpha=alpha, newton_rtol=1e-10, kappa_ratio=1.0))
+    gp.set_design(rho)
+    op.set_design(rho)
+    gp.solve_state()
+    op.solve_state()
+    P, T, _ = gp.get_fields(velocity=False)
+    s = np.empty(2 * op.mesh.n_nodes)
+    s[0::2], s[1::2] = P.cpu().numpy(), T.cpu().numpy()
+    f = gp.objective(lib.NC_OBJ_SUPG_COMPLIANCE)
+    assert f == pytest.approx(op.supg_compliance(s), rel=1e-12)
+    assert f == pytest.approx(op.supg_compliance(), rel=tol)
+    fa, _ = gp.solve_adjoint(lib.NC_OBJ_SUPG_COMPLIANCE)
+    assert fa == f
+    lam_o = op.solve_adjoint("supg_compliance")
+    assert rel(gp.adjoint().cpu().numpy(), lam_o) < 1e-6
+    assert rel(gp.sensitivities().cpu().numpy(), op.sensitivities()) < 1e-6
+    gp.close()
