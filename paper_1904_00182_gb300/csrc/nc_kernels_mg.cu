@@ -65,9 +65,8 @@ __device__ __forceinline__ void add_diag_block(R* __restrict__ diag, long long n
 template <typename R>
 __device__ __forceinline__ void galerkin_phase2(R (*Jc)[16 * NC_LD], R (*Tc)[16 * NC_LD], R* __restrict__ out) {
   const int t = threadIdx.x;
-  const int c = t >> 4, rc = t & 15;
-  {
-    const int row = rc;
+  for (int it = t; it < 128; it += blockDim.x) {   // (child, row) pairs
+    const int c = it >> 4, row = it & 15;
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
       R in[8], o[8];
@@ -79,8 +78,8 @@ __device__ __forceinline__ void galerkin_phase2(R (*Jc)[16 * NC_LD], R (*Tc)[16 
     }
   }
   __syncthreads();
-  {
-    const int col = rc;
+  for (int it = t; it < 128; it += blockDim.x) {   // (child, column) pairs
+    const int c = it >> 4, col = it & 15;
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
       R in[8], o[8];
@@ -92,7 +91,7 @@ __device__ __forceinline__ void galerkin_phase2(R (*Jc)[16 * NC_LD], R (*Tc)[16 
     }
   }
   __syncthreads();
-  for (int idx = t; idx < 256; idx += 128) {
+  for (int idx = t; idx < 256; idx += blockDim.x) {
     const int r = idx >> 4, q = idx & 15;
     R acc = R(0);
 #pragma unroll
@@ -101,8 +100,14 @@ __device__ __forceinline__ void galerkin_phase2(R (*Jc)[16 * NC_LD], R (*Tc)[16 
   }
 }
 
+// Columns of the element Jacobian per thread (block of 128 / CPT threads): the thread computes its
+// child's Gauss-point state once for its CPT columns.
+#ifndef NC_GALERKIN_CPT
+#define NC_GALERKIN_CPT 4
+#endif
+
 template <typename R>
-__global__ void __launch_bounds__(128) k_galerkin_fine(Grid gf, Grid gc, Phys ph, ElemConst<R> C,
+__global__ void __launch_bounds__(128 / NC_GALERKIN_CPT) k_galerkin_fine(Grid gf, Grid gc, Phys ph, ElemConst<R> C,
                                                        const typename Vec2<R>::type* __restrict__ s,
                                                        const typename Vec2<R>::type* __restrict__ mat,
                                                        R* __restrict__ diag_f, R* __restrict__ ebe_c) {
@@ -111,8 +116,9 @@ __global__ void __launch_bounds__(128) k_galerkin_fine(Grid gf, Grid gc, Phys ph
   const long long E = blockIdx.x;
   int I, J, K;
   elem_ijk(gc, E, I, J, K);
+  constexpr int kCols = 16 / NC_GALERKIN_CPT;   // threads per child
   const int t = threadIdx.x;
-  const int c = t >> 4, col = t & 15;
+  const int c = t / kCols, col0 = t % kCols;
   const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
   R p[8], tt[8];
 #pragma unroll
@@ -125,19 +131,22 @@ __global__ void __launch_bounds__(128) k_galerkin_fine(Grid gf, Grid gc, Phys ph
   const typename Vec2<R>::type m = mat[e];
   ElemState<R> st;
   elem_state(C, p, tt, m.x, k < ph.heated_layers ? (R)ph.Q : R(0), st);
-  R oP[8], oT[8];
-  elem_jac_column<R>(C, st, m.y, col, oP, oT);
+  for (int cc = 0; cc < NC_GALERKIN_CPT; ++cc) {
+    const int col = col0 + cc * kCols;
+    R oP[8], oT[8];
+    elem_jac_column<R>(C, st, m.y, col, oP, oT);
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    Jc[c][r * NC_LD + col] = oP[r];
-    Jc[c][(8 + r) * NC_LD + col] = oT[r];
-  }
-  // block diagonal of level 0 (row-major [PP PT; TP TT]) on free nodes
-  const int a = col & 7;
-  if (k + (a >> 2) < gf.nz) {
-    const long long n = corner_node(gf, i, j, k, a);
-    if (col < 8) { add_diag_block(diag_f, n, 0, oP[a]); add_diag_block(diag_f, n, 2, oT[a]); }
-    else { add_diag_block(diag_f, n, 1, oP[a]); add_diag_block(diag_f, n, 3, oT[a]); }
+    for (int r = 0; r < 8; ++r) {
+      Jc[c][r * NC_LD + col] = oP[r];
+      Jc[c][(8 + r) * NC_LD + col] = oT[r];
+    }
+    // block diagonal of level 0 (row-major [PP PT; TP TT]) on free nodes
+    const int a = col & 7;
+    if (k + (a >> 2) < gf.nz) {
+      const long long n = corner_node(gf, i, j, k, a);
+      if (col < 8) { add_diag_block(diag_f, n, 0, oP[a]); add_diag_block(diag_f, n, 2, oT[a]); }
+      else { add_diag_block(diag_f, n, 1, oP[a]); add_diag_block(diag_f, n, 3, oT[a]); }
+    }
   }
   __syncthreads();
   galerkin_phase2<R>(Jc, Tc, ebe_c + E * 256);
@@ -815,11 +824,12 @@ template <typename R>
 cudaError_t launch_galerkin_fine(const Grid& gf, const Grid& gc, const Phys& ph, const typename Vec2<R>::type* s,
                                  const typename Vec2<R>::type* mat, R* diag_f, R* ebe_c, cudaStream_t st,
                                  Counters* c) {
-  k_galerkin_fine<R><<<(unsigned)gc.ne, 128, 0, st>>>(gf, gc, ph, make_econst<R>(ph), s, mat, diag_f, ebe_c);
+  k_galerkin_fine<R><<<(unsigned)gc.ne, 128 / NC_GALERKIN_CPT, 0, st>>>(gf, gc, ph, make_econst<R>(ph), s, mat, diag_f,
+                                                                      ebe_c);
   if (c) {
     c->launches += 1;
     c->bytes += sizeof(R) * (2.0 * gf.nn + 2.0 * gf.ne + 4.0 * gf.nn + 256.0 * gc.ne);
-    c->flops += 16.0 * (kFlopsState + kFlopsJacColumn) * gf.ne;
+    c->flops += (kFlopsState + 16.0 * kFlopsJacColumn) * gf.ne;   // one element state, 16 columns
   }
   return cudaGetLastError();
 }
