@@ -66,6 +66,10 @@ struct MG {
   float* W = nullptr;      // Gauss-Jordan scratch (nf x 2nf)
   double* cw = nullptr;    // coarse-solve scratch (3 nf)
   int nf = 0;
+  // during a preconditioner call with FP64 vectors: its input (read by the first finest-level
+  // update) and output (written by the last one); null otherwise
+  const double* in64 = nullptr;
+  double* out64 = nullptr;
 };
 
 }  // namespace
@@ -461,10 +465,14 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
       for (int sw = 0; sw < (nu1 - 1) + nu2; ++sw) std::swap(mg.lev[q].x, mg.lev[q].xn);
     return NC_OK;
   }
-  auto sweep = [&]() -> nc_status {
+  auto sweep = [&](bool last) -> nc_status {
     if (l == 0) {
       CKS(level_apply<R>(pb, l, tr, d.x, d.y));
-      PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.xn, om, tr, false, pb->st, &pb->cnt));
+      if (last && mg.out64)
+        PCK(NC_PROF_SMOOTH, launch_jacobi_io<R>(d.g, d.dinv, d.b, nullptr, d.y, d.x, d.xn, mg.out64, om, tr, false,
+                                                pb->st, &pb->cnt));
+      else
+        PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.xn, om, tr, false, pb->st, &pb->cnt));
     } else {
       PCK(l == 1 ? NC_PROF_MG_STENCIL_L1 : NC_PROF_MG_STENCIL,
           launch_stencil_apply<R>(d.g, d.S, d.x, d.b, d.dinv, om, d.xn, tr, 2, pb->st, &pb->cnt));
@@ -472,8 +480,12 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
     std::swap(d.x, d.xn);
     return NC_OK;
   };
-  PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.x, om, tr, true, pb->st, &pb->cnt));
-  for (int it = 1; it < nu1; ++it) CKS(sweep());
+  if (l == 0 && mg.in64)
+    PCK(NC_PROF_SMOOTH, launch_jacobi_io<R>(d.g, d.dinv, d.b, mg.in64, d.y, d.x, d.x, nullptr, om, tr, true, pb->st,
+                                            &pb->cnt));
+  else
+    PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.x, om, tr, true, pb->st, &pb->cnt));
+  for (int it = 1; it < nu1; ++it) CKS(sweep(false));
   MGLevelDev<R>& c = mg.lev[l + 1];
   if (l == 0) {
     // residual b - A x restricted directly, without storing it
@@ -486,22 +498,33 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
   }
   CKS(vcycle<R>(pb, l + 1, tr));
   PCK(NC_PROF_SMOOTH, launch_prolong_add<R>(d.g, c.g, c.x, d.x, pb->st, &pb->cnt));
-  for (int it = 0; it < nu2; ++it) CKS(sweep());
+  for (int it = 0; it < nu2; ++it) CKS(sweep(it == nu2 - 1));
   return NC_OK;
 }
 
 // z = M^-1 v (one V-cycle), v and z FP64 state vectors.
 nc_status precondition(nc_problem* pb, bool tr, const double* v, double* z) {
+  // the finest level's first and last updates read v and write z directly (no separate casts);
+  // without post-smoothing z is copied out after the cycle
+  const bool post = pb->par.nu_post > 0;
   if (pb->par.precision == NC_PREC_FP64) {
     MG<double>& mg = pb->mg64;
-    PCK(NC_PROF_OTHER, launch_to_mg<double>(v, mg.lev[0].b, pb->g.nn, pb->st, &pb->cnt));
-    CKS(vcycle<double>(pb, 0, tr));
-    PCK(NC_PROF_OTHER, launch_from_mg<double>(mg.lev[0].x, z, pb->g.nn, pb->st, &pb->cnt));
+    mg.in64 = v;
+    mg.out64 = post ? z : nullptr;
+    nc_status s = vcycle<double>(pb, 0, tr);
+    mg.in64 = nullptr;
+    mg.out64 = nullptr;
+    CKS(s);
+    if (!post) PCK(NC_PROF_OTHER, launch_from_mg<double>(mg.lev[0].x, z, pb->g.nn, pb->st, &pb->cnt));
   } else {
     MG<float>& mg = pb->mg32;
-    PCK(NC_PROF_OTHER, launch_to_mg<float>(v, mg.lev[0].b, pb->g.nn, pb->st, &pb->cnt));
-    CKS(vcycle<float>(pb, 0, tr));
-    PCK(NC_PROF_OTHER, launch_from_mg<float>(mg.lev[0].x, z, pb->g.nn, pb->st, &pb->cnt));
+    mg.in64 = v;
+    mg.out64 = post ? z : nullptr;
+    nc_status s = vcycle<float>(pb, 0, tr);
+    mg.in64 = nullptr;
+    mg.out64 = nullptr;
+    CKS(s);
+    if (!post) PCK(NC_PROF_OTHER, launch_from_mg<float>(mg.lev[0].x, z, pb->g.nn, pb->st, &pb->cnt));
   }
   return NC_OK;
 }

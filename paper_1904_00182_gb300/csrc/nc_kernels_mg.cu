@@ -250,6 +250,41 @@ __global__ void k_jacobi(long long nn, const R* __restrict__ dinv, const typenam
   xn[n] = mk2<R>(x0 + omega * z0, x1 + omega * z1);
 }
 
+// The same update at the finest level of a preconditioner call, reading and writing the caller's FP64
+// vectors directly: FIRST takes b from b64 (and keeps its R copy in b for the later sweeps); z64
+// (nullable) receives the new x in FP64 as well.
+template <typename R, bool TR, bool FIRST>
+__global__ void k_jacobi_io(long long nn, const R* __restrict__ dinv, typename Vec2<R>::type* __restrict__ b,
+                            const double2* __restrict__ b64, const typename Vec2<R>::type* __restrict__ y,
+                            const typename Vec2<R>::type* __restrict__ x, typename Vec2<R>::type* __restrict__ xn,
+                            double2* __restrict__ z64, R omega) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  R r0, r1;
+  if (FIRST) {
+    const double2 v = b64[n];
+    r0 = (R)v.x; r1 = (R)v.y;
+    b[n] = mk2<R>(r0, r1);
+  } else {
+    const typename Vec2<R>::type bb = b[n];
+    r0 = bb.x; r1 = bb.y;
+  }
+  R x0 = R(0), x1 = R(0);
+  if (!FIRST) {
+    const typename Vec2<R>::type yy = y[n];
+    const typename Vec2<R>::type xx = x[n];
+    r0 -= yy.x; r1 -= yy.y;
+    x0 = xx.x; x1 = xx.y;
+  }
+  const R* d = dinv + 4 * n;
+  R z0, z1;
+  if (TR) { z0 = d[0] * r0 + d[2] * r1; z1 = d[1] * r0 + d[3] * r1; }
+  else { z0 = d[0] * r0 + d[1] * r1; z1 = d[2] * r0 + d[3] * r1; }
+  const R o0 = x0 + omega * z0, o1 = x1 + omega * z1;
+  xn[n] = mk2<R>(o0, o1);
+  if (z64) z64[n] = make_double2((double)o0, (double)o1);
+}
+
 template <typename R>
 __global__ void k_sub(long long nn, const typename Vec2<R>::type* __restrict__ b,
                       const typename Vec2<R>::type* __restrict__ y, typename Vec2<R>::type* __restrict__ r) {
@@ -886,6 +921,29 @@ cudaError_t launch_jacobi_update(const Grid& g, const R* dinv, const typename Ve
 }
 
 template <typename R>
+cudaError_t launch_jacobi_io(const Grid& g, const R* dinv, typename Vec2<R>::type* b, const double* b64,
+                             const typename Vec2<R>::type* y, const typename Vec2<R>::type* x,
+                             typename Vec2<R>::type* xn, double* z64, R omega, bool transpose, bool first,
+                             cudaStream_t st, Counters* c) {
+  const unsigned nb = grid_blocks(g.nn, 256);
+  const double2* bi = (const double2*)b64;
+  double2* zo = (double2*)z64;
+  if (first) {
+    if (transpose) k_jacobi_io<R, true, true><<<nb, 256, 0, st>>>(g.nn, dinv, b, bi, y, x, xn, zo, omega);
+    else k_jacobi_io<R, false, true><<<nb, 256, 0, st>>>(g.nn, dinv, b, bi, y, x, xn, zo, omega);
+  } else {
+    if (transpose) k_jacobi_io<R, true, false><<<nb, 256, 0, st>>>(g.nn, dinv, b, bi, y, x, xn, zo, omega);
+    else k_jacobi_io<R, false, false><<<nb, 256, 0, st>>>(g.nn, dinv, b, bi, y, x, xn, zo, omega);
+  }
+  if (c) {
+    c->launches += 1;
+    c->bytes += (first ? 16.0 + 2.0 * sizeof(R) : 6.0 * sizeof(R)) * g.nn + 4.0 * sizeof(R) * g.nn +
+                2.0 * sizeof(R) * g.nn + (z64 ? 16.0 * g.nn : 0.0);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_sub(const Grid& g, const typename Vec2<R>::type* b, const typename Vec2<R>::type* y,
                        typename Vec2<R>::type* r, cudaStream_t st, Counters* c) {
   k_sub<R><<<grid_blocks(g.nn, 256), 256, 0, st>>>(g.nn, b, y, r);
@@ -1075,6 +1133,9 @@ cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st
   template cudaError_t launch_jacobi_update<R>(const Grid&, const R*, const Vec2<R>::type*,                   \
                                                const Vec2<R>::type*, const Vec2<R>::type*, Vec2<R>::type*, R, \
                                                bool, bool, cudaStream_t, Counters*);                           \
+  template cudaError_t launch_jacobi_io<R>(const Grid&, const R*, Vec2<R>::type*, const double*,              \
+                                           const Vec2<R>::type*, const Vec2<R>::type*, Vec2<R>::type*, double*, \
+                                           R, bool, bool, cudaStream_t, Counters*);                             \
   template cudaError_t launch_sub<R>(const Grid&, const Vec2<R>::type*, const Vec2<R>::type*, Vec2<R>::type*, \
                                      cudaStream_t, Counters*);                                                 \
   template cudaError_t launch_restrict<R>(const Grid&, const Grid&, const Vec2<R>::type*, Vec2<R>::type*,     \

@@ -230,6 +230,13 @@ cudaError_t launch_jacobi_update(const Grid& g, const R* dinv, const typename Ve
                                  const typename Vec2<R>::type* y, const typename Vec2<R>::type* x,
                                  typename Vec2<R>::type* xn, R omega, bool transpose, bool first,
                                  cudaStream_t st, Counters* c);
+// The finest-level update of a preconditioner call with FP64 input / output: first = true reads b
+// from b64 (storing its R copy in b); z64 (nullable) also receives the new x in FP64.
+template <typename R>
+cudaError_t launch_jacobi_io(const Grid& g, const R* dinv, typename Vec2<R>::type* b, const double* b64,
+                             const typename Vec2<R>::type* y, const typename Vec2<R>::type* x,
+                             typename Vec2<R>::type* xn, double* z64, R omega, bool transpose, bool first,
+                             cudaStream_t st, Counters* c);
 // r = b - y
 template <typename R>
 cudaError_t launch_sub(const Grid& g, const typename Vec2<R>::type* b, const typename Vec2<R>::type* y,
