@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--levels", type=int, default=6)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--fast-steps", type=int, default=2)
+    ap.add_argument("--concurrent-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -417,6 +418,39 @@ def run_gpu(args, rank, world, local):
                              "residual and sensitivities; FP32 Krylov basis with FP64 cross-thread sums; "
                              "convergence still judged on the FP64 residual norm")
 
+    # two independent problems in flight on two streams (the serving pattern at one grid size): FP64-
+    # and FP32-bound phases of the two solves overlap on the device
+    concurrent = None
+    if args.concurrent_steps > 0:
+        streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+        pcs = [nc.Problem(n, n, n, 1.0 / n, stream=streams[i].cuda_stream, device=dev, alpha=args.alpha,
+                          mg_levels=args.levels) for i in range(2)]
+
+        def worker(i, steps):
+            for j in range(steps):
+                pcs[i].set_design(rho_dev[(i + j) % ndes])
+                pcs[i].solve_state()
+                pcs[i].solve_adjoint()
+                pcs[i].sensitivities()
+
+        def run_both(steps):
+            ths = [threading.Thread(target=worker, args=(i, steps)) for i in range(2)]
+            for t in ths:
+                t.start()
+            for t in ths:
+                t.join()
+            torch.cuda.synchronize(dev)
+
+        run_both(1)
+        t0 = time.perf_counter()
+        run_both(args.concurrent_steps)
+        wall_c = time.perf_counter() - t0
+        for pc in pcs:
+            pc.close()
+        concurrent = {"in_flight": 2, "value": 2 * args.concurrent_steps / wall_c, "unit": UNIT,
+                      "ms_per_solve_per_problem": wall_c / args.concurrent_steps * 1e3,
+                      "timed": "host wall clock around both threads, device synchronised"}
+
     serving = None
     if not args.no_serve and rank == 0:
         serving = run_serving(args, dev)
@@ -455,7 +489,7 @@ def run_gpu(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
             "config": workload_config(args), "clocks": clk, "e2e": e2e,
             "gpu_launches": int(l1 - l0), "roofline": roof, "cpu_baseline": cpu,
-            "fp64_path": fp64, "mixed_fast": fast, "serving": serving,
+            "fp64_path": fp64, "mixed_fast": fast, "concurrent": concurrent, "serving": serving,
             "solver": {"newton_its": [s[0]["newton_its"] for s in timed_stats],
                        "krylov_its": [s[0]["krylov_its"] for s in timed_stats],
                        "adjoint_krylov_its": [s[1]["krylov_its"] for s in timed_stats],
