@@ -108,8 +108,10 @@ typedef struct {
   double timeout_s;     /* wall-clock limit of one call [600] */
   double adjoint_rtol;  /* adjoint stops at ||df/ds - J^T lambda|| <= adjoint_rtol ||df/ds||;
                            <= 0: the state's newton_rtol [0] */
-  int coarse_refactor;  /* 1: invert the coarsest multigrid matrix at every set-up; 0: at the first
-                           set-up of each solve call, later set-ups refine against the new matrix [0] */
+  int coarse_refactor;  /* when the coarsest multigrid matrix is inverted anew: 1 at every set-up; 0 at
+                           the first set-up of each solve call; 2 only once per problem. Later set-ups
+                           keep the inverse and the coarse solve's FP64 refinement step against the
+                           current matrix corrects for the change [0] */
   double krylov_eta_min; /* lower bound of the Newton forcing term; <= 0: 1e-12 [0] */
   double adjoint_eta_first; /* FGMRES tolerance of the first adjoint refinement pass; <= 0: 1e-5 with
                                NC_PREC_MIXED, the adjoint tolerance with NC_PREC_FP64 [0] */

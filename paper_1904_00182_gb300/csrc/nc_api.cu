@@ -70,6 +70,7 @@ struct MG {
   // update) and output (written by the last one); null otherwise
   const double* in64 = nullptr;
   double* out64 = nullptr;
+  bool factored = false;   // Ainv32 holds an inverse of some earlier coarsest matrix
 };
 
 }  // namespace
@@ -407,9 +408,12 @@ nc_status mg_setup(nc_problem* pb, bool refactor) {
     PCK(NC_PROF_MG_COARSE_SETUP, launch_stencil_build<R>(mg.lev[l].g, mg.lev[l].ebe, mg.lev[l].S, pb->st, &pb->cnt));
   PCK(NC_PROF_MG_COARSE_SETUP, launch_dense_assemble<R>(mg.lev[L - 1].g, mg.lev[L - 1].ebe, mg.Ac, mg.nf, pb->st, &pb->cnt));
   // The FP32 inverse of the coarsest matrix is refreshed at the first set-up of each solve call
-  // (or at every set-up if coarse_refactor is set); later set-ups keep it and the coarse solve's
+  // (every set-up with coarse_refactor = 1, once per problem with 2); later set-ups keep it and the coarse solve's
   // FP64 refinement step against the current matrix corrects for the change.
-  if (refactor || pb->par.coarse_refactor)
+  const bool factor = pb->par.coarse_refactor == 1 || !mg.factored ||
+                      (pb->par.coarse_refactor == 0 && refactor);
+  mg.factored = true;
+  if (factor)
     PCK(NC_PROF_COARSE_FACTOR, launch_coarse_factor(mg.Ac, mg.W, mg.Ainv32, mg.nf, pb->dflag, pb->st, &pb->cnt));
   for (int l = 0; l < L - 1; ++l) PCK(NC_PROF_MG_COARSE_SETUP, launch_invert_diag<R>(mg.lev[l].g, mg.lev[l].dinv, pb->dflag, pb->st, &pb->cnt));
   CK(cudaMemcpyAsync(pb->hflag, pb->dflag, sizeof(int), cudaMemcpyDeviceToHost, pb->st));
@@ -904,6 +908,7 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (!(p->krylov_reorth <= 1.0)) { *why = "krylov_reorth must be <= 1"; return NC_ERR_ARG; }
   if (p->mg_tail_nodes < 0) { *why = "mg_tail_nodes must be >= 0"; return NC_ERR_ARG; }
   if (!(p->mg_reuse_below >= 0.0)) { *why = "mg_reuse_below must be >= 0"; return NC_ERR_ARG; }
+  if (p->coarse_refactor < 0 || p->coarse_refactor > 2) { *why = "coarse_refactor must be 0, 1 or 2"; return NC_ERR_ARG; }
   if (!(p->newton_rtol > 0) || p->newton_maxit < 0 || p->krylov_maxit < 1) { *why = "bad tolerances"; return NC_ERR_ARG; }
   if (!(p->filter_radius >= 0) || !(p->filter_rtol > 0)) { *why = "bad filter parameters"; return NC_ERR_ARG; }
   Grid g0 = make_grid(g->nx, g->ny, g->nz, g->h);
@@ -1159,6 +1164,7 @@ nc_status nc_set_params(nc_problem* pb, const nc_params* p) {
   CK(launch_cast_d2f(pb->fdinvf, pb->fdinv, pb->g.nn, pb->st, nullptr));
   CKS(sync(pb, "set_params"));
   pb->have_R0 = false;   // R(0) depends on the source and the heated layers
+  pb->mg32.factored = pb->mg64.factored = false;   // a new operator: invert the coarsest matrix anew
   pb->stage = 0;
   return NC_OK;
 }
