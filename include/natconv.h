@@ -277,8 +277,8 @@ nc_status nc_counters(const nc_problem* pb, long long* launches, double* bytes);
  * Returns NC_ERR_ARG for NULL pointers or bad sizes and NC_ERR_CUDA if a launch fails. */
 nc_status nc_norm2_free_noalloc(const nc_grid* g, const double* s_dev, double* out_dev, void* stream);
 
-/* Message of the last failed call on pb (or of the last failed nc_create_problem if pb is
- * NULL). Never NULL. */
+/* Message of the last failed call on pb (or, if pb is NULL, of the calling thread's last failed
+ * call without a problem, e.g. nc_create_problem). Never NULL. */
 const char* nc_last_error(const nc_problem* pb);
 
 #ifdef __cplusplus

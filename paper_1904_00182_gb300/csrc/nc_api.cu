@@ -137,7 +137,7 @@ struct nc_problem {
 
 namespace {
 
-std::string g_create_error = "no error";
+thread_local std::string g_create_error = "no error";   // per thread: problems are created from several threads
 
 nc_status fail(nc_problem* pb, nc_status s, const std::string& msg) {
   if (pb) pb->err = msg; else g_create_error = msg;

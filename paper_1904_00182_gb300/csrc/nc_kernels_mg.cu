@@ -13,11 +13,15 @@
 // coarse residual is computed in FP64 against the FP64 Galerkin matrix).
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "nc_launch.h"
 
 namespace nc {
 
 namespace {
+
+const int kMaxDevices = 64;   // per-device caches of function attributes
 
 // Loads of the node bodies of the transfer and stencil operators: plain (separate launches; read-only data may take the
 // non-coherent path) or L2-coherent (the fused tail kernel, whose vectors change between its steps).
@@ -993,7 +997,14 @@ cudaError_t launch_coarse_factor(const double* A, float* work, float* Ainv32, in
   if (nf <= NC_GJ_SMEM_MAX) {
     const int ld = (nf + 3) & ~3;
     const size_t sm = sizeof(float) * ((size_t)nf * ld + ld + 2 * nf);
-    static bool attr_set = false;
+    static std::mutex mu;
+    static bool attr_set_dev[kMaxDevices] = {false};
+    int dev = 0;
+    cudaError_t ge = cudaGetDevice(&dev);
+    if (ge != cudaSuccess) return ge;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    bool& attr_set = attr_set_dev[dev];
     if (!attr_set) {
       cudaError_t e = cudaFuncSetAttribute(k_gj32_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(sizeof(float) * (NC_GJ_SMEM_MAX * NC_GJ_SMEM_MAX + 3 * NC_GJ_SMEM_MAX)));
@@ -1076,7 +1087,13 @@ cudaError_t launch_from_mg(const typename Vec2<R>::type* x, double* z, long long
 // Cluster size of the tail kernel: 16 (non-portable) where the device schedules it, else 8.
 template <typename R, bool TR>
 static int tail_cluster_size() {
-  static int cs = 0;
+  // decided once per device (function attributes and occupancy are per device)
+  static std::mutex mu;
+  static int cs_dev[kMaxDevices] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 8;
+  std::lock_guard<std::mutex> lock(mu);
+  int& cs = cs_dev[dev];
   if (cs) return cs;
   cs = 8;
   if (cudaFuncSetAttribute(k_mg_tail<R, TR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
