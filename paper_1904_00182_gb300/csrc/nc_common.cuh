@@ -40,6 +40,15 @@ __device__ __forceinline__ typename Vec2<R>::type mk2(R a, R b) {
   typename Vec2<R>::type v; v.x = a; v.y = b; return v;
 }
 
+// Atomic add of a (P, T) pair to p[0], p[1] (p 8-byte aligned for float: one vector reduction).
+__device__ __forceinline__ void atomic_add_pair(float* p, float a, float b) {
+  atomicAdd(reinterpret_cast<float2*>(p), make_float2(a, b));
+}
+__device__ __forceinline__ void atomic_add_pair(double* p, double a, double b) {
+  atomicAdd(p, a);
+  atomicAdd(p + 1, b);
+}
+
 // Node index of local corner a = ax + 2 ay + 4 az of element (i,j,k).
 __device__ __forceinline__ long long corner_node(const Grid& g, int i, int j, int k, int a) {
   return (long long)(i + (a & 1)) + (long long)g.NX * ((j + ((a >> 1) & 1)) + (long long)g.NY * (k + (a >> 2)));

@@ -40,8 +40,7 @@ __device__ __forceinline__ void scatter_add(const Grid& g, O* __restrict__ out, 
   for (int a = 0; a < 8; ++a) {
     if (top && (a >> 2)) continue;
     const int n = n0 + corner_off(g, a);
-    atomicAdd(out + 2 * n, (O)oP[a]);
-    atomicAdd(out + 2 * n + 1, (O)oT[a]);
+    atomic_add_pair(out + 2 * n, (O)oP[a], (O)oT[a]);
   }
 }
 

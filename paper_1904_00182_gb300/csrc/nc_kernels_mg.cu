@@ -227,8 +227,7 @@ __global__ void k_level0_apply(Grid g, Phys ph, ElemConst<R> C, const typename V
   for (int a = 0; a < 8; ++a) {
     if (top && (a >> 2)) continue;
     const int n = n0 + corner_off(g, a);
-    atomicAdd(y + 2 * n, oP[a]);
-    atomicAdd(y + 2 * n + 1, oT[a]);
+    atomic_add_pair(y + 2 * n, oP[a], oT[a]);
   }
 }
 

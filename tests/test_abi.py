@@ -74,6 +74,31 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
         footprint_bytes(Grid(16, 16, 16, 1 / 16), p)
 
 
+def _struct_fields(name):
+    """Field names, in order, of the typedef struct `name` in the header."""
+    text = open(os.path.join(ROOT, "include", "natconv.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + ";", text)
+    assert m, name
+    names = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        parts = decl.split(None, 1)
+        if parts[0] in ("long", "unsigned"):
+            parts = parts[1].split(None, 1)
+        for v in parts[1].split(","):
+            names.append(re.sub(r"\[.*\]", "", v).strip().lstrip("*"))
+    return names
+
+
+@pytest.mark.parametrize("cname, pyname", [("nc_params", "Params"), ("nc_stats", "Stats"), ("nc_grid", "Grid")])
+def test_python_structures_mirror_the_header(cname, pyname):
+    from paper_1904_00182_gb300 import _abi
+    assert [f for f, _ in getattr(_abi, pyname)._fields_] == _struct_fields(cname)
+
+
 def test_product_has_no_cpu_fallback():
     """The package never imports the oracle and raises when the library is missing."""
     pkg = os.path.join(ROOT, "paper_1904_00182_gb300")
