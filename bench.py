@@ -237,8 +237,9 @@ def workload_config(args):
             "grid": [args.n, args.n, args.n], "alpha": args.alpha, "volfrac": args.volfrac,
             "mg_levels": args.levels, "newton_rtol": 1e-8,
             "precision": "mixed: FP32 multigrid preconditioner and FP32 Krylov operator; IEEE FP64 Newton "
-                         "residual, Krylov basis and Gram-Schmidt, adjoint refinement residual, sensitivities, "
-                         "coarse-grid residual, Hessenberg and Newton update",
+                         "residual, Krylov basis and Gram-Schmidt, accepting adjoint residual, sensitivities, "
+                         "coarse-grid residual, Hessenberg and Newton update; adjoint refinement residuals that "
+                         "only steer a correction in double-float (48-bit significand)",
             "l2": "inputs larger than L2 (Krylov basis ~1 GB, multigrid hierarchy ~0.4 GB per solve)",
             "parallelism": "replicas (one independent problem per GPU)"}
 
@@ -249,7 +250,7 @@ def workload_config(args):
 # lanes per SM -> 80.5 TFLOP/s, FP64 2 FMA units per SM -> 1.26 TFLOP/s); the rest stream vectors
 # or stencils and are bound by HBM (measured copy bandwidth).
 ALU_CLASSES = {"mg_op0": "fp32", "outer_op32": "fp32", "mg_setup_fine": "fp32",
-               "residual": "fp64", "outer_op64": "fp64", "sens": "fp64"}
+               "residual": "fp64", "outer_op64": "fp64", "sens": "fp64", "adjoint_df64": "fp32"}
 # On the mixed-precision path the outer residual classes run in double-float on the FP32 units; the
 # library then counts their FP32 operations (a double-float add 11, a multiply 10 flops).
 DF64_CLASSES = ("residual", "outer_op64", "sens")
@@ -275,7 +276,7 @@ def roofline_entry(name, v, peaks, df64=False):
         achieved = flops / n / per_launch_s / 1e12
         peak = ALU_PEAK_TFLOPS[kind]
         return {"bound": "alu", "kernel_class": name,
-                "arith": "df64 on fp32" if (df64 and name in DF64_CLASSES) else kind,
+                "arith": "df64 on fp32" if ((df64 and name in DF64_CLASSES) or name == "adjoint_df64") else kind,
                 "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "per_launch_us": per_launch_s * 1e6,
                 "launches": n, "alg_flops_per_launch": flops / n, "alg_bytes_per_launch": nbytes / n,

@@ -131,6 +131,13 @@ typedef struct {
   double krylov_reorth; /* classical Gram-Schmidt takes a second pass when the first kept less than
                            this fraction of ||w||^2 (1/2: the DGKS test; 1: always); <= 0: the
                            default of the basis type [0] */
+  int adjoint_df64_steps; /* NC_PREC_MIXED with outer_arith = NC_ARITH_FP64: an adjoint refinement
+                           residual df/ds - J^T lambda that is not expected to meet the tolerance
+                           (previous relative residual times the last FGMRES reduction above
+                           10 x the tolerance) only steers the next correction and is computed in
+                           double-float; every residual that accepts lambda is IEEE FP64 (a
+                           double-float one inside the tolerance is recomputed in FP64 first).
+                           0: every refinement residual in FP64 [1] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */
@@ -245,7 +252,8 @@ enum {
   NC_PROF_COARSE_SOLVE = 13,    /* coarsest-level solve inside the V-cycle */
   NC_PROF_MG_STENCIL_L1 = 14,   /* stencil operators of multigrid level 1 (the largest stencil level) */
   NC_PROF_MG_TAIL = 15,         /* fused V-cycle on the small coarse levels (one cluster kernel) */
-  NC_PROF_NCLASSES = 16
+  NC_PROF_ADJ_DF64 = 16,        /* double-float J^T lambda of steering adjoint refinement passes */
+  NC_PROF_NCLASSES = 17
 };
 
 /* Per-launch CUDA-event timing of kernel classes for calls on pb: bit c of class_mask times class

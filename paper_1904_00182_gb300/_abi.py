@@ -28,7 +28,7 @@ EXPORTS = ("nc_default_params", "nc_create_problem", "nc_destroy_problem", "nc_f
 
 PROF_CLASSES = ("residual", "outer_op64", "outer_op32", "mg_op0", "mg_stencil", "mg_setup_fine", "smooth",
                 "krylov_vec", "filter", "sens", "other", "mg_setup_coarse", "coarse_factor", "coarse_solve",
-                "mg_stencil_l1", "mg_tail")
+                "mg_stencil_l1", "mg_tail", "adjoint_df64")
 
 
 class NatConvError(RuntimeError):
@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
         ("timeout_s", ctypes.c_double), ("adjoint_rtol", ctypes.c_double), ("coarse_refactor", ctypes.c_int),
         ("krylov_eta_min", ctypes.c_double), ("adjoint_eta_first", ctypes.c_double),
         ("mg_tail_nodes", ctypes.c_int), ("mg_reuse_below", ctypes.c_double), ("outer_arith", ctypes.c_int),
-        ("krylov_basis", ctypes.c_int), ("krylov_reorth", ctypes.c_double),
+        ("krylov_basis", ctypes.c_int), ("krylov_reorth", ctypes.c_double), ("adjoint_df64_steps", ctypes.c_int),
     ]
 
     def as_dict(self):

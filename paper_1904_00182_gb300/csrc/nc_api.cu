@@ -325,6 +325,22 @@ nc_status outer_jtv(nc_problem* pb, int cls, const double2* s, const double2* w,
   return NC_OK;
 }
 
+// Adjoint refinement residual w = df/ds - J^T lambda on the free rows, rr = ||w||^2. steer: J^T lambda
+// in double-float (a residual that only steers the next correction); otherwise in the arithmetic of
+// the outer residuals, storing the element design derivatives in dl.
+nc_status adjoint_residual(nc_problem* pb, bool steer, double* rr) {
+  const long long n = 2 * pb->g.nn;
+  if (steer)
+    PCK(NC_PROF_ADJ_DF64, launch_jtv_df(pb->g, pb->ph, pb->s, pb->mat_df, pb->s_df, pb->lam, pb->w_df, pb->w, nullptr,
+                                        pb->st, &pb->cnt));
+  else
+    CKS(outer_jtv(pb, NC_PROF_OUTER_OP64, pb->s, pb->lam, pb->w, pb->dl));
+  PCK(NC_PROF_OTHER, launch_axpby(pb->w, pb->rhs, 1.0, -1.0, n, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_zero_dirichlet(pb->g, pb->w, pb->st, &pb->cnt));
+  CKS(norm2_free(pb, pb->w, rr));
+  return NC_OK;
+}
+
 nc_status residual(nc_problem* pb, const double2* s, double* R, double* phi) {
   if (outer_df(pb))
     PCK(NC_PROF_RESIDUAL, launch_residual_df(pb->g, pb->ph, s, pb->mat_df, pb->s_df, R, pb->st, &pb->cnt));
@@ -908,6 +924,7 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (!(p->krylov_reorth <= 1.0)) { *why = "krylov_reorth must be <= 1"; return NC_ERR_ARG; }
   if (p->mg_tail_nodes < 0) { *why = "mg_tail_nodes must be >= 0"; return NC_ERR_ARG; }
   if (!(p->mg_reuse_below >= 0.0)) { *why = "mg_reuse_below must be >= 0"; return NC_ERR_ARG; }
+  if (p->adjoint_df64_steps != 0 && p->adjoint_df64_steps != 1) { *why = "adjoint_df64_steps must be 0 or 1"; return NC_ERR_ARG; }
   if (p->coarse_refactor < 0 || p->coarse_refactor > 2) { *why = "coarse_refactor must be 0, 1 or 2"; return NC_ERR_ARG; }
   if (!(p->newton_rtol > 0) || p->newton_maxit < 0 || p->krylov_maxit < 1) { *why = "bad tolerances"; return NC_ERR_ARG; }
   if (!(p->filter_radius >= 0) || !(p->filter_rtol > 0)) { *why = "bad filter parameters"; return NC_ERR_ARG; }
@@ -1057,6 +1074,7 @@ nc_status nc_default_params(nc_params* p) {
   p->krylov_reorth = 0.0;
   p->mg_tail_nodes = 5000;
   p->mg_reuse_below = 1e-4;
+  p->adjoint_df64_steps = 1;
   return NC_OK;
 }
 
@@ -1307,19 +1325,23 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
   if (bnorm == 0.0) { pb->stage = 3; return NC_OK; }
   const bool fp32 = pb->par.precision != NC_PREC_FP64;
   const double kAdjointRtol = pb->par.adjoint_rtol > 0 ? pb->par.adjoint_rtol : pb->par.newton_rtol;
-  // refinement: r = b - J^T lam in FP64, correction from FGMRES on the (FP32 or FP64) operator
+  // refinement: r = b - J^T lam in FP64, correction from FGMRES on the (FP32 or FP64) operator.
+  // With adjoint_df64_steps, a residual that cannot be expected to meet the tolerance (the previous
+  // one times the reduction the last FGMRES reached is above 10x the tolerance) only steers the next
+  // correction and is computed in double-float; acceptance is decided on an FP64 residual only.
+  const bool steer_df = fp32 && pb->par.adjoint_df64_steps && !outer_df(pb);
+  double rel_prev = 1.0, red_prev = 1.0;
   for (int pass = 0;; ++pass) {
     double rr;
     if (pass == 0) {
       CK(cudaMemcpyAsync(pb->w, pb->rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
       rr = bb;
     } else {
-      // the same pass stores the element design derivatives at this lambda; if it is the last
+      // an FP64 pass stores the element design derivatives at this lambda; if it is the last
       // (converged) one, the sensitivities need no element sweep of their own
-      CKS(outer_jtv(pb, NC_PROF_OUTER_OP64, pb->s, pb->lam, pb->w, pb->dl));
-      PCK(NC_PROF_OTHER, launch_axpby(pb->w, pb->rhs, 1.0, -1.0, n, pb->st, &pb->cnt));
-      PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->w, pb->st, &pb->cnt));
-      CKS(norm2_free(pb, pb->w, &rr));
+      const bool steer = steer_df && rel_prev * red_prev > 10.0 * kAdjointRtol;
+      CKS(adjoint_residual(pb, steer, &rr));
+      if (steer && std::sqrt(rr) / bnorm <= kAdjointRtol) CKS(adjoint_residual(pb, false, &rr));
     }
     const double rel = std::sqrt(rr) / bnorm;
     if (stats) {
@@ -1356,6 +1378,8 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
       stats->newton_its++;
     }
     PCK(NC_PROF_OTHER, launch_axpby((double*)pb->lam, pb->dx, 1.0, 1.0, n, pb->st, &pb->cnt));
+    rel_prev = rel;
+    red_prev = lres;
   }
   CKS(sync(pb, "adjoint"));
   if (stats) {

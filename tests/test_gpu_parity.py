@@ -132,7 +132,32 @@ def test_double_float_outer_operators(lib, shape, alpha, seed):
 # mixed path variants: the default (IEEE FP64 outer residuals and Krylov basis) and the fast one
 # (double-float outer residuals, FP32 Krylov basis)
 VARIANTS = {"fp64": (1, 1e-8, {}), "mixed": (0, 1e-6, {}),
+            "mixed_fp64_refinement": (0, 1e-6, {"adjoint_df64_steps": 0}),
             "mixed_fast": (0, 1e-6, {"outer_arith": 0, "krylov_basis": 1})}
+
+
+@pytest.mark.parametrize("shape,alpha,seed", CASES)
+def test_adjoint_steering_residuals(lib, shape, alpha, seed):
+    """Adjoint refinement residuals that only steer a correction run in double-float (their own
+    kernel class); the residual that accepts lambda is FP64 and meets the tolerance. Lambda and the
+    sensitivities agree with the all-FP64 refinement and with the oracle."""
+    out = {}
+    for steps in (0, 1):
+        gp, op, rho = make_pair(lib, shape, alpha, seed, precision=0, adjoint_df64_steps=steps, adjoint_rtol=1e-10)
+        gp.solve_state()
+        gp.set_profiling(True)
+        f, ast = gp.solve_adjoint()
+        assert ast["rel_residual"] <= 1e-10
+        out[steps] = (gp.adjoint().cpu().numpy(), gp.sensitivities().cpu().numpy(), gp.profile(), ast)
+        gp.close()
+    prof0, prof1 = out[0][2], out[1][2]
+    assert prof0["adjoint_df64"][1] == 0 and prof1["adjoint_df64"][1] >= 1
+    assert prof1["outer_op64"][1] >= 1            # the accepting residual
+    assert rel(out[1][0], out[0][0]) < 1e-7
+    assert rel(out[1][1], out[0][1]) < 1e-7
+    op.solve_state()
+    op.solve_adjoint()
+    assert rel(out[1][1], op.sensitivities()) < 1e-6
 
 
 @pytest.mark.parametrize("shape,alpha,seed", CASES)
