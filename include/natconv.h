@@ -120,7 +120,7 @@ typedef struct {
                            same arithmetic as separate launches); 0: separate launches [5000] */
   double mg_reuse_below; /* a Newton step whose relative residual is at most this keeps the multigrid
                             hierarchy of the previous step (lagged preconditioner); 0: rebuild at
-                            every step [1e-4] */
+                            every step [1e-2] */
   int outer_arith;      /* NC_PREC_MIXED only: arithmetic of the Newton residual, the adjoint
                            refinement residual J^T lambda and the sensitivities. NC_ARITH_FP64: IEEE
                            FP64; NC_ARITH_DF64: double-float (hi + lo pairs of floats, about 48

@@ -1073,7 +1073,7 @@ nc_status nc_default_params(nc_params* p) {
   p->krylov_basis = NC_BASIS_FP64;
   p->krylov_reorth = 0.0;
   p->mg_tail_nodes = 5000;
-  p->mg_reuse_below = 1e-4;
+  p->mg_reuse_below = 1e-2;
   p->adjoint_df64_steps = 1;
   return NC_OK;
 }
