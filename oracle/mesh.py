@@ -66,5 +66,18 @@ class Mesh:
         """Boolean mask of the elements in the bottom ``layers`` element layers."""
         return self.elem_ijk()[:, 2] < layers
 
+    def box_elems(self, nx, ny, z0, z1):
+        """Boolean mask of the elements with i < nx, j < ny and z0 <= k < z1 (a box at the corner x = y = 0)."""
+        e = self.elem_ijk()
+        return (e[:, 0] < nx) & (e[:, 1] < ny) & (e[:, 2] >= z0) & (e[:, 2] < z1)
+
+    def cavity_dirichlet(self):
+        """(maskP, maskT) of the quarter cavity of Sec. 6.1 (symmetry planes x = 0 and y = 0): T fixed on
+        the outer walls x = nx h, y = ny h and on the top; P fixed at the top outer corner."""
+        ijk = self.node_ijk()
+        maskT = (ijk[:, 0] == self.nx) | (ijk[:, 1] == self.ny) | (ijk[:, 2] == self.nz)
+        maskP = (ijk[:, 0] == self.nx) & (ijk[:, 1] == self.ny) & (ijk[:, 2] == self.nz)
+        return maskP, maskT
+
     def extent(self):
         return (self.nx * self.h, self.ny * self.h, self.nz * self.h)

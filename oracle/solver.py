@@ -54,6 +54,16 @@ class Params:
     newton_rtol: float = 1e-8
     newton_maxit: int = 50
     h: float = 1.0                       # set from the mesh
+    # geometry: "top" (P = T = 0 on the top face) or "cavity" (Mesh.cavity_dirichlet); the heated box
+    # (heat_nx, heat_ny) x heated_layers and the design box (design_nx, design_ny) x [heated_layers,
+    # heated_layers + design_nz) at the corner x = y = 0 (None: the full extent); elements in neither
+    # box are passive fluid
+    bc: str = "top"
+    heat_nx: Optional[int] = None
+    heat_ny: Optional[int] = None
+    design_nx: Optional[int] = None
+    design_ny: Optional[int] = None
+    design_nz: Optional[int] = None
 
     def resolved(self, mesh):
         kf = self.kappa_f if self.kappa_f else kappa_f_tuned(self.alpha)
@@ -82,8 +92,14 @@ class Problem:
         self.conn = mesh.connectivity()
         n = mesh.n_nodes
         if dirichlet is None:
-            top = mesh.top_nodes()
-            dirichlet = (top, np.zeros(n), top, np.zeros(n))
+            if self.par.bc == "top":
+                top = mesh.top_nodes()
+                dirichlet = (top, np.zeros(n), top, np.zeros(n))
+            elif self.par.bc == "cavity":
+                mP, mT = mesh.cavity_dirichlet()
+                dirichlet = (mP, np.zeros(n), mT, np.zeros(n))
+            else:
+                raise ValueError("unknown bc")
         maskP, valP, maskT, valT = dirichlet
         self.dir_mask = np.zeros(2 * n, dtype=bool)
         self.dir_mask[0::2] = maskP
@@ -92,7 +108,13 @@ class Problem:
         self.dir_val[0::2] = np.where(maskP, valP, 0.0)
         self.dir_val[1::2] = np.where(maskT, valT, 0.0)
         self.free = np.flatnonzero(~self.dir_mask)
-        self.heated = mesh.heated_elems(self.par.heated_layers)
+        par = self.par
+        hl = par.heated_layers
+        self.heated = mesh.box_elems(par.heat_nx or mesh.nx, par.heat_ny or mesh.ny, 0, hl)
+        self.design = mesh.box_elems(par.design_nx or mesh.nx, par.design_ny or mesh.ny, hl,
+                                     hl + par.design_nz if par.design_nz else mesh.nz) & ~self.heated
+        self.passive = ~self.design                        # heated (solid) or passive fluid
+        self.fluid = self.passive & ~self.heated
         vol_h = self.heated.sum() * mesh.h ** 3
         if Qe is None:
             Qval = self.par.Q if self.par.Q is not None else 1.0 / vol_h
@@ -108,12 +130,13 @@ class Problem:
 
     # ---- design -> materials --------------------------------------------------------------
     def design_pipeline(self, gamma):
-        """gamma (E) -> gamma~ (E): passive elements set to 1, PDE filter, passive set to 1."""
+        """gamma (E) -> gamma~ (E): passive elements set (heated 1, fluid 0), PDE filter, passive set."""
         if self.filter is None:
             self.filter = HelmholtzFilter(self.mesh, self.par.filter_radius)
-        g = np.where(self.heated, 1.0, gamma)
+        passive_value = np.where(self.heated, 1.0, 0.0)
+        g = np.where(self.passive, passive_value, gamma)
         gt = self.filter.apply(g)
-        return np.where(self.heated, 1.0, gt)
+        return np.where(self.passive, passive_value, gt)
 
     def set_design(self, gamma):
         gamma = np.asarray(gamma, dtype=np.float64)
@@ -359,7 +382,7 @@ class Problem:
         return lam
 
     def sensitivity_gamma_tilde(self):
-        """df/dgamma~_e = -lambda_e^T (dR_e/dkappa kappa' + dR_e/dk k'); 0 on Omega_h."""
+        """df/dgamma~_e = -lambda_e^T (dR_e/dkappa kappa' + dR_e/dk k'); 0 on passive elements."""
         out = np.empty(self.mesh.n_elems)
         for sl in self._chunks():
             pe, te = self.gather(self.s, sl)
@@ -369,13 +392,13 @@ class Problem:
             dL_dkappa = (lp * dkP).sum(1) + (lt * dkT).sum(1)
             dL_dk = (lp * dcP).sum(1) + (lt * dcT).sum(1)
             out[sl] = -(dL_dkappa * self.dkappa[sl] + dL_dk * self.dk[sl])
-        out[self.heated] = 0.0
+        out[self.passive] = 0.0
         return out
 
     def sensitivities(self):
-        """df/dgamma for the raw design (filter transpose applied); 0 on Omega_h."""
+        """df/dgamma for the raw design (filter transpose applied); 0 on passive elements."""
         g = self.filter.apply_transpose(self.sensitivity_gamma_tilde())
-        g[self.heated] = 0.0
+        g[self.passive] = 0.0
         return g
 
     # ---- sampled rows (large-grid checks) -----------------------------------------------------
