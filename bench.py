@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cavity-steps", type=int, default=2)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=300)
     return ap.parse_args()
@@ -452,6 +453,40 @@ def run_gpu(args, rank, world, local):
                       "ms_per_solve_per_problem": wall_c / args.concurrent_steps * 1e3,
                       "timed": "host wall clock around both threads, device synchronised"}
 
+    # the paper's benchmark geometry (Sec. 6.1): quarter of the closed 1 m cavity on 80 x 80 x 160 elements
+    # (h = 1/160 m), heat source 0.05^3 m (quarter) with Q = 1e4 W/m^3, design box 0.375 x 0.375 x 0.75 m
+    # on top of it with the initial design gamma = 0.05, passive fluid elsewhere; state solve from zero
+    cavity = None
+    if args.cavity_steps > 0 and rank == 0:
+        cavity = []
+        for alpha_c in (1e3, 1e6):
+            pcv = nc.Problem(80, 80, 160, 1.0 / 160, stream=stream.cuda_stream, device=dev, alpha=alpha_c,
+                             Q=1e4, bc=nc.NC_BC_CAVITY, heat_nx=8, heat_ny=8, heated_layers=8, design_nx=60,
+                             design_ny=60, design_nz=120, timeout_s=60.0)
+            rho_c = torch.full((80 * 80 * 160,), 0.05, dtype=torch.float64, device=dev)
+            entry = {"alpha": alpha_c, "grid": [80, 80, 160]}
+            try:
+                pcv.set_design(rho_c)
+                pcv.solve_state()
+                torch.cuda.synchronize(dev)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sts = []
+                for _ in range(args.cavity_steps):
+                    pcv.set_design(rho_c)
+                    sts.append(pcv.solve_state())
+                e1.record(stream)
+                e1.synchronize()
+                msc = e0.elapsed_time(e1) / args.cavity_steps
+                entry.update({"ms_per_state_solve": msc, "steps": args.cavity_steps,
+                              "newton_its": [x["newton_its"] for x in sts], "krylov_its": [x["krylov_its"] for x in sts],
+                              "ramped": [x["ramped"] for x in sts], "rel_residual": [x["rel_residual"] for x in sts]})
+            except nc.NatConvError as e:
+                entry["error"] = str(e)
+            pcv.close()
+            cavity.append(entry)
+
     serving = None
     if not args.no_serve and rank == 0:
         serving = run_serving(args, dev)
@@ -490,7 +525,7 @@ def run_gpu(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
             "config": workload_config(args), "clocks": clk, "e2e": e2e,
             "gpu_launches": int(l1 - l0), "roofline": roof, "cpu_baseline": cpu,
-            "fp64_path": fp64, "mixed_fast": fast, "concurrent": concurrent, "serving": serving,
+            "fp64_path": fp64, "mixed_fast": fast, "concurrent": concurrent, "cavity": cavity, "serving": serving,
             "solver": {"newton_its": [s[0]["newton_its"] for s in timed_stats],
                        "krylov_its": [s[0]["krylov_its"] for s in timed_stats],
                        "adjoint_krylov_its": [s[1]["krylov_its"] for s in timed_stats],

@@ -72,6 +72,12 @@ enum { NC_BASIS_FP64 = 0, NC_BASIS_FP32 = 1 };
  * Eq. objdiscr, sum_e f_tQ,e^T t_e, whose SUPG-weighted source load depends on the state. */
 enum { NC_OBJ_MEAN_T_HEATED = 0, NC_OBJ_SUPG_COMPLIANCE = 1 };
 
+/* Boundary conditions (nc_params.bc). NC_BC_TOP: P = T = 0 on the top face z = nz h, every other face
+ * natural (no flux, no normal Darcy flow). NC_BC_CAVITY: the quarter of a closed cavity with symmetry
+ * planes x = 0 and y = 0 (Sec. 6.1): T = 0 on the outer walls x = nx h, y = ny h and the top, the
+ * bottom insulated, no normal flow through any face, and P = 0 at the top outer corner. */
+enum { NC_BC_TOP = 0, NC_BC_CAVITY = 1 };
+
 typedef struct nc_problem nc_problem;
 
 typedef struct {
@@ -138,6 +144,12 @@ typedef struct {
                            double-float; every residual that accepts lambda is IEEE FP64 (a
                            double-float one inside the tolerance is recomputed in FP64 first).
                            0: every refinement residual in FP64 [1] */
+  int bc;               /* NC_BC_TOP or NC_BC_CAVITY, fixed at creation [NC_BC_TOP] */
+  int heat_nx, heat_ny; /* heated region (passive solid holding the source Q): the element box
+                           [0, heat_nx) x [0, heat_ny) x [0, heated_layers); 0: the full extent [0, 0] */
+  int design_nx, design_ny, design_nz; /* design region: [0, design_nx) x [0, design_ny) x
+                           [heated_layers, heated_layers + design_nz); 0: the full extent. Elements
+                           outside both boxes are passive fluid (filtered density 0) [0, 0, 0] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */
@@ -177,12 +189,13 @@ nc_status nc_footprint_bytes(const nc_grid* g, const nc_params* p, size_t* bytes
 nc_status nc_set_params(nc_problem* pb, const nc_params* p);
 
 /* Design pipeline, Sec. 5.1-5.2: rho (E values in [0,1], finite; NC_ERR_ARG otherwise) ->
- * gamma = 1 on Omega_h -> PDE filter -> gamma~ = 1 on Omega_h -> RAMP kappa_e, k_e.
+ * gamma = 1 on Omega_h (the heated box) and 0 on passive fluid -> PDE filter -> gamma~ = 1 on Omega_h
+ * and 0 on passive fluid -> RAMP kappa_e, k_e. Values of rho outside the design box are ignored.
  * Resets the state to zero unless nc_set_state is called afterwards. */
 nc_status nc_set_design(nc_problem* pb, const double* rho);
 
 /* Warm start (Sec. 5.4): P and T (N values each) become the initial Newton guess. Values on
- * the Dirichlet top face are forced to 0. Requires a design. */
+ * the Dirichlet set of params.bc are forced to 0. Requires a design. */
 nc_status nc_set_state(nc_problem* pb, const double* P, const double* T);
 
 /* Damped Newton state solve (Sec. 5.4) to params.newton_rtol. Requires a design.
@@ -197,7 +210,7 @@ nc_status nc_objective(nc_problem* pb, int objective, double* f);
  * writes the objective to *f_out (may be NULL). */
 nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stats* stats);
 
-/* df/drho (E values) by the chain rule through RAMP and the filter transpose; 0 on Omega_h.
+/* df/drho (E values) by the chain rule through RAMP and the filter transpose; 0 on passive elements.
  * Requires a solved adjoint. */
 nc_status nc_sensitivities(nc_problem* pb, double* dfdrho);
 
@@ -217,7 +230,7 @@ nc_status nc_get_permeabilities(const nc_problem* pb, double* kappa_f, double* k
 nc_status nc_get_design_fields(const nc_problem* pb, double* gamma_tilde, double* kappa, double* k);
 
 /* Operator-level entry points: one step of the path on caller data, for parity checks.
- * s, v, w, out are state vectors (2N doubles). Entries on the Dirichlet top face of v and w
+ * s, v, w, out are state vectors (2N doubles). Entries of v and w on the Dirichlet set of params.bc
  * are ignored; the corresponding outputs are: R_d = s_d (residual), 0 (products). */
 
 /* R(s) (Eq. finalsyseq) and ||R_free(s)||^2 (norm2_free may be NULL), in the arithmetic of the
@@ -284,6 +297,7 @@ nc_status nc_counters(const nc_problem* pb, long long* launches, double* bytes);
  * shares the array and leaves its last contents there; calls that overlap on the GPU race.
  * Returns NC_ERR_ARG for NULL pointers or bad sizes and NC_ERR_CUDA if a launch fails. */
 nc_status nc_norm2_free_noalloc(const nc_grid* g, const double* s_dev, double* out_dev, void* stream);
+/* (The free rows above are those of NC_BC_TOP.) */
 
 /* Message of the last failed call on pb (or, if pb is NULL, of the calling thread's last failed
  * call without a problem, e.g. nc_create_problem). Never NULL. */

@@ -15,6 +15,8 @@ NC_BASIS_FP64 = 0
 NC_BASIS_FP32 = 1
 NC_OBJ_MEAN_T_HEATED = 0
 NC_OBJ_SUPG_COMPLIANCE = 1
+NC_BC_TOP = 0
+NC_BC_CAVITY = 1
 
 STATUS_NAMES = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_OOM", 3: "NC_ERR_CUDA", 4: "NC_ERR_DIVERGED",
                 5: "NC_ERR_MAXIT", 6: "NC_ERR_NAN", 7: "NC_ERR_TIMEOUT", 8: "NC_ERR_STATE"}
@@ -57,6 +59,8 @@ class Params(ctypes.Structure):
         ("krylov_eta_min", ctypes.c_double), ("adjoint_eta_first", ctypes.c_double),
         ("mg_tail_nodes", ctypes.c_int), ("mg_reuse_below", ctypes.c_double), ("outer_arith", ctypes.c_int),
         ("krylov_basis", ctypes.c_int), ("krylov_reorth", ctypes.c_double), ("adjoint_df64_steps", ctypes.c_int),
+        ("bc", ctypes.c_int), ("heat_nx", ctypes.c_int), ("heat_ny", ctypes.c_int), ("design_nx", ctypes.c_int),
+        ("design_ny", ctypes.c_int), ("design_nz", ctypes.c_int),
     ]
 
     def as_dict(self):

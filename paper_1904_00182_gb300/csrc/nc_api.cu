@@ -50,10 +50,11 @@ Levels plan_levels(const Grid& g0, int max_levels) {
     const Grid& c = L.g.back();
     if (max_levels > 0 && (int)L.g.size() >= max_levels) break;
     if (c.nx % 2 || c.ny % 2 || c.nz % 2) break;
-    L.g.push_back(make_grid(c.nx / 2, c.ny / 2, c.nz / 2, c.h * 2.0));
+    Grid gc = make_grid(c.nx / 2, c.ny / 2, c.nz / 2, c.h * 2.0);
+    gc.bc = g0.bc;
+    L.g.push_back(gc);
   }
-  const Grid& c = L.g.back();
-  L.nf = 2 * c.NX * c.NY * c.nz;
+  L.nf = coarse_rows(L.g.back());
   return L;
 }
 
@@ -63,7 +64,7 @@ struct MG {
   std::vector<MGLevelDev<R>> lev;
   double* Ac = nullptr;     // coarsest-level Galerkin matrix (FP64, free DOFs)
   float* Ainv32 = nullptr; // its FP32 inverse
-  float* W = nullptr;      // Gauss-Jordan scratch (nf x 2nf)
+  float* W = nullptr;      // Gauss-Jordan scratch (nf x 2nf, then 3 nf of pivot bookkeeping)
   double* cw = nullptr;    // coarse-solve scratch (3 nf)
   int nf = 0;
   // during a preconditioner call with FP64 vectors: its input (read by the first finest-level
@@ -365,6 +366,8 @@ nc_status outer_op(nc_problem* pb, bool transpose, bool fp32, const double* x, d
     if (transpose) PCK(NC_PROF_OUTER_OP64, launch_jtv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, nullptr, pb->st, &pb->cnt));
     else PCK(NC_PROF_OUTER_OP64, launch_jv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, pb->st, &pb->cnt));
   }
+  // with kBcTop the element kernels leave the Dirichlet rows zero; otherwise they are zeroed here
+  if (g.bc != kBcTop) PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, y, pb->st, &pb->cnt));
   return NC_OK;
 }
 
@@ -402,7 +405,7 @@ nc_status mg_alloc(nc_problem* pb) {
   mg.nf = pb->lv.nf;
   CKS(dalloc(pb, &mg.Ac, (size_t)mg.nf * mg.nf));
   CKS(dalloc(pb, &mg.Ainv32, (size_t)mg.nf * mg.nf));
-  CKS(dalloc(pb, &mg.W, (size_t)mg.nf * 2 * mg.nf));
+  CKS(dalloc(pb, &mg.W, (size_t)mg.nf * 2 * mg.nf + 3 * (size_t)mg.nf));   // + pivot bookkeeping
   CKS(dalloc(pb, &mg.cw, (size_t)3 * mg.nf));
   return NC_OK;
 }
@@ -585,6 +588,7 @@ nc_status kry_op(nc_problem* pb, bool tr, bool fp32, const float* z, float* w) {
   (void)fp32;
   PCK(NC_PROF_OUTER_OP32, launch_level0_apply<float>(pb->g, pb->ph, pb->s32, pb->mat32, (const float2*)z, (float2*)w,
                                                      tr, pb->st, &pb->cnt));
+  if (pb->g.bc != kBcTop) PCK(NC_PROF_OTHER, launch_zero_dirichlet(pb->g, w, pb->st, &pb->cnt));
   return NC_OK;
 }
 
@@ -596,6 +600,7 @@ nc_status kry_op(nc_problem* pb, bool tr, bool fp32, const double* z, double* w)
     PCK(NC_PROF_OUTER_OP32, launch_level0_apply<float>(g, pb->ph, pb->s32, pb->mat32, pb->mg32.lev[0].x, pb->y32, tr,
                                                        pb->st, &pb->cnt));
     PCK(NC_PROF_OUTER_OP32, launch_cast_f2d(w, (const float*)pb->y32, 2 * g.nn, pb->st, &pb->cnt));
+    if (g.bc != kBcTop) PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, w, pb->st, &pb->cnt));
     return NC_OK;
   }
   return outer_op(pb, tr, false, z, w);
@@ -928,7 +933,14 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (p->coarse_refactor < 0 || p->coarse_refactor > 2) { *why = "coarse_refactor must be 0, 1 or 2"; return NC_ERR_ARG; }
   if (!(p->newton_rtol > 0) || p->newton_maxit < 0 || p->krylov_maxit < 1) { *why = "bad tolerances"; return NC_ERR_ARG; }
   if (!(p->filter_radius >= 0) || !(p->filter_rtol > 0)) { *why = "bad filter parameters"; return NC_ERR_ARG; }
+  if (p->bc != NC_BC_TOP && p->bc != NC_BC_CAVITY) { *why = "unknown bc"; return NC_ERR_ARG; }
+  if (p->heat_nx < 0 || p->heat_nx > g->nx || p->heat_ny < 0 || p->heat_ny > g->ny || p->design_nx < 0 ||
+      p->design_nx > g->nx || p->design_ny < 0 || p->design_ny > g->ny || p->design_nz < 0 ||
+      p->heated_layers + p->design_nz > g->nz) {
+    *why = "heated and design boxes must lie inside the grid"; return NC_ERR_ARG;
+  }
   Grid g0 = make_grid(g->nx, g->ny, g->nz, g->h);
+  g0.bc = p->bc;
   Levels lv = plan_levels(g0, p->mg_levels);
   if (lv.g.size() < 2) { *why = "the multigrid hierarchy needs even grid dimensions"; return NC_ERR_ARG; }
   if (lv.nf > kMaxCoarseDofs) { *why = "coarsest multigrid level too large (use more levels)"; return NC_ERR_ARG; }
@@ -937,6 +949,7 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
 
 size_t footprint(const nc_grid* gr, const nc_params* p) {
   Grid g = make_grid(gr->nx, gr->ny, gr->nz, gr->h);
+  g.bc = p->bc;
   Levels lv = plan_levels(g, p->mg_levels);
   auto al = [](size_t b) { return (std::max<size_t>(b, 1) + 255) & ~size_t(255); };
   size_t b = 0;
@@ -957,7 +970,7 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
     if (l > 0) b += al(256 * rs * lv.g[l].ne);
     if (l > 0 && l + 1 < lv.g.size()) b += al(108 * rs * lv.g[l].nn);
   }
-  b += al(8 * (size_t)lv.nf * lv.nf) + al(4 * (size_t)lv.nf * lv.nf) + al(8 * (size_t)lv.nf * lv.nf);
+  b += al(8 * (size_t)lv.nf * lv.nf) + al(4 * (size_t)lv.nf * lv.nf) + al(8 * (size_t)lv.nf * lv.nf + 12 * (size_t)lv.nf);
   b += al(4);
   return b;
 }
@@ -968,7 +981,12 @@ void apply_params(nc_problem* pb, const nc_params* p) {
   const Grid& g = pb->g;
   pb->kappa_f = p->kappa_f > 0 ? p->kappa_f : kappa_f_tuned(p->alpha, p->tune_dT);
   pb->kappa_s = p->kappa_ratio * pb->kappa_f;
-  pb->vol_h = (double)g.nx * g.ny * p->heated_layers * g.h * g.h * g.h;
+  pb->ph.heat_nx = p->heat_nx > 0 ? p->heat_nx : g.nx;
+  pb->ph.heat_ny = p->heat_ny > 0 ? p->heat_ny : g.ny;
+  pb->ph.design_nx = p->design_nx > 0 ? p->design_nx : g.nx;
+  pb->ph.design_ny = p->design_ny > 0 ? p->design_ny : g.ny;
+  pb->ph.design_z1 = p->design_nz > 0 ? p->heated_layers + p->design_nz : g.nz;
+  pb->vol_h = (double)pb->ph.heat_nx * pb->ph.heat_ny * p->heated_layers * g.h * g.h * g.h;
   pb->Q_full = p->Q > 0 ? p->Q : (pb->vol_h > 0 ? 1.0 / pb->vol_h : 0.0);
   pb->ph.h = g.h;
   pb->ph.beta = p->rho0 * p->alpha * p->g;
@@ -1096,6 +1114,7 @@ nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream,
   nc_problem* pb = new nc_problem();
   cudaGetDevice(&pb->device);
   pb->g = make_grid(gr->nx, gr->ny, gr->nz, gr->h);
+  pb->g.bc = p->bc;
   pb->par = *p;
   pb->m = p->restart;
   const Grid& g = pb->g;
@@ -1173,8 +1192,8 @@ nc_status nc_set_params(nc_problem* pb, const nc_params* p) {
   nc_status vs = validate(&gr, p, &why);
   if (vs != NC_OK) return fail(pb, vs, why);
   if (p->precision != pb->par.precision || p->mg_levels != pb->par.mg_levels || p->restart != pb->par.restart ||
-      p->krylov_basis != pb->par.krylov_basis)
-    return fail(pb, NC_ERR_ARG, "precision, mg_levels, restart and krylov_basis are fixed at creation");
+      p->krylov_basis != pb->par.krylov_basis || p->bc != pb->par.bc)
+    return fail(pb, NC_ERR_ARG, "precision, mg_levels, restart, krylov_basis and bc are fixed at creation");
   DeviceGuard dg(pb->device);
   CKS(sync(pb, "set_params"));
   apply_params(pb, p);
@@ -1199,9 +1218,9 @@ nc_status nc_set_design(nc_problem* pb, const double* rho) {
   CKS(sync(pb, "design check"));
   if (*pb->hflag) return fail(pb, NC_ERR_ARG, "design values must be finite and in [0, 1]");
   // filter: b = T^T gamma with gamma = 1 on the heated region
-  PCK(NC_PROF_FILTER, launch_filter_rhs(g, pb->rho, pb->par.heated_layers, pb->F.t0, pb->fb, pb->st, &pb->cnt));
+  PCK(NC_PROF_FILTER, launch_filter_rhs(g, pb->ph, true, pb->rho, pb->F.t0, pb->fb, pb->st, &pb->cnt));
   CKS(filter_solve(pb));
-  PCK(NC_PROF_FILTER, launch_elem_from_nodes(g, pb->fx, 0.125, pb->par.heated_layers, 1.0, pb->gamma_t, pb->st, &pb->cnt));
+  PCK(NC_PROF_FILTER, launch_elem_from_nodes(g, pb->ph, pb->fx, 0.125, 1.0, pb->gamma_t, pb->st, &pb->cnt));
   RampConst rc{pb->kappa_f, pb->kappa_s, pb->par.k_f, pb->par.k_s, pb->par.q_c, pb->par.q_p};
   PCK(NC_PROF_OTHER, launch_ramp(pb->gamma_t, g.ne, rc, pb->mat, pb->dmat, pb->mat32, pb->st, &pb->cnt));
   if (pb->mat_df) PCK(NC_PROF_OTHER, launch_split2(pb->mat, pb->mat_df, g.ne, pb->st, &pb->cnt));
@@ -1279,13 +1298,15 @@ nc_status nc_objective(nc_problem* pb, int objective, double* f) {
     set_q_scale(pb, 1.0);
     const long long nh = (long long)g.nx * g.ny * pb->par.heated_layers;
     PCK(NC_PROF_OTHER, launch_obj_supg(g, pb->ph, pb->s, pb->mat, pb->gsens, pb->rhs, pb->st, &pb->cnt));
+    PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->rhs, pb->st, &pb->cnt));
     PCK(NC_PROF_OTHER, launch_sum(pb->gsens, nh, pb->part, pb->dres, pb->st, &pb->cnt));
     CK(cudaMemcpyAsync(pb->hres, pb->dres, sizeof(double), cudaMemcpyDeviceToHost, pb->st));
     CKS(sync(pb, "objective"));
     *f = pb->hres[0];
     return NC_OK;
   }
-  PCK(NC_PROF_OTHER, launch_dfds(g, pb->par.heated_layers, g.h * g.h * g.h / 8.0 / pb->vol_h, pb->rhs, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_dfds(g, pb->ph, g.h * g.h * g.h / 8.0 / pb->vol_h, pb->rhs, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->rhs, pb->st, &pb->cnt));
   CKS(dots(pb, pb->rhs, 0, 1, (const double*)pb->s, 2 * g.nn, f));
   return NC_OK;
 }
@@ -1400,16 +1421,16 @@ nc_status nc_sensitivities(nc_problem* pb, double* dfdrho) {
   const Grid& g = pb->g;
   set_q_scale(pb, 1.0);
   if (pb->dl_ready)
-    PCK(NC_PROF_SENS, launch_sens_from_dl(g, pb->par.heated_layers, pb->dl, pb->dmat, pb->gsens, pb->st, &pb->cnt));
+    PCK(NC_PROF_SENS, launch_sens_from_dl(g, pb->ph, pb->dl, pb->dmat, pb->gsens, pb->st, &pb->cnt));
   else if (outer_df(pb))
     PCK(NC_PROF_SENS, launch_sens_df(g, pb->ph, pb->s, pb->lam, pb->mat_df, pb->dmat, pb->s_df, pb->w_df, pb->gsens,
                                      pb->st, &pb->cnt));
   else
     PCK(NC_PROF_SENS, launch_sens_elem(g, pb->ph, pb->s, pb->lam, pb->mat, pb->dmat, pb->gsens, pb->st, &pb->cnt));
   // filter transpose: gamma~_e = (1/8) sum_a x_a, x = A^-1 T^T gamma  =>  df/dgamma = T A^-1 (1/8 sum)
-  PCK(NC_PROF_FILTER, launch_filter_rhs(g, pb->gsens, 0, 0.125, pb->fb, pb->st, &pb->cnt));
+  PCK(NC_PROF_FILTER, launch_filter_rhs(g, pb->ph, false, pb->gsens, 0.125, pb->fb, pb->st, &pb->cnt));
   CKS(filter_solve(pb));
-  PCK(NC_PROF_FILTER, launch_elem_from_nodes(g, pb->fx, pb->F.t0, pb->par.heated_layers, 0.0, pb->gsens, pb->st, &pb->cnt));
+  PCK(NC_PROF_FILTER, launch_elem_from_nodes(g, pb->ph, pb->fx, pb->F.t0, 0.0, pb->gsens, pb->st, &pb->cnt));
   CKS(copy_out(pb, dfdrho, pb->gsens, sizeof(double) * g.ne));
   CKS(sync(pb, "sensitivities"));
   return NC_OK;
@@ -1487,6 +1508,7 @@ static nc_status apply_generic(nc_problem* pb, const double* s, const double* v,
   CKS(copy_in(pb, pb->s_try, s, sizeof(double) * n));
   CKS(copy_in(pb, pb->w, v, sizeof(double) * n));
   const Grid& g = pb->g;
+  PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->w, pb->st, &pb->cnt));   // the operator acts on free entries
   if (fp32) {
     PCK(NC_PROF_OTHER, launch_cast_d2f((float*)pb->s32, (const double*)pb->s_try, n, pb->st, &pb->cnt));
     CKS(outer_op(pb, tr, true, pb->w, pb->R_try));
@@ -1494,6 +1516,7 @@ static nc_status apply_generic(nc_problem* pb, const double* s, const double* v,
     if (tr) CKS(outer_jtv(pb, NC_PROF_OTHER, pb->s_try, (const double2*)pb->w, pb->R_try));
     else PCK(NC_PROF_OTHER, launch_jv_f64(g, pb->ph, pb->s_try, pb->mat, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
   }
+  PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->R_try, pb->st, &pb->cnt));   // Dirichlet rows of the projected operator
   CKS(copy_out(pb, out, pb->R_try, sizeof(double) * n));
   CKS(sync(pb, "operator"));
   return NC_OK;

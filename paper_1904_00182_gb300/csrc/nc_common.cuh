@@ -2,14 +2,19 @@
 //
 // Grid: nx x ny x nz cubic Q1 elements of edge h; node (i,j,k) -> i + NX*(j + NY*k) with
 // NX = nx+1, NY = ny+1 (x fastest); element (i,j,k) -> i + nx*(j + ny*k). A state vector is
-// node-interleaved (P, T): double2 (FP64) or float2 (FP32) per node. The Dirichlet set is
-// the top node plane k = nz (P = T = 0 there).
+// node-interleaved (P, T): double2 (FP64) or float2 (FP32) per node. Dirichlet values are 0; the
+// fixed set depends on the boundary conditions (Grid::bc): kBcTop fixes P and T on the top node plane
+// k = nz; kBcCavity (the quarter of a closed cavity, symmetry planes x = 0 and y = 0) fixes T on the
+// outer walls i = nx, j = ny and the top k = nz, and P at the top outer corner (nx, ny, nz). Both sets
+// are unions of grid planes and a grid corner, so on every multigrid level they are the same planes.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace nc {
+
+constexpr int kBcTop = 0, kBcCavity = 1;
 
 struct Grid {
   int nx, ny, nz;   // elements
@@ -18,7 +23,36 @@ struct Grid {
   long long nn;     // nodes (< 2^31: node indices fit in int)
   long long ne;     // elements
   double h;
+  int bc;           // kBcTop or kBcCavity
 };
+
+// Fixed components of node (i, j, k): bit 0 P, bit 1 T.
+__host__ __device__ __forceinline__ int fixed_bits(const Grid& g, int i, int j, int k) {
+  if (g.bc == kBcTop) return k == g.nz ? 3 : 0;
+  const int t = (i == g.nx || j == g.ny || k == g.nz) ? 2 : 0;
+  return t | ((i == g.nx && j == g.ny && k == g.nz) ? 1 : 0);
+}
+
+// Nodes carrying fixed components, enumerated plane by plane (kBcTop: the top plane; kBcCavity: the
+// top plane, then the planes i = nx and j = ny; edge nodes appear in more than one plane).
+__host__ __device__ __forceinline__ long long boundary_count(const Grid& g) {
+  return g.bc == kBcTop ? (long long)g.NXY : (long long)g.NXY + (long long)g.NY * g.NZ + (long long)g.NX * g.NZ;
+}
+__device__ __forceinline__ bool boundary_node(const Grid& g, long long t, int& i, int& j, int& k) {
+  if (t < g.NXY) { k = g.nz; j = (int)(t / g.NX); i = (int)(t - (long long)j * g.NX); return true; }
+  if (g.bc == kBcTop) return false;
+  t -= g.NXY;
+  if (t < (long long)g.NY * g.NZ) { i = g.nx; k = (int)(t / g.NY); j = (int)(t - (long long)k * g.NY); return true; }
+  t -= (long long)g.NY * g.NZ;
+  if (t < (long long)g.NX * g.NZ) { j = g.ny; k = (int)(t / g.NX); i = (int)(t - (long long)k * g.NX); return true; }
+  return false;
+}
+
+// Free (P, T) rows of the level's dense coarse system: kBcTop keeps the nodes below the top plane
+// (their rows lead the node order); kBcCavity keeps every node (fixed rows become identity rows).
+inline int coarse_rows(const Grid& g) {
+  return g.bc == kBcTop ? 2 * g.NX * g.NY * g.nz : (int)(2 * g.nn);
+}
 
 inline Grid make_grid(int nx, int ny, int nz, double h) {
   Grid g;
@@ -28,6 +62,7 @@ inline Grid make_grid(int nx, int ny, int nz, double h) {
   g.nn = (long long)g.NX * g.NY * g.NZ;
   g.ne = (long long)nx * ny * nz;
   g.h = h;
+  g.bc = kBcTop;
   return g;
 }
 

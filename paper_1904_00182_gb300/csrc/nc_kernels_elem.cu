@@ -49,11 +49,11 @@ __device__ __forceinline__ void scatter_add(const Grid& g, O* __restrict__ out, 
   if (i >= g.nx || j >= g.ny) return;                           \
   const int n0 = i + g.NX * j + g.NXY * k;                      \
   const int e = i + g.nx * (j + g.ny * k);                      \
-  const bool top = (k + 1 == g.nz);
+  const bool top = g.bc == kBcTop && (k + 1 == g.nz);
 
 template <typename R>
-__device__ __forceinline__ R elem_source(const Phys& ph, int k) {
-  return k < ph.heated_layers ? (R)ph.Q : R(0);
+__device__ __forceinline__ R elem_source(const Phys& ph, int i, int j, int k) {
+  return elem_heated(ph, i, j, k) ? (R)ph.Q : R(0);
 }
 
 __global__ void k_residual(Grid g, Phys ph, ElemConst<double> C, const double2* __restrict__ s,
@@ -63,18 +63,19 @@ __global__ void k_residual(Grid g, Phys ph, ElemConst<double> C, const double2* 
   gather_state<double>(g, s, n0, p, t);
   const double2 m = mat[e];
   double RP[8], RT[8];
-  elem_residual<double>(C, p, t, m.x, m.y, elem_source<double>(ph, k), RP, RT);
+  elem_residual<double>(C, p, t, m.x, m.y, elem_source<double>(ph, i, j, k), RP, RT);
   scatter_add(g, out, n0, top, RP, RT);
 }
 
-// Dirichlet rows of the residual: R_d = s_d (boundary value 0).
+// Dirichlet rows of the residual: R_d = s_d (boundary value 0), per fixed component.
 __global__ void k_residual_bc(Grid g, const double2* __restrict__ s, double* __restrict__ out) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long plane = (long long)g.NX * g.NY;
-  if (t >= plane) return;
-  const long long n = (long long)g.nz * plane + t;
-  out[2 * n] = s[n].x;
-  out[2 * n + 1] = s[n].y;
+  int i, j, k;
+  if (!boundary_node(g, t, i, j, k)) return;
+  const int b = fixed_bits(g, i, j, k);
+  const long long n = i + (long long)g.NX * (j + (long long)g.NY * k);
+  if (b & 1) out[2 * n] = s[n].x;
+  if (b & 2) out[2 * n + 1] = s[n].y;
 }
 
 // J v or J^T w. With DL (transpose only), the pass also stores the element derivatives
@@ -89,7 +90,7 @@ __global__ void k_jprod(Grid g, Phys ph, ElemConst<R> C, const SV* __restrict__ 
   gather_dir<R>(g, v, n0, top, dp, dt);
   const typename Vec2<R>::type m = mat[e];
   ElemState<R> st;
-  elem_state(C, p, t, m.x, elem_source<R>(ph, k), st);
+  elem_state(C, p, t, m.x, elem_source<R>(ph, i, j, k), st);
   R oP[8], oT[8];
   if (TRANSPOSE && DL) {
     R dkap, dk;
@@ -103,12 +104,14 @@ __global__ void k_jprod(Grid g, Phys ph, ElemConst<R> C, const SV* __restrict__ 
   scatter_add(g, out, n0, top, oP, oT);
 }
 
-// df/dgamma~_e = -(dL/dkappa kappa' + dL/dk k') from stored element derivatives; 0 on heated elements.
-__global__ void k_sens_from_dl(long long ne, long long heated, const double2* __restrict__ dl,
-                               const double2* __restrict__ dmat, double* __restrict__ out) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+// df/dgamma~_e = -(dL/dkappa kappa' + dL/dk k') from stored element derivatives; 0 on passive elements.
+__global__ void k_sens_from_dl(Grid g, Phys ph, const double2* __restrict__ dl, const double2* __restrict__ dmat,
+                               double* __restrict__ out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < g.ne; e += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    elem_ijk(g, e, i, j, k);
     const double2 a = dl[e], d = dmat[e];
-    out[e] = e < heated ? 0.0 : -(a.x * d.x + a.y * d.y);
+    out[e] = elem_design(ph, i, j, k) ? -(a.x * d.x + a.y * d.y) : 0.0;
   }
 }
 
@@ -116,7 +119,7 @@ __global__ void k_sens(Grid g, Phys ph, ElemConst<double> C, const double2* __re
                        const double2* __restrict__ lam, const double2* __restrict__ mat,
                        const double2* __restrict__ dmat, double* __restrict__ out) {
   NC_ELEM_PROLOGUE();
-  if (k < ph.heated_layers) { out[e] = 0.0; return; }
+  if (!elem_design(ph, i, j, k)) { out[e] = 0.0; return; }
   double p[8], t[8], lp[8], lt[8];
   gather_state<double>(g, s, n0, p, t);
   gather_dir<double>(g, lam, n0, top, lp, lt);
@@ -156,7 +159,7 @@ __global__ void k_obj_supg(Grid g, Phys ph, ElemConst<double> C, const double2* 
   double p[8], t[8];
   gather_state<double>(g, s, n0, p, t);
   const double2 m = mat[e];
-  const double Q = elem_source<double>(ph, k);
+  const double Q = elem_source<double>(ph, i, j, k);
   ElemState<double> st;
   elem_state(C, p, t, m.x, Q, st);
   double Gx = 0, Gy = 0, Gz = 0, tsum = 0;
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(128, NC_LB_RESIDUAL_DF) k_residual_df(Grid g, 
   df64 p[8], t[8];
   gather_df(g, s, n0, false, p, t);
   const float4 m = mat[e];
-  const df64 Q = k < ph.heated_layers ? Qh : df64(0.0f, 0.0f);
+  const df64 Q = elem_heated(ph, i, j, k) ? Qh : df64(0.0f, 0.0f);
   df64 RP[8], RT[8];
   elem_residual<df64>(C, p, t, df64(m.x, m.y), df64(m.z, m.w), Q, RP, RT);
   scatter_add(g, out, n0, top, RP, RT);
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(128, NC_LB_JTV_DF) k_jtv_df(Grid g, Phys ph, E
   gather_df(g, w, n0, top, lp, lt);
   const float4 m = mat[e];
   ElemState<df64> st;
-  elem_state(C, p, t, df64(m.x, m.y), k < ph.heated_layers ? Qh : df64(0.0f, 0.0f), st);
+  elem_state(C, p, t, df64(m.x, m.y), elem_heated(ph, i, j, k) ? Qh : df64(0.0f, 0.0f), st);
   df64 oP[8], oT[8];
   if (DL) {
     df64 dkap, dk;
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(128, NC_LB_SENS_DF) k_sens_df(Grid g, Phys ph,
                           const float4* __restrict__ lam, const float4* __restrict__ mat,
                           const double2* __restrict__ dmat, double* __restrict__ out) {
   NC_ELEM_PROLOGUE();
-  if (k < ph.heated_layers) { out[e] = 0.0; return; }
+  if (!elem_design(ph, i, j, k)) { out[e] = 0.0; return; }
   df64 p[8], t[8], lp[8], lt[8];
   gather_df(g, s, n0, false, p, t);
   gather_df(g, lam, n0, top, lp, lt);
@@ -294,8 +297,7 @@ cudaError_t launch_residual_df(const Grid& g, const Phys& ph, const double2* s, 
   if (err != cudaSuccess) return err;
   const Launch3 L = launch_elems(g);
   k_residual_df<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<df64>(ph), df64(ph.Q), s_df, mat_df, out);
-  const long long plane = (long long)g.NX * g.NY;
-  k_residual_bc<<<grid_blocks(plane, 256), 256, 0, st>>>(g, s, out);
+  k_residual_bc<<<grid_blocks(boundary_count(g), 256), 256, 0, st>>>(g, s, out);
   if (c) { c->launches += 2; c->bytes += 16.0 * g.nn * 2 + 16.0 * g.ne; c->flops += kFlopsResidualDF * g.ne; }
   return cudaGetLastError();
 }
@@ -334,8 +336,7 @@ cudaError_t launch_residual(const Grid& g, const Phys& ph, const double2* s, con
   if (err != cudaSuccess) return err;
   const Launch3 L = launch_elems(g);
   k_residual<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<double>(ph), s, mat, out);
-  const long long plane = (long long)g.NX * g.NY;
-  k_residual_bc<<<grid_blocks(plane, 256), 256, 0, st>>>(g, s, out);
+  k_residual_bc<<<grid_blocks(boundary_count(g), 256), 256, 0, st>>>(g, s, out);
   if (c) { c->launches += 2; c->bytes += 16.0 * g.nn * 2 + 16.0 * g.ne; c->flops += kFlopsResidual * g.ne; }
   return cudaGetLastError();
 }
@@ -369,10 +370,9 @@ cudaError_t launch_jtv_f64(const Grid& g, const Phys& ph, const double2* s, cons
   return jprod<double, double2, true>(g, ph, s, mat, w, out, dl, st, c);
 }
 
-cudaError_t launch_sens_from_dl(const Grid& g, int heated_layers, const double2* dl, const double2* dmat, double* out,
+cudaError_t launch_sens_from_dl(const Grid& g, const Phys& ph, const double2* dl, const double2* dmat, double* out,
                                 cudaStream_t st, Counters* c) {
-  const long long heated = (long long)heated_layers * g.nx * g.ny;
-  k_sens_from_dl<<<grid_blocks(g.ne, 256, 152 * 16), 256, 0, st>>>(g.ne, heated, dl, dmat, out);
+  k_sens_from_dl<<<grid_blocks(g.ne, 256, 152 * 16), 256, 0, st>>>(g, ph, dl, dmat, out);
   if (c) { c->launches += 1; c->bytes += 40.0 * g.ne; }
   return cudaGetLastError();
 }

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(128 / NC_GALERKIN_CPT) k_galerkin_fine(Grid gf
   const long long e = i + (long long)gf.nx * (j + (long long)gf.ny * k);
   const typename Vec2<R>::type m = mat[e];
   ElemState<R> st;
-  elem_state(C, p, tt, m.x, k < ph.heated_layers ? (R)ph.Q : R(0), st);
+  elem_state(C, p, tt, m.x, elem_heated(ph, i, j, k) ? (R)ph.Q : R(0), st);
   for (int cc = 0; cc < NC_GALERKIN_CPT; ++cc) {
     const int col = col0 + cc * kCols;
     R oP[8], oT[8];
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(128 / NC_GALERKIN_CPT) k_galerkin_fine(Grid gf
     }
     // block diagonal of level 0 (row-major [PP PT; TP TT]) on free nodes
     const int a = col & 7;
-    if (k + (a >> 2) < gf.nz) {
+    if (gf.bc != kBcTop || k + (a >> 2) < gf.nz) {
       const long long n = corner_node(gf, i, j, k, a);
       if (col < 8) { add_diag_block(diag_f, n, 0, oP[a]); add_diag_block(diag_f, n, 2, oT[a]); }
       else { add_diag_block(diag_f, n, 1, oP[a]); add_diag_block(diag_f, n, 3, oT[a]); }
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(128) k_galerkin_coarse(Grid gf, Grid gc, const
   if (t < 64) {
     const int c = t >> 3, a = t & 7;
     const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
-    if (k + (a >> 2) < gf.nz) {
+    if (gf.bc != kBcTop || k + (a >> 2) < gf.nz) {
       const long long n = corner_node(gf, i, j, k, a);
       add_diag_block(diag_f, n, 0, Jc[c][a * NC_LD + a]);
       add_diag_block(diag_f, n, 1, Jc[c][a * NC_LD + 8 + a]);
@@ -192,7 +192,18 @@ __global__ void k_invert_diag(Grid g, R* __restrict__ diag, int* flag) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nn) return;
   R* d = diag + 4 * n;
-  if (n >= (long long)g.NX * g.NY * g.nz) { d[0] = d[1] = d[2] = d[3] = R(0); return; }
+  int i, j, k;
+  node_ijk(g, n, i, j, k);
+  const int fb = fixed_bits(g, i, j, k);
+  if (fb == 3) { d[0] = d[1] = d[2] = d[3] = R(0); return; }
+  if (fb) {   // one fixed component: invert the free one alone, zero rows and columns of the fixed one
+    const R v = fb == 2 ? d[0] : d[3];
+    if (!(v != R(0)) || !isfinite((double)v)) { atomicExch(flag, 1); d[0] = d[1] = d[2] = d[3] = R(0); return; }
+    d[1] = d[2] = R(0);
+    d[0] = fb == 2 ? R(1) / v : R(0);
+    d[3] = fb == 2 ? R(0) : R(1) / v;
+    return;
+  }
   const R a = d[0], b = d[1], c = d[2], e = d[3];
   const R det = a * e - b * c;
   if (!(det != R(0)) || !isfinite((double)det)) { atomicExch(flag, 1); d[0] = d[1] = d[2] = d[3] = R(0); return; }
@@ -207,7 +218,7 @@ __global__ void k_level0_apply(Grid g, Phys ph, ElemConst<R> C, const typename V
   NC_IJK_3D();
   if (i >= g.nx || j >= g.ny) return;
   const int n0 = i + g.NX * j + g.NXY * k;
-  const bool top = (k + 1 == g.nz);
+  const bool top = g.bc == kBcTop && (k + 1 == g.nz);
   R p[8], t[8], dp[8], dt[8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
@@ -219,7 +230,7 @@ __global__ void k_level0_apply(Grid g, Phys ph, ElemConst<R> C, const typename V
   }
   const typename Vec2<R>::type m = mat[i + g.nx * (j + g.ny * k)];
   ElemState<R> st;
-  elem_state(C, p, t, m.x, k < ph.heated_layers ? (R)ph.Q : R(0), st);
+  elem_state(C, p, t, m.x, elem_heated(ph, i, j, k) ? (R)ph.Q : R(0), st);
   R oP[8], oT[8];
   if (TR) elem_jtv<R, false>(C, st, m.y, dp, dt, oP, oT, nullptr, nullptr);
   else elem_jv_dir<R>(C, st, m.y, dp, dt, oP, oT);
@@ -297,6 +308,16 @@ __global__ void k_sub(long long nn, const typename Vec2<R>::type* __restrict__ b
   r[n] = mk2<R>(bb.x - yy.x, bb.y - yy.y);
 }
 
+// The value v at node (i, j, k) with its fixed components set to zero.
+template <typename R>
+__device__ __forceinline__ typename Vec2<R>::type mask_fixed(const Grid& g, int i, int j, int k,
+                                                             typename Vec2<R>::type v) {
+  const int b = fixed_bits(g, i, j, k);
+  if (b & 1) v.x = R(0);
+  if (b & 2) v.y = R(0);
+  return v;
+}
+
 // Full weighting (R = P^T) at coarse node (I, J, K): the fine residual rf at the 27 fine nodes
 // around it, weights 1, 1/2, 1/4, 1/8 by distance; the top (Dirichlet) plane gets 0.
 template <typename R, typename FETCH>
@@ -345,10 +366,10 @@ __global__ void k_restrict_res(Grid gf, Grid gc, const typename Vec2<R>::type* _
   const int K = blockIdx.y;
   const int J = pidx / gc.NX;
   const int I = pidx - J * gc.NX;
-  bc[pidx + gc.NXY * K] = restrict_node_f<R>(gf, I, J, K, K >= gc.nz, [&](int m) {
+  bc[pidx + gc.NXY * K] = mask_fixed<R>(gc, I, J, K, restrict_node_f<R>(gf, I, J, K, gc.bc == kBcTop && K >= gc.nz, [&](int m) {
     const typename Vec2<R>::type bb = b[m], yy = y[m];
     return mk2<R>(bb.x - yy.x, bb.y - yy.y);
-  });
+  }));
 }
 
 template <typename R>
@@ -359,7 +380,8 @@ __global__ void k_restrict(Grid gf, Grid gc, const typename Vec2<R>::type* __res
   const int K = blockIdx.y;
   const int J = pidx / gc.NX;
   const int I = pidx - J * gc.NX;
-  bc[pidx + gc.NXY * K] = restrict_node<R>(gf, rf, I, J, K, K >= gc.nz, LdPlain());
+  bc[pidx + gc.NXY * K] =
+      mask_fixed<R>(gc, I, J, K, restrict_node<R>(gf, rf, I, J, K, gc.bc == kBcTop && K >= gc.nz, LdPlain()));
 }
 
 // Trilinear interpolation of the coarse correction at fine node (i, j, k), added to xf.
@@ -390,7 +412,7 @@ template <typename R>
 __global__ void k_prolong_add(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ xc,
                               typename Vec2<R>::type* __restrict__ xf) {
   NC_NODE_FLAT(gf);
-  if (k == gf.nz) return;
+  if (fixed_bits(gf, i, j, k) == 3) return;   // a partly fixed node receives zero in its fixed component
   prolong_node<R>(gf, gc, xc, xf, pidx + gf.NXY * k, i, j, k, LdPlain());
 }
 
@@ -403,10 +425,25 @@ __global__ void k_dense_assemble(Grid g, const R* __restrict__ ebe, double* __re
   int i, j, k;
   elem_ijk(g, e, i, j, k);
   const int ar = r & 7, aq = q & 7;
-  if (k + (ar >> 2) == g.nz || k + (aq >> 2) == g.nz) return;
+  if ((fixed_bits(g, i + (ar & 1), j + ((ar >> 1) & 1), k + (ar >> 2)) >> (r >> 3)) & 1) return;
+  if ((fixed_bits(g, i + (aq & 1), j + ((aq >> 1) & 1), k + (aq >> 2)) >> (q >> 3)) & 1) return;
   const long long row = 2 * corner_node(g, i, j, k, ar) + (r >> 3);
   const long long col = 2 * corner_node(g, i, j, k, aq) + (q >> 3);
   atomicAdd(A + row * nf + col, (double)ebe[t]);
+}
+
+// Identity rows for the fixed components of a level whose dense system keeps every node (kBcCavity).
+__global__ void k_dense_fixed_rows(Grid g, double* __restrict__ A, int nf) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (!boundary_node(g, t, i, j, k)) return;
+  const int b = fixed_bits(g, i, j, k);
+  const long long n = i + (long long)g.NX * (j + (long long)g.NY * k);
+  for (int f = 0; f < 2; ++f)
+    if ((b >> f) & 1) {
+      const long long r = 2 * n + f;
+      if (r < nf) A[r * nf + r] = 1.0;
+    }
 }
 
 template <typename R>
@@ -443,8 +480,7 @@ __global__ void k_stencil_build(Grid g, const R* __restrict__ ebe, R* __restrict
   const int oi = o % 3 - 1, oj = (o / 3) % 3 - 1, ok = o / 9 - 1;
   const int mi = i + oi, mj = j + oj, mk = k + ok;
   R acc[4] = {R(0), R(0), R(0), R(0)};
-  const bool valid = mi >= 0 && mi <= g.nx && mj >= 0 && mj <= g.ny && mk >= 0 && mk <= g.nz &&
-                     k < g.nz && mk < g.nz;   // Dirichlet rows and columns stay zero
+  const bool valid = mi >= 0 && mi <= g.nx && mj >= 0 && mj <= g.ny && mk >= 0 && mk <= g.nz;
   if (valid) {
     // elements containing both node (i,j,k) and node (mi,mj,mk)
     const int ei0 = oi ? min(i, mi) : i - 1, ei1 = oi ? min(i, mi) : i;
@@ -467,6 +503,11 @@ __global__ void k_stencil_build(Grid g, const R* __restrict__ ebe, R* __restrict
         }
       }
     }
+    // Dirichlet rows and columns stay zero, per component (entry (f, c): row field f, column field c)
+    const int rb = fixed_bits(g, i, j, k), cb = fixed_bits(g, mi, mj, mk);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (((rb >> (q >> 1)) & 1) || ((cb >> (q & 1)) & 1)) acc[q] = R(0);
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) S[((long long)o * g.nn + n) * 4 + q] = acc[q];
@@ -539,71 +580,95 @@ __global__ void __launch_bounds__(128) k_stencil_apply(Grid g, const R* __restri
                                                        typename Vec2<R>::type* __restrict__ out) {
   NC_NODE_FLAT(g);
   const int n = pidx + g.NXY * k;
-  if (k == g.nz) { out[n] = mk2<R>(R(0), R(0)); return; }
+  if (g.bc == kBcTop && k == g.nz) { out[n] = mk2<R>(R(0), R(0)); return; }
   stencil_node<R, TR, MODE>(g, S, x, b, dinv, omega, out, n, i, j, k, LdPlain());
 }
 
-// ---- coarsest level: FP32 Gauss-Jordan inverse with partial pivoting (one block) ------------------
-// W: nf x 2nf scratch (FP32). Ainv32 receives the inverse. flag = 1 on a zero pivot.
-__global__ void __launch_bounds__(1024) k_gj32(const double* __restrict__ A, float* __restrict__ W,
-                                               float* __restrict__ Ainv32, int nf, int* flag) {
-  extern __shared__ float fac[];
+// ---- coarsest level: FP32 Gauss-Jordan inverse with partial pivoting ----------------------------
+// Ainv32 receives the inverse of the FP64 matrix A rounded to FP32; flag = 1 on a zero pivot.
+
+// Gauss-Jordan inversion with partial pivoting for coarse matrices too large for one block's shared
+// memory (FP32), spread over the whole GPU with one launch pair per column and no block waiting on
+// another. W = [A | I] (nf x 2nf, global memory). Step k: the pivot kernel (one block) picks the row p
+// not yet used as a pivot with the largest |W[p][k]| (partial pivoting without row exchanges; ties to
+// the lower row), records the multipliers m_r = W[r][k] of the other rows and scales row p by
+// 1 / W[p][k]; the update kernel subtracts m_r times row p from every other row r. Columns left of k
+// are zero outside the earlier pivot rows, so the update starts at column k. After nf steps the left
+// half is the permutation with a 1 at (piv[k], k), the right half is that permutation times A^-1, and
+// row k of A^-1 is row piv[k] of the right half.
+__global__ void k_gjm_init(const double* __restrict__ A, float* __restrict__ W, int nf, int* __restrict__ used) {
+  const long long w2 = 2LL * nf;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nf * w2;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / w2), c = (int)(idx % w2);
+    W[idx] = c < nf ? (float)A[(long long)r * nf + c] : (c - nf == r ? 1.f : 0.f);
+    if (idx < nf) used[idx] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_gjm_pivot(float* __restrict__ W, int nf, int k, int* __restrict__ piv,
+                                                    int* __restrict__ used, float* __restrict__ m, int* flag) {
   __shared__ float s_val[32];
   __shared__ int s_idx[32];
   __shared__ int s_piv;
-  const int t = threadIdx.x, nt = blockDim.x, w2 = 2 * nf;
-  for (int idx = t; idx < nf * w2; idx += nt) {
-    const int r = idx / w2, c = idx % w2;
-    W[idx] = c < nf ? (float)A[r * nf + c] : (c - nf == r ? 1.f : 0.f);
+  const int t = threadIdx.x, nt = blockDim.x;
+  const long long w2 = 2LL * nf;
+  float best = -1.f;
+  int bi = nf;
+  for (int r = t; r < nf; r += nt) {
+    if (used[r]) continue;
+    const float v = fabsf(W[r * w2 + k]);
+    if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_down_sync(0xffffffffu, best, o);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  }
+  if ((t & 31) == 0) { s_val[t >> 5] = best; s_idx[t >> 5] = bi; }
+  __syncthreads();
+  if (t == 0) {
+    float bb = -1.f;
+    int bidx = nf;
+    for (int w = 0; w < (nt >> 5); ++w)
+      if (s_val[w] > bb || (s_val[w] == bb && s_idx[w] < bidx)) { bb = s_val[w]; bidx = s_idx[w]; }
+    const bool ok = bb > 0.f && isfinite(bb) && bidx < nf;
+    s_piv = ok ? bidx : -1;
+    piv[k] = s_piv;
+    if (ok) used[bidx] = 1;
+    else atomicExch(flag, 1);
   }
   __syncthreads();
-  for (int k = 0; k < nf; ++k) {
-    float best = -1.f;
-    int bi = nf;
-    for (int r = k + t; r < nf; r += nt) {
-      const float v = fabsf(W[r * w2 + k]);
-      if (v > best) { best = v; bi = r; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_down_sync(0xffffffffu, best, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if ((t & 31) == 0) { s_val[t >> 5] = best; s_idx[t >> 5] = bi; }
-    __syncthreads();
-    if (t == 0) {
-      float bb = -1.f;
-      int bidx = nf;
-      for (int w = 0; w < (nt >> 5); ++w)
-        if (s_val[w] > bb || (s_val[w] == bb && s_idx[w] < bidx)) { bb = s_val[w]; bidx = s_idx[w]; }
-      s_piv = (bb > 0.f && bidx < nf) ? bidx : -1;
-    }
-    __syncthreads();
-    const int p = s_piv;
-    if (p < 0) { if (t == 0) atomicExch(flag, 1); return; }
-    if (p != k)
-      for (int c = t; c < w2; c += nt) {
-        const float a = W[k * w2 + c];
-        W[k * w2 + c] = W[p * w2 + c];
-        W[p * w2 + c] = a;
-      }
-    __syncthreads();
-    const float inv = 1.f / W[k * w2 + k];
-    __syncthreads();
-    for (int c = t; c < w2; c += nt) W[k * w2 + c] *= inv;
-    for (int r = t; r < nf; r += nt) fac[r] = W[r * w2 + k];
-    __syncthreads();
-    for (int idx = t; idx < nf * w2; idx += nt) {
-      const int r = idx / w2, c = idx % w2;
-      if (r == k || c < k) continue;
-      W[idx] -= fac[r] * W[k * w2 + c];
-    }
-    __syncthreads();
-  }
-  for (int idx = t; idx < nf * nf; idx += nt) {
-    const int r = idx / nf, c = idx % nf;
-    Ainv32[idx] = W[r * w2 + nf + c];
+  const int p = s_piv;
+  if (p < 0) return;
+  for (int r = t; r < nf; r += nt) m[r] = r == p ? 0.f : W[r * w2 + k];
+  const float inv = 1.f / W[p * w2 + k];
+  __syncthreads();   // every thread has read W[p][k] before row p is scaled
+  for (long long c = k + t; c < w2; c += nt) W[p * w2 + c] *= inv;
+}
+
+__global__ void k_gjm_update(float* __restrict__ W, int nf, int k, const int* __restrict__ piv,
+                             const float* __restrict__ m) {
+  const int p = piv[k];
+  const int r = blockIdx.y;
+  if (p < 0 || r == p) return;
+  const float mr = m[r];
+  if (mr == 0.f) return;
+  const long long w2 = 2LL * nf;
+  for (long long c = k + (long long)blockIdx.x * blockDim.x + threadIdx.x; c < w2;
+       c += (long long)gridDim.x * blockDim.x)
+    W[r * w2 + c] -= mr * W[p * w2 + c];
+}
+
+__global__ void k_gjm_permute(const float* __restrict__ W, int nf, const int* __restrict__ piv,
+                              float* __restrict__ Ainv32) {
+  const long long w2 = 2LL * nf;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)nf * nf;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(idx / nf), c = (int)(idx % nf);
+    const int p = piv[k];
+    Ainv32[idx] = p >= 0 ? W[p * w2 + nf + c] : 0.f;
   }
 }
 
@@ -772,7 +837,7 @@ __global__ void __launch_bounds__(1024, 1) k_mg_tail(const TailArgs<R> A) {
     const TailLevel<R>& d = A.lev[l];
     for (int n = t; n < (int)d.g.nn; n += T) {
       const int i = n % d.g.NX, j = (n / d.g.NX) % d.g.NY, k = n / d.g.NXY;
-      if (k == d.g.nz) xn[l][n] = mk2<R>(R(0), R(0));
+      if (d.g.bc == kBcTop && k == d.g.nz) xn[l][n] = mk2<R>(R(0), R(0));
       else stencil_node<R, TR, 2>(d.g, d.S, x[l], d.b, d.dinv, A.omega, xn[l], n, i, j, k, ld);
     }
     barrier();
@@ -792,14 +857,14 @@ __global__ void __launch_bounds__(1024, 1) k_mg_tail(const TailArgs<R> A) {
     for (int it = 1; it < A.nu1; ++it) smooth(l);
     for (int n = t; n < (int)d.g.nn; n += T) {   // residual into xn
       const int i = n % d.g.NX, j = (n / d.g.NX) % d.g.NY, k = n / d.g.NXY;
-      if (k == d.g.nz) xn[l][n] = mk2<R>(R(0), R(0));
+      if (d.g.bc == kBcTop && k == d.g.nz) xn[l][n] = mk2<R>(R(0), R(0));
       else stencil_node<R, TR, 1>(d.g, d.S, x[l], d.b, d.dinv, A.omega, xn[l], n, i, j, k, ld);
     }
     barrier();
     const Grid& gc = A.lev[l + 1].g;
     for (int n = t; n < (int)gc.nn; n += T) {
       const int I = n % gc.NX, J = (n / gc.NX) % gc.NY, K = n / gc.NXY;
-      A.lev[l + 1].b[n] = restrict_node<R>(d.g, xn[l], I, J, K, K >= gc.nz, ld);
+      A.lev[l + 1].b[n] = mask_fixed<R>(gc, I, J, K, restrict_node<R>(d.g, xn[l], I, J, K, gc.bc == kBcTop && K >= gc.nz, ld));
     }
     barrier();
   }
@@ -849,7 +914,7 @@ __global__ void __launch_bounds__(1024, 1) k_mg_tail(const TailArgs<R> A) {
     const TailLevel<R>& d = A.lev[l];
     for (int n = t; n < (int)d.g.nn; n += T) {
       const int i = n % d.g.NX, j = (n / d.g.NX) % d.g.NY, k = n / d.g.NXY;
-      if (k < d.g.nz) prolong_node<R>(d.g, A.lev[l + 1].g, x[l + 1], x[l], n, i, j, k, ld);
+      if (fixed_bits(d.g, i, j, k) != 3) prolong_node<R>(d.g, A.lev[l + 1].g, x[l + 1], x[l], n, i, j, k, ld);
     }
     barrier();
     for (int it = 0; it < A.nu2; ++it) smooth(l);
@@ -988,6 +1053,10 @@ cudaError_t launch_dense_assemble(const Grid& g, const R* ebe, double* A, int nf
   if (err != cudaSuccess) return err;
   k_dense_assemble<R><<<grid_blocks(g.ne * 256, 256), 256, 0, st>>>(g, ebe, A, nf);
   if (c) c->launches += 1;
+  if (g.bc != kBcTop) {
+    k_dense_fixed_rows<<<grid_blocks(boundary_count(g), 256), 256, 0, st>>>(g, A, nf);
+    if (c) c->launches += 1;
+  }
   return cudaGetLastError();
 }
 
@@ -1011,10 +1080,22 @@ cudaError_t launch_coarse_factor(const double* A, float* work, float* Ainv32, in
       attr_set = true;
     }
     k_gj32_smem<<<1, dim3(32, 32), sm, st>>>(A, Ainv32, nf, flag);
+    if (c) c->launches += 1;
   } else {
-    k_gj32<<<1, 1024, sizeof(float) * nf, st>>>(A, work, Ainv32, nf, flag);
+    // work: W (nf x 2nf floats), then piv, used (nf ints each) and the multipliers (nf floats)
+    float* W = work;
+    int* piv = reinterpret_cast<int*>(W + 2LL * nf * nf);
+    int* used = piv + nf;
+    float* m = reinterpret_cast<float*>(used + nf);
+    k_gjm_init<<<grid_blocks(2LL * nf * nf, 256, 152 * 16), 256, 0, st>>>(A, W, nf, used);
+    const dim3 ug((unsigned)((2 * nf + 255) / 256), (unsigned)nf);
+    for (int k = 0; k < nf; ++k) {
+      k_gjm_pivot<<<1, 1024, 0, st>>>(W, nf, k, piv, used, m, flag);
+      k_gjm_update<<<ug, 256, 0, st>>>(W, nf, k, piv, m);
+    }
+    k_gjm_permute<<<grid_blocks((long long)nf * nf, 256, 152 * 16), 256, 0, st>>>(W, nf, piv, Ainv32);
+    if (c) c->launches += 2 + 2LL * nf;
   }
-  if (c) c->launches += 1;
   return cudaGetLastError();
 }
 

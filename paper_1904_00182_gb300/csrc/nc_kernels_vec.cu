@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(256) k_cgs_reorth(T* __restrict__ w, const T* 
   }
 }
 
-// Sum of squares over the free rows of a state vector (rows of nodes below the top plane).
+// Sum of squares over the leading nfree2 entries of a state vector: the free rows for kBcTop, every row
+// for kBcCavity (whose fixed entries are zero in every vector this is applied to).
 __global__ void k_norm2_free_part(const double* __restrict__ a, long long nfree2, double* __restrict__ part) {
   __shared__ double sh[32];
   const long long seg = (nfree2 + gridDim.x - 1) / gridDim.x;
@@ -260,12 +261,13 @@ __global__ void k_cast_f2d(double* __restrict__ y, const float* __restrict__ x, 
 
 template <typename T>
 __global__ void k_zero_dirichlet(Grid g, T* __restrict__ a) {
-  const long long plane = (long long)g.NX * g.NY;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= plane) return;
-  const long long n = (long long)g.nz * plane + t;
-  a[2 * n] = (T)0;
-  a[2 * n + 1] = (T)0;
+  int i, j, k;
+  if (!boundary_node(g, t, i, j, k)) return;
+  const int b = fixed_bits(g, i, j, k);
+  const long long n = i + (long long)g.NX * (j + (long long)g.NY * k);
+  if (b & 1) a[2 * n] = (T)0;
+  if (b & 2) a[2 * n + 1] = (T)0;
 }
 
 __global__ void k_check_design(const double* __restrict__ rho, long long n, int* flag) {
@@ -278,7 +280,7 @@ __global__ void k_check_design(const double* __restrict__ rho, long long n, int*
 
 // Node n gathers from the (up to 8) elements around it. Element (ei,ej,ek) contains node n as
 // local corner a = (i-ei) + 2 (j-ej) + 4 (k-ek).
-__global__ void k_filter_rhs(Grid g, const double* __restrict__ gamma, int heated_layers, double t0,
+__global__ void k_filter_rhs(Grid g, Phys ph, bool passive, const double* __restrict__ gamma, double t0,
                              double* __restrict__ b) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nn) return;
@@ -294,7 +296,9 @@ __global__ void k_filter_rhs(Grid g, const double* __restrict__ gamma, int heate
       for (int di = -1; di <= 0; ++di) {
         const int ei = i + di;
         if (ei < 0 || ei >= g.nx) continue;
-        const double v = ek < heated_layers ? 1.0 : gamma[ei + (long long)g.nx * (ej + (long long)g.ny * ek)];
+        const double v = !passive || elem_design(ph, ei, ej, ek)
+                             ? gamma[ei + (long long)g.nx * (ej + (long long)g.ny * ek)]
+                             : (elem_heated(ph, ei, ej, ek) ? 1.0 : 0.0);
         acc += v;
       }
     }
@@ -378,13 +382,16 @@ __global__ void k_helmholtz_diag(Grid g, double d, double* __restrict__ dinv) {
   dinv[n] = 1.0 / (d * cx * cy * cz);
 }
 
-__global__ void k_elem_from_nodes(Grid g, const double* __restrict__ x, double scale, int heated_layers,
+__global__ void k_elem_from_nodes(Grid g, Phys ph, const double* __restrict__ x, double scale,
                                   double heated_value, double* __restrict__ out) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.ne) return;
   int i, j, k;
   elem_ijk(g, e, i, j, k);
-  if (heated_value >= 0.0 && k < heated_layers) { out[e] = heated_value; return; }
+  if (heated_value >= 0.0 && !elem_design(ph, i, j, k)) {
+    out[e] = elem_heated(ph, i, j, k) ? heated_value : 0.0;
+    return;
+  }
   double acc = 0.0;
 #pragma unroll
   for (int a = 0; a < 8; ++a) acc += x[corner_node(g, i, j, k, a)];
@@ -409,16 +416,18 @@ __global__ void k_ramp(const double* __restrict__ gt, long long n, RampConst r, 
 }
 
 // df/ds for f = (1/|Omega_h|) sum_{e in Omega_h} int_e N t_e: T entry = w_node x (number of heated
-// elements around the node), P entry 0, Dirichlet rows 0.
-__global__ void k_dfds(Grid g, int heated_layers, double w_node, double* __restrict__ out) {
+// elements around the node; the heated region is a box at the origin corner), P entry 0, Dirichlet
+// rows 0.
+__global__ void k_dfds(Grid g, Phys ph, double w_node, double* __restrict__ out) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nn) return;
   int i, j, k;
   node_ijk(g, n, i, j, k);
   int cnt = 0;
-  if (k < g.nz) {
-    const int cx = (i > 0) + (i < g.nx), cy = (j > 0) + (j < g.ny);
-    const int cz = (k > 0 && k - 1 < heated_layers) + (k < g.nz && k < heated_layers);
+  if (!(fixed_bits(g, i, j, k) & 2)) {
+    const int hx = min(ph.heat_nx, g.nx), hy = min(ph.heat_ny, g.ny), hz = min(ph.heated_layers, g.nz);
+    const int cx = (i > 0 && i - 1 < hx) + (i < hx), cy = (j > 0 && j - 1 < hy) + (j < hy);
+    const int cz = (k > 0 && k - 1 < hz) + (k < hz);
     cnt = cx * cy * cz;
   }
   out[2 * n] = 0.0;
@@ -490,7 +499,7 @@ cudaError_t launch_sum(const double* a, long long n, double* part, double* res, 
 
 cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, double* res, cudaStream_t st,
                               Counters* c) {
-  const long long nfree2 = 2LL * g.NX * g.NY * g.nz;
+  const long long nfree2 = g.bc == kBcTop ? 2LL * g.NX * g.NY * g.nz : 2LL * g.nn;
   const int nb = reduce_blocks(nfree2);
   k_norm2_free_part<<<nb, kRedThreads, 0, st>>>(a, nfree2, part);
   k_sum_parts<<<1, 256, 0, st>>>(part, nb, 1, res);
@@ -621,15 +630,13 @@ cudaError_t launch_cast_f2d(double* y, const float* x, long long n, cudaStream_t
 }
 
 cudaError_t launch_zero_dirichlet(const Grid& g, double* a, cudaStream_t st, Counters* c) {
-  const long long plane = (long long)g.NX * g.NY;
-  k_zero_dirichlet<<<grid_blocks(plane, 256), 256, 0, st>>>(g, a);
+  k_zero_dirichlet<<<grid_blocks(boundary_count(g), 256), 256, 0, st>>>(g, a);
   if (c) c->launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_zero_dirichlet(const Grid& g, float* a, cudaStream_t st, Counters* c) {
-  const long long plane = (long long)g.NX * g.NY;
-  k_zero_dirichlet<<<grid_blocks(plane, 256), 256, 0, st>>>(g, a);
+  k_zero_dirichlet<<<grid_blocks(boundary_count(g), 256), 256, 0, st>>>(g, a);
   if (c) c->launches += 1;
   return cudaGetLastError();
 }
@@ -639,9 +646,9 @@ cudaError_t launch_check_design(const double* rho, long long ne, int* flag, cuda
   return cudaGetLastError();
 }
 
-cudaError_t launch_filter_rhs(const Grid& g, const double* gamma, int heated_layers, double t0, double* b,
+cudaError_t launch_filter_rhs(const Grid& g, const Phys& ph, bool passive, const double* gamma, double t0, double* b,
                               cudaStream_t st, Counters* c) {
-  k_filter_rhs<<<grid_blocks(g.nn, 256), 256, 0, st>>>(g, gamma, heated_layers, t0, b);
+  k_filter_rhs<<<grid_blocks(g.nn, 256), 256, 0, st>>>(g, ph, passive, gamma, t0, b);
   if (c) { c->launches += 1; c->bytes += 8.0 * (g.ne + g.nn); }
   return cudaGetLastError();
 }
@@ -688,9 +695,9 @@ cudaError_t launch_helmholtz_diag(const Grid& g, const FilterConst& F, double* d
   return cudaGetLastError();
 }
 
-cudaError_t launch_elem_from_nodes(const Grid& g, const double* x, double scale, int heated_layers,
+cudaError_t launch_elem_from_nodes(const Grid& g, const Phys& ph, const double* x, double scale,
                                    double heated_value, double* out, cudaStream_t st, Counters* c) {
-  k_elem_from_nodes<<<grid_blocks(g.ne, 256), 256, 0, st>>>(g, x, scale, heated_layers, heated_value, out);
+  k_elem_from_nodes<<<grid_blocks(g.ne, 256), 256, 0, st>>>(g, ph, x, scale, heated_value, out);
   if (c) { c->launches += 1; c->bytes += 8.0 * (g.ne + g.nn); }
   return cudaGetLastError();
 }
@@ -702,9 +709,9 @@ cudaError_t launch_ramp(const double* gt, long long ne, const RampConst& r, doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_dfds(const Grid& g, int heated_layers, double w_node, double* out, cudaStream_t st,
+cudaError_t launch_dfds(const Grid& g, const Phys& ph, double w_node, double* out, cudaStream_t st,
                         Counters* c) {
-  k_dfds<<<grid_blocks(g.nn, 256), 256, 0, st>>>(g, heated_layers, w_node, out);
+  k_dfds<<<grid_blocks(g.nn, 256), 256, 0, st>>>(g, ph, w_node, out);
   if (c) { c->launches += 1; c->bytes += 16.0 * g.nn; }
   return cudaGetLastError();
 }

@@ -8,10 +8,24 @@
 namespace nc {
 
 // Physical constants of one problem, in FP64; converted to ElemConst<R> per launch.
+// Regions of elements: heated (passive solid with the source) [0, heat_nx) x [0, heat_ny) x
+// [0, heated_layers); design [0, design_nx) x [0, design_ny) x [heated_layers, design_z1) minus the
+// heated box; every other element is passive fluid. With the full extents (the default) the heated
+// region is the bottom layers and every element above them is a design element.
 struct Phys {
-  double h, beta, rc, mu, he, tau3, Q;  // Q: source in the heated layers (already ramped)
+  double h, beta, rc, mu, he, tau3, Q;  // Q: source in the heated region (already ramped)
   int heated_layers;
+  int heat_nx, heat_ny;
+  int design_nx, design_ny, design_z1;
 };
+
+__host__ __device__ __forceinline__ bool elem_heated(const Phys& ph, int i, int j, int k) {
+  return i < ph.heat_nx && j < ph.heat_ny && k < ph.heated_layers;
+}
+__host__ __device__ __forceinline__ bool elem_design(const Phys& ph, int i, int j, int k) {
+  return !elem_heated(ph, i, j, k) && i < ph.design_nx && j < ph.design_ny && k >= ph.heated_layers &&
+         k < ph.design_z1;
+}
 
 template <typename R>
 inline ElemConst<R> make_econst(const Phys& p) {
@@ -60,10 +74,10 @@ cudaError_t launch_jv_f64(const Grid& g, const Phys& ph, const double2* s, const
 // L = w . R_e, stored by the same pass.
 cudaError_t launch_jtv_f64(const Grid& g, const Phys& ph, const double2* s, const double2* mat,
                            const double2* w, double* out, double2* dl, cudaStream_t st, Counters* c);
-// df/dgamma~ = -(dL/dkappa kappa' + dL/dk k') from stored dl; 0 on the heated layers.
-cudaError_t launch_sens_from_dl(const Grid& g, int heated_layers, const double2* dl, const double2* dmat, double* out,
+// df/dgamma~ = -(dL/dkappa kappa' + dL/dk k') from stored dl; 0 on passive (heated, fluid) elements.
+cudaError_t launch_sens_from_dl(const Grid& g, const Phys& ph, const double2* dl, const double2* dmat, double* out,
                                 cudaStream_t st, Counters* c);
-// d f / d gamma~_e = -(dL/dkappa kappa' + dL/dk k'), 0 on heated elements; dmat: (kappa', k').
+// d f / d gamma~_e = -(dL/dkappa kappa' + dL/dk k'), 0 on passive elements; dmat: (kappa', k').
 cudaError_t launch_sens_elem(const Grid& g, const Phys& ph, const double2* s, const double2* lam,
                              const double2* mat, const double2* dmat, double* out, cudaStream_t st,
                              Counters* c);
@@ -98,7 +112,8 @@ cudaError_t launch_multidot(const float* V, long long ld, int nvec, const float*
                             double* part, double* res, cudaStream_t st, Counters* c);
 // res[0] = sum of a[0..n) (deterministic two-stage reduction).
 cudaError_t launch_sum(const double* a, long long n, double* part, double* res, cudaStream_t st, Counters* c);
-// res[0] = sum over free entries (Dirichlet rows excluded) of a^2, for a state vector.
+// res[0] = sum over free entries of a^2, for a state vector (kBcTop: the rows below the top plane;
+// kBcCavity: every row, the fixed ones being zero in every vector this is called on).
 cudaError_t launch_norm2_free(const Grid& g, const double* a, double* part, double* res,
                               cudaStream_t st, Counters* c);
 // Gram-Schmidt step of FGMRES (nvec <= 32) from the first-pass dots d1 (device: V_i . w, then w . w):
@@ -130,7 +145,7 @@ cudaError_t launch_scale_copy(float* y, const double* x, double a, long long n, 
                               Counters* c);
 cudaError_t launch_cast_d2f(float* y, const double* x, long long n, cudaStream_t st, Counters* c);
 cudaError_t launch_cast_f2d(double* y, const float* x, long long n, cudaStream_t st, Counters* c);
-// Zero the Dirichlet (top plane) entries of a state vector.
+// Zero the Dirichlet entries of a state vector (the fixed set of g.bc).
 cudaError_t launch_zero_dirichlet(const Grid& g, double* a, cudaStream_t st, Counters* c);
 cudaError_t launch_zero_dirichlet(const Grid& g, float* a, cudaStream_t st, Counters* c);
 // Design check: flag = 1 if any value is NaN or outside [0,1].
@@ -148,13 +163,16 @@ cudaError_t launch_cheb_step(const Grid& g, const FilterConstF& F, const float* 
                              float* x, float* r, float c1, float c2, cudaStream_t st, Counters* c);
 // y += (double) x
 cudaError_t launch_add_f2d(double* y, const float* x, long long n, cudaStream_t st, Counters* c);
-cudaError_t launch_filter_rhs(const Grid& g, const double* gamma, int heated_layers, double scale_elem,
+// b = T^T g with g = gamma on design elements, 1 on heated and 0 on fluid elements (passive=true) or
+// g = gamma everywhere (passive=false).
+cudaError_t launch_filter_rhs(const Grid& g, const Phys& ph, bool passive, const double* gamma, double scale_elem,
                               double* b, cudaStream_t st, Counters* c);
 cudaError_t launch_helmholtz(const Grid& g, const FilterConst& F, const double* x, double* y,
                              cudaStream_t st, Counters* c);
 cudaError_t launch_helmholtz_diag(const Grid& g, const FilterConst& F, double* dinv, cudaStream_t st);
-// out_e = scale * sum_a x_{n(e,a)}; heated elements get `heated_value` if heated_value >= 0
-cudaError_t launch_elem_from_nodes(const Grid& g, const double* x, double scale, int heated_layers,
+// out_e = scale * sum_a x_{n(e,a)}; if heated_value >= 0, heated elements get heated_value and fluid
+// elements 0
+cudaError_t launch_elem_from_nodes(const Grid& g, const Phys& ph, const double* x, double scale,
                                    double heated_value, double* out, cudaStream_t st, Counters* c);
 // RAMP (Eqs. condRAMP, permRAMP): mat = (kappa, k), dmat = (kappa', k'), mat32 FP32 copy.
 struct RampConst { double kappa_f, kappa_s, k_f, k_s, q_c, q_p; };
@@ -164,7 +182,7 @@ cudaError_t launch_ramp(const double* gt, long long ne, const RampConst& r, doub
 cudaError_t launch_vmul(double* z, const double* a, const double* b, long long n, cudaStream_t st,
                         Counters* c);
 // Objective weights df/ds (mean T over the heated region) and objective value.
-cudaError_t launch_dfds(const Grid& g, int heated_layers, double w_node, double* out, cudaStream_t st,
+cudaError_t launch_dfds(const Grid& g, const Phys& ph, double w_node, double* out, cudaStream_t st,
                         Counters* c);
 
 // ---------------- multigrid (nc_kernels_mg.cu) ----------------

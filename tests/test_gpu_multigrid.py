@@ -38,3 +38,33 @@ def test_fused_tail_matches_launches(nc, shape, levels):
     assert abs(a[3] - b[3]) <= 1 and abs(a[4] - b[4]) <= 1
     for x, y, tol in zip(a[:3], b[:3], (1e-8, 1e-8, 1e-6)):
         assert np.linalg.norm(x - y) <= tol * np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_large_coarse_matrix(nc, precision):
+    """A coarsest matrix too large for the single-block shared-memory inverse (2 levels at 12^3: 588
+    free DOFs) goes through the multi-launch Gauss-Jordan inverse; the state, objective and
+    sensitivities match the oracle as with 3 levels (96 free DOFs, shared-memory inverse)."""
+    import oracle
+    n = 12
+    rho = filtered_random(n, n, n, seed=6, volfrac=0.2)
+    tol = 1e-8 if precision == 1 else 1e-6
+    op = oracle.Problem(oracle.Mesh(n, n, n, 1.0 / n), oracle.Params(alpha=1e4, newton_rtol=1e-10))
+    op.set_design(rho)
+    op.solve_state()
+    Po, To = op.fields()
+    op.solve_adjoint()
+    go = op.sensitivities()
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    for levels in (2, 3):
+        pb = nc.Problem(n, n, n, 1.0 / n, alpha=1e4, mg_levels=levels, precision=precision, newton_rtol=1e-10)
+        pb.set_design(rho)
+        st = pb.solve_state()
+        assert st["rel_residual"] <= 1e-10
+        P, T, _ = pb.get_fields(velocity=False)
+        f, _ = pb.solve_adjoint()
+        g = pb.sensitivities().cpu().numpy()
+        assert rel(P.cpu().numpy(), Po) < tol and rel(T.cpu().numpy(), To) < tol
+        assert f == pytest.approx(op.objective(), rel=tol)
+        assert rel(g, go) < 1e-6
+        pb.close()
