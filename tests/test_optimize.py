@@ -63,3 +63,43 @@ def test_optimisation_loop_32():
     rho = out["rho"].cpu().numpy()
     assert rho.min() >= 0.0 and rho.max() <= 1.0
     assert np.all(rho[: 2 * 32 * 32] == 1.0)       # the heated layers stay solid
+
+
+def test_region_masks_and_cavity_setup():
+    """Design and heated masks follow the boxes of nc_params; the cavity setup reproduces Sec. 6.1's
+    proportions (80 -> 80 x 80 x 160 mesh, heat source 8^3 elements, design box 60 x 60 x 120)."""
+    import torch
+    from paper_1904_00182_gb300 import _abi
+    from paper_1904_00182_gb300.optimize import cavity_params, region_masks
+    p = _abi.default_params()
+    d, h = region_masks(4, 3, 5, p)
+    assert int(h.sum()) == 4 * 3 * 2 and int(d.sum()) == 4 * 3 * 3 and not bool((d & h).any())
+    g = cavity_params(80)
+    assert (g["heat_nx"], g["heated_layers"], g["design_nx"], g["design_nz"]) == (8, 8, 60, 120)
+    p = _abi.default_params(**{k: v for k, v in g.items() if k != "Q"})
+    d, h = region_masks(80, 80, 160, p)
+    assert int(h.sum()) == 8 ** 3 and int(d.sum()) == 60 * 60 * 120
+    e = torch.arange(80 * 80 * 160)
+    i, j, k = e % 80, (e // 80) % 80, e // 6400
+    assert bool(((i < 60) & (j < 60) & (k >= 8) & (k < 128))[d].all())
+    with pytest.raises(ValueError):
+        cavity_params(50)
+
+
+@pytest.mark.gpu
+def test_optimisation_loop_cavity():
+    """A few MMA iterations on the quarter cavity (24 x 24 x 48, the design box 3/4 of the width and
+    36 layers on a 2^3 heat box, Q = 1e4, 5 % volume): f decreases, every iterate is feasible, passive
+    elements keep their values."""
+    from paper_1904_00182_gb300 import build
+    build.build()
+    import paper_1904_00182_gb300 as nc
+    from paper_1904_00182_gb300.optimize import optimize
+    geom = dict(bc=nc.NC_BC_CAVITY, Q=1e4, heat_nx=2, heat_ny=2, heated_layers=2, design_nx=18, design_ny=18,
+                design_nz=36)
+    out = optimize(24, 24, 48, 1e3, 0.05, 8, stages=({"q_c": 8.81, "q_p": 8.0},), **geom)
+    h = out["history"]
+    assert h[-1]["f"] < h[0]["f"]
+    assert all(r["g"] <= 1e-6 for r in h)
+    rho = out["rho"].cpu().numpy().reshape(48, 24, 24)
+    assert np.all(rho[:2, :2, :2] == 1.0) and np.all(rho[38:, :, :] == 0.0) and np.all(rho[2:38, :, 18:] == 0.0)
