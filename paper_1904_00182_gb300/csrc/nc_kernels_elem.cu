@@ -2,7 +2,8 @@
 // centroid velocities. One thread per element (3D launch: 32 x 4 element columns per block, one
 // z-layer per blockIdx.z, 32-bit index arithmetic) gathers its 8 nodes, evaluates the element
 // arithmetic of nc_element.cuh and scatters the 16 row contributions with atomic adds
-// (Dirichlet rows on the top plane are skipped and set by the caller's convention).
+// (with kBcTop the Dirichlet rows on the top plane are skipped; otherwise the caller zeroes or sets the
+// fixed rows, see fixed_bits).
 #include "nc_launch.h"
 
 namespace nc {
@@ -20,7 +21,8 @@ __device__ __forceinline__ void gather_state(const Grid& g, const V* __restrict_
   }
 }
 
-// Gather a direction vector with its Dirichlet (top-plane) entries treated as zero.
+// Gather a direction vector; with `top` (kBcTop, element below the top plane) its Dirichlet entries are
+// treated as zero (other boundary conditions keep every vector zero on the fixed set).
 template <typename R, typename V>
 __device__ __forceinline__ void gather_dir(const Grid& g, const V* __restrict__ v, int n0, bool top,
                                            R p[8], R t[8]) {

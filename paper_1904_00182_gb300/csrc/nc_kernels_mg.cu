@@ -319,7 +319,8 @@ __device__ __forceinline__ typename Vec2<R>::type mask_fixed(const Grid& g, int 
 }
 
 // Full weighting (R = P^T) at coarse node (I, J, K): the fine residual rf at the 27 fine nodes
-// around it, weights 1, 1/2, 1/4, 1/8 by distance; the top (Dirichlet) plane gets 0.
+// around it, weights 1, 1/2, 1/4, 1/8 by distance; `top` (the kBcTop Dirichlet plane) gets 0, and the
+// callers zero the fixed components of other boundary conditions (mask_fixed).
 template <typename R, typename FETCH>
 __device__ __forceinline__ typename Vec2<R>::type restrict_node_f(const Grid& gf, int I, int J, int K, bool top,
                                                                   FETCH fetch) {
@@ -526,7 +527,7 @@ __device__ __forceinline__ Blk4<double> ld_blk(const double* __restrict__ S, int
 }
 
 // y = A x (MODE 0), r = b - A x (MODE 1) or x_new = x + omega D^-1 (b - A x) (MODE 2), with A the
-// assembled stencil or (TR) its transpose, at node n = (i, j, k) below the top plane: gathers the
+// assembled stencil or (TR) its transpose, at node n = (i, j, k) (below the top plane for kBcTop): gathers the
 // 27 neighbours. A neighbour outside the grid is read at the node itself (always in range) and its
 // value replaced by zero, so the loop has no branches and all 54 loads can be in flight together.
 // S and dinv are read-only; x and b go through the load policy.
@@ -571,7 +572,8 @@ __device__ __forceinline__ void stencil_node(const Grid& g, const R* __restrict_
   out[n] = mk2<R>(xs.x + omega * z0, xs.y + omega * z1);
 }
 
-// One thread per node (flat z-plane launch); the top (Dirichlet) plane gets 0.
+// One thread per node (flat z-plane launch); with kBcTop the top (Dirichlet) plane gets 0, otherwise the
+// zero stencil rows and block inverses of fixed components keep them at zero.
 template <typename R, bool TR, int MODE>
 __global__ void __launch_bounds__(128) k_stencil_apply(Grid g, const R* __restrict__ S,
                                                        const typename Vec2<R>::type* __restrict__ x,
