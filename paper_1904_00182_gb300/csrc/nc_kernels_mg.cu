@@ -543,7 +543,7 @@ __device__ __forceinline__ void stencil_node(const Grid& g, const R* __restrict_
   for (int o = 0; o < 27; ++o) {
     const int oi = o % 3 - 1, oj = (o / 3) % 3 - 1, ok = o / 9 - 1;
     const bool inside = !((oi < 0 && i == 0) || (oi > 0 && i == g.nx) || (oj < 0 && j == 0) ||
-                          (oj > 0 && j == g.ny) || (ok < 0 && k == 0));
+                          (oj > 0 && j == g.ny) || (ok < 0 && k == 0) || (ok > 0 && k == g.nz));
     const int m = inside ? n + oi + g.NX * oj + g.NXY * ok : n;
     xv[o] = ld(x + m);
     c[o] = TR ? ld_blk(S, (26 - o) * nn + m) : ld_blk(S, o * nn + n);   // TR: offset -o seen from m

@@ -139,9 +139,7 @@ def region_masks(nx, ny, nz, params):
 def cavity_params(n):
     """The benchmark of Sec. 6.1 on the quarter cavity of n x n x 2n elements (h = 1 / 2n): heat source
     0.05^3 m (n / 10 elements per side), Q = 1e4 W/m^3, design box 0.375 x 0.375 x 0.75 m on top of it.
-    n must be a multiple of 20 (80 gives the 80 x 80 x 160 mesh of Table 3). These grids coarsen to a
-    5 x 5 x 10 coarsest multigrid level, on which the cavity adjoint currently returns NC_ERR_NAN, so
-    the loop stops at its first adjoint there; the state solve works."""
+    n must be a multiple of 20 (80 gives the 80 x 80 x 160 mesh of Table 3)."""
     if n % 20:
         raise ValueError("n must be a multiple of 20")
     return dict(bc=_abi.NC_BC_CAVITY, Q=1e4, heat_nx=n // 10, heat_ny=n // 10, heated_layers=n // 10,

@@ -89,7 +89,8 @@ def test_region_masks_and_cavity_setup():
 @pytest.mark.gpu
 def test_optimisation_loop_cavity():
     """A few MMA iterations on the quarter cavity (24 x 24 x 48, the design box 3/4 of the width and
-    36 layers on a 2^3 heat box, Q = 1e4, 5 % volume): f decreases, every iterate is feasible, passive
+    36 layers on a 2^3 heat box, Q = 1e4, 5 % volume; four multigrid levels, so the stencil levels
+    include top-plane nodes that are free in P): f decreases, every iterate is feasible, passive
     elements keep their values."""
     from paper_1904_00182_gb300 import build
     build.build()
