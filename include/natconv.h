@@ -78,6 +78,14 @@ enum { NC_OBJ_MEAN_T_HEATED = 0, NC_OBJ_SUPG_COMPLIANCE = 1 };
  * bottom insulated, no normal flow through any face, and P = 0 at the top outer corner. */
 enum { NC_BC_TOP = 0, NC_BC_CAVITY = 1 };
 
+/* Shape of the heated and design regions (nc_params.region_shape). NC_REGION_BOX: boxes at the corner
+ * x = y = 0 (heat_nx ..., design_nx ...). NC_REGION_CYLINDER (the suspended cylinder of Sec. 7): the
+ * heated region is the cylinder of radius heat_radius around the z axis through that corner, over the
+ * element layers [heat_z0, heat_z0 + heated_layers); the design region is the annulus out to
+ * design_radius over the same layers. An element belongs to a region when its centroid does; radii
+ * are in element sizes. */
+enum { NC_REGION_BOX = 0, NC_REGION_CYLINDER = 1 };
+
 typedef struct nc_problem nc_problem;
 
 typedef struct {
@@ -150,6 +158,9 @@ typedef struct {
   int design_nx, design_ny, design_nz; /* design region: [0, design_nx) x [0, design_ny) x
                            [heated_layers, heated_layers + design_nz); 0: the full extent. Elements
                            outside both boxes are passive fluid (filtered density 0) [0, 0, 0] */
+  int region_shape;     /* NC_REGION_BOX or NC_REGION_CYLINDER [NC_REGION_BOX] */
+  double heat_radius, design_radius; /* NC_REGION_CYLINDER: radii in element sizes [0, 0] */
+  int heat_z0;          /* NC_REGION_CYLINDER: first element layer of both regions [0] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */

@@ -71,6 +71,14 @@ class Mesh:
         e = self.elem_ijk()
         return (e[:, 0] < nx) & (e[:, 1] < ny) & (e[:, 2] >= z0) & (e[:, 2] < z1)
 
+    def cylinder_elems(self, radius, z0, z1, inner=0.0):
+        """Boolean mask of the elements whose centroid lies at distance in [inner, radius) (element sizes)
+        from the z axis through the corner x = y = 0, in the layers z0 <= k < z1 (Sec. 7's suspended
+        cylinder and the annulus around it, quarter domain)."""
+        e = self.elem_ijk()
+        r2 = (e[:, 0] + 0.5) ** 2 + (e[:, 1] + 0.5) ** 2
+        return (r2 < radius ** 2) & (r2 >= inner ** 2) & (e[:, 2] >= z0) & (e[:, 2] < z1)
+
     def cavity_dirichlet(self):
         """(maskP, maskT) of the quarter cavity of Sec. 6.1 (symmetry planes x = 0 and y = 0): T fixed on
         the outer walls x = nx h, y = ny h and on the top; P fixed at the top outer corner."""

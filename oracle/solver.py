@@ -64,6 +64,13 @@ class Params:
     design_nx: Optional[int] = None
     design_ny: Optional[int] = None
     design_nz: Optional[int] = None
+    # region_shape "cylinder": heated cylinder of heat_radius and design annulus out to design_radius
+    # (element sizes) about the z axis through x = y = 0, both over the layers [heat_z0, heat_z0 +
+    # heated_layers); the box fields above are then unused
+    region_shape: str = "box"
+    heat_radius: float = 0.0
+    design_radius: float = 0.0
+    heat_z0: int = 0
 
     def resolved(self, mesh):
         kf = self.kappa_f if self.kappa_f else kappa_f_tuned(self.alpha)
@@ -110,9 +117,16 @@ class Problem:
         self.free = np.flatnonzero(~self.dir_mask)
         par = self.par
         hl = par.heated_layers
-        self.heated = mesh.box_elems(par.heat_nx or mesh.nx, par.heat_ny or mesh.ny, 0, hl)
-        self.design = mesh.box_elems(par.design_nx or mesh.nx, par.design_ny or mesh.ny, hl,
-                                     hl + par.design_nz if par.design_nz else mesh.nz) & ~self.heated
+        if par.region_shape == "cylinder":
+            z0, z1 = par.heat_z0, par.heat_z0 + hl
+            self.heated = mesh.cylinder_elems(par.heat_radius, z0, z1)
+            self.design = mesh.cylinder_elems(par.design_radius, z0, z1, inner=par.heat_radius)
+        elif par.region_shape == "box":
+            self.heated = mesh.box_elems(par.heat_nx or mesh.nx, par.heat_ny or mesh.ny, 0, hl)
+            self.design = mesh.box_elems(par.design_nx or mesh.nx, par.design_ny or mesh.ny, hl,
+                                         hl + par.design_nz if par.design_nz else mesh.nz) & ~self.heated
+        else:
+            raise ValueError("unknown region_shape")
         self.passive = ~self.design                        # heated (solid) or passive fluid
         self.fluid = self.passive & ~self.heated
         vol_h = self.heated.sum() * mesh.h ** 3

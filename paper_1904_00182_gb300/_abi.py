@@ -17,6 +17,8 @@ NC_OBJ_MEAN_T_HEATED = 0
 NC_OBJ_SUPG_COMPLIANCE = 1
 NC_BC_TOP = 0
 NC_BC_CAVITY = 1
+NC_REGION_BOX = 0
+NC_REGION_CYLINDER = 1
 
 STATUS_NAMES = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_OOM", 3: "NC_ERR_CUDA", 4: "NC_ERR_DIVERGED",
                 5: "NC_ERR_MAXIT", 6: "NC_ERR_NAN", 7: "NC_ERR_TIMEOUT", 8: "NC_ERR_STATE"}
@@ -60,7 +62,8 @@ class Params(ctypes.Structure):
         ("mg_tail_nodes", ctypes.c_int), ("mg_reuse_below", ctypes.c_double), ("outer_arith", ctypes.c_int),
         ("krylov_basis", ctypes.c_int), ("krylov_reorth", ctypes.c_double), ("adjoint_df64_steps", ctypes.c_int),
         ("bc", ctypes.c_int), ("heat_nx", ctypes.c_int), ("heat_ny", ctypes.c_int), ("design_nx", ctypes.c_int),
-        ("design_ny", ctypes.c_int), ("design_nz", ctypes.c_int),
+        ("design_ny", ctypes.c_int), ("design_nz", ctypes.c_int), ("region_shape", ctypes.c_int),
+        ("heat_radius", ctypes.c_double), ("design_radius", ctypes.c_double), ("heat_z0", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -934,6 +934,15 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (!(p->newton_rtol > 0) || p->newton_maxit < 0 || p->krylov_maxit < 1) { *why = "bad tolerances"; return NC_ERR_ARG; }
   if (!(p->filter_radius >= 0) || !(p->filter_rtol > 0)) { *why = "bad filter parameters"; return NC_ERR_ARG; }
   if (p->bc != NC_BC_TOP && p->bc != NC_BC_CAVITY) { *why = "unknown bc"; return NC_ERR_ARG; }
+  if (p->region_shape != NC_REGION_BOX && p->region_shape != NC_REGION_CYLINDER) {
+    *why = "unknown region_shape"; return NC_ERR_ARG;
+  }
+  if (p->region_shape == NC_REGION_CYLINDER &&
+      (!(p->heat_radius > 0) || !(p->design_radius >= p->heat_radius) || p->heat_z0 < 0 ||
+       p->heat_z0 + p->heated_layers > g->nz || p->heated_layers < 1 ||
+       4.0 * p->design_radius * p->design_radius > 2e9)) {
+    *why = "cylinder regions need 0 < heat_radius <= design_radius and layers inside the grid"; return NC_ERR_ARG;
+  }
   if (p->heat_nx < 0 || p->heat_nx > g->nx || p->heat_ny < 0 || p->heat_ny > g->ny || p->design_nx < 0 ||
       p->design_nx > g->nx || p->design_ny < 0 || p->design_ny > g->ny || p->design_nz < 0 ||
       p->heated_layers + p->design_nz > g->nz) {
@@ -986,7 +995,19 @@ void apply_params(nc_problem* pb, const nc_params* p) {
   pb->ph.design_nx = p->design_nx > 0 ? p->design_nx : g.nx;
   pb->ph.design_ny = p->design_ny > 0 ? p->design_ny : g.ny;
   pb->ph.design_z1 = p->design_nz > 0 ? p->heated_layers + p->design_nz : g.nz;
-  pb->vol_h = (double)pb->ph.heat_nx * pb->ph.heat_ny * p->heated_layers * g.h * g.h * g.h;
+  pb->ph.shape = p->region_shape;
+  pb->ph.z0 = p->heat_z0;
+  pb->ph.q_heat = (int)std::ceil(4.0 * p->heat_radius * p->heat_radius);
+  pb->ph.q_design = (int)std::ceil(4.0 * p->design_radius * p->design_radius);
+  pb->ph.heated_layers = p->heated_layers;
+  if (p->region_shape == NC_REGION_CYLINDER) {
+    long long cross = 0;   // heated elements of one layer
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) cross += elem_heated(pb->ph, i, j, p->heat_z0) ? 1 : 0;
+    pb->vol_h = (double)cross * p->heated_layers * g.h * g.h * g.h;
+  } else {
+    pb->vol_h = (double)pb->ph.heat_nx * pb->ph.heat_ny * p->heated_layers * g.h * g.h * g.h;
+  }
   pb->Q_full = p->Q > 0 ? p->Q : (pb->vol_h > 0 ? 1.0 / pb->vol_h : 0.0);
   pb->ph.h = g.h;
   pb->ph.beta = p->rho0 * p->alpha * p->g;
@@ -995,7 +1016,6 @@ void apply_params(nc_problem* pb, const nc_params* p) {
   pb->ph.he = std::sqrt(3.0) * g.h;
   pb->ph.tau3 = p->rho0 * p->cp * pb->ph.he * pb->ph.he / (4.0 * p->k_f);
   pb->ph.Q = pb->Q_full;
-  pb->ph.heated_layers = p->heated_layers;
   // filter element matrix r^2 K0 + M0 (Q1 cube: K0 = h/12 [4,0,-1,-1], M0 = h^3/216 [8,4,2,1] by
   // the number of differing reference coordinates), r = R / (2 sqrt 3)
   {
@@ -1296,7 +1316,7 @@ nc_status nc_objective(nc_problem* pb, int objective, double* f) {
   const Grid& g = pb->g;
   if (objective == NC_OBJ_SUPG_COMPLIANCE) {
     set_q_scale(pb, 1.0);
-    const long long nh = (long long)g.nx * g.ny * pb->par.heated_layers;
+    const long long nh = pb->ph.shape == 1 ? g.ne : (long long)g.nx * g.ny * pb->par.heated_layers;
     PCK(NC_PROF_OTHER, launch_obj_supg(g, pb->ph, pb->s, pb->mat, pb->gsens, pb->rhs, pb->st, &pb->cnt));
     PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->rhs, pb->st, &pb->cnt));
     PCK(NC_PROF_OTHER, launch_sum(pb->gsens, nh, pb->part, pb->dres, pb->st, &pb->cnt));

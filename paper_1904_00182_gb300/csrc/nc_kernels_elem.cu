@@ -279,9 +279,10 @@ cudaError_t launch_obj_supg(const Grid& g, const Phys& ph, const double2* s, con
   cudaError_t err = cudaMemsetAsync(d, 0, sizeof(double) * 2 * g.nn, st);
   if (err != cudaSuccess) return err;
   Launch3 L = launch_elems(g);
-  L.grid.z = (unsigned)ph.heated_layers;   // the source lies in the heated layers only
+  // boxes: the source lies in the bottom heated layers only; cylinders: every layer is visited
+  if (ph.shape != 1) L.grid.z = (unsigned)ph.heated_layers;
   k_obj_supg<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<double>(ph), s, mat, fe, d);
-  if (c) { c->launches += 1; c->bytes += 16.0 * g.nn + 24.0 * g.nx * g.ny * ph.heated_layers; }
+  if (c) { c->launches += 1; c->bytes += 16.0 * g.nn + 24.0 * g.nx * g.ny * L.grid.z; }
   return cudaGetLastError();
 }
 

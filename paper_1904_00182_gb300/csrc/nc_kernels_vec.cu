@@ -425,10 +425,18 @@ __global__ void k_dfds(Grid g, Phys ph, double w_node, double* __restrict__ out)
   node_ijk(g, n, i, j, k);
   int cnt = 0;
   if (!(fixed_bits(g, i, j, k) & 2)) {
-    const int hx = min(ph.heat_nx, g.nx), hy = min(ph.heat_ny, g.ny), hz = min(ph.heated_layers, g.nz);
-    const int cx = (i > 0 && i - 1 < hx) + (i < hx), cy = (j > 0 && j - 1 < hy) + (j < hy);
-    const int cz = (k > 0 && k - 1 < hz) + (k < hz);
-    cnt = cx * cy * cz;
+    if (ph.shape == 1) {   // count the heated elements among the (up to 8) around the node
+      for (int ek = k - 1; ek <= k; ++ek)
+        for (int ej = j - 1; ej <= j; ++ej)
+          for (int ei = i - 1; ei <= i; ++ei)
+            if (ei >= 0 && ei < g.nx && ej >= 0 && ej < g.ny && ek >= 0 && ek < g.nz && elem_heated(ph, ei, ej, ek))
+              ++cnt;
+    } else {
+      const int hx = min(ph.heat_nx, g.nx), hy = min(ph.heat_ny, g.ny), hz = min(ph.heated_layers, g.nz);
+      const int cx = (i > 0 && i - 1 < hx) + (i < hx), cy = (j > 0 && j - 1 < hy) + (j < hy);
+      const int cz = (k > 0 && k - 1 < hz) + (k < hz);
+      cnt = cx * cy * cz;
+    }
   }
   out[2 * n] = 0.0;
   out[2 * n + 1] = w_node * cnt;

@@ -12,17 +12,29 @@ namespace nc {
 // [0, heated_layers); design [0, design_nx) x [0, design_ny) x [heated_layers, design_z1) minus the
 // heated box; every other element is passive fluid. With the full extents (the default) the heated
 // region is the bottom layers and every element above them is a design element.
+// With shape = 1 (cylinders about the z axis through the corner x = y = 0) an element is heated when
+// its centroid lies within the heat radius and its layer in [z0, z0 + heated_layers), and a design
+// element when its centroid lies within the design radius (and not the heat radius) over the same
+// layers. The radius tests are exact integer ones: (2i+1)^2 + (2j+1)^2 < 4 r^2, held as
+// q < ceil(4 r^2).
 struct Phys {
   double h, beta, rc, mu, he, tau3, Q;  // Q: source in the heated region (already ramped)
   int heated_layers;
   int heat_nx, heat_ny;
   int design_nx, design_ny, design_z1;
+  int shape, z0, q_heat, q_design;
 };
 
+__host__ __device__ __forceinline__ int centroid_q(int i, int j) { return (2 * i + 1) * (2 * i + 1) + (2 * j + 1) * (2 * j + 1); }
+
 __host__ __device__ __forceinline__ bool elem_heated(const Phys& ph, int i, int j, int k) {
+  if (ph.shape == 1) return k >= ph.z0 && k < ph.z0 + ph.heated_layers && centroid_q(i, j) < ph.q_heat;
   return i < ph.heat_nx && j < ph.heat_ny && k < ph.heated_layers;
 }
 __host__ __device__ __forceinline__ bool elem_design(const Phys& ph, int i, int j, int k) {
+  if (ph.shape == 1)
+    return k >= ph.z0 && k < ph.z0 + ph.heated_layers && centroid_q(i, j) < ph.q_design &&
+           centroid_q(i, j) >= ph.q_heat;
   return !elem_heated(ph, i, j, k) && i < ph.design_nx && j < ph.design_ny && k >= ph.heated_layers &&
          k < ph.design_z1;
 }
@@ -92,7 +104,8 @@ cudaError_t launch_jtv_df(const Grid& g, const Phys& ph, const double2* s, const
 cudaError_t launch_sens_df(const Grid& g, const Phys& ph, const double2* s, const double2* lam, const float4* mat_df,
                            const double2* dmat, float4* s_df, float4* l_df, double* out, cudaStream_t st, Counters* c);
 // Thermal compliance of Eq. objdiscr on the heated elements: fe[e] = f_tQ,e . t_e for e in the heated
-// layers (other entries untouched) and d = its state derivative (2N, zeroed first).
+// layers (boxes; every element for cylinders; other entries untouched) and d = its state derivative
+// (2N, zeroed first).
 cudaError_t launch_obj_supg(const Grid& g, const Phys& ph, const double2* s, const double2* mat, double* fe,
                             double* d, cudaStream_t st, Counters* c);
 // Centroid Darcy velocity (3 per element).

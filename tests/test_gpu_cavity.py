@@ -148,3 +148,34 @@ def test_parameters_and_errors(lib):
     with pytest.raises(lib.NatConvError):
         gp.set_params(bc=lib.NC_BC_TOP)
     gp.close()
+
+
+def test_cylinder_regions(lib):
+    """Sec. 7's suspended cylinder on the quarter cavity (12 x 12 x 24; heat radius 4, design radius 9,
+    layers 8-13): filtered design, state, both objectives and sensitivities against the oracle on the
+    mixed path."""
+    geom = dict(heat_radius=4.0, design_radius=9.0, heat_z0=8, heated_layers=6, Q=100.0)
+    n, nz = 12, 24
+    rho = filtered_random(n, n, nz, 2, volfrac=0.3)
+    gp = lib.Problem(n, n, nz, 1.0 / nz, alpha=1e4, precision=0, newton_rtol=1e-10, bc=lib.NC_BC_CAVITY,
+                     region_shape=lib.NC_REGION_CYLINDER, **geom)
+    gp.set_design(rho)
+    op = oracle.Problem(oracle.Mesh(n, n, nz, 1.0 / nz),
+                        oracle.Params(alpha=1e4, newton_rtol=1e-10, bc="cavity", region_shape="cylinder", **geom))
+    op.set_design(rho)
+    gt = gp.design_fields()[0].cpu().numpy()
+    assert np.abs(gt - op.gamma_t).max() < 1e-10
+    st = gp.solve_state()
+    assert st["rel_residual"] <= 1e-10
+    op.solve_state()
+    P, T, _ = gp.get_fields(velocity=False)
+    Po, To = op.fields()
+    assert rel(P.cpu().numpy(), Po) < 1e-6 and rel(T.cpu().numpy(), To) < 1e-6
+    assert gp.objective(lib.NC_OBJ_SUPG_COMPLIANCE) == pytest.approx(op.supg_compliance(), rel=1e-6)
+    f, _ = gp.solve_adjoint()
+    assert f == pytest.approx(op.objective(), rel=1e-6)
+    op.solve_adjoint()
+    g = gp.sensitivities().cpu().numpy()
+    assert rel(g, op.sensitivities()) < 1e-6
+    assert np.all(g[op.passive] == 0.0) and np.abs(g[op.design]).max() > 0
+    gp.close()

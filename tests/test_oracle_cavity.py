@@ -136,3 +136,31 @@ def test_cavity_gradient_matches_central_differences():
     pr.set_design(g0)
     pr.solve_state(rtol=1e-13)
     assert f1 == pytest.approx(pr.objective(), rel=1e-12)
+
+
+def test_cylinder_regions_and_solution_symmetry():
+    """Sec. 7's suspended cylinder (quarter domain): the voxelised heated cylinder and design annulus
+    approach the quarter-disc areas, lie in the given layers and do not overlap; the solution is
+    symmetric under the exchange x <-> y, which the quarter geometry and its boundary conditions keep."""
+    n, nz = 12, 24
+    m = Mesh(n, n, nz, 1.0 / nz)
+    par = Params(alpha=1e4, bc="cavity", region_shape="cylinder", heat_radius=4.0, design_radius=9.0,
+                 heat_z0=8, heated_layers=6, Q=100.0, newton_rtol=1e-12)
+    pr = Problem(m, par)
+    e = m.elem_ijk()
+    assert np.all((e[pr.heated, 2] >= 8) & (e[pr.heated, 2] < 14)) and not np.any(pr.heated & pr.design)
+    per_layer_h = pr.heated.sum() / 6
+    per_layer_d = pr.design.sum() / 6
+    assert abs(per_layer_h - np.pi * 16 / 4) < 0.2 * np.pi * 16 / 4
+    assert abs(per_layer_h + per_layer_d - np.pi * 81 / 4) < 0.1 * np.pi * 81 / 4
+    rng = np.random.default_rng(4)
+    g = rng.random((nz, n, n))
+    g = 0.5 * (g + g.transpose(0, 2, 1))                 # a design symmetric under x <-> y
+    pr.set_design(g.ravel())
+    pr.solve_state()
+    P, T = pr.fields()
+    Tn = T.reshape(nz + 1, n + 1, n + 1)
+    Pn = P.reshape(nz + 1, n + 1, n + 1)
+    assert np.abs(Tn - Tn.transpose(0, 2, 1)).max() <= 1e-9 * np.abs(Tn).max()
+    assert np.abs(Pn - Pn.transpose(0, 2, 1)).max() <= 1e-9 * np.abs(Pn).max()
+    assert pr.vol_h == pytest.approx(pr.heated.sum() / nz ** 3)
