@@ -127,11 +127,17 @@ def region_masks(nx, ny, nz, params):
     [heated_layers, heated_layers + design_nz) minus it, a zero extent meaning the full one (nc_params).
     Elements in neither are passive fluid."""
     hl = params.heated_layers
+    k, j, i = torch.meshgrid(torch.arange(nz), torch.arange(ny), torch.arange(nx), indexing="ij")
+    i, j, k = i.reshape(-1), j.reshape(-1), k.reshape(-1)
+    if params.region_shape == _abi.NC_REGION_CYLINDER:
+        # centroid within the radius: (2i+1)^2 + (2j+1)^2 < 4 r^2
+        q = (2 * i + 1) ** 2 + (2 * j + 1) ** 2
+        layers = (k >= params.heat_z0) & (k < params.heat_z0 + hl)
+        heated = layers & (q < 4.0 * params.heat_radius ** 2)
+        return layers & (q < 4.0 * params.design_radius ** 2) & ~heated, heated
     hx, hy = params.heat_nx or nx, params.heat_ny or ny
     dx, dy = params.design_nx or nx, params.design_ny or ny
     z1 = hl + params.design_nz if params.design_nz else nz
-    k, j, i = torch.meshgrid(torch.arange(nz), torch.arange(ny), torch.arange(nx), indexing="ij")
-    i, j, k = i.reshape(-1), j.reshape(-1), k.reshape(-1)
     heated = (i < hx) & (j < hy) & (k < hl)
     return (i < dx) & (j < dy) & (k >= hl) & (k < z1) & ~heated, heated
 
@@ -144,6 +150,17 @@ def cavity_params(n):
         raise ValueError("n must be a multiple of 20")
     return dict(bc=_abi.NC_BC_CAVITY, Q=1e4, heat_nx=n // 10, heat_ny=n // 10, heated_layers=n // 10,
                 design_nx=3 * n // 4, design_ny=3 * n // 4, design_nz=3 * n // 2)
+
+
+def cylinder_params(n):
+    """The suspended cylinder of Sec. 7 on the quarter cavity of n x n x 2n elements (h = 1 / 2n): heated
+    cylinder of radius 0.1 m and height 0.2 m centred in the cavity (Q = 1e3 W/m^3), design annulus out to
+    0.25 m over the same height, kappa_f = 0.000676 m^2 as the paper sets it. n must be a multiple of 5
+    (160 gives the paper's 160 x 160 x 320 mesh)."""
+    if n % 5:
+        raise ValueError("n must be a multiple of 5")
+    return dict(bc=_abi.NC_BC_CAVITY, region_shape=_abi.NC_REGION_CYLINDER, Q=1e3, kappa_f=0.000676,
+                heat_radius=0.2 * n, design_radius=0.5 * n, heat_z0=4 * n // 5, heated_layers=2 * n // 5)
 
 
 def optimize(nx, ny, nz, alpha, volfrac, iters, move=0.2, stages=PAPER_CONTINUATION, stage_every=None,
@@ -217,9 +234,11 @@ if __name__ == "__main__":
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--cavity", action="store_true",
                     help="the Sec. 6.1 benchmark on the quarter cavity of n x n x 2n elements (n a multiple of 20)")
+    ap.add_argument("--cylinder", action="store_true",
+                    help="Sec. 7's suspended cylinder on the quarter cavity of n x n x 2n elements (n a multiple of 5)")
     a = ap.parse_args()
-    geom = cavity_params(a.n) if a.cavity else {}
-    out = optimize(a.n, a.n, 2 * a.n if a.cavity else a.n, a.alpha, a.volfrac, a.iters, **geom,
+    geom = cavity_params(a.n) if a.cavity else cylinder_params(a.n) if a.cylinder else {}
+    out = optimize(a.n, a.n, 2 * a.n if (a.cavity or a.cylinder) else a.n, a.alpha, a.volfrac, a.iters, **geom,
                    callback=lambda r: print("it %3d f %.6e g %+.2e change %.3f stage %d newton %d krylov %d/%d %.3f s"
                                             % (r["it"], r["f"], r["g"], r["change"], r["stage"], r["newton_its"],
                                                r["krylov_its"], r["adjoint_krylov_its"], r["seconds"]), flush=True))

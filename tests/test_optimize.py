@@ -86,6 +86,26 @@ def test_region_masks_and_cavity_setup():
         cavity_params(50)
 
 
+def test_cylinder_setup_and_masks():
+    """Sec. 7's cylinder proportions (160 -> radii 32 and 80 elements, layers 128-191) and the masks the
+    volume constraint uses: heated and design elements in the right layers, annulus between the radii."""
+    from paper_1904_00182_gb300 import _abi
+    from paper_1904_00182_gb300.optimize import cylinder_params, region_masks
+    g = cylinder_params(160)
+    assert (g["heat_radius"], g["design_radius"], g["heat_z0"], g["heated_layers"]) == (32.0, 80.0, 128, 64)
+    g = cylinder_params(20)
+    p = _abi.default_params(**{k: v for k, v in g.items() if k not in ("Q", "kappa_f")})
+    d, h = region_masks(20, 20, 40, p)
+    i = np.arange(20 * 20 * 40) % 20
+    j = (np.arange(20 * 20 * 40) // 20) % 20
+    k = np.arange(20 * 20 * 40) // 400
+    r2 = (i + 0.5) ** 2 + (j + 0.5) ** 2
+    d, h = d.numpy(), h.numpy()
+    assert np.all((k[h] >= 16) & (k[h] < 24)) and np.all(r2[h] < 16.0)
+    assert np.all((r2[d] >= 16.0) & (r2[d] < 100.0)) and not np.any(d & h)
+    assert int(h.sum()) == 8 * int((r2[:400] < 16.0).sum())
+
+
 @pytest.mark.gpu
 def test_optimisation_loop_cavity():
     """A few MMA iterations on the quarter cavity (24 x 24 x 48, the design box 3/4 of the width and
