@@ -24,7 +24,6 @@ using namespace nc;
 namespace {
 
 const int kMaxRestart = 64;
-const int kMaxCoarseDofs = 1024;
 
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();

@@ -784,7 +784,7 @@ __device__ __forceinline__ AccT row_dot(const T* __restrict__ M, int nf, int r, 
 template <typename R, bool TR>
 __global__ void __launch_bounds__(256) k_coarse_x0(const float* __restrict__ Ainv32, int nf, const R* __restrict__ b,
                                                    double* __restrict__ bd, double* __restrict__ x0) {
-  __shared__ double sb[1024];
+  __shared__ double sb[kMaxCoarseDofs];
   for (int c = threadIdx.x; c < nf; c += blockDim.x) sb[c] = (double)b[c];
   __syncthreads();
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -1198,7 +1198,7 @@ static int tail_cluster_size() {
 
 template <typename R>
 cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st, Counters* c) {
-  if (a.nlev < 2 || a.nlev > kTailMaxLevels || a.nf > 1024) return cudaErrorInvalidValue;
+  if (a.nlev < 2 || a.nlev > kTailMaxLevels || a.nf > kMaxCoarseDofs) return cudaErrorInvalidValue;
   const int cs = transpose ? tail_cluster_size<R, true>() : tail_cluster_size<R, false>();
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];

@@ -199,6 +199,8 @@ cudaError_t launch_dfds(const Grid& g, const Phys& ph, double w_node, double* ou
                         Counters* c);
 
 // ---------------- multigrid (nc_kernels_mg.cu) ----------------
+// Largest coarsest-level system (rows of the dense matrix) the coarse solve stages in shared memory.
+constexpr int kMaxCoarseDofs = 2048;
 template <typename R> struct MGLevelDev {
   Grid g;
   typename Vec2<R>::type* x;

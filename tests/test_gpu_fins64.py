@@ -4,8 +4,7 @@ to 1e-6 (relative L2).
 
 Too large for the oracle's direct solves, so the oracle checks each GPU state through its residual
 on sampled nodes (|R_i| <= ||R_free|| <= 1e-8 ||R_free(0)|| on free rows). The multigrid has 5
-levels here: with 4 the coarsest grid (8^3 elements, 1296 free DOFs) exceeds the dense coarse
-solver's 1024-DOF limit.
+levels here (4 levels, a 1296-DOF coarsest system, are checked against 5 in test_gpu_multigrid).
 """
 
 import numpy as np

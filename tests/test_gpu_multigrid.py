@@ -68,3 +68,24 @@ def test_large_coarse_matrix(nc, precision):
         assert f == pytest.approx(op.objective(), rel=tol)
         assert rel(g, go) < 1e-6
         pb.close()
+
+
+def test_four_levels_at_64(nc):
+    """64^3 with 4 levels (coarsest 8^3 elements, 1296 free DOFs: the multi-launch inverse and a
+    coarse solve staged for up to 2048 rows) reaches the tolerance and agrees with 5 levels."""
+    n = 64
+    rho = filtered_random(n, n, n, seed=7, volfrac=0.2)
+    out = {}
+    for levels in (4, 5):
+        pb = nc.Problem(n, n, n, 1.0 / n, alpha=1e4, mg_levels=levels, newton_rtol=1e-10)
+        pb.set_design(rho)
+        st = pb.solve_state()
+        assert st["rel_residual"] <= 1e-10
+        P, T, _ = pb.get_fields(velocity=False)
+        f, ast = pb.solve_adjoint()
+        g = pb.sensitivities()
+        out[levels] = (P.cpu().numpy(), T.cpu().numpy(), g.cpu().numpy(), f)
+        pb.close()
+    for x, y in zip(out[4][:3], out[5][:3]):
+        assert np.linalg.norm(x - y) <= 1e-6 * np.linalg.norm(y)
+    assert out[4][3] == pytest.approx(out[5][3], rel=1e-8)
