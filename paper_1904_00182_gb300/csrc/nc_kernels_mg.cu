@@ -299,15 +299,6 @@ __global__ void k_jacobi_io(long long nn, const R* __restrict__ dinv, typename V
   if (z64) z64[n] = make_double2((double)o0, (double)o1);
 }
 
-template <typename R>
-__global__ void k_sub(long long nn, const typename Vec2<R>::type* __restrict__ b,
-                      const typename Vec2<R>::type* __restrict__ y, typename Vec2<R>::type* __restrict__ r) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= nn) return;
-  const typename Vec2<R>::type bb = b[n], yy = y[n];
-  r[n] = mk2<R>(bb.x - yy.x, bb.y - yy.y);
-}
-
 // The value v at node (i, j, k) with its fixed components set to zero.
 template <typename R>
 __device__ __forceinline__ typename Vec2<R>::type mask_fixed(const Grid& g, int i, int j, int k,
@@ -445,14 +436,6 @@ __global__ void k_dense_fixed_rows(Grid g, double* __restrict__ A, int nf) {
       const long long r = 2 * n + f;
       if (r < nf) A[r * nf + r] = 1.0;
     }
-}
-
-template <typename R>
-__global__ void k_to_mg(const double2* __restrict__ v, typename Vec2<R>::type* __restrict__ b, long long nn) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= nn) return;
-  const double2 a = v[n];
-  b[n] = mk2<R>((R)a.x, (R)a.y);
 }
 
 template <typename R>
@@ -1014,14 +997,6 @@ cudaError_t launch_jacobi_io(const Grid& g, const R* dinv, typename Vec2<R>::typ
 }
 
 template <typename R>
-cudaError_t launch_sub(const Grid& g, const typename Vec2<R>::type* b, const typename Vec2<R>::type* y,
-                       typename Vec2<R>::type* r, cudaStream_t st, Counters* c) {
-  k_sub<R><<<grid_blocks(g.nn, 256), 256, 0, st>>>(g.nn, b, y, r);
-  if (c) { c->launches += 1; c->bytes += sizeof(R) * 6.0 * g.nn; }
-  return cudaGetLastError();
-}
-
-template <typename R>
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* rf,
                             typename Vec2<R>::type* bc, cudaStream_t st, Counters* c) {
   const Launch3 L = launch_nodes_flat(gc);
@@ -1153,13 +1128,6 @@ cudaError_t launch_coarse_solve(const double* A, const float* Ainv32, double* wo
 }
 
 template <typename R>
-cudaError_t launch_to_mg(const double* v, typename Vec2<R>::type* b, long long nn, cudaStream_t st, Counters* c) {
-  k_to_mg<R><<<grid_blocks(nn, 256), 256, 0, st>>>((const double2*)v, b, nn);
-  if (c) { c->launches += 1; c->bytes += (16.0 + 2.0 * sizeof(R)) * nn; }
-  return cudaGetLastError();
-}
-
-template <typename R>
 cudaError_t launch_from_mg(const typename Vec2<R>::type* x, double* z, long long nn, cudaStream_t st, Counters* c) {
   k_from_mg<R><<<grid_blocks(nn, 256), 256, 0, st>>>(x, (double2*)z, nn);
   if (c) { c->launches += 1; c->bytes += (16.0 + 2.0 * sizeof(R)) * nn; }
@@ -1235,8 +1203,6 @@ cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st
   template cudaError_t launch_jacobi_io<R>(const Grid&, const R*, Vec2<R>::type*, const double*,              \
                                            const Vec2<R>::type*, const Vec2<R>::type*, Vec2<R>::type*, double*, \
                                            R, bool, bool, cudaStream_t, Counters*);                             \
-  template cudaError_t launch_sub<R>(const Grid&, const Vec2<R>::type*, const Vec2<R>::type*, Vec2<R>::type*, \
-                                     cudaStream_t, Counters*);                                                 \
   template cudaError_t launch_restrict<R>(const Grid&, const Grid&, const Vec2<R>::type*, Vec2<R>::type*,     \
                                           cudaStream_t, Counters*);                                            \
   template cudaError_t launch_restrict_residual<R>(const Grid&, const Grid&, const Vec2<R>::type*,            \
@@ -1246,7 +1212,6 @@ cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st
   template cudaError_t launch_dense_assemble<R>(const Grid&, const R*, double*, int, cudaStream_t, Counters*);\
   template cudaError_t launch_coarse_solve<R>(const double*, const float*, double*, int, const Vec2<R>::type*, \
                                               Vec2<R>::type*, long long, bool, cudaStream_t, Counters*);        \
-  template cudaError_t launch_to_mg<R>(const double*, Vec2<R>::type*, long long, cudaStream_t, Counters*);    \
   template cudaError_t launch_from_mg<R>(const Vec2<R>::type*, double*, long long, cudaStream_t, Counters*); \
   template cudaError_t launch_stencil_build<R>(const Grid&, const R*, R*, cudaStream_t, Counters*);           \
   template cudaError_t launch_stencil_apply<R>(const Grid&, const R*, const Vec2<R>::type*,                  \

@@ -240,13 +240,6 @@ __global__ void k_scale_copy(T* __restrict__ y, const double* __restrict__ x, do
     y[t] = (T)(a * x[t]);
 }
 
-__global__ void k_vmul(double* __restrict__ z, const double* __restrict__ a, const double* __restrict__ b,
-                       long long n) {
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    z[t] = a[t] * b[t];
-}
-
 __global__ void k_cast_d2f(float* __restrict__ y, const double* __restrict__ x, long long n) {
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
@@ -618,13 +611,6 @@ cudaError_t launch_scale_copy(float* y, const double* x, double a, long long n, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_vmul(double* z, const double* a, const double* b, long long n, cudaStream_t st,
-                        Counters* c) {
-  k_vmul<<<stream_blocks(n), 256, 0, st>>>(z, a, b, n);
-  if (c) { c->launches += 1; c->bytes += 24.0 * n; }
-  return cudaGetLastError();
-}
-
 cudaError_t launch_cast_d2f(float* y, const double* x, long long n, cudaStream_t st, Counters* c) {
   k_cast_d2f<<<stream_blocks(n), 256, 0, st>>>(y, x, n);
   if (c) { c->launches += 1; c->bytes += 12.0 * n; }
@@ -666,14 +652,6 @@ cudaError_t launch_helmholtz(const Grid& g, const FilterConst& F, const double* 
   const Launch3 L = launch_nodes_flat(g);
   k_helmholtz<double, FilterConst><<<L.grid, L.block, 0, st>>>(g, F, x, y);
   if (c) { c->launches += 1; c->bytes += 16.0 * g.nn; }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_helmholtz_f32(const Grid& g, const FilterConstF& F, const float* x, float* y, cudaStream_t st,
-                                 Counters* c) {
-  const Launch3 L = launch_nodes_flat(g);
-  k_helmholtz<float, FilterConstF><<<L.grid, L.block, 0, st>>>(g, F, x, y);
-  if (c) { c->launches += 1; c->bytes += 8.0 * g.nn; }
   return cudaGetLastError();
 }
 

@@ -166,10 +166,9 @@ cudaError_t launch_check_design(const double* rho, long long ne, int* flag, cuda
 // Filter pieces (Helmholtz (r^2 K + M) x = T^T gamma, Q1 nodal, element mean out).
 struct FilterConst { double A[64]; double C27[27]; double t0; double diag; };
 struct FilterConstF { float A[64]; float C27[27]; };
-// y = (r^2 K + M) x in FP64 (F) or FP32 (Ff); Chebyshev iteration in FP32 on D^-1 (r^2 K + M):
+// y = (r^2 K + M) x (FP64 residual with F; FP32 inside the Chebyshev step with Ff); Chebyshev iteration
+// in FP32 on D^-1 (r^2 K + M):
 //   init: x = 0, d = c0 dinv r;   step: x += d, r -= A d, dn = c1 d + c2 dinv r
-cudaError_t launch_helmholtz_f32(const Grid& g, const FilterConstF& F, const float* x, float* y, cudaStream_t st,
-                                 Counters* c);
 cudaError_t launch_cheb_init(long long n, const float* dinv, const float* r, float* x, float* d, float c0,
                              cudaStream_t st, Counters* c);
 cudaError_t launch_cheb_step(const Grid& g, const FilterConstF& F, const float* dinv, const float* d, float* dn,
@@ -191,9 +190,6 @@ cudaError_t launch_elem_from_nodes(const Grid& g, const Phys& ph, const double* 
 struct RampConst { double kappa_f, kappa_s, k_f, k_s, q_c, q_p; };
 cudaError_t launch_ramp(const double* gt, long long ne, const RampConst& r, double2* mat, double2* dmat,
                         float2* mat32, cudaStream_t st, Counters* c);
-// PCG helpers: z = dinv .* r
-cudaError_t launch_vmul(double* z, const double* a, const double* b, long long n, cudaStream_t st,
-                        Counters* c);
 // Objective weights df/ds (mean T over the heated region) and objective value.
 cudaError_t launch_dfds(const Grid& g, const Phys& ph, double w_node, double* out, cudaStream_t st,
                         Counters* c);
@@ -270,10 +266,6 @@ cudaError_t launch_jacobi_io(const Grid& g, const R* dinv, typename Vec2<R>::typ
                              const typename Vec2<R>::type* y, const typename Vec2<R>::type* x,
                              typename Vec2<R>::type* xn, double* z64, R omega, bool transpose, bool first,
                              cudaStream_t st, Counters* c);
-// r = b - y
-template <typename R>
-cudaError_t launch_sub(const Grid& g, const typename Vec2<R>::type* b, const typename Vec2<R>::type* y,
-                       typename Vec2<R>::type* r, cudaStream_t st, Counters* c);
 // b_c = P^T r_f (full weighting, Dirichlet coarse rows 0)
 template <typename R>
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* rf,
@@ -308,10 +300,7 @@ cudaError_t launch_stencil_apply(const Grid& g, const R* S, const typename Vec2<
                                  const typename Vec2<R>::type* b, const R* dinv, R omega,
                                  typename Vec2<R>::type* out, bool transpose, int mode, cudaStream_t st,
                                  Counters* c);
-// Cast a FP64 state vector into the multigrid type and back.
-template <typename R>
-cudaError_t launch_to_mg(const double* v, typename Vec2<R>::type* b, long long nn, cudaStream_t st,
-                         Counters* c);
+// Cast a multigrid-type state vector to FP64.
 template <typename R>
 cudaError_t launch_from_mg(const typename Vec2<R>::type* x, double* z, long long nn, cudaStream_t st,
                            Counters* c);
