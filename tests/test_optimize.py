@@ -124,3 +124,35 @@ def test_optimisation_loop_cavity():
     assert all(r["g"] <= 1e-6 for r in h)
     rho = out["rho"].cpu().numpy().reshape(48, 24, 24)
     assert np.all(rho[:2, :2, :2] == 1.0) and np.all(rho[38:, :, :] == 0.0) and np.all(rho[2:38, :, 18:] == 0.0)
+
+
+@pytest.mark.parametrize("shape", ["box", "cylinder"])
+def test_region_masks_match_the_oracle(shape):
+    """The optimiser's design and heated masks (the volume constraint's elements) are the oracle's
+    regions for the same parameters."""
+    import oracle
+    from paper_1904_00182_gb300 import _abi
+    from paper_1904_00182_gb300.optimize import region_masks
+    n, nz = 10, 20
+    if shape == "box":
+        kw = dict(heat_nx=3, heat_ny=2, heated_layers=2, design_nx=8, design_ny=7, design_nz=12)
+        okw = dict(kw)
+    else:
+        kw = dict(region_shape=_abi.NC_REGION_CYLINDER, heat_radius=3.0, design_radius=7.5, heat_z0=6,
+                  heated_layers=5)
+        okw = dict(region_shape="cylinder", heat_radius=3.0, design_radius=7.5, heat_z0=6, heated_layers=5)
+    d, h = region_masks(n, n, nz, _abi.default_params(bc=_abi.NC_BC_CAVITY, **kw))
+    op = oracle.Problem(oracle.Mesh(n, n, nz, 1.0 / nz), oracle.Params(bc="cavity", **okw))
+    assert np.array_equal(d.numpy(), op.design) and np.array_equal(h.numpy(), op.heated)
+
+
+def test_full_size_geometries_validate():
+    """The paper's two set-ups at their full meshes pass the library's parameter validation and fit in
+    one GPU's memory: the Sec. 6.1 cavity on 80 x 80 x 160 and the Sec. 7 cylinder on 160 x 160 x 320
+    (both coarsen to a 5 x 5 x 10 coarsest level, 792 rows)."""
+    from paper_1904_00182_gb300 import Grid, default_params, footprint_bytes
+    from paper_1904_00182_gb300.optimize import cavity_params, cylinder_params
+    for n, geom in ((80, cavity_params(80)), (160, cylinder_params(160))):
+        p = default_params(**geom)
+        b = footprint_bytes(Grid(n, n, 2 * n, 1.0 / (2 * n)), p)
+        assert 0 < b < 40e9, (n, b)
