@@ -13,7 +13,7 @@ Follows Appendix A of the paper:
 * the source load ``f_tQ,e = int N*^T Q`` (SUPG-weighted, App. A), and no boundary terms
   because the natural fluxes q_u = q_h = 0 in every setup used here.
 
-Readings (the paper is silent or garbled; each is listed in the design doc):
+Readings (where the paper is silent or garbled):
 
 * quadrature: 2x2x2 Gauss-Legendre (exact for every product that appears except the
   convective term, which is cubic-by-quadratic);

@@ -2,7 +2,7 @@
 
 Sec. 5.1 regularises the design with a PDE-based filter (Lazarov & Sigmund 2011; Aage et al.
 2014) and Sec. 6.3 sets its radius to 2.5 element sizes. The paper gives no formula, so the
-cited filter is written out here (readings listed in the design doc):
+cited filter is written out here, with these readings:
 
 * continuous form  -r^2 lap(x) + x = gamma  with homogeneous Neumann conditions on the box;
 * r = R / (2 sqrt 3) with R the filter radius (the Lazarov-Sigmund radius convention);

@@ -6,9 +6,9 @@
   region Omega_h is solid and not designed (Sec. 2.2), so gamma and gamma~ are 1 there.
 * Nonlinear solve: damped Newton whose damping factor minimises the L2 norm of the residual,
   stopping on a relative residual reduction, with source ramping on failure (Sec. 5.4).
-  The paper does not say how the minimiser is found; the rule used here is the one listed
-  in the design doc (full step if it reduces phi = ||R||^2 by 1e-4 phi0, else the best of a
-  parabola through phi(0), phi(1/2), phi(1) and those two points, else halving).
+  The paper does not say how the minimiser is found; the rule used here: the full step if it
+  reduces phi = ||R||^2 by 1e-4 phi0, else the best of a parabola through phi(0), phi(1/2),
+  phi(1) and those two points, else halving.
 * Objective: the mean temperature over the heated region (Galerkin weights), the
   normalised thermal compliance of Eq. objfunc for a uniform source; and the discrete thermal
   compliance of Eq. objdiscr, sum_e f_tQ,e^T t_e with the SUPG-weighted source load (its state
