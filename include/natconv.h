@@ -294,21 +294,27 @@ nc_status nc_get_profile(const nc_problem* pb, int cls, double* ms, long long* l
  * (monotonic counters; any output pointer may be NULL). */
 nc_status nc_counters(const nc_problem* pb, long long* launches, double* bytes);
 
-/* Allocation-free squared norm of the free rows of a state vector: *out_dev = sum over the nodes
- * below the top face of P_n^2 + T_n^2 (the norm of the Newton stopping test), for the grid g.
+/* Allocation-free squared norm of the free rows of a state vector (the norm of the Newton stopping
+ * test): *out_dev = sum of a_r^2 over the rows r of s_dev that are free under the boundary conditions
+ * bc (NC_BC_TOP: P and T of every node below the top face; NC_BC_CAVITY: every component outside the
+ * closed cavity's fixed set, i.e. T off the outer walls and the top, P everywhere except the top outer
+ * corner). For a residual of a state that meets the boundary conditions this is the norm that
+ * nc_eval_residual reports; the fixed rows of such a residual hold s on the fixed set and are never
+ * summed here.
  * The paper has no counterpart: this entry point serves callers that cannot allocate device memory
  * on this path (all device memory handed out from their own pre-reserved pool, a hard memory budget,
  * or no cudaMalloc/cudaFree because those calls can synchronise the device). It allocates nothing:
  * its partial sums live in a fixed 64 KiB device array owned by the library (one per device that
- * loads it, kept until exit), so grids with more than 8192 * 4096 free entries are rejected with
- * NC_ERR_ARG. s_dev (2N doubles) and out_dev (1 double) are device pointers of the current device.
- * The work is queued on `stream` (a cudaStream_t, NULL = the legacy default stream); *out_dev is
- * valid once the stream has completed it. The first call on a device looks up the device address of
- * the array (cudaGetSymbolAddress), so make that first call before any stream capture. Every call
- * shares the array and leaves its last contents there; calls that overlap on the GPU race.
- * Returns NC_ERR_ARG for NULL pointers or bad sizes and NC_ERR_CUDA if a launch fails. */
-nc_status nc_norm2_free_noalloc(const nc_grid* g, const double* s_dev, double* out_dev, void* stream);
-/* (The free rows above are those of NC_BC_TOP.) */
+ * loads it, kept until exit), so grids with more than 8192 * 4096 summed entries are rejected with
+ * NC_ERR_ARG. s_dev (2N doubles, node-interleaved P, T) and out_dev (1 double) are device pointers of
+ * the current device. The work is queued on `stream` (a cudaStream_t, NULL = the legacy default
+ * stream); *out_dev is valid once the stream has completed it. The first call on a device looks up
+ * the device address of the array (cudaGetSymbolAddress), so make that first call before any stream
+ * capture; the address is kept for the life of the process, so do not call this entry point on a
+ * device again after a cudaDeviceReset of it. Every call shares the array and leaves its last
+ * contents there; calls that overlap on the GPU race.
+ * Returns NC_ERR_ARG for NULL pointers, an unknown bc or bad sizes and NC_ERR_CUDA if a launch fails. */
+nc_status nc_norm2_free_noalloc(const nc_grid* g, int bc, const double* s_dev, double* out_dev, void* stream);
 
 /* Message of the last failed call on pb (or, if pb is NULL, of the calling thread's last failed
  * call without a problem, e.g. nc_create_problem). Never NULL. */

@@ -124,7 +124,7 @@ def load_library(path=None):
         "nc_set_profiling": ([vp, i], i),
         "nc_get_profile": ([vp, i, dp, ctypes.POINTER(ctypes.c_longlong), dp, dp], i),
         "nc_counters": ([vp, ctypes.POINTER(ctypes.c_longlong), dp], i),
-        "nc_norm2_free_noalloc": ([ctypes.POINTER(Grid), vp, vp, vp], i),
+        "nc_norm2_free_noalloc": ([ctypes.POINTER(Grid), i, vp, vp, vp], i),
         "nc_last_error": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():

@@ -978,7 +978,9 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
     if (l > 0) b += al(256 * rs * lv.g[l].ne);
     if (l > 0 && l + 1 < lv.g.size()) b += al(108 * rs * lv.g[l].nn);
   }
+  // coarsest level: Ac (FP64), Ainv32, the Gauss-Jordan work array W and the coarse-solve scratch cw (3 nf FP64)
   b += al(8 * (size_t)lv.nf * lv.nf) + al(4 * (size_t)lv.nf * lv.nf) + al(8 * (size_t)lv.nf * lv.nf + 12 * (size_t)lv.nf);
+  b += al(24 * (size_t)lv.nf);
   b += al(4);
   return b;
 }

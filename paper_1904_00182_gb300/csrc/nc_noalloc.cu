@@ -22,12 +22,23 @@ namespace {
 
 static __device__ __align__(256) double g_noalloc_parts[NC_NOALLOC_MAX_PARTS];
 
-__global__ void k_noalloc_norm2_parts(const double* __restrict__ a, long long nfree2, double* __restrict__ parts) {
+// Partial sums of squares over NC_NOALLOC_CHUNK entries per block. With kBcTop the free rows are the
+// leading 2 NX NY nz entries (nodes below the top plane) and nfree2 is their count; otherwise every
+// row of the 2 nn entries is visited and the fixed components of the grid's set are skipped.
+__global__ void k_noalloc_norm2_parts(nc::Grid g, const double* __restrict__ a, long long nfree2,
+                                      double* __restrict__ parts) {
   __shared__ double sh[32];
   const long long lo = (long long)blockIdx.x * NC_NOALLOC_CHUNK;
   const long long hi = min(nfree2, lo + NC_NOALLOC_CHUNK);
   double acc = 0.0;
-  for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) acc += a[t] * a[t];
+  for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+    if (g.bc != nc::kBcTop) {
+      int i, j, k;
+      nc::node_ijk(g, t >> 1, i, j, k);
+      if ((nc::fixed_bits(g, i, j, k) >> (t & 1)) & 1) continue;
+    }
+    acc += a[t] * a[t];
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
@@ -54,7 +65,9 @@ __global__ void k_noalloc_sum(const double* __restrict__ parts, int nparts, doub
   }
 }
 
-// Device address of g_noalloc_parts, looked up once per device (with that device current).
+// Device address of g_noalloc_parts, looked up once per device (with that device current) at the
+// first call on it and kept for the life of the process. A cudaDeviceReset ends the context that
+// address belongs to: a process that resets a device must not call this entry point on it again.
 const int kMaxDevices = 64;
 double* g_parts_addr[kMaxDevices] = {nullptr};
 std::mutex g_parts_mutex;
@@ -63,7 +76,7 @@ cudaError_t parts_address(int dev, double** out) {
   std::lock_guard<std::mutex> lock(g_parts_mutex);
   if (!g_parts_addr[dev]) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_parts);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_parts);
     if (e != cudaSuccess) return e;
     g_parts_addr[dev] = (double*)p;
   }
@@ -73,11 +86,15 @@ cudaError_t parts_address(int dev, double** out) {
 
 }  // namespace
 
-extern "C" nc_status nc_norm2_free_noalloc(const nc_grid* g, const double* s_dev, double* out_dev, void* stream) {
+extern "C" nc_status nc_norm2_free_noalloc(const nc_grid* g, int bc, const double* s_dev, double* out_dev,
+                                           void* stream) {
   if (!g || !s_dev || !out_dev) return NC_ERR_ARG;
   if (g->nx < 1 || g->ny < 1 || g->nz < 1) return NC_ERR_ARG;
-  const long long plane = (long long)(g->nx + 1) * (g->ny + 1);
-  const long long nfree2 = 2LL * plane * g->nz;
+  if (bc != NC_BC_TOP && bc != NC_BC_CAVITY) return NC_ERR_ARG;
+  nc::Grid gr = nc::make_grid(g->nx, g->ny, g->nz, g->h);
+  gr.bc = bc == NC_BC_TOP ? nc::kBcTop : nc::kBcCavity;
+  if (gr.nn >= (1LL << 31)) return NC_ERR_ARG;
+  const long long nfree2 = bc == NC_BC_TOP ? 2LL * gr.NXY * gr.nz : 2LL * gr.nn;
   const long long nparts = (nfree2 + NC_NOALLOC_CHUNK - 1) / NC_NOALLOC_CHUNK;
   if (nparts > NC_NOALLOC_MAX_PARTS) return NC_ERR_ARG;   // beyond the fixed scratch array
   int dev = 0;
@@ -85,7 +102,7 @@ extern "C" nc_status nc_norm2_free_noalloc(const nc_grid* g, const double* s_dev
   double* parts = nullptr;
   if (parts_address(dev, &parts) != cudaSuccess) { cudaGetLastError(); return NC_ERR_CUDA; }
   cudaStream_t st = (cudaStream_t)stream;
-  k_noalloc_norm2_parts<<<(unsigned)nparts, 256, 0, st>>>(s_dev, nfree2, parts);
+  k_noalloc_norm2_parts<<<(unsigned)nparts, 256, 0, st>>>(gr, s_dev, nfree2, parts);
   k_noalloc_sum<<<1, 256, 0, st>>>(parts, (int)nparts, out_dev);
   return cudaGetLastError() == cudaSuccess ? NC_OK : NC_ERR_CUDA;
 }
