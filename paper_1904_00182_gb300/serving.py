@@ -21,20 +21,25 @@ from .problem import Problem
 
 
 class Request:
+    """One request: a state solve (or a state solve, its adjoint and the sensitivities) of `design` on
+    an n^3 grid at buoyancy factor alpha. The design may be a host array or a device tensor that is
+    ready (its producing work complete) when the request arrives."""
     __slots__ = ("rid", "t_arrival", "n", "alpha", "adjoint", "design", "t_start", "t_done", "f", "grad",
-                 "state_stats", "error")
+                 "fields", "state_stats", "error")
 
     def __init__(self, rid, t_arrival, n, alpha, adjoint, design):
         self.rid, self.t_arrival, self.n, self.alpha, self.adjoint, self.design = rid, t_arrival, n, alpha, adjoint, design
         self.t_start = self.t_done = None
-        self.f = self.grad = self.state_stats = self.error = None
+        self.f = self.grad = self.fields = self.state_stats = self.error = None
 
 
 class Server:
-    def __init__(self, slots=6, hbm_budget_bytes=64 << 30, keep_gradients=False, device="cuda", **params):
+    def __init__(self, slots=6, hbm_budget_bytes=64 << 30, keep_gradients=False, keep_fields=False, device="cuda",
+                 **params):
         self.slots = slots
         self.budget = hbm_budget_bytes
         self.keep_gradients = keep_gradients
+        self.keep_fields = keep_fields   # keep (P, T, u) of every request (device tensors)
         self.device = device
         self.params = params
         self.pool = collections.defaultdict(list)    # n -> idle Problems
@@ -75,6 +80,8 @@ class Server:
             pb.set_params(alpha=req.alpha)
         pb.set_design(req.design)
         req.state_stats = pb.solve_state()
+        if self.keep_fields:
+            req.fields = pb.get_fields()
         if req.adjoint:
             req.f, _ = pb.solve_adjoint()
             g = pb.sensitivities()
@@ -146,10 +153,15 @@ class Server:
 
 
 def summarize(done, wall):
-    lat = np.array([r.t_done - r.t_arrival for r in done if r.error is None])
-    solves = sum(1 + (1 if r.adjoint else 0) for r in done if r.error is None)
-    return {"requests": len(done), "errors": sum(r.error is not None for r in done),
+    """Latency percentiles (arrival to completion) and rates over the wall time of the stream:
+    requests_per_s counts each completed request once (a state solve, or a state solve with its adjoint
+    and sensitivities, the unit of the one-problem benchmark's whole path); state_solves_per_s and
+    adjoint_solves_per_s count the solves of each kind."""
+    ok = [r for r in done if r.error is None]
+    lat = np.array([r.t_done - r.t_arrival for r in ok])
+    return {"requests": len(done), "errors": len(done) - len(ok),
             "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
             "mean_ms": float(lat.mean() * 1e3) if len(lat) else None,
-            "requests_per_s": len(lat) / wall, "solves_per_s": solves / wall, "wall_s": wall}
+            "requests_per_s": len(ok) / wall, "state_solves_per_s": len(ok) / wall,
+            "adjoint_solves_per_s": sum(1 for r in ok if r.adjoint) / wall, "wall_s": wall}

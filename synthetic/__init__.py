@@ -15,6 +15,8 @@ Design families (element arrays ordered i + nx*(j + ny*k), gamma = 1 solid, 0 fl
 * ``request_stream``: Poisson arrivals (rate 20/s), grid edge uniform over
   {32, 48, 64, 96, 128}, buoyancy factor log-uniform in [1e3, 1e5], half state-only and half
   state+adjoint, each with its own filtered-random design seed.
+* ``filtered_random_torch``: the filtered_random recipe in torch on a device, seeded by torch's
+  own generator (used where hundreds of designs must be drawn quickly, e.g. the serving stream).
 """
 
-from .designs import filtered_random, fin_plates, request_stream  # noqa: F401
+from .designs import filtered_random, filtered_random_torch, fin_plates, request_stream  # noqa: F401

@@ -64,3 +64,43 @@ def request_stream(n=300, rate=20.0, seed=12345, sizes=(32, 48, 64, 96, 128),
     seeds = rng.integers(0, 2**31 - 1, size=n)
     return [dict(t_arrival=float(t[i]), n=int(edge[i]), alpha=float(np.exp(la[i])),
                  adjoint=bool(adj[i]), design_seed=int(seeds[i])) for i in range(n)]
+
+
+def filtered_random_torch(nx, ny, nz, seed, volfrac=None, device="cpu", noise=None):
+    """The filtered_random recipe computed with torch on `device` (for streams of many designs that
+    should be drawn in milliseconds on the device): N(0, 1) per element from torch's generator seeded
+    with `seed` (or the given (nz, ny, nx) `noise`), the same cone smoothing, min-max map and
+    volume-fraction bisection (on the device, no host round trips). Not byte-identical to
+    filtered_random, whose normals come from NumPy's PCG64."""
+    import torch
+    if noise is None:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(int(seed))
+        x = torch.randn((nz, ny, nx), generator=gen, device=device, dtype=torch.float64)
+    else:
+        x = torch.as_tensor(noise, dtype=torch.float64, device=device)
+    radius, r = 1.5, 1
+    acc = torch.zeros_like(x)
+    norm = torch.zeros_like(x)
+    for dk in range(-r, r + 1):
+        for dj in range(-r, r + 1):
+            for di in range(-r, r + 1):
+                wgt = radius - float(np.sqrt(di * di + dj * dj + dk * dk))
+                if wgt <= 0:
+                    continue
+                src = tuple(slice(max(0, d), n + min(0, d)) for d, n in zip((dk, dj, di), (nz, ny, nx)))
+                dst = tuple(slice(max(0, -d), n + min(0, -d)) for d, n in zip((dk, dj, di), (nz, ny, nx)))
+                acc[dst] += wgt * x[src]
+                norm[dst] += wgt
+    x = acc / norm
+    x = (x - x.min()) / (x.max() - x.min())
+    if volfrac is not None:
+        lo = torch.full((), -1.0, dtype=torch.float64, device=device)
+        hi = torch.full((), 1.0, dtype=torch.float64, device=device)
+        for _ in range(100):
+            c = 0.5 * (lo + hi)
+            below = torch.clamp(x + c, 0.0, 1.0).mean() < volfrac
+            lo = torch.where(below, c, lo)
+            hi = torch.where(below, hi, c)
+        x = torch.clamp(x + 0.5 * (lo + hi), 0.0, 1.0)
+    return x.reshape(-1).contiguous()

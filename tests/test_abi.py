@@ -6,6 +6,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -109,3 +110,20 @@ def test_product_has_no_cpu_fallback():
     from paper_1904_00182_gb300 import _abi
     with pytest.raises(ImportError):
         _abi.load_library(os.path.join(ROOT, "does_not_exist.so"))
+
+
+def test_torch_design_recipe_matches_numpy_recipe():
+    """The device-side design generator follows the same recipe as the NumPy one: given the same
+    normals it gives the same smoothed field and the requested volume fraction."""
+    import torch
+    from synthetic import designs
+    rng = np.random.default_rng(5)
+    noise = rng.standard_normal((6, 5, 7))
+    a = designs._cone_smooth(noise, 1.5)
+    a = (a - a.min()) / (a.max() - a.min())
+    b = designs.filtered_random_torch(7, 5, 6, seed=0, noise=noise).numpy()
+    assert np.abs(a.ravel() - b).max() < 1e-14
+    c = designs.filtered_random_torch(12, 12, 12, seed=3, volfrac=0.2).numpy()
+    assert abs(c.mean() - 0.2) < 1e-6 and c.min() >= 0.0 and c.max() <= 1.0
+    d = designs.filtered_random_torch(12, 12, 12, seed=3, volfrac=0.2).numpy()
+    assert np.array_equal(c, d)

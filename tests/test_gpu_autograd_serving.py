@@ -4,8 +4,9 @@
 * At 64^3 the autograd gradient agrees with central differences of the GPU objective on 50 seeded
   design entries: step 1e-6 (the workload's step) to 5e-3 relative L2 — f changes by only ~1e-11 of
   itself there, so the FP64 floor of the solves bounds the agreement — and step 1e-4 to 1e-4.
-* Serving: every request's objective is the same when served alone and in a concurrent mix (1e-6,
-  the mixed-precision tolerance), and the pool never exceeds its HBM budget.
+* Serving: every request's P, T, u, objective and gradient are the same when served alone and in a
+  concurrent mix on 16^3 to 64^3 grids (1e-6, the mixed-precision tolerance), and the pool never
+  exceeds its HBM budget.
 """
 
 import numpy as np
@@ -92,36 +93,49 @@ def test_gradient_central_differences_64(nc):
     pb.close()
 
 
-def _requests(nc, seed, count):
+def _requests(nc, seed, count, sizes=(16, 32, 48, 64)):
     from paper_1904_00182_gb300.serving import Request
     rng = np.random.default_rng(seed)
     reqs = []
     t = 0.0
     for i in range(count):
         t += rng.exponential(0.01)
-        n = int(rng.choice([16, 24, 32]))
+        n = int(rng.choice(sizes))
         alpha = float(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
         reqs.append(Request(i, t, n, alpha, bool(rng.random() < 0.5),
                             filtered_random(n, n, n, seed=100 + i, volfrac=0.2)))
     return reqs
 
 
+def _rel(a, b):
+    return float((a - b).norm() / b.norm())
+
+
 def test_serving_results_alone_equal_in_the_mix(nc):
+    """Every request's P, T, centroid velocities, objective and (for state+adjoint requests) gradient
+    are the same served alone and in a concurrent mix of requests on 16^3 to 64^3 grids (1e-6, the
+    mixed-precision tolerance); the pool stays within its HBM budget."""
     from paper_1904_00182_gb300.serving import Server, summarize
     alone = {}
-    for req in _requests(nc, 7, 10):
-        srv = Server(slots=1, hbm_budget_bytes=4 << 30)
+    for req in _requests(nc, 7, 12):
+        srv = Server(slots=1, hbm_budget_bytes=4 << 30, keep_gradients=True, keep_fields=True)
         req.t_arrival = 0.0
         done = srv.run([req])
         srv.close()
         assert done[0].error is None, done[0].error
-        alone[req.rid] = done[0].f
-    budget = 1 << 30
-    srv = Server(slots=4, hbm_budget_bytes=budget)
-    done = srv.run(_requests(nc, 7, 10))
+        alone[req.rid] = done[0]
+    assert {r.n for r in alone.values()} >= {48, 64}
+    budget = 2 << 30
+    srv = Server(slots=4, hbm_budget_bytes=budget, keep_gradients=True, keep_fields=True)
+    done = srv.run(_requests(nc, 7, 12))
     stats = summarize(done, srv.t_total)
     srv.close()
-    assert stats["errors"] == 0 and stats["requests"] == 10
+    assert stats["errors"] == 0 and stats["requests"] == 12
     assert srv.peak_bytes <= budget
     for req in done:
-        assert req.f == pytest.approx(alone[req.rid], rel=1e-6), (req.rid, req.f, alone[req.rid])
+        a = alone[req.rid]
+        assert req.f == pytest.approx(a.f, rel=1e-6), (req.rid, req.f, a.f)
+        for got, ref, name in zip(req.fields, a.fields, ("P", "T", "u")):
+            assert _rel(got, ref) <= 1e-6, (req.rid, req.n, name, _rel(got, ref))
+        if req.adjoint:
+            assert _rel(req.grad, a.grad) <= 1e-6, (req.rid, req.n, "grad", _rel(req.grad, a.grad))
