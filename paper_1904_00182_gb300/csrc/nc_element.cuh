@@ -14,6 +14,12 @@
 // sum factorisation (three 1D stages of 2x2 interpolation / differencing), and the test-function
 // side (sum over points of N_a A_q + grad N_a . B_q) by the transposed stages.
 //
+// Units: gradients are carried in element units, i.e. multiplied by h (a 1D stage yields the nodal
+// difference f1 - f0 = h df/dx); every factor 1/h is folded into per-element constants, and the
+// test-function stage takes its gradient weights pre-multiplied by 1/h. A 1D stage evaluates the
+// Gauss-point values cp f0 + cm f1 and cm f0 + cp f1 (cp = 1 - cm) as f0 + cm d and f1 - cm d with
+// d = f1 - f0: one subtraction and two fused multiply-adds per node pair.
+//
 // Index conventions: local node a = ax + 2 ay + 4 az; Gauss point q = qx + 2 qy + 4 qz with
 // reference coordinate (2 q_d - 1)/sqrt(3) along each axis.
 #pragma once
@@ -25,65 +31,55 @@ namespace nc {
 
 template <typename R>
 struct ElemConst {
-  R cp, cm;     // 1D interpolation weights at a Gauss point: (1 + 1/sqrt3)/2, (1 - 1/sqrt3)/2
+  R cm;         // 1D interpolation weight (1 - 1/sqrt3)/2 of the far node at a Gauss point
   R ih;         // 1 / h
   R w;          // Gauss weight x det J = (h/2)^3
+  R wih;        // w / h
+  R wih2;       // w / h^2
   R beta;       // rho0 alpha g
+  R betah;      // rho0 alpha g h
   R rc;         // rho0 c_p
+  R rcih2;      // rho0 c_p / h^2
   R imu;        // 1 / mu
   R c4he2;      // 4 / h_e^2
   R itau3sq;    // 1 / tau3^2
 };
 
-// Values and Cartesian gradients of the trilinear interpolant of nodal values f at the 8 Gauss
-// points.
+// One 1D stage on a node pair: the values at the two Gauss points and the difference f1 - f0.
 template <typename R>
-__device__ __forceinline__ void q1_forward(const R f[8], const R cp, const R cm, const R ih,
-                                           R v[8], R gx[8], R gy[8], R gz[8]) {
+__device__ __forceinline__ void q1_pair(const R f0, const R f1, const R cm, R& v0, R& v1, R& d) {
+  d = f1 - f0;
+  v0 = f0 + cm * d;
+  v1 = f1 - cm * d;
+}
+
+// Values and element-unit gradients (h grad f) of the trilinear interpolant of nodal values f at the
+// 8 Gauss points.
+template <typename R>
+__device__ __forceinline__ void q1_forward(const R f[8], const R cm, R v[8], R gx[8], R gy[8], R gz[8]) {
   R A[8], Dx[4];
 #pragma unroll
-  for (int yz = 0; yz < 4; ++yz) {          // yz = ay + 2 az
-    const R f0 = f[2 * yz], f1 = f[2 * yz + 1];
-    A[2 * yz] = cp * f0 + cm * f1;          // A index qx + 2 ay + 4 az
-    A[2 * yz + 1] = cm * f0 + cp * f1;
-    Dx[yz] = (f1 - f0) * ih;                // Dx index ay + 2 az
-  }
-  R B[8], Dy[4], Cx[4];
+  for (int yz = 0; yz < 4; ++yz)            // yz = ay + 2 az; A index qx + 2 ay + 4 az
+    q1_pair(f[2 * yz], f[2 * yz + 1], cm, A[2 * yz], A[2 * yz + 1], Dx[yz]);
+  R B[8], Dy[4], Cx[4], dd;
 #pragma unroll
   for (int qx = 0; qx < 2; ++qx)
 #pragma unroll
-    for (int az = 0; az < 2; ++az) {
-      const R a0 = A[qx + 4 * az], a1 = A[qx + 2 + 4 * az];
-      B[qx + 4 * az] = cp * a0 + cm * a1;   // B index qx + 2 qy + 4 az
-      B[qx + 2 + 4 * az] = cm * a0 + cp * a1;
-      Dy[qx + 2 * az] = (a1 - a0) * ih;     // Dy index qx + 2 az
-    }
+    for (int az = 0; az < 2; ++az)          // B index qx + 2 qy + 4 az, Dy index qx + 2 az
+      q1_pair(A[qx + 4 * az], A[qx + 2 + 4 * az], cm, B[qx + 4 * az], B[qx + 2 + 4 * az], Dy[qx + 2 * az]);
 #pragma unroll
-  for (int az = 0; az < 2; ++az) {
-    const R d0 = Dx[2 * az], d1 = Dx[1 + 2 * az];
-    Cx[2 * az] = cp * d0 + cm * d1;         // Cx index qy + 2 az
-    Cx[1 + 2 * az] = cm * d0 + cp * d1;
-  }
+  for (int az = 0; az < 2; ++az)            // Cx index qy + 2 az
+    q1_pair(Dx[2 * az], Dx[1 + 2 * az], cm, Cx[2 * az], Cx[1 + 2 * az], dd);
   R Gz[4], Gy[4], Gx[4];
 #pragma unroll
-  for (int xy = 0; xy < 4; ++xy) {          // xy = qx + 2 qy
-    const R b0 = B[xy], b1 = B[xy + 4];
-    v[xy] = cp * b0 + cm * b1;
-    v[xy + 4] = cm * b0 + cp * b1;
-    Gz[xy] = (b1 - b0) * ih;                // Gz index qx + 2 qy
-  }
+  for (int xy = 0; xy < 4; ++xy)            // xy = qx + 2 qy; Gz index qx + 2 qy
+    q1_pair(B[xy], B[xy + 4], cm, v[xy], v[xy + 4], Gz[xy]);
 #pragma unroll
-  for (int qx = 0; qx < 2; ++qx) {
-    const R y0 = Dy[qx], y1 = Dy[qx + 2];
-    Gy[qx] = cp * y0 + cm * y1;             // Gy index qx + 2 qz
-    Gy[qx + 2] = cm * y0 + cp * y1;
-  }
+  for (int qx = 0; qx < 2; ++qx)            // Gy index qx + 2 qz
+    q1_pair(Dy[qx], Dy[qx + 2], cm, Gy[qx], Gy[qx + 2], dd);
 #pragma unroll
-  for (int qy = 0; qy < 2; ++qy) {
-    const R x0 = Cx[qy], x1 = Cx[qy + 2];
-    Gx[qy] = cp * x0 + cm * x1;             // Gx index qy + 2 qz
-    Gx[qy + 2] = cm * x0 + cp * x1;
-  }
+  for (int qy = 0; qy < 2; ++qy)            // Gx index qy + 2 qz
+    q1_pair(Cx[qy], Cx[qy + 2], cm, Gx[qy], Gx[qy + 2], dd);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int qx = q & 1, qy = (q >> 1) & 1, qz = q >> 2;
@@ -93,11 +89,21 @@ __device__ __forceinline__ void q1_forward(const R f[8], const R cp, const R cm,
   }
 }
 
-// out_a = sum_q ( N_a(q) A_q + dN_a/dx(q) Bx_q + dN_a/dy(q) By_q + dN_a/dz(q) Bz_q ).
+// Transposed 1D stage: (a0, a1) at the Gauss points -> the two nodes, minus / plus d (the summed
+// gradient weight of the pair): o0 = cp a0 + cm a1 - d = a0 + cm s - d, o1 = a1 - cm s + d, s = a1 - a0.
+template <typename R>
+__device__ __forceinline__ void q1_pair_t(const R a0, const R a1, const R d, const R cm, R& o0, R& o1) {
+  const R s = a1 - a0;
+  o0 = (a0 - d) + cm * s;
+  o1 = (a1 + d) - cm * s;
+}
+
+// out_a = sum_q ( N_a(q) A_q + h dN_a/dx(q) Bx_q + h dN_a/dy(q) By_q + h dN_a/dz(q) Bz_q ), i.e. the
+// test-function sums sum_q ( N_a A_q + grad N_a . B_q ) for gradient weights given as B / h.
 // HAS_A = false treats A as zero.
 template <typename R, bool HAS_A>
 __device__ __forceinline__ void q1_test(const R* A, const R Bx[8], const R By[8], const R Bz[8],
-                                        const R cp, const R cm, const R ih, R out[8]) {
+                                        const R cm, R out[8]) {
   R bx[4], by[4], bz[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -109,45 +115,26 @@ __device__ __forceinline__ void q1_test(const R* A, const R Bx[8], const R By[8]
   R Az[8];                                                    // index qx + 2 qy + 4 az
 #pragma unroll
   for (int xy = 0; xy < 4; ++xy) {
-    const R a0 = HAS_A ? A[xy] : R(0), a1 = HAS_A ? A[xy + 4] : R(0);
-    const R d = bz[xy] * ih;
-    Az[xy] = cp * a0 + cm * a1 - d;
-    Az[xy + 4] = cm * a0 + cp * a1 + d;
+    if (HAS_A) q1_pair_t(A[xy], A[xy + 4], bz[xy], cm, Az[xy], Az[xy + 4]);
+    else { Az[xy] = -bz[xy]; Az[xy + 4] = bz[xy]; }
   }
-  R byz[4], bxz[4];                                           // index qx + 2 az, qy + 2 az
+  R byz[4], bxz[4], dd;                                       // index qx + 2 az, qy + 2 az
 #pragma unroll
   for (int l = 0; l < 2; ++l) {
-    const R b0 = by[l], b1 = by[l + 2];
-    byz[l] = cp * b0 + cm * b1;
-    byz[l + 2] = cm * b0 + cp * b1;
-    const R c0 = bx[l], c1 = bx[l + 2];
-    bxz[l] = cp * c0 + cm * c1;
-    bxz[l + 2] = cm * c0 + cp * c1;
+    q1_pair(by[l], by[l + 2], cm, byz[l], byz[l + 2], dd);
+    q1_pair(bx[l], bx[l + 2], cm, bxz[l], bxz[l + 2], dd);
   }
   R Ay[8];                                                    // index qx + 2 ay + 4 az
 #pragma unroll
   for (int qx = 0; qx < 2; ++qx)
 #pragma unroll
-    for (int az = 0; az < 2; ++az) {
-      const R a0 = Az[qx + 4 * az], a1 = Az[qx + 2 + 4 * az];
-      const R d = byz[qx + 2 * az] * ih;
-      Ay[qx + 4 * az] = cp * a0 + cm * a1 - d;
-      Ay[qx + 2 + 4 * az] = cm * a0 + cp * a1 + d;
-    }
+    for (int az = 0; az < 2; ++az)
+      q1_pair_t(Az[qx + 4 * az], Az[qx + 2 + 4 * az], byz[qx + 2 * az], cm, Ay[qx + 4 * az], Ay[qx + 2 + 4 * az]);
   R bxy[4];                                                   // index ay + 2 az
 #pragma unroll
-  for (int az = 0; az < 2; ++az) {
-    const R b0 = bxz[2 * az], b1 = bxz[1 + 2 * az];
-    bxy[2 * az] = cp * b0 + cm * b1;
-    bxy[1 + 2 * az] = cm * b0 + cp * b1;
-  }
+  for (int az = 0; az < 2; ++az) q1_pair(bxz[2 * az], bxz[1 + 2 * az], cm, bxy[2 * az], bxy[1 + 2 * az], dd);
 #pragma unroll
-  for (int yz = 0; yz < 4; ++yz) {
-    const R a0 = Ay[2 * yz], a1 = Ay[2 * yz + 1];
-    const R d = bxy[yz] * ih;
-    out[2 * yz] = cp * a0 + cm * a1 - d;
-    out[2 * yz + 1] = cm * a0 + cp * a1 + d;
-  }
+  for (int yz = 0; yz < 4; ++yz) q1_pair_t(Ay[2 * yz], Ay[2 * yz + 1], bxy[yz], cm, out[2 * yz], out[2 * yz + 1]);
 }
 
 template <typename R> __device__ __forceinline__ R nc_rsqrt(R x);
@@ -155,8 +142,9 @@ template <> __device__ __forceinline__ double nc_rsqrt<double>(double x) { retur
 template <> __device__ __forceinline__ float nc_rsqrt<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ df64 nc_rsqrt<df64>(df64 x) { return df_rsqrt(x); }
 
-// Gauss-point state of an element: V_q = grad P_q - beta T_q e_z (so u_q = -c V_q, c = kappa/mu),
-// grad T_q, S_q = rho0 c_p u_q . grad T_q - Q, centroid velocity u0 and tau.
+// Gauss-point state of an element: V_q = h (grad P_q - beta T_q e_z) (so u_q = -(c/h) V_q, c = kappa/mu),
+// H_q = h grad T_q, S_q = rho0 c_p u_q . grad T_q - Q, centroid velocity u0 and tau (u0, S, tau in
+// physical units).
 template <typename R>
 struct ElemState {
   R vx[8], vy[8], vz[8];
@@ -169,19 +157,19 @@ template <typename R>
 __device__ __forceinline__ void elem_state(const ElemConst<R>& C, const R p[8], const R t[8],
                                            const R kappa, const R Q, ElemState<R>& st) {
   R T[8];
-  q1_forward(p, C.cp, C.cm, C.ih, T, st.vx, st.vy, st.vz);   // T reused as scratch for P values
-  q1_forward(t, C.cp, C.cm, C.ih, T, st.hx, st.hy, st.hz);
+  q1_forward(p, C.cm, T, st.vx, st.vy, st.vz);   // T reused as scratch for P values
+  q1_forward(t, C.cm, T, st.hx, st.hy, st.hz);
   st.c = kappa * C.imu;
   R sx = 0, sy = 0, sz = 0;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    st.vz[q] -= C.beta * T[q];
+    st.vz[q] -= C.betah * T[q];
     sx += st.vx[q]; sy += st.vy[q]; sz += st.vz[q];
   }
-  const R m = -st.c * R(0.125);
+  const R m = -st.c * C.ih * R(0.125);
   st.u0x = m * sx; st.u0y = m * sy; st.u0z = m * sz;
   st.tau = nc_rsqrt<R>(C.c4he2 * (st.u0x * st.u0x + st.u0y * st.u0y + st.u0z * st.u0z) + C.itau3sq);
-  const R mrc = -st.c * C.rc;
+  const R mrc = -st.c * C.rcih2;
 #pragma unroll
   for (int q = 0; q < 8; ++q)
     st.S[q] = mrc * (st.vx[q] * st.hx[q] + st.vy[q] * st.hy[q] + st.vz[q] * st.hz[q]) - Q;
@@ -194,26 +182,28 @@ __device__ __forceinline__ void elem_residual(const ElemConst<R>& C, const R p[8
                                               R RP[8], R RT[8]) {
   ElemState<R> st;
   elem_state(C, p, t, kappa, Q, st);
-  const R wc = C.w * st.c;       // B^P = -w u = w c V
+  const R wc = C.wih2 * st.c;    // B^P / h = -w u / h = (w c / h^2) V
   R bx[8], by[8], bz[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) { bx[q] = wc * st.vx[q]; by[q] = wc * st.vy[q]; bz[q] = wc * st.vz[q]; }
-  q1_test<R, false>(nullptr, bx, by, bz, C.cp, C.cm, C.ih, RP);
+  q1_test<R, false>(nullptr, bx, by, bz, C.cm, RP);
   R A[8];
-  const R wk = C.w * kc;
+  const R wk = C.wih2 * kc;
+  const R wt = C.wih * st.tau;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     A[q] = C.w * st.S[q];
-    const R s = A[q] * st.tau;
+    const R s = wt * st.S[q];
     bx[q] = s * st.u0x + wk * st.hx[q];
     by[q] = s * st.u0y + wk * st.hy[q];
     bz[q] = s * st.u0z + wk * st.hz[q];
   }
-  q1_test<R, true>(A, bx, by, bz, C.cp, C.cm, C.ih, RT);
+  q1_test<R, true>(A, bx, by, bz, C.cm, RT);
 }
 
-// Exact Newton Jacobian product at the element state st for a direction given at the Gauss points:
-// dV_q = grad dP_q - beta dT_q e_z and dH_q = grad dT_q (includes d tau and d N*).
+// Exact Newton Jacobian product at the element state st for a direction given at the Gauss points
+// (element units): dV_q = h (grad dP_q - beta dT_q e_z) and dH_q = h grad dT_q (includes d tau and
+// d N*).
 template <typename R>
 __device__ __forceinline__ void elem_jv_gauss(const ElemConst<R>& C, const ElemState<R>& st, const R kc,
                                               const R dvx[8], const R dvy[8], const R dvz[8],
@@ -222,30 +212,31 @@ __device__ __forceinline__ void elem_jv_gauss(const ElemConst<R>& C, const ElemS
   R sx = 0, sy = 0, sz = 0;
 #pragma unroll
   for (int q = 0; q < 8; ++q) { sx += dvx[q]; sy += dvy[q]; sz += dvz[q]; }
-  const R m = -st.c * R(0.125);
+  const R m = -st.c * C.ih * R(0.125);
   const R du0x = m * sx, du0y = m * sy, du0z = m * sz;
   const R tau = st.tau;
   const R dtau = -tau * tau * tau * C.c4he2 * (st.u0x * du0x + st.u0y * du0y + st.u0z * du0z);
-  const R wc = C.w * st.c;
-  const R mrc = -st.c * C.rc;
-  const R wk = C.w * kc;
+  const R wc = C.wih2 * st.c;
+  const R mrc = -st.c * C.rcih2;
+  const R wk = C.wih2 * kc;
+  const R wt = C.wih * tau, wdt = C.wih * dtau;
   R A[8], bx[8], by[8], bz[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    // dS = rho0 c_p (du . H + u . dH), u = -c V
+    // dS = rho0 c_p (du . grad T + u . grad dT), u = -(c/h) V
     const R dS = mrc * (dvx[q] * st.hx[q] + dvy[q] * st.hy[q] + dvz[q] * st.hz[q]
                       + st.vx[q] * dhx[q] + st.vy[q] * dhy[q] + st.vz[q] * dhz[q]);
     A[q] = C.w * dS;
-    const R a = C.w * (tau * dS + dtau * st.S[q]);      // coefficient of u0
-    const R b = C.w * tau * st.S[q];                    // coefficient of du0
+    const R a = wt * dS + wdt * st.S[q];      // coefficient of u0 (divided by h)
+    const R b = wt * st.S[q];                 // coefficient of du0 (divided by h)
     bx[q] = a * st.u0x + b * du0x + wk * dhx[q];
     by[q] = a * st.u0y + b * du0y + wk * dhy[q];
     bz[q] = a * st.u0z + b * du0z + wk * dhz[q];
   }
-  q1_test<R, true>(A, bx, by, bz, C.cp, C.cm, C.ih, oT);
+  q1_test<R, true>(A, bx, by, bz, C.cm, oT);
 #pragma unroll
   for (int q = 0; q < 8; ++q) { bx[q] = wc * dvx[q]; by[q] = wc * dvy[q]; bz[q] = wc * dvz[q]; }
-  q1_test<R, false>(nullptr, bx, by, bz, C.cp, C.cm, C.ih, oP);
+  q1_test<R, false>(nullptr, bx, by, bz, C.cm, oP);
 }
 
 // Exact Newton Jacobian product J_e (dp, dt) at the element state st.
@@ -254,31 +245,34 @@ __device__ __forceinline__ void elem_jv_dir(const ElemConst<R>& C, const ElemSta
                                             const R kc, const R dp[8], const R dt[8],
                                             R oP[8], R oT[8]) {
   R dvx[8], dvy[8], dvz[8], dT[8];
-  q1_forward(dp, C.cp, C.cm, C.ih, dT, dvx, dvy, dvz);
+  q1_forward(dp, C.cm, dT, dvx, dvy, dvz);
   R dhx[8], dhy[8], dhz[8];
-  q1_forward(dt, C.cp, C.cm, C.ih, dT, dhx, dhy, dhz);
+  q1_forward(dt, C.cm, dT, dhx, dhy, dhz);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) dvz[q] -= C.beta * dT[q];
+  for (int q = 0; q < 8; ++q) dvz[q] -= C.betah * dT[q];
   elem_jv_gauss(C, st, kc, dvx, dvy, dvz, dhx, dhy, dhz, oP, oT);
 }
 
 // Column b of the element Jacobian (b < 8: P at local node b, else T at node b - 8): the
-// Gauss-point values of the unit direction are products of the 1D shape-function tables.
+// Gauss-point values of the unit direction are products of the 1D shape-function tables (the
+// 1D shape function is cp = 1 - cm at the near Gauss point and cm at the far one; its element-unit
+// derivative is -1 or +1).
 template <typename R>
 __device__ __forceinline__ void elem_jac_column(const ElemConst<R>& C, const ElemState<R>& st, const R kc,
                                                 int b, R oP[8], R oT[8]) {
   const int a = b & 7;
   const bool isT = b >= 8;
   const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
-  const R gxd = ax ? C.ih : -C.ih, gyd = ay ? C.ih : -C.ih, gzd = az ? C.ih : -C.ih;
+  const R cp = R(1) - C.cm;
+  const R gxd = ax ? R(1) : R(-1), gyd = ay ? R(1) : R(-1), gzd = az ? R(1) : R(-1);
   R dvx[8], dvy[8], dvz[8], dhx[8], dhy[8], dhz[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int qx = q & 1, qy = (q >> 1) & 1, qz = q >> 2;
-    const R nx = (qx == ax) ? C.cp : C.cm, ny = (qy == ay) ? C.cp : C.cm, nz = (qz == az) ? C.cp : C.cm;
+    const R nx = (qx == ax) ? cp : C.cm, ny = (qy == ay) ? cp : C.cm, nz = (qz == az) ? cp : C.cm;
     const R gx = gxd * ny * nz, gy = nx * gyd * nz, gz = nx * ny * gzd;
     if (isT) {
-      dvx[q] = R(0); dvy[q] = R(0); dvz[q] = -C.beta * nx * ny * nz;
+      dvx[q] = R(0); dvy[q] = R(0); dvz[q] = -C.betah * nx * ny * nz;
       dhx[q] = gx; dhy[q] = gy; dhz[q] = gz;
     } else {
       dvx[q] = gx; dvy[q] = gy; dvz[q] = gz;
@@ -290,54 +284,57 @@ __device__ __forceinline__ void elem_jac_column(const ElemConst<R>& C, const Ele
 
 // Adjoint side: given multipliers (lp, lt) of the element rows, the gradient of
 // L = lp . R^P + lt . R^T with respect to the element state (J_e^T l), and optionally the
-// derivatives dL/dkappa and dL/dk used by the design sensitivities.
+// derivatives dL/dkappa and dL/dk used by the design sensitivities. Gradients of lp, lt at the
+// Gauss points are in element units (h grad); G below is h dL/du_q.
 template <typename R, bool SENS>
 __device__ __forceinline__ void elem_jtv(const ElemConst<R>& C, const ElemState<R>& st,
                                          const R kc, const R lp[8], const R lt[8],
                                          R oP[8], R oT[8], R* dL_dkappa, R* dL_dk) {
   R Mx[8], My[8], Mz[8], m[8];
-  q1_forward(lp, C.cp, C.cm, C.ih, m, Mx, My, Mz);
+  q1_forward(lp, C.cm, m, Mx, My, Mz);
   R Nx[8], Ny[8], Nz[8];
-  q1_forward(lt, C.cp, C.cm, C.ih, m, Nx, Ny, Nz);
+  q1_forward(lt, C.cm, m, Nx, Ny, Nz);
   const R c = st.c;
-  const R rc = C.rc;
-  const R wk = C.w * kc;
-  R gx[8], gy[8], gz[8];         // dL/du_q (without the centroid part)
+  const R wk2 = C.wih2 * kc;
+  const R tih = st.tau * C.ih;
+  const R cih2 = c * C.ih * C.ih;
+  R gx[8], gy[8], gz[8];         // h dL/du_q (without the centroid part)
   R g0x = 0, g0y = 0, g0z = 0, sdot = 0, kdot = 0;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const R u0M = st.u0x * Nx[q] + st.u0y * Ny[q] + st.u0z * Nz[q];
-    const R W = m[q] + st.tau * u0M;
-    const R wWrc = C.w * W * rc;
+    const R u0M = st.u0x * Nx[q] + st.u0y * Ny[q] + st.u0z * Nz[q];   // h u0 . grad lt
+    const R W = m[q] + tih * u0M;                                      // sum_a lt_a N*_a(q)
+    const R wWrc = C.w * W * C.rc;
     gx[q] = -C.w * Mx[q] + wWrc * st.hx[q];
     gy[q] = -C.w * My[q] + wWrc * st.hy[q];
     gz[q] = -C.w * Mz[q] + wWrc * st.hz[q];
     const R wS = C.w * st.S[q];
     g0x += wS * Nx[q]; g0y += wS * Ny[q]; g0z += wS * Nz[q];
     sdot += wS * u0M;
-    if (SENS) kdot += C.w * (Nx[q] * st.hx[q] + Ny[q] * st.hy[q] + Nz[q] * st.hz[q]);
-    // dL/dH_q = w (W rho0 c_p u_q + k grad lt_q), u_q = -c V_q; stored in N*
-    const R a = -wWrc * c;
-    Nx[q] = a * st.vx[q] + wk * Nx[q];
-    Ny[q] = a * st.vy[q] + wk * Ny[q];
-    Nz[q] = a * st.vz[q] + wk * Nz[q];
+    if (SENS) kdot += Nx[q] * st.hx[q] + Ny[q] * st.hy[q] + Nz[q] * st.hz[q];
+    // dL/dgrad T_q / h = (w W rho0 c_p u_q + w k grad lt_q) / h, u_q = -(c/h) V_q; stored in N
+    const R a = -wWrc * cih2;
+    Nx[q] = a * st.vx[q] + wk2 * Nx[q];
+    Ny[q] = a * st.vy[q] + wk2 * Ny[q];
+    Nz[q] = a * st.vz[q] + wk2 * Nz[q];
   }
   const R t3 = -st.tau * st.tau * st.tau * C.c4he2 * sdot;
   g0x = R(0.125) * (st.tau * g0x + t3 * st.u0x);
   g0y = R(0.125) * (st.tau * g0y + t3 * st.u0y);
   g0z = R(0.125) * (st.tau * g0z + t3 * st.u0z);
   R kap = 0;
+  const R cbih = c * C.beta * C.ih;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     gx[q] += g0x; gy[q] += g0y; gz[q] += g0z;
     if (SENS) kap += gx[q] * st.vx[q] + gy[q] * st.vy[q] + gz[q] * st.vz[q];
-    m[q] = c * C.beta * gz[q];   // dL/dT_q
+    m[q] = cbih * gz[q];   // dL/dT_q
   }
-  if (SENS) { *dL_dkappa = -C.imu * kap; *dL_dk = kdot; }
-  q1_test<R, true>(m, Nx, Ny, Nz, C.cp, C.cm, C.ih, oT);
+  if (SENS) { *dL_dkappa = -C.imu * C.ih * C.ih * kap; *dL_dk = C.wih2 * kdot; }
+  q1_test<R, true>(m, Nx, Ny, Nz, C.cm, oT);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) { gx[q] *= -c; gy[q] *= -c; gz[q] *= -c; }
-  q1_test<R, false>(nullptr, gx, gy, gz, C.cp, C.cm, C.ih, oP);
+  for (int q = 0; q < 8; ++q) { gx[q] *= -cih2; gy[q] *= -cih2; gz[q] *= -cih2; }
+  q1_test<R, false>(nullptr, gx, gy, gz, C.cm, oP);
 }
 
 }  // namespace nc

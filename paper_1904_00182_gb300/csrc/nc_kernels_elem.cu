@@ -154,7 +154,8 @@ __global__ void k_u_centroid(Grid g, Phys ph, ElemConst<double> C, const double2
 // dtau = -tau^3 (4/h_e^2) u0 . du0:
 //   df_e = Q w [ sum_q dT_q + tau u0 . sum_q grad dT_q + A . du0 ],  A = tau G - tau^3 (4/h_e^2)(u0 . G) u0,
 // i.e. test-function sums with constant coefficients: T rows N-part Q w (1 + (c/8) beta A_z) and
-// gradient part Q w tau u0; P rows gradient part -Q w (c/8) A.
+// gradient part Q w tau u0; P rows gradient part -Q w (c/8) A. Gradients are in element units here
+// (Gh = h G, Ah = h A) and the test-function stage takes its gradient weights divided by h.
 __global__ void k_obj_supg(Grid g, Phys ph, ElemConst<double> C, const double2* __restrict__ s,
                            const double2* __restrict__ mat, double* __restrict__ fe, double* __restrict__ d) {
   NC_ELEM_PROLOGUE();
@@ -168,21 +169,23 @@ __global__ void k_obj_supg(Grid g, Phys ph, ElemConst<double> C, const double2* 
 #pragma unroll
   for (int q = 0; q < 8; ++q) { Gx += st.hx[q]; Gy += st.hy[q]; Gz += st.hz[q]; tsum += t[q]; }
   const double Qw = Q * C.w;
-  const double u0G = st.u0x * Gx + st.u0y * Gy + st.u0z * Gz;
-  fe[e] = Qw * (tsum + st.tau * u0G);
+  const double u0G = st.u0x * Gx + st.u0y * Gy + st.u0z * Gz;   // h u0 . G
+  fe[e] = Qw * (tsum + st.tau * C.ih * u0G);
   const double t3 = st.tau * st.tau * st.tau * C.c4he2 * u0G;
   const double Ax = st.tau * Gx - t3 * st.u0x, Ay = st.tau * Gy - t3 * st.u0y, Az = st.tau * Gz - t3 * st.u0z;
   const double cb = 0.125 * st.c;
   double An[8], Bx[8], By[8], Bz[8], oP[8], oT[8];
+  const double Qwt = Qw * st.tau * C.ih;
+  const double Qwc = -Qw * cb * C.ih * C.ih;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    An[q] = Qw * (1.0 + cb * C.beta * Az);
-    Bx[q] = Qw * st.tau * st.u0x; By[q] = Qw * st.tau * st.u0y; Bz[q] = Qw * st.tau * st.u0z;
+    An[q] = Qw * (1.0 + cb * C.beta * C.ih * Az);
+    Bx[q] = Qwt * st.u0x; By[q] = Qwt * st.u0y; Bz[q] = Qwt * st.u0z;
   }
-  q1_test<double, true>(An, Bx, By, Bz, C.cp, C.cm, C.ih, oT);
+  q1_test<double, true>(An, Bx, By, Bz, C.cm, oT);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) { Bx[q] = -Qw * cb * Ax; By[q] = -Qw * cb * Ay; Bz[q] = -Qw * cb * Az; }
-  q1_test<double, false>(nullptr, Bx, By, Bz, C.cp, C.cm, C.ih, oP);
+  for (int q = 0; q < 8; ++q) { Bx[q] = Qwc * Ax; By[q] = Qwc * Ay; Bz[q] = Qwc * Az; }
+  q1_test<double, false>(nullptr, Bx, By, Bz, C.cm, oP);
   scatter_add(g, d, n0, top, oP, oT);
 }
 

@@ -43,12 +43,15 @@ template <typename R>
 inline ElemConst<R> make_econst(const Phys& p) {
   ElemConst<R> C;
   const double g = 1.0 / 1.7320508075688772935;   // 1/sqrt(3)
-  C.cp = (R)(0.5 * (1.0 + g));
   C.cm = (R)(0.5 * (1.0 - g));
   C.ih = (R)(1.0 / p.h);
   C.w = (R)(0.125 * p.h * p.h * p.h);
+  C.wih = (R)(0.125 * p.h * p.h);
+  C.wih2 = (R)(0.125 * p.h);
   C.beta = (R)p.beta;
+  C.betah = (R)(p.beta * p.h);
   C.rc = (R)p.rc;
+  C.rcih2 = (R)(p.rc / (p.h * p.h));
   C.imu = (R)(1.0 / p.mu);
   C.c4he2 = (R)(4.0 / (p.he * p.he));
   C.itau3sq = (R)(1.0 / (p.tau3 * p.tau3));
@@ -63,17 +66,18 @@ struct Counters {
 };
 
 // Floating-point operations per element of the element kernels (adds + multiplies, an FMA counts
-// two), counted from nc_element.cuh: residual; element state; J v direction part; J^T w part;
-// J^T w with design derivatives; one element-Jacobian column.
-const double kFlopsResidual = 801.0, kFlopsState = 375.0, kFlopsJv = 928.0, kFlopsJtv = 953.0,
-             kFlopsSens = 1058.0, kFlopsJacColumn = 696.0;
+// two), counted from nc_element.cuh by instantiating it with a counting number type: residual;
+// element state; J v direction part; J^T w part; J^T w with design derivatives; one element-Jacobian
+// column (the mean of the 8 P and 8 T columns).
+const double kFlopsResidual = 629.0, kFlopsState = 290.0, kFlopsJv = 743.0, kFlopsJtv = 778.0,
+             kFlopsSens = 878.0, kFlopsJacColumn = 608.0;
 // The same element code in double-float arithmetic, in FP32 flops: a double-float sum is 11 FP32
 // additions, a product 1 multiplication + 3 FMAs + 3 additions (10 flops). Adds / multiplies per
-// element: residual 323 / 478, element state 155 / 220, J^T w part 371 / 582, with design
-// derivatives 419 / 639.
+// element: residual 351 / 278, element state 167 / 123, J^T w part 399 / 379, with design
+// derivatives 447 / 431.
 const double kDfAdd = 11.0, kDfMul = 10.0;
-const double kFlopsResidualDF = 323 * kDfAdd + 478 * kDfMul, kFlopsStateDF = 155 * kDfAdd + 220 * kDfMul,
-             kFlopsJtvDF = 371 * kDfAdd + 582 * kDfMul, kFlopsSensDF = 419 * kDfAdd + 639 * kDfMul;
+const double kFlopsResidualDF = 351 * kDfAdd + 278 * kDfMul, kFlopsStateDF = 167 * kDfAdd + 123 * kDfMul,
+             kFlopsJtvDF = 399 * kDfAdd + 379 * kDfMul, kFlopsSensDF = 447 * kDfAdd + 431 * kDfMul;
 
 // ---------------- element operators (nc_kernels_elem.cu) ----------------
 // out (2N doubles) = R(s); Dirichlet rows = s. s: double2 per node; mat: (kappa, k) per element.
