@@ -163,17 +163,51 @@ def cylinder_params(n):
                 heat_radius=0.2 * n, design_radius=0.5 * n, heat_z0=4 * n // 5, heated_layers=2 * n // 5)
 
 
+class LibraryEvaluator:
+    """f, df/drho and the warm-start state of a design through the library (the default evaluator of
+    optimize): set_design, Newton warm-started from the previous state (Sec. 5.4), adjoint,
+    sensitivities."""
+
+    def __init__(self, nx, ny, nz, alpha, device="cuda", **params):
+        self.pb = Problem(nx, ny, nz, 1.0 / nz, device=device, alpha=alpha, **params)
+        self.params = self.pb.params
+        self.kappa_f, _ = self.pb.permeabilities()
+        self.state = None
+
+    def set_stage(self, **overrides):
+        self.pb.set_params(**overrides)
+
+    def __call__(self, rho):
+        pb = self.pb
+        pb.set_design(rho)
+        if self.state is not None:
+            pb.set_state(*self.state)
+        sst = pb.solve_state()
+        f, ast = pb.solve_adjoint()
+        grad = pb.sensitivities()
+        P, T, _ = pb.get_fields(velocity=False)
+        self.state = (P.clone(), T.clone())
+        return f, grad, {"newton_its": sst["newton_its"], "krylov_its": sst["krylov_its"],
+                         "adjoint_krylov_its": ast["krylov_its"]}
+
+    def close(self):
+        self.pb.close()
+
+
 def optimize(nx, ny, nz, alpha, volfrac, iters, move=0.2, stages=PAPER_CONTINUATION, stage_every=None,
-             rho0=None, device="cuda", callback=None, **params):
+             rho0=None, device="cuda", callback=None, evaluator=None, keep_iterates=False, **params):
     """Run `iters` MMA iterations of Eq. optprob on an nx x ny x nz grid (h = 1/nz).
 
     stages: continuation stages (dicts of q_c, q_p and kappa_s or kappa_ratio), each used for
-    stage_every iterations (default: iters split evenly). Returns {"rho": final design, "history": one
-    record per iteration (f, g, max change, stage, Newton and Krylov iterations, seconds)}.
+    stage_every iterations (default: iters split evenly). evaluator: an object with `params` (nc_params
+    of the regions), `kappa_f`, set_stage(**overrides), __call__(rho) -> (f, df/drho, stats dict) and
+    close(); default LibraryEvaluator. Returns {"rho": final design, "history": one record per
+    iteration (f, g, max change, stage, solver iterations, seconds; with keep_iterates the new design
+    variables "x" as well)}.
     """
-    pb = Problem(nx, ny, nz, 1.0 / nz, device=device, alpha=alpha, **params)
+    ev = evaluator if evaluator is not None else LibraryEvaluator(nx, ny, nz, alpha, device=device, **params)
     ne = nx * ny * nz
-    design, heated = (m.to(device) for m in region_masks(nx, ny, nz, pb.params))
+    design, heated = (m.to(device) for m in region_masks(nx, ny, nz, ev.params))
     nd = int(design.sum())
     rho = torch.full((ne,), float(volfrac), dtype=torch.float64, device=device) if rho0 is None else \
         torch.as_tensor(rho0, dtype=torch.float64, device=device).clone()
@@ -181,10 +215,9 @@ def optimize(nx, ny, nz, alpha, volfrac, iters, move=0.2, stages=PAPER_CONTINUAT
     x = rho[design].clone()
     mma = MMA(torch.zeros_like(x), torch.ones_like(x), move=move)
     stage_every = stage_every or max(1, math.ceil(iters / max(1, len(stages))))
-    kf, _ = pb.permeabilities()
+    kf = ev.kappa_f
     history = []
     fscale = None
-    state = None
     stage = -1
     for it in range(iters):
         s = min(it // stage_every, len(stages) - 1) if stages else -1
@@ -193,17 +226,10 @@ def optimize(nx, ny, nz, alpha, volfrac, iters, move=0.2, stages=PAPER_CONTINUAT
             st = dict(stages[s])
             if "kappa_s" in st:
                 st["kappa_ratio"] = st.pop("kappa_s") / kf
-            pb.set_params(**st)
+            ev.set_stage(**st)
         t0 = time.perf_counter()
         rho[design] = x
-        pb.set_design(rho)
-        if state is not None:
-            pb.set_state(*state)
-        sst = pb.solve_state()
-        f, ast = pb.solve_adjoint()
-        grad = pb.sensitivities()
-        P, T, _ = pb.get_fields(velocity=False)
-        state = (P.clone(), T.clone())
+        f, grad, stats = ev(rho)
         gval = float(x.mean()) - volfrac
         # scaling for MMA's fixed regularisation (1e-5 per variable): objective and constraint are
         # scaled so that their largest per-element gradients are of order one (the objective's scale
@@ -214,14 +240,16 @@ def optimize(nx, ny, nz, alpha, volfrac, iters, move=0.2, stages=PAPER_CONTINUAT
         x_new = mma.step(x, f * fscale, df * fscale, gval * nd, torch.ones_like(x))
         change = float((x_new - x).abs().max())
         x = x_new
-        rec = {"it": it, "f": f, "g": gval, "change": change, "stage": stage, "newton_its": sst["newton_its"],
-               "krylov_its": sst["krylov_its"], "adjoint_krylov_its": ast["krylov_its"],
-               "seconds": time.perf_counter() - t0}
+        rec = {"it": it, "f": f, "g": gval, "change": change, "stage": stage, "seconds": time.perf_counter() - t0}
+        if keep_iterates:
+            rec["x"] = x.clone()
+        rec.update(stats)
         history.append(rec)
         if callback:
             callback(rec)
     rho[design] = x
-    pb.close()
+    if evaluator is None:
+        ev.close()
     return {"rho": rho, "history": history}
 
 

@@ -156,3 +156,62 @@ def test_full_size_geometries_validate():
         p = default_params(**geom)
         b = footprint_bytes(Grid(n, n, 2 * n, 1.0 / (2 * n)), p)
         assert 0 < b < 40e9, (n, b)
+
+
+class _OracleEvaluator:
+    """f and df/drho of the FP64 oracle (Sec. 5.1 adjoint, filter transpose), with the same warm start
+    (Sec. 5.4) and the same region parameters as the library's evaluator."""
+
+    def __init__(self, n, alpha, lib_params, rtol):
+        import oracle
+        self.oracle = oracle
+        self.n, self.alpha, self.rtol = n, alpha, rtol
+        self.params = lib_params
+        self.overrides = {}
+        self.op = self._make()
+        self.kappa_f = self.op.par.kappa_f
+        self.state = None
+
+    def _make(self):
+        o = self.oracle
+        return o.Problem(o.Mesh(self.n, self.n, self.n, 1.0 / self.n),
+                         o.Params(alpha=self.alpha, newton_rtol=self.rtol, **self.overrides))
+
+    def set_stage(self, **overrides):
+        self.overrides.update(overrides)
+        self.op = self._make()
+
+    def __call__(self, rho):
+        import torch
+        op = self.op
+        op.set_design(rho.cpu().numpy())
+        op.solve_state(s0=self.state)
+        self.state = op.s.copy()
+        op.solve_adjoint()
+        return op.objective(), torch.from_numpy(op.sensitivities()), {}
+
+    def close(self):
+        pass
+
+
+@pytest.mark.gpu
+def test_optimisation_iterates_follow_the_oracle():
+    """Three MMA iterations of Eq. optprob (Sec. 5.1-5.3) driven by the library's objective and
+    adjoint gradient give the same iterates as three driven by the oracle's, from the same start."""
+    from paper_1904_00182_gb300 import build
+    build.build()
+    from paper_1904_00182_gb300.optimize import LibraryEvaluator, optimize
+    n, alpha, rtol = 8, 1e4, 1e-10
+    stages = ({"q_c": 8.81, "q_p": 8.0},)
+    lib = LibraryEvaluator(n, n, n, alpha, newton_rtol=rtol)
+    a = optimize(n, n, n, alpha, 0.2, 3, stages=stages, evaluator=lib, keep_iterates=True)
+    ora = _OracleEvaluator(n, alpha, lib.params, rtol)
+    assert ora.kappa_f == pytest.approx(lib.kappa_f, rel=1e-14)
+    b = optimize(n, n, n, alpha, 0.2, 3, stages=stages, evaluator=ora, device="cpu", keep_iterates=True)
+    lib.close()
+    for ra, rb in zip(a["history"], b["history"]):
+        assert ra["f"] == pytest.approx(rb["f"], rel=1e-6), (ra["it"], ra["f"], rb["f"])
+        dx = float((ra["x"].cpu() - rb["x"]).abs().max())
+        assert dx <= 1e-6, (ra["it"], dx)
+    assert a["history"][-1]["f"] < a["history"][0]["f"]
+    assert float((a["history"][-1]["x"].cpu() - a["history"][0]["x"].cpu()).abs().max()) > 1e-3   # the design moved
