@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--alpha", type=float, default=1e4)
     ap.add_argument("--volfrac", type=float, default=0.2)
     ap.add_argument("--levels", type=int, default=6)
+    ap.add_argument("--mg-op0", default="exact", choices=["exact", "picard"],
+                    help="finest-level multigrid operator of the mixed path: the exact Jacobian or the "
+                         "frozen-coefficient (Picard) operator")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--fast-steps", type=int, default=2)
     ap.add_argument("--concurrent-steps", type=int, default=3)
@@ -241,7 +244,8 @@ def run_serving(args, dev):
                for r in stream]
     torch.cuda.synchronize(dev)
     reqs = [Request(i, r["t_arrival"], r["n"], r["alpha"], r["adjoint"], designs[i]) for i, r in enumerate(stream)]
-    srv = Server(slots=6, hbm_budget_bytes=48 << 30, device=dev)
+    srv = Server(slots=6, hbm_budget_bytes=48 << 30, device=dev,
+                 mg_op0=1 if args.mg_op0 == "picard" else 0)
     # warm the pools with one request per grid size (problem creation is not part of serving)
     sizes = sorted({r.n for r in reqs})
     warm = [Request(-1 - k, 0.0, n, 1e4, True,
@@ -263,7 +267,7 @@ def workload_config(args):
                         "mixed GMG (%d levels), Newton to 1e-8 + adjoint + sensitivities"
                         % (args.n, args.n, args.n, args.volfrac, args.alpha, args.levels),
             "grid": [args.n, args.n, args.n], "alpha": args.alpha, "volfrac": args.volfrac,
-            "mg_levels": args.levels, "newton_rtol": 1e-8,
+            "mg_levels": args.levels, "newton_rtol": 1e-8, "mg_op0": args.mg_op0,
             "precision": "mixed: FP32 multigrid and Krylov operator; IEEE FP64 Newton residual, Krylov basis, "
                          "accepting adjoint residual, sensitivities, coarse residual",
             "l2": "inputs larger than L2 (Krylov basis ~1 GB, multigrid hierarchy ~0.4 GB per solve)",
@@ -337,8 +341,9 @@ def run_gpu(args, rank, world, local):
     grad_dev = torch.empty(E, dtype=torch.float64, device=dev)
     grad_host = torch.empty(E, dtype=torch.float64).pin_memory()
     stream = torch.cuda.Stream(device=dev)
+    mg_op0 = nc.NC_MGOP_PICARD if args.mg_op0 == "picard" else nc.NC_MGOP_EXACT
     pb = nc.Problem(n, n, n, 1.0 / n, stream=stream.cuda_stream, device=dev, alpha=args.alpha,
-                    mg_levels=args.levels, precision=nc.NC_PREC_MIXED)
+                    mg_levels=args.levels, precision=nc.NC_PREC_MIXED, mg_op0=mg_op0)
     pb_params = pb.params.as_dict()
     stats_log = []
 
@@ -439,7 +444,7 @@ def run_gpu(args, rank, world, local):
     if fp64:
         fp64["precision"] = "IEEE FP64 throughout (multigrid, Krylov, residuals, coarse solve)"
     fast = time_variant(args.fast_steps, precision=nc.NC_PREC_MIXED, outer_arith=nc.NC_ARITH_DF64,
-                        krylov_basis=nc.NC_BASIS_FP32)
+                        krylov_basis=nc.NC_BASIS_FP32, mg_op0=mg_op0)
     if fast:
         fast["precision"] = ("mixed, further reduced: double-float (48-bit significand) Newton residual, adjoint "
                              "residual and sensitivities; FP32 Krylov basis with FP64 cross-thread sums; "
@@ -451,7 +456,7 @@ def run_gpu(args, rank, world, local):
     if args.concurrent_steps > 0:
         streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
         pcs = [nc.Problem(n, n, n, 1.0 / n, stream=streams[i].cuda_stream, device=dev, alpha=args.alpha,
-                          mg_levels=args.levels) for i in range(2)]
+                          mg_levels=args.levels, mg_op0=mg_op0) for i in range(2)]
 
         def worker(i, steps):
             for j in range(steps):
@@ -487,7 +492,7 @@ def run_gpu(args, rank, world, local):
         for alpha_c in (1e3, 1e6):
             pcv = nc.Problem(80, 80, 160, 1.0 / 160, stream=stream.cuda_stream, device=dev, alpha=alpha_c,
                              Q=1e4, bc=nc.NC_BC_CAVITY, heat_nx=8, heat_ny=8, heated_layers=8, design_nx=60,
-                             design_ny=60, design_nz=120, timeout_s=60.0)
+                             design_ny=60, design_nz=120, timeout_s=60.0, mg_op0=mg_op0)
             rho_c = torch.full((80 * 80 * 160,), 0.05, dtype=torch.float64, device=dev)
             entry = {"alpha": alpha_c, "grid": [80, 80, 160]}
             try:

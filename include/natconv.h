@@ -86,6 +86,14 @@ enum { NC_BC_TOP = 0, NC_BC_CAVITY = 1 };
  * are in element sizes. */
 enum { NC_REGION_BOX = 0, NC_REGION_CYLINDER = 1 };
 
+/* Operator of the multigrid's finest level on the NC_PREC_MIXED path (nc_params.mg_op0). The outer
+ * FGMRES is flexible (Sec. 5.4), so its preconditioner may apply another operator than J.
+ * NC_MGOP_EXACT: the exact Newton Jacobian J(s) (FP32). NC_MGOP_PICARD: the frozen-coefficient
+ * operator: the continuity rows of J; energy rows sum_q w [N*_a rho0 c_p u0 . grad dT + k grad N_a .
+ * grad dT] with the element's centroid velocity u0 and tau frozen at s (no derivatives of u, u0 or
+ * tau, no dP coupling): about 40 % of the arithmetic of J. The Krylov operator stays exact. */
+enum { NC_MGOP_EXACT = 0, NC_MGOP_PICARD = 1 };
+
 typedef struct nc_problem nc_problem;
 
 typedef struct {
@@ -161,6 +169,7 @@ typedef struct {
   int region_shape;     /* NC_REGION_BOX or NC_REGION_CYLINDER [NC_REGION_BOX] */
   double heat_radius, design_radius; /* NC_REGION_CYLINDER: radii in element sizes [0, 0] */
   int heat_z0;          /* NC_REGION_CYLINDER: first element layer of both regions [0] */
+  int mg_op0;           /* NC_PREC_MIXED only: NC_MGOP_EXACT or NC_MGOP_PICARD [NC_MGOP_EXACT] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */
@@ -258,6 +267,13 @@ nc_status nc_apply_jacobian(nc_problem* pb, const double* s, const double* v, do
 nc_status nc_apply_jacobian_transpose(nc_problem* pb, const double* s, const double* w,
                                       double* out);
 
+/* The frozen-coefficient finest-level multigrid operator (NC_MGOP_PICARD) at the state s applied to v
+ * (transpose = 0) or its transpose (transpose = 1), computed in FP32 from FP64 inputs: s, v, out are
+ * 2N doubles (node-interleaved P, T; device or host). Fixed rows of v are ignored and those of out are
+ * zero, as for nc_apply_jacobian. Requires a design. Has no counterpart in the paper (an operator of
+ * this library's preconditioner); it exists so the operator can be checked on its own. */
+nc_status nc_apply_picard(nc_problem* pb, const double* s, const double* v, double* out, int transpose);
+
 /* Kernel classes timed when profiling is on (nc_set_profiling). */
 enum {
   NC_PROF_RESIDUAL = 0,     /* FP64 residual element sweep */
@@ -277,7 +293,8 @@ enum {
   NC_PROF_MG_STENCIL_L1 = 14,   /* stencil operators of multigrid level 1 (the largest stencil level) */
   NC_PROF_MG_TAIL = 15,         /* fused V-cycle on the small coarse levels (one cluster kernel) */
   NC_PROF_ADJ_DF64 = 16,        /* double-float J^T lambda of steering adjoint refinement passes */
-  NC_PROF_NCLASSES = 17
+  NC_PROF_MG_OP0_PICARD = 17,   /* multigrid finest-level operator, frozen-coefficient (NC_MGOP_PICARD) */
+  NC_PROF_NCLASSES = 18
 };
 
 /* Per-launch CUDA-event timing of kernel classes for calls on pb: bit c of class_mask times class

@@ -175,6 +175,31 @@ class ElementModel:
                          zeros_H, np.ones_like(k))
         return d_kappa, d_k
 
+    def picard_jvp(self, pe, te, kappa, k, dpe, dte):
+        """Frozen-coefficient (Picard) linearisation of the element residual along (dpe, dte).
+
+        Not a step of the paper's method: the library's multigrid may use this operator on its finest
+        level as a cheaper stand-in for J (the outer Krylov solver is flexible, so the preconditioner
+        may differ from J). Definition: the continuity rows exactly as in jvp (R^P is linear in the
+        state); the energy rows with the convective velocity and the SUPG weight frozen at the
+        element-constant centroid velocity u0 and tau of the state (pe, te), and no derivative of u,
+        u0 or tau:  sum_q w [ N*_a(q) rho0 c_p u0 . grad dT_q + k grad N_a . grad dT_q ].
+        """
+        st = self.gauss_state(pe, te, kappa)
+        c = (kappa / self.p.mu)[:, None]
+        N, D, w = self.N, self.D, self.w
+        dTq = dte @ N.T
+        duq = -c[:, :, None] * np.einsum("qai,ea->eqi", D, dpe)
+        duq[:, :, 2] += c * self.beta * dTq
+        dRP = -w * np.einsum("qai,eqi->ea", D, duq)
+        dHq = np.einsum("qai,ea->eqi", D, dte)
+        u0, tau = st["u0"], st["tau"]
+        conv = self.p.rho0 * self.p.cp * np.einsum("ei,eqi->eq", u0, dHq)
+        Nstar = N[None] + tau[:, None, None] * np.einsum("ei,qai->eqa", u0, D)
+        dRT = w * np.einsum("eqa,eq->ea", Nstar, conv)
+        dRT += w * k[:, None] * np.einsum("qai,eqi->ea", D, dHq)
+        return dRP, dRT
+
     def centroid_velocity(self, pe, te, kappa):
         """Darcy velocity u0 at each element centroid (E, 3), Eq. finaldarcy."""
         return self.gauss_state(pe, te, kappa)["u0"]

@@ -220,6 +220,40 @@ class Problem:
             self.scatter(dRP, dRT, sl, out)
         return out
 
+    def picard_jvp_raw(self, s, v):
+        """Frozen-coefficient operator (ElementModel.picard_jvp) applied to v over all DOFs, no BC rows."""
+        out = np.zeros(2 * self.mesh.n_nodes)
+        for sl in self._chunks():
+            pe, te = self.gather(s, sl)
+            dp, dt = self.gather(v, sl)
+            dRP, dRT = self.em.picard_jvp(pe, te, self.kappa[sl], self.k[sl], dp, dt)
+            self.scatter(dRP, dRT, sl, out)
+        return out
+
+    def picard_matrix_full(self, s):
+        """Assembled frozen-coefficient operator over all DOFs (no BC treatment), CSR; column b of an
+        element's matrix is picard_jvp along the unit vector e_b."""
+        rows, cols, vals = [], [], []
+        for sl in self._chunks():
+            pe, te = self.gather(s, sl)
+            E = pe.shape[0]
+            Je = np.empty((E, 16, 16))
+            for b in range(16):
+                dp = np.zeros((E, 8))
+                dt = np.zeros((E, 8))
+                (dp if b < 8 else dt)[:, b % 8] = 1.0
+                dRP, dRT = self.em.picard_jvp(pe, te, self.kappa[sl], self.k[sl], dp, dt)
+                Je[:, :8, b] = dRP
+                Je[:, 8:, b] = dRT
+            c = self.conn[sl]
+            dof = np.concatenate([2 * c, 2 * c + 1], axis=1)
+            rows.append(np.repeat(dof, 16, axis=1).ravel())
+            cols.append(np.tile(dof, (1, 16)).ravel())
+            vals.append(Je.ravel())
+        n2 = 2 * self.mesh.n_nodes
+        return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(n2, n2))
+
     def jacobian_full(self, s):
         """Assembled sparse Jacobian dR/ds over all DOFs (no BC treatment), CSR."""
         rows, cols, vals = [], [], []

@@ -19,6 +19,8 @@ NC_BC_TOP = 0
 NC_BC_CAVITY = 1
 NC_REGION_BOX = 0
 NC_REGION_CYLINDER = 1
+NC_MGOP_EXACT = 0
+NC_MGOP_PICARD = 1
 
 STATUS_NAMES = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_OOM", 3: "NC_ERR_CUDA", 4: "NC_ERR_DIVERGED",
                 5: "NC_ERR_MAXIT", 6: "NC_ERR_NAN", 7: "NC_ERR_TIMEOUT", 8: "NC_ERR_STATE"}
@@ -27,12 +29,12 @@ STATUS_NAMES = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_OOM", 3: "NC_ERR_CUDA", 
 EXPORTS = ("nc_default_params", "nc_create_problem", "nc_destroy_problem", "nc_footprint_bytes", "nc_set_params",
            "nc_set_design", "nc_set_state", "nc_solve_state", "nc_objective", "nc_solve_adjoint",
            "nc_sensitivities", "nc_get_fields", "nc_get_adjoint", "nc_get_permeabilities", "nc_get_design_fields", "nc_eval_residual",
-           "nc_apply_jacobian", "nc_apply_jacobian_transpose", "nc_set_profiling", "nc_get_profile",
+           "nc_apply_jacobian", "nc_apply_jacobian_transpose", "nc_apply_picard", "nc_set_profiling", "nc_get_profile",
            "nc_counters", "nc_norm2_free_noalloc", "nc_last_error")
 
 PROF_CLASSES = ("residual", "outer_op64", "outer_op32", "mg_op0", "mg_stencil", "mg_setup_fine", "smooth",
                 "krylov_vec", "filter", "sens", "other", "mg_setup_coarse", "coarse_factor", "coarse_solve",
-                "mg_stencil_l1", "mg_tail", "adjoint_df64")
+                "mg_stencil_l1", "mg_tail", "adjoint_df64", "mg_op0_picard")
 
 
 class NatConvError(RuntimeError):
@@ -64,6 +66,7 @@ class Params(ctypes.Structure):
         ("bc", ctypes.c_int), ("heat_nx", ctypes.c_int), ("heat_ny", ctypes.c_int), ("design_nx", ctypes.c_int),
         ("design_ny", ctypes.c_int), ("design_nz", ctypes.c_int), ("region_shape", ctypes.c_int),
         ("heat_radius", ctypes.c_double), ("design_radius", ctypes.c_double), ("heat_z0", ctypes.c_int),
+        ("mg_op0", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -121,6 +124,7 @@ def load_library(path=None):
         "nc_eval_residual": ([vp, vp, vp, dp], i),
         "nc_apply_jacobian": ([vp, vp, vp, vp, i], i),
         "nc_apply_jacobian_transpose": ([vp, vp, vp, vp], i),
+        "nc_apply_picard": ([vp, vp, vp, vp, i], i),
         "nc_set_profiling": ([vp, i], i),
         "nc_get_profile": ([vp, i, dp, ctypes.POINTER(ctypes.c_longlong), dp, dp], i),
         "nc_counters": ([vp, ctypes.POINTER(ctypes.c_longlong), dp], i),

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "natconv.h"
@@ -94,6 +95,7 @@ struct nc_problem {
   double2* dl = nullptr;   // element (dL/dkappa, dL/dk) at the adjoint solution (see dl_ready)
   bool dl_ready = false;   // dl holds the derivatives of the current lambda
   float2 *mat32 = nullptr, *s32 = nullptr, *v32 = nullptr, *y32 = nullptr;
+  float4* fz = nullptr;   // frozen (u0, tau) per element of the Picard finest-level operator (NC_MGOP_PICARD)
   // double-float copies (mixed path with NC_ARITH_DF64): materials per element, split scratch per node
   float4 *mat_df = nullptr, *s_df = nullptr, *w_df = nullptr;
   // Krylov
@@ -370,6 +372,15 @@ nc_status outer_op(nc_problem* pb, bool transpose, bool fp32, const double* x, d
   return NC_OK;
 }
 
+// The FP32 state copy used by the FP32 Krylov operator and the finest multigrid level, and with
+// NC_MGOP_PICARD the frozen coefficients of the finest-level operator at that state.
+nc_status refresh_state32(nc_problem* pb, const double2* s, int cls) {
+  PCK(cls, launch_cast_d2f((float*)pb->s32, (const double*)s, 2 * pb->g.nn, pb->st, &pb->cnt));
+  if (pb->par.mg_op0 == NC_MGOP_PICARD)
+    PCK(cls, launch_frozen(pb->g, pb->ph, pb->s32, pb->mat32, pb->fz, pb->st, &pb->cnt));
+  return NC_OK;
+}
+
 // ---------------------------------------------------------------- multigrid --------
 template <typename R> MG<R>& mg_of(nc_problem* pb);
 template <> MG<float>& mg_of<float>(nc_problem* pb) { return pb->mg32; }
@@ -413,7 +424,7 @@ template <typename R>
 nc_status mg_setup(nc_problem* pb, bool refactor) {
   MG<R>& mg = mg_of<R>(pb);
   const int L = (int)mg.lev.size();
-  if (sizeof(R) == 4) PCK(NC_PROF_MG_COARSE_SETUP, launch_cast_d2f((float*)pb->s32, (const double*)pb->s, 2 * pb->g.nn, pb->st, &pb->cnt));
+  if (sizeof(R) == 4) CKS(refresh_state32(pb, pb->s, NC_PROF_MG_COARSE_SETUP));
   for (int l = 0; l < L - 1; ++l) CK(cudaMemsetAsync(mg.lev[l].dinv, 0, sizeof(R) * 4 * mg.lev[l].g.nn, pb->st));
   CK(cudaMemsetAsync(pb->dflag, 0, sizeof(int), pb->st));
   if (L == 1) return fail(pb, NC_ERR_ARG, "grid dimensions must be even for the multigrid hierarchy");
@@ -444,6 +455,12 @@ template <typename R>
 nc_status level_apply(nc_problem* pb, int l, bool tr, const typename Vec2<R>::type* x, typename Vec2<R>::type* y) {
   MG<R>& mg = mg_of<R>(pb);
   if (l != 0) return fail(pb, NC_ERR_ARG, "level_apply is for the finest level");
+  if constexpr (std::is_same<R, float>::value) {
+    if (pb->par.mg_op0 == NC_MGOP_PICARD) {
+      PCK(NC_PROF_MG_OP0_PICARD, launch_level0_picard(mg.lev[0].g, pb->ph, pb->fz, pb->mat32, x, y, tr, pb->st, &pb->cnt));
+      return NC_OK;
+    }
+  }
   PCK(NC_PROF_MG_OP0, launch_level0_apply<R>(mg.lev[0].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), x, y, tr, pb->st, &pb->cnt));
   return NC_OK;
 }
@@ -841,7 +858,7 @@ nc_status newton(nc_problem* pb, double rtol, double ref, nc_stats* stats, bool*
       if (stats) stats->mg_setups++;
     } else if (pb->par.precision != NC_PREC_FP64) {
       // the Krylov operator and the finest multigrid level use the current state
-      PCK(NC_PROF_MG_COARSE_SETUP, launch_cast_d2f((float*)pb->s32, (const double*)pb->s, 2 * pb->g.nn, pb->st, &pb->cnt));
+      CKS(refresh_state32(pb, pb->s, NC_PROF_MG_COARSE_SETUP));
     }
     double t1 = now_s();
     PCK(NC_PROF_OTHER, launch_scale_copy(pb->rhs, pb->R, -1.0, n, pb->st, &pb->cnt));
@@ -929,6 +946,7 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (p->mg_tail_nodes < 0) { *why = "mg_tail_nodes must be >= 0"; return NC_ERR_ARG; }
   if (!(p->mg_reuse_below >= 0.0)) { *why = "mg_reuse_below must be >= 0"; return NC_ERR_ARG; }
   if (p->adjoint_df64_steps != 0 && p->adjoint_df64_steps != 1) { *why = "adjoint_df64_steps must be 0 or 1"; return NC_ERR_ARG; }
+  if (p->mg_op0 != NC_MGOP_EXACT && p->mg_op0 != NC_MGOP_PICARD) { *why = "unknown mg_op0"; return NC_ERR_ARG; }
   if (p->coarse_refactor < 0 || p->coarse_refactor > 2) { *why = "coarse_refactor must be 0, 1 or 2"; return NC_ERR_ARG; }
   if (!(p->newton_rtol > 0) || p->newton_maxit < 0 || p->krylov_maxit < 1) { *why = "bad tolerances"; return NC_ERR_ARG; }
   if (!(p->filter_radius >= 0) || !(p->filter_rtol > 0)) { *why = "bad filter parameters"; return NC_ERR_ARG; }
@@ -966,6 +984,7 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
   b += 6 * al(16 * nn);                 // R, R_try, dx, w, rhs, R0
   b += 3 * al(8 * ne) + al(24 * ne);    // rho, gamma_t, gsens, u
   b += 3 * al(16 * ne) + al(8 * ne) + 3 * al(8 * nn);   // mat, dmat, dl, mat32, s32, v32, y32
+  b += al(16 * ne);                                      // fz
   const size_t ks = (p->precision == NC_PREC_FP64 || p->krylov_basis == NC_BASIS_FP64) ? 8 : 4;   // basis entry
   b += al(2 * ks * nn * (m + 1)) + al(2 * ks * nn * m);     // V, Z
   if (p->precision != NC_PREC_FP64) b += al(16 * ne) + 2 * al(16 * nn);   // mat_df, s_df, w_df
@@ -1155,7 +1174,7 @@ nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream,
   A(dalloc(pb, &pb->w, 2 * nn)); A(dalloc(pb, &pb->rhs, 2 * nn)); A(dalloc(pb, &pb->R0, 2 * nn));
   A(dalloc(pb, &pb->rho, ne)); A(dalloc(pb, &pb->gamma_t, ne)); A(dalloc(pb, &pb->gsens, ne)); A(dalloc(pb, &pb->u, 3 * ne));
   A(dalloc(pb, &pb->mat, ne)); A(dalloc(pb, &pb->dmat, ne)); A(dalloc(pb, &pb->dl, ne)); A(dalloc(pb, &pb->mat32, ne)); A(dalloc(pb, &pb->s32, nn));
-  A(dalloc(pb, &pb->v32, nn)); A(dalloc(pb, &pb->y32, nn));
+  A(dalloc(pb, &pb->v32, nn)); A(dalloc(pb, &pb->y32, nn)); A(dalloc(pb, &pb->fz, ne));
   if (p->precision == NC_PREC_FP64 || p->krylov_basis == NC_BASIS_FP64) {
     A(dalloc(pb, &pb->V, (size_t)2 * nn * (pb->m + 1))); A(dalloc(pb, &pb->Z, (size_t)2 * nn * pb->m));
   } else {
@@ -1354,7 +1373,7 @@ nc_status nc_solve_adjoint(nc_problem* pb, int objective, double* f_out, nc_stat
   double t0 = now_s();
   if (pb->mg_ready) {
     if (pb->par.precision != NC_PREC_FP64)
-      PCK(NC_PROF_MG_COARSE_SETUP, launch_cast_d2f((float*)pb->s32, (const double*)pb->s, 2 * g.nn, pb->st, &pb->cnt));
+      CKS(refresh_state32(pb, pb->s, NC_PROF_MG_COARSE_SETUP));
   } else {
     CKS(mg_setup_any(pb, true));
   }
@@ -1531,13 +1550,34 @@ static nc_status apply_generic(nc_problem* pb, const double* s, const double* v,
   const Grid& g = pb->g;
   PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->w, pb->st, &pb->cnt));   // the operator acts on free entries
   if (fp32) {
-    PCK(NC_PROF_OTHER, launch_cast_d2f((float*)pb->s32, (const double*)pb->s_try, n, pb->st, &pb->cnt));
+    CKS(refresh_state32(pb, pb->s_try, NC_PROF_OTHER));
     CKS(outer_op(pb, tr, true, pb->w, pb->R_try));
   } else {
     if (tr) CKS(outer_jtv(pb, NC_PROF_OTHER, pb->s_try, (const double2*)pb->w, pb->R_try));
     else PCK(NC_PROF_OTHER, launch_jv_f64(g, pb->ph, pb->s_try, pb->mat, (const double2*)pb->w, pb->R_try, pb->st, &pb->cnt));
   }
   PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->R_try, pb->st, &pb->cnt));   // Dirichlet rows of the projected operator
+  CKS(copy_out(pb, out, pb->R_try, sizeof(double) * n));
+  CKS(sync(pb, "operator"));
+  return NC_OK;
+}
+
+nc_status nc_apply_picard(nc_problem* pb, const double* s, const double* v, double* out, int transpose) {
+  if (!pb) return NC_ERR_ARG;
+  if (pb->stage < 1) return fail(pb, NC_ERR_STATE, "operator needs a design");
+  if (!out) return fail(pb, NC_ERR_ARG, "NULL output");
+  DeviceGuard dg(pb->device);
+  const long long n = 2 * pb->g.nn;
+  const Grid& g = pb->g;
+  CKS(copy_in(pb, pb->s_try, s, sizeof(double) * n));
+  CKS(copy_in(pb, pb->w, v, sizeof(double) * n));
+  PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->w, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_cast_d2f((float*)pb->s32, (const double*)pb->s_try, n, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_frozen(g, pb->ph, pb->s32, pb->mat32, pb->fz, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_cast_d2f((float*)pb->v32, pb->w, n, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_level0_picard(g, pb->ph, pb->fz, pb->mat32, pb->v32, pb->y32, transpose != 0, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_cast_f2d(pb->R_try, (const float*)pb->y32, n, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->R_try, pb->st, &pb->cnt));
   CKS(copy_out(pb, out, pb->R_try, sizeof(double) * n));
   CKS(sync(pb, "operator"));
   return NC_OK;

@@ -337,4 +337,71 @@ __device__ __forceinline__ void elem_jtv(const ElemConst<R>& C, const ElemState<
   q1_test<R, false>(nullptr, gx, gy, gz, C.cm, oP);
 }
 
+// Frozen-coefficient (Picard) element operator, a cheaper stand-in for J_e on the multigrid's finest
+// level (the outer Krylov solver is flexible, so its preconditioner may use another operator): the
+// continuity rows exactly as J_e (they are linear in the state); the energy rows
+//   sum_q w [ N*_a(q) rho0 c_p u0 . grad dT_q + k grad N_a . grad dT_q ],  N* = N + tau u0 . grad N,
+// with the centroid velocity u0 and tau of the linearisation state frozen: no derivatives of u, u0 or
+// tau and no coupling of dP into the energy rows. c = kappa / mu, kc = k.
+template <typename R>
+__device__ __forceinline__ void elem_picard(const ElemConst<R>& C, const R c, const R kc, const R u0x, const R u0y,
+                                            const R u0z, const R tau, const R dp[8], const R dt[8],
+                                            R oP[8], R oT[8]) {
+  R vx[8], vy[8], vz[8], dT[8];
+  q1_forward(dp, C.cm, dT, vx, vy, vz);    // dT: scratch for the (unused) P values
+  R hx[8], hy[8], hz[8];
+  q1_forward(dt, C.cm, dT, hx, hy, hz);
+  const R wc = C.wih2 * c;
+  R bx[8], by[8], bz[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    bx[q] = wc * vx[q];
+    by[q] = wc * vy[q];
+    bz[q] = wc * (vz[q] - C.betah * dT[q]);
+  }
+  q1_test<R, false>(nullptr, bx, by, bz, C.cm, oP);
+  const R a = C.wih * C.rc;      // A_q = w rho0 c_p u0 . grad dT_q = (w rho0 c_p / h) u0 . H_q
+  const R th = tau * C.ih;       // B_q / h = (tau / h) A_q u0 + (w k / h^2) H_q
+  const R wk = C.wih2 * kc;
+  R A[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    A[q] = a * (u0x * hx[q] + u0y * hy[q] + u0z * hz[q]);
+    const R sq = th * A[q];
+    bx[q] = sq * u0x + wk * hx[q];
+    by[q] = sq * u0y + wk * hy[q];
+    bz[q] = sq * u0z + wk * hz[q];
+  }
+  q1_test<R, true>(A, bx, by, bz, C.cm, oT);
+}
+
+// Transpose of elem_picard: the gradient of L = lp . A^P(d) + lt . A^T(d) with respect to d = (dP, dT).
+template <typename R>
+__device__ __forceinline__ void elem_picard_t(const ElemConst<R>& C, const R c, const R kc, const R u0x, const R u0y,
+                                              const R u0z, const R tau, const R lp[8], const R lt[8],
+                                              R oP[8], R oT[8]) {
+  R Mx[8], My[8], Mz[8], lv[8];
+  q1_forward(lp, C.cm, lv, Mx, My, Mz);    // lv: scratch for the (unused) lp values
+  R Nx[8], Ny[8], Nz[8];
+  q1_forward(lt, C.cm, lv, Nx, Ny, Nz);
+  const R wc = C.wih2 * c;
+  R bx[8], by[8], bz[8], A[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { bx[q] = wc * Mx[q]; by[q] = wc * My[q]; bz[q] = wc * Mz[q]; }
+  q1_test<R, false>(nullptr, bx, by, bz, C.cm, oP);
+  const R ab = -C.wih * c * C.beta;   // continuity rows into dT: A_q = -(w c beta / h) h dlp/dz
+  const R a = C.wih * C.rc;           // energy rows: B_q / h = (w rho0 c_p / h) lt*_q u0 + (w k / h^2) h grad lt
+  const R th = tau * C.ih;            // lt*_q = lt_q + tau u0 . grad lt_q
+  const R wk = C.wih2 * kc;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    A[q] = ab * Mz[q];
+    const R sq = a * (lv[q] + th * (u0x * Nx[q] + u0y * Ny[q] + u0z * Nz[q]));
+    bx[q] = sq * u0x + wk * Nx[q];
+    by[q] = sq * u0y + wk * Ny[q];
+    bz[q] = sq * u0z + wk * Nz[q];
+  }
+  q1_test<R, true>(A, bx, by, bz, C.cm, oT);
+}
+
 }  // namespace nc

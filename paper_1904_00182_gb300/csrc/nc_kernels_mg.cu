@@ -242,6 +242,53 @@ __global__ void k_level0_apply(Grid g, Phys ph, ElemConst<R> C, const typename V
   }
 }
 
+// Frozen coefficients of the Picard operator: centroid velocity u0 and tau of each element at the
+// state s (the same element state as the exact operator), as (u0x, u0y, u0z, tau).
+__global__ void k_frozen(Grid g, Phys ph, ElemConst<float> C, const float2* __restrict__ s,
+                         const float2* __restrict__ mat, float4* __restrict__ fz) {
+  NC_IJK_3D();
+  if (i >= g.nx || j >= g.ny) return;
+  const int n0 = i + g.NX * j + g.NXY * k;
+  float p[8], t[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const float2 v = s[n0 + corner_off(g, a)];
+    p[a] = v.x; t[a] = v.y;
+  }
+  const int e = i + g.nx * (j + g.ny * k);
+  ElemState<float> st;
+  elem_state(C, p, t, mat[e].x, 0.f, st);
+  fz[e] = make_float4(st.u0x, st.u0y, st.u0z, st.tau);
+}
+
+// Frozen-coefficient (Picard) finest-level operator y = A x (TR: A^T x), FP32, one thread per element.
+template <bool TR>
+__global__ void k_level0_picard(Grid g, ElemConst<float> C, const float4* __restrict__ fz,
+                                const float2* __restrict__ mat, const float2* __restrict__ x, float* __restrict__ y) {
+  NC_IJK_3D();
+  if (i >= g.nx || j >= g.ny) return;
+  const int n0 = i + g.NX * j + g.NXY * k;
+  const bool top = g.bc == kBcTop && (k + 1 == g.nz);
+  float dp[8], dt[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    if (top && (a >> 2)) { dp[a] = 0.f; dt[a] = 0.f; }
+    else { const float2 w = x[n0 + corner_off(g, a)]; dp[a] = w.x; dt[a] = w.y; }
+  }
+  const int e = i + g.nx * (j + g.ny * k);
+  const float2 m = mat[e];
+  const float4 f = fz[e];
+  const float c = m.x * C.imu;
+  float oP[8], oT[8];
+  if (TR) elem_picard_t<float>(C, c, m.y, f.x, f.y, f.z, f.w, dp, dt, oP, oT);
+  else elem_picard<float>(C, c, m.y, f.x, f.y, f.z, f.w, dp, dt, oP, oT);
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    if (top && (a >> 2)) continue;
+    atomic_add_pair(y + 2 * (n0 + corner_off(g, a)), oP[a], oT[a]);
+  }
+}
+
 template <typename R, bool TR, bool FIRST>
 __global__ void k_jacobi(long long nn, const R* __restrict__ dinv, const typename Vec2<R>::type* __restrict__ b,
                          const typename Vec2<R>::type* __restrict__ y, const typename Vec2<R>::type* __restrict__ x,
@@ -952,6 +999,33 @@ cudaError_t launch_level0_apply(const Grid& g, const Phys& ph, const typename Ve
     c->launches += 1;
     c->bytes += sizeof(R) * (6.0 * g.nn + 2.0 * g.ne);   // s, x, y per node; (kappa, k) per element
     c->flops += (kFlopsState + (transpose ? kFlopsJtv : kFlopsJv)) * g.ne;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frozen(const Grid& g, const Phys& ph, const float2* s, const float2* mat, float4* fz,
+                          cudaStream_t st, Counters* c) {
+  const Launch3 L = launch_elems(g);
+  k_frozen<<<L.grid, L.block, 0, st>>>(g, ph, make_econst<float>(ph), s, mat, fz);
+  if (c) {
+    c->launches += 1;
+    c->bytes += 8.0 * g.nn + 24.0 * g.ne;
+    c->flops += kFlopsState * g.ne;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_level0_picard(const Grid& g, const Phys& ph, const float4* fz, const float2* mat, const float2* x,
+                                 float2* y, bool transpose, cudaStream_t st, Counters* c) {
+  cudaError_t err = cudaMemsetAsync(y, 0, sizeof(float) * 2 * g.nn, st);
+  if (err != cudaSuccess) return err;
+  const Launch3 L = launch_elems(g);
+  if (transpose) k_level0_picard<true><<<L.grid, L.block, 0, st>>>(g, make_econst<float>(ph), fz, mat, x, (float*)y);
+  else k_level0_picard<false><<<L.grid, L.block, 0, st>>>(g, make_econst<float>(ph), fz, mat, x, (float*)y);
+  if (c) {
+    c->launches += 1;
+    c->bytes += 4.0 * (4.0 * g.nn + 6.0 * g.ne);   // x, y per node; (kappa, k), (u0, tau) per element
+    c->flops += (transpose ? kFlopsPicardT : kFlopsPicard) * g.ne;
   }
   return cudaGetLastError();
 }

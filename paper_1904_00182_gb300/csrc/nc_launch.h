@@ -71,6 +71,8 @@ struct Counters {
 // column (the mean of the 8 P and 8 T columns).
 const double kFlopsResidual = 629.0, kFlopsState = 290.0, kFlopsJv = 743.0, kFlopsJtv = 778.0,
              kFlopsSens = 878.0, kFlopsJacColumn = 608.0;
+// Frozen-coefficient (Picard) element operator and its transpose.
+const double kFlopsPicard = 576.0, kFlopsPicardT = 578.0;
 // The same element code in double-float arithmetic, in FP32 flops: a double-float sum is 11 FP32
 // additions, a product 1 multiplication + 3 FMAs + 3 additions (10 flops). Adds / multiplies per
 // element: residual 351 / 278, element state 167 / 123, J^T w part 399 / 379, with design
@@ -253,6 +255,12 @@ cudaError_t launch_galerkin_coarse(const Grid& gf, const Grid& gc, const R* ebe_
 template <typename R>
 cudaError_t launch_invert_diag(const Grid& g, R* diag, int* flag, cudaStream_t st, Counters* c);
 // y = A x on the finest level: matrix-free J(s) (or J^T).
+// Frozen coefficients (u0x, u0y, u0z, tau) per element of the Picard operator at the FP32 state s.
+cudaError_t launch_frozen(const Grid& g, const Phys& ph, const float2* s, const float2* mat, float4* fz,
+                          cudaStream_t st, Counters* c);
+// y = A x (transpose: A^T x) with the frozen-coefficient (Picard) finest-level operator, FP32.
+cudaError_t launch_level0_picard(const Grid& g, const Phys& ph, const float4* fz, const float2* mat, const float2* x,
+                                 float2* y, bool transpose, cudaStream_t st, Counters* c);
 template <typename R>
 cudaError_t launch_level0_apply(const Grid& g, const Phys& ph, const typename Vec2<R>::type* s,
                                 const typename Vec2<R>::type* mat, const typename Vec2<R>::type* x,

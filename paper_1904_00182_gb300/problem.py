@@ -195,6 +195,13 @@ class Problem:
         self._check(self.lib.nc_apply_jacobian(self.h, _ptr(s), _ptr(v), _ptr(out), precision))
         return out
 
+    def apply_picard(self, s, v, transpose=False):
+        """The frozen-coefficient finest-level multigrid operator (FP32) at s applied to v (or its transpose)."""
+        s, v = _as_f64(s), _as_f64(v)
+        out = self._empty(2 * self.nn)
+        self._check(self.lib.nc_apply_picard(self.h, _ptr(s), _ptr(v), _ptr(out), 1 if transpose else 0))
+        return out
+
     def apply_jacobian_transpose(self, s, w):
         s, w = _as_f64(s), _as_f64(w)
         out = self._empty(2 * self.nn)

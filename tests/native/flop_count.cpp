@@ -65,5 +65,9 @@ int main() {
   show("sens");
   for (int col = 0; col < 16; ++col) elem_jac_column<Cnt>(C, st, Cnt(2.0), col, oP, oT);
   show("jac16");
+  elem_picard<Cnt>(C, Cnt(1e-3), Cnt(2.0), Cnt(0.1), Cnt(0.2), Cnt(0.3), Cnt(0.01), dp, dt, oP, oT);
+  show("picard");
+  elem_picard_t<Cnt>(C, Cnt(1e-3), Cnt(2.0), Cnt(0.1), Cnt(0.2), Cnt(0.3), Cnt(0.01), dp, dt, oP, oT);
+  show("picard_t");
   return 0;
 }

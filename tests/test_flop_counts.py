@@ -42,6 +42,8 @@ def test_flop_constants_match_the_element_code(tmp_path):
     assert vals["kFlopsJtv"] == tot["jtv"]
     assert vals["kFlopsSens"] == tot["sens"]
     assert vals["kFlopsJacColumn"] == tot["jac16"] / 16
+    assert vals["kFlopsPicard"] == tot["picard"]
+    assert vals["kFlopsPicardT"] == tot["picard_t"]
     assert df["kFlopsResidualDF"] == cnt["residual"]
     assert df["kFlopsStateDF"] == cnt["state"]
     assert df["kFlopsJtvDF"] == cnt["jtv"]

@@ -133,7 +133,8 @@ def test_double_float_outer_operators(lib, shape, alpha, seed):
 # (double-float outer residuals, FP32 Krylov basis)
 VARIANTS = {"fp64": (1, 1e-8, {}), "mixed": (0, 1e-6, {}),
             "mixed_fp64_refinement": (0, 1e-6, {"adjoint_df64_steps": 0}),
-            "mixed_fast": (0, 1e-6, {"outer_arith": 0, "krylov_basis": 1})}
+            "mixed_fast": (0, 1e-6, {"outer_arith": 0, "krylov_basis": 1}),
+            "mixed_picard": (0, 1e-6, {"mg_op0": 1})}
 
 
 @pytest.mark.parametrize("shape,alpha,seed", CASES)
