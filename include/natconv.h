@@ -170,6 +170,8 @@ typedef struct {
   double heat_radius, design_radius; /* NC_REGION_CYLINDER: radii in element sizes [0, 0] */
   int heat_z0;          /* NC_REGION_CYLINDER: first element layer of both regions [0] */
   int mg_op0;           /* NC_PREC_MIXED only: NC_MGOP_EXACT or NC_MGOP_PICARD [NC_MGOP_EXACT] */
+  int mg_tail_ctas;     /* CTAs (1024 threads each) of the thread-block cluster that runs the fused
+                           multigrid tail, 1..16; 0: the largest cluster the device schedules [0] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */

@@ -498,7 +498,7 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
       tl.g = dq.g; tl.S = dq.S; tl.dinv = dq.dinv; tl.x = dq.x; tl.xn = dq.xn; tl.b = dq.b;
     }
     a.nlev = L - l; a.Ac = mg.Ac; a.Ainv32 = mg.Ainv32; a.cw = mg.cw; a.nf = mg.nf;
-    a.omega = om; a.nu1 = nu1; a.nu2 = nu2;
+    a.omega = om; a.nu1 = nu1; a.nu2 = nu2; a.ctas = pb->par.mg_tail_ctas;
     PCK(NC_PROF_MG_TAIL, launch_mg_tail<R>(a, tr, pb->st, &pb->cnt));
     for (int q = l; q < L - 1; ++q)
       for (int sw = 0; sw < (nu1 - 1) + nu2; ++sw) std::swap(mg.lev[q].x, mg.lev[q].xn);
@@ -947,6 +947,7 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (!(p->mg_reuse_below >= 0.0)) { *why = "mg_reuse_below must be >= 0"; return NC_ERR_ARG; }
   if (p->adjoint_df64_steps != 0 && p->adjoint_df64_steps != 1) { *why = "adjoint_df64_steps must be 0 or 1"; return NC_ERR_ARG; }
   if (p->mg_op0 != NC_MGOP_EXACT && p->mg_op0 != NC_MGOP_PICARD) { *why = "unknown mg_op0"; return NC_ERR_ARG; }
+  if (p->mg_tail_ctas < 0 || p->mg_tail_ctas > 16) { *why = "mg_tail_ctas must be in [0, 16]"; return NC_ERR_ARG; }
   if (p->coarse_refactor < 0 || p->coarse_refactor > 2) { *why = "coarse_refactor must be 0, 1 or 2"; return NC_ERR_ARG; }
   if (!(p->newton_rtol > 0) || p->newton_maxit < 0 || p->krylov_maxit < 1) { *why = "bad tolerances"; return NC_ERR_ARG; }
   if (!(p->filter_radius >= 0) || !(p->filter_rtol > 0)) { *why = "bad filter parameters"; return NC_ERR_ARG; }

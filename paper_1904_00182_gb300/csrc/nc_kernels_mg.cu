@@ -1241,7 +1241,8 @@ static int tail_cluster_size() {
 template <typename R>
 cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st, Counters* c) {
   if (a.nlev < 2 || a.nlev > kTailMaxLevels || a.nf > kMaxCoarseDofs) return cudaErrorInvalidValue;
-  const int cs = transpose ? tail_cluster_size<R, true>() : tail_cluster_size<R, false>();
+  const int cmax = transpose ? tail_cluster_size<R, true>() : tail_cluster_size<R, false>();
+  const int cs = a.ctas > 0 ? std::min(a.ctas, cmax) : cmax;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;

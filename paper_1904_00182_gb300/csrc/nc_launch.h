@@ -237,6 +237,7 @@ template <typename R> struct TailArgs {
   int nf;
   R omega;
   int nu1, nu2;
+  int ctas;     // CTAs of the cluster (1..16); 0: the largest cluster the device schedules (16, else 8)
 };
 template <typename R>
 cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st, Counters* c);

@@ -44,7 +44,7 @@ def test_picard_operator_and_transpose(lib, shape, alpha, seed, bc):
     n = op.mesh.n_nodes
     for trial in range(2):
         s = np.empty(2 * n)
-        s[0::2] = 1.0 / op.par.kappa_f * rng.standard_normal(n)   # Darcy speeds of order one
+        s[0::2] = 5.0 / op.par.kappa_f * rng.standard_normal(n)   # Darcy speeds of order one and above
         s[1::2] = rng.random(n)
         s[op.dir_mask] = 0.0
         v = rng.standard_normal(2 * n)
