@@ -172,6 +172,9 @@ typedef struct {
   int mg_op0;           /* NC_PREC_MIXED only: NC_MGOP_EXACT or NC_MGOP_PICARD [NC_MGOP_EXACT] */
   int mg_tail_ctas;     /* CTAs (1024 threads each) of the thread-block cluster that runs the fused
                            multigrid tail, 1..16; 0: the largest cluster the device schedules [0] */
+  int elem_chunk;       /* FP32 finest-level operators (Krylov operator and multigrid level 0): elements
+                           per thread along z, each thread walking a column of elements (1, 2, 4, 8, 16;
+                           0: 4), or -1: one thread per element [0] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */

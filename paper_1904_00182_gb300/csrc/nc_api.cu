@@ -361,7 +361,7 @@ nc_status outer_op(nc_problem* pb, bool transpose, bool fp32, const double* x, d
   if (fp32) {
     PCK(NC_PROF_OUTER_OP32, launch_cast_d2f((float*)pb->v32, x, 2 * g.nn, pb->st, &pb->cnt));
     PCK(NC_PROF_OUTER_OP32, launch_level0_apply<float>(g, pb->ph, pb->s32, pb->mat32, pb->v32, pb->y32, transpose,
-                                                       pb->st, &pb->cnt));
+                                                       pb->st, &pb->cnt, pb->par.elem_chunk));
     PCK(NC_PROF_OUTER_OP32, launch_cast_f2d(y, (const float*)pb->y32, 2 * g.nn, pb->st, &pb->cnt));
   } else {
     if (transpose) PCK(NC_PROF_OUTER_OP64, launch_jtv_f64(g, pb->ph, pb->s, pb->mat, (const double2*)x, y, nullptr, pb->st, &pb->cnt));
@@ -457,11 +457,11 @@ nc_status level_apply(nc_problem* pb, int l, bool tr, const typename Vec2<R>::ty
   if (l != 0) return fail(pb, NC_ERR_ARG, "level_apply is for the finest level");
   if constexpr (std::is_same<R, float>::value) {
     if (pb->par.mg_op0 == NC_MGOP_PICARD) {
-      PCK(NC_PROF_MG_OP0_PICARD, launch_level0_picard(mg.lev[0].g, pb->ph, pb->fz, pb->mat32, x, y, tr, pb->st, &pb->cnt));
+      PCK(NC_PROF_MG_OP0_PICARD, launch_level0_picard(mg.lev[0].g, pb->ph, pb->fz, pb->mat32, x, y, tr, pb->st, &pb->cnt, pb->par.elem_chunk));
       return NC_OK;
     }
   }
-  PCK(NC_PROF_MG_OP0, launch_level0_apply<R>(mg.lev[0].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), x, y, tr, pb->st, &pb->cnt));
+  PCK(NC_PROF_MG_OP0, launch_level0_apply<R>(mg.lev[0].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), x, y, tr, pb->st, &pb->cnt, pb->par.elem_chunk));
   return NC_OK;
 }
 
@@ -603,7 +603,7 @@ nc_status kry_precondition(nc_problem* pb, bool tr, const double* v, double* z) 
 nc_status kry_op(nc_problem* pb, bool tr, bool fp32, const float* z, float* w) {
   (void)fp32;
   PCK(NC_PROF_OUTER_OP32, launch_level0_apply<float>(pb->g, pb->ph, pb->s32, pb->mat32, (const float2*)z, (float2*)w,
-                                                     tr, pb->st, &pb->cnt));
+                                                     tr, pb->st, &pb->cnt, pb->par.elem_chunk));
   if (pb->g.bc != kBcTop) PCK(NC_PROF_OTHER, launch_zero_dirichlet(pb->g, w, pb->st, &pb->cnt));
   return NC_OK;
 }
@@ -614,7 +614,7 @@ nc_status kry_op(nc_problem* pb, bool tr, bool fp32, const double* z, double* w)
     // finest level's x) is still in the hierarchy, so the operator reads it without a cast
     const Grid& g = pb->g;
     PCK(NC_PROF_OUTER_OP32, launch_level0_apply<float>(g, pb->ph, pb->s32, pb->mat32, pb->mg32.lev[0].x, pb->y32, tr,
-                                                       pb->st, &pb->cnt));
+                                                       pb->st, &pb->cnt, pb->par.elem_chunk));
     PCK(NC_PROF_OUTER_OP32, launch_cast_f2d(w, (const float*)pb->y32, 2 * g.nn, pb->st, &pb->cnt));
     if (g.bc != kBcTop) PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, w, pb->st, &pb->cnt));
     return NC_OK;
@@ -948,6 +948,8 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (p->adjoint_df64_steps != 0 && p->adjoint_df64_steps != 1) { *why = "adjoint_df64_steps must be 0 or 1"; return NC_ERR_ARG; }
   if (p->mg_op0 != NC_MGOP_EXACT && p->mg_op0 != NC_MGOP_PICARD) { *why = "unknown mg_op0"; return NC_ERR_ARG; }
   if (p->mg_tail_ctas < 0 || p->mg_tail_ctas > 16) { *why = "mg_tail_ctas must be in [0, 16]"; return NC_ERR_ARG; }
+  if (p->elem_chunk != -1 && p->elem_chunk != 0 && p->elem_chunk != 1 && p->elem_chunk != 2 && p->elem_chunk != 4 &&
+      p->elem_chunk != 8 && p->elem_chunk != 16) { *why = "elem_chunk must be -1, 0, 1, 2, 4, 8 or 16"; return NC_ERR_ARG; }
   if (p->coarse_refactor < 0 || p->coarse_refactor > 2) { *why = "coarse_refactor must be 0, 1 or 2"; return NC_ERR_ARG; }
   if (!(p->newton_rtol > 0) || p->newton_maxit < 0 || p->krylov_maxit < 1) { *why = "bad tolerances"; return NC_ERR_ARG; }
   if (!(p->filter_radius >= 0) || !(p->filter_rtol > 0)) { *why = "bad filter parameters"; return NC_ERR_ARG; }
@@ -1576,7 +1578,7 @@ nc_status nc_apply_picard(nc_problem* pb, const double* s, const double* v, doub
   PCK(NC_PROF_OTHER, launch_cast_d2f((float*)pb->s32, (const double*)pb->s_try, n, pb->st, &pb->cnt));
   PCK(NC_PROF_OTHER, launch_frozen(g, pb->ph, pb->s32, pb->mat32, pb->fz, pb->st, &pb->cnt));
   PCK(NC_PROF_OTHER, launch_cast_d2f((float*)pb->v32, pb->w, n, pb->st, &pb->cnt));
-  PCK(NC_PROF_OTHER, launch_level0_picard(g, pb->ph, pb->fz, pb->mat32, pb->v32, pb->y32, transpose != 0, pb->st, &pb->cnt));
+  PCK(NC_PROF_OTHER, launch_level0_picard(g, pb->ph, pb->fz, pb->mat32, pb->v32, pb->y32, transpose != 0, pb->st, &pb->cnt, pb->par.elem_chunk));
   PCK(NC_PROF_OTHER, launch_cast_f2d(pb->R_try, (const float*)pb->y32, n, pb->st, &pb->cnt));
   PCK(NC_PROF_OTHER, launch_zero_dirichlet(g, pb->R_try, pb->st, &pb->cnt));
   CKS(copy_out(pb, out, pb->R_try, sizeof(double) * n));

@@ -14,6 +14,7 @@
 #include <cooperative_groups.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "nc_launch.h"
 
@@ -288,6 +289,125 @@ __global__ void k_level0_picard(Grid g, ElemConst<float> C, const float4* __rest
     atomic_add_pair(y + 2 * (n0 + corner_off(g, a)), oP[a], oT[a]);
   }
 }
+
+// ---- finest-level operators, column-walking form (FP32) -----------------------------------------
+// One thread per (i, j) column of elements walks KC elements up in z. The node plane an element
+// shares with the one below is kept in registers: its 4 corner values (x, and the state s of the
+// exact operator) are loaded once, and the contributions of both elements to its rows are summed in
+// registers before they leave the thread. A plane leaves as the (i, j) and (i, j + 1) nodes of each
+// lane, the x-neighbour's (i + 1) contributions added by a warp shuffle, so about 2 float2 atomic
+// adds per element remain instead of 8. Warps are one row (fixed j) of 32 columns.
+// MODE 0: the exact Jacobian J(s) (TR: J^T) at the state s; MODE 1: the frozen-coefficient operator.
+
+// Adds the plane totals aP, aT (corners ax + 2 ay of this lane's column) into y at plane kp.
+__device__ __forceinline__ void emit_plane(const Grid& g, float* __restrict__ y, int lane, int i, int j, int kp,
+                                           const float aP[4], const float aT[4]) {
+  const int base = i + g.NX * j + g.NXY * kp;
+#pragma unroll
+  for (int ay = 0; ay < 2; ++ay) {
+    const float lP = __shfl_up_sync(0xffffffffu, aP[1 + 2 * ay], 1);
+    const float lT = __shfl_up_sync(0xffffffffu, aT[1 + 2 * ay], 1);
+    float vP = aP[2 * ay], vT = aT[2 * ay];
+    if (lane > 0) { vP += lP; vT += lT; }
+    const int n = base + ay * g.NX;
+    if (i <= g.nx) atomic_add_pair(y + 2 * n, vP, vT);
+    if (lane == 31 && i < g.nx) atomic_add_pair(y + 2 * (n + 1), aP[1 + 2 * ay], aT[1 + 2 * ay]);
+  }
+}
+
+template <int MODE, bool TR, int KC>
+__global__ void __launch_bounds__(128) k_level0_z(Grid g, Phys ph, ElemConst<float> C, const float2* __restrict__ s,
+                                                  const float4* __restrict__ fz, const float2* __restrict__ mat,
+                                                  const float2* __restrict__ x, float* __restrict__ y) {
+  const int lane = threadIdx.x;
+  const int i = blockIdx.x * 32 + lane;
+  const int j = blockIdx.y * 4 + threadIdx.y;
+  if (j >= g.ny) return;                     // whole warps
+  const bool act = i < g.nx;
+  const int k0 = blockIdx.z * KC;
+  const int k1 = min(k0 + KC, g.nz);
+  const bool bctop = g.bc == kBcTop;
+  const int col = i + g.NX * j;
+  float dpb[4], dtb[4], pb[4], tb[4];         // bottom-plane corners (ax + 2 ay) of x and s
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    dpb[c] = dtb[c] = pb[c] = tb[c] = 0.f;
+    if (act) {
+      const int n = col + (c & 1) + (c >> 1) * g.NX + k0 * g.NXY;
+      const float2 w = x[n];
+      dpb[c] = w.x; dtb[c] = w.y;
+      if (MODE == 0) { const float2 v = s[n]; pb[c] = v.x; tb[c] = v.y; }
+    }
+  }
+  float aP[4] = {0.f, 0.f, 0.f, 0.f}, aT[4] = {0.f, 0.f, 0.f, 0.f};   // the element below's share of the bottom plane
+  for (int k = k0; k < k1; ++k) {
+    float dp[8], dt[8], oP[8], oT[8];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { dp[c] = dpb[c]; dt[c] = dtb[c]; }
+    const bool topx = bctop && k + 1 == g.nz;   // Dirichlet plane above: direction entries are 0 there
+    float p[8], t[8];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      dp[4 + c] = dt[4 + c] = 0.f;
+      p[4 + c] = t[4 + c] = 0.f;
+      p[c] = pb[c]; t[c] = tb[c];
+      if (act) {
+        const int n = col + (c & 1) + (c >> 1) * g.NX + (k + 1) * g.NXY;
+        if (!topx) { const float2 w = x[n]; dp[4 + c] = w.x; dt[4 + c] = w.y; }
+        if (MODE == 0) { const float2 v = s[n]; p[4 + c] = v.x; t[4 + c] = v.y; }
+      }
+    }
+    if (act) {
+      const int e = i + g.nx * (j + g.ny * k);
+      const float2 m = mat[e];
+      if (MODE == 0) {
+        ElemState<float> st;
+        elem_state(C, p, t, m.x, elem_heated(ph, i, j, k) ? (float)ph.Q : 0.f, st);
+        if (TR) elem_jtv<float, false>(C, st, m.y, dp, dt, oP, oT, nullptr, nullptr);
+        else elem_jv_dir<float>(C, st, m.y, dp, dt, oP, oT);
+      } else {
+        const float4 f = fz[e];
+        const float c = m.x * C.imu;
+        if (TR) elem_picard_t<float>(C, c, m.y, f.x, f.y, f.z, f.w, dp, dt, oP, oT);
+        else elem_picard<float>(C, c, m.y, f.x, f.y, f.z, f.w, dp, dt, oP, oT);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 8; ++a) { oP[a] = 0.f; oT[a] = 0.f; }
+    }
+    float tP[4], tT[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { tP[c] = aP[c] + oP[c]; tT[c] = aT[c] + oT[c]; }
+    emit_plane(g, y, lane, i, j, k, tP, tT);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      aP[c] = oP[4 + c]; aT[c] = oT[4 + c];
+      dpb[c] = dp[4 + c]; dtb[c] = dt[4 + c];
+      pb[c] = p[4 + c]; tb[c] = t[4 + c];
+    }
+  }
+  if (!(bctop && k1 == g.nz)) emit_plane(g, y, lane, i, j, k1, aP, aT);
+}
+
+template <int MODE, bool TR>
+static void launch_level0_z(const Grid& g, const Phys& ph, const float2* s, const float4* fz, const float2* mat,
+                            const float2* x, float* y, int kc, cudaStream_t st) {
+  const dim3 block(32, 4, 1);
+  const unsigned gx = (unsigned)((g.nx + 31) / 32), gy = (unsigned)((g.ny + 3) / 4);
+  const ElemConst<float> C = make_econst<float>(ph);
+#define NC_L0Z(KC) k_level0_z<MODE, TR, KC><<<dim3(gx, gy, (unsigned)((g.nz + KC - 1) / KC)), block, 0, st>>>(g, ph, C, s, fz, mat, x, y)
+  switch (kc) {
+    case 1: NC_L0Z(1); break;
+    case 2: NC_L0Z(2); break;
+    case 8: NC_L0Z(8); break;
+    case 16: NC_L0Z(16); break;
+    default: NC_L0Z(4); break;
+  }
+#undef NC_L0Z
+}
+
+// Elements per thread along z of the column-walking kernels: 0 picks 4.
+static int level0_kc(int requested) { return requested > 0 ? requested : 4; }
 
 template <typename R, bool TR, bool FIRST>
 __global__ void k_jacobi(long long nn, const R* __restrict__ dinv, const typename Vec2<R>::type* __restrict__ b,
@@ -987,14 +1107,24 @@ cudaError_t launch_invert_diag(const Grid& g, R* diag, int* flag, cudaStream_t s
 template <typename R>
 cudaError_t launch_level0_apply(const Grid& g, const Phys& ph, const typename Vec2<R>::type* s,
                                 const typename Vec2<R>::type* mat, const typename Vec2<R>::type* x,
-                                typename Vec2<R>::type* y, bool transpose, cudaStream_t st, Counters* c) {
+                                typename Vec2<R>::type* y, bool transpose, cudaStream_t st, Counters* c, int kc) {
   cudaError_t err = cudaMemsetAsync(y, 0, sizeof(R) * 2 * g.nn, st);
   if (err != cudaSuccess) return err;
-  const Launch3 L = launch_elems(g);
-  if (transpose)
-    k_level0_apply<R, true><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, x, (R*)y);
-  else
-    k_level0_apply<R, false><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, x, (R*)y);
+  bool done = false;
+  if constexpr (std::is_same<R, float>::value) {
+    if (kc >= 0) {
+      if (transpose) launch_level0_z<0, true>(g, ph, s, nullptr, mat, x, (float*)y, level0_kc(kc), st);
+      else launch_level0_z<0, false>(g, ph, s, nullptr, mat, x, (float*)y, level0_kc(kc), st);
+      done = true;
+    }
+  }
+  if (!done) {
+    const Launch3 L = launch_elems(g);
+    if (transpose)
+      k_level0_apply<R, true><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, x, (R*)y);
+    else
+      k_level0_apply<R, false><<<L.grid, L.block, 0, st>>>(g, ph, make_econst<R>(ph), s, mat, x, (R*)y);
+  }
   if (c) {
     c->launches += 1;
     c->bytes += sizeof(R) * (6.0 * g.nn + 2.0 * g.ne);   // s, x, y per node; (kappa, k) per element
@@ -1016,12 +1146,17 @@ cudaError_t launch_frozen(const Grid& g, const Phys& ph, const float2* s, const 
 }
 
 cudaError_t launch_level0_picard(const Grid& g, const Phys& ph, const float4* fz, const float2* mat, const float2* x,
-                                 float2* y, bool transpose, cudaStream_t st, Counters* c) {
+                                 float2* y, bool transpose, cudaStream_t st, Counters* c, int kc) {
   cudaError_t err = cudaMemsetAsync(y, 0, sizeof(float) * 2 * g.nn, st);
   if (err != cudaSuccess) return err;
-  const Launch3 L = launch_elems(g);
-  if (transpose) k_level0_picard<true><<<L.grid, L.block, 0, st>>>(g, make_econst<float>(ph), fz, mat, x, (float*)y);
-  else k_level0_picard<false><<<L.grid, L.block, 0, st>>>(g, make_econst<float>(ph), fz, mat, x, (float*)y);
+  if (kc >= 0) {
+    if (transpose) launch_level0_z<1, true>(g, ph, nullptr, fz, mat, x, (float*)y, level0_kc(kc), st);
+    else launch_level0_z<1, false>(g, ph, nullptr, fz, mat, x, (float*)y, level0_kc(kc), st);
+  } else {
+    const Launch3 L = launch_elems(g);
+    if (transpose) k_level0_picard<true><<<L.grid, L.block, 0, st>>>(g, make_econst<float>(ph), fz, mat, x, (float*)y);
+    else k_level0_picard<false><<<L.grid, L.block, 0, st>>>(g, make_econst<float>(ph), fz, mat, x, (float*)y);
+  }
   if (c) {
     c->launches += 1;
     c->bytes += 4.0 * (4.0 * g.nn + 6.0 * g.ne);   // x, y per node; (kappa, k), (u0, tau) per element
@@ -1271,7 +1406,7 @@ cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st
   template cudaError_t launch_invert_diag<R>(const Grid&, R*, int*, cudaStream_t, Counters*);                 \
   template cudaError_t launch_level0_apply<R>(const Grid&, const Phys&, const Vec2<R>::type*,                 \
                                               const Vec2<R>::type*, const Vec2<R>::type*, Vec2<R>::type*,     \
-                                              bool, cudaStream_t, Counters*);                                  \
+                                              bool, cudaStream_t, Counters*, int);                             \
   template cudaError_t launch_jacobi_update<R>(const Grid&, const R*, const Vec2<R>::type*,                   \
                                                const Vec2<R>::type*, const Vec2<R>::type*, Vec2<R>::type*, R, \
                                                bool, bool, cudaStream_t, Counters*);                           \

@@ -260,12 +260,13 @@ cudaError_t launch_invert_diag(const Grid& g, R* diag, int* flag, cudaStream_t s
 cudaError_t launch_frozen(const Grid& g, const Phys& ph, const float2* s, const float2* mat, float4* fz,
                           cudaStream_t st, Counters* c);
 // y = A x (transpose: A^T x) with the frozen-coefficient (Picard) finest-level operator, FP32.
+// kc: elements per thread along z (column walking; 0: automatic), or -1: one thread per element.
 cudaError_t launch_level0_picard(const Grid& g, const Phys& ph, const float4* fz, const float2* mat, const float2* x,
-                                 float2* y, bool transpose, cudaStream_t st, Counters* c);
+                                 float2* y, bool transpose, cudaStream_t st, Counters* c, int kc);
 template <typename R>
 cudaError_t launch_level0_apply(const Grid& g, const Phys& ph, const typename Vec2<R>::type* s,
                                 const typename Vec2<R>::type* mat, const typename Vec2<R>::type* x,
-                                typename Vec2<R>::type* y, bool transpose, cudaStream_t st, Counters* c);
+                                typename Vec2<R>::type* y, bool transpose, cudaStream_t st, Counters* c, int kc = -1);
 // x_new = x + omega D^-1 (b - y)   (y = A x; first == true: x = 0, y unused)
 template <typename R>
 cudaError_t launch_jacobi_update(const Grid& g, const R* dinv, const typename Vec2<R>::type* b,
