@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--alpha", type=float, default=1e4)
     ap.add_argument("--volfrac", type=float, default=0.2)
     ap.add_argument("--levels", type=int, default=6)
-    ap.add_argument("--mg-op0", default="exact", choices=["exact", "picard"],
+    ap.add_argument("--mg-op0", default="picard", choices=["exact", "picard"],
                     help="finest-level multigrid operator of the mixed path: the exact Jacobian or the "
                          "frozen-coefficient (Picard) operator")
     ap.add_argument("--fp64-steps", type=int, default=1)

@@ -139,7 +139,9 @@ typedef struct {
                                NC_PREC_MIXED, the adjoint tolerance with NC_PREC_FP64 [0] */
   int mg_tail_nodes;    /* the multigrid levels below the finest with at most this many nodes, down
                            to the coarsest, run as one fused kernel on a thread-block cluster (the
-                           same arithmetic as separate launches); 0: separate launches [5000] */
+                           same arithmetic as separate launches); 0: separate launches, the faster
+                           choice measured on GB300 (the fused kernel's cluster barriers between its
+                           steps cost more than the launches they save) [0] */
   double mg_reuse_below; /* a Newton step whose relative residual is at most this keeps the multigrid
                             hierarchy of the previous step (lagged preconditioner); 0: rebuild at
                             every step [1e-2] */
@@ -169,12 +171,13 @@ typedef struct {
   int region_shape;     /* NC_REGION_BOX or NC_REGION_CYLINDER [NC_REGION_BOX] */
   double heat_radius, design_radius; /* NC_REGION_CYLINDER: radii in element sizes [0, 0] */
   int heat_z0;          /* NC_REGION_CYLINDER: first element layer of both regions [0] */
-  int mg_op0;           /* NC_PREC_MIXED only: NC_MGOP_EXACT or NC_MGOP_PICARD [NC_MGOP_EXACT] */
+  int mg_op0;           /* NC_PREC_MIXED only: NC_MGOP_EXACT or NC_MGOP_PICARD [NC_MGOP_PICARD] */
   int mg_tail_ctas;     /* CTAs (1024 threads each) of the thread-block cluster that runs the fused
                            multigrid tail, 1..16; 0: the largest cluster the device schedules [0] */
-  int elem_chunk;       /* FP32 finest-level operators (Krylov operator and multigrid level 0): elements
-                           per thread along z, each thread walking a column of elements (1, 2, 4, 8, 16;
-                           0: 4), or -1: one thread per element [0] */
+  int elem_chunk;       /* FP32 finest-level operators (Krylov operator and multigrid level 0): -1 one
+                           thread per element; 1, 2, 4, 8, 16 (0: 4) elements per thread, each thread
+                           walking a column of elements with the shared node plane in registers (fewer
+                           loads and atomics, but more registers: measured slower on GB300) [-1] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */

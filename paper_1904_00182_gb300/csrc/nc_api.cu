@@ -1133,7 +1133,9 @@ nc_status nc_default_params(nc_params* p) {
   p->outer_arith = NC_ARITH_FP64;
   p->krylov_basis = NC_BASIS_FP64;
   p->krylov_reorth = 0.0;
-  p->mg_tail_nodes = 5000;
+  p->mg_tail_nodes = 0;
+  p->mg_op0 = NC_MGOP_PICARD;
+  p->elem_chunk = -1;
   p->mg_reuse_below = 1e-2;
   p->adjoint_df64_steps = 1;
   return NC_OK;

@@ -406,7 +406,7 @@ static void launch_level0_z(const Grid& g, const Phys& ph, const float2* s, cons
 #undef NC_L0Z
 }
 
-// Elements per thread along z of the column-walking kernels: 0 picks 4.
+// Elements per thread along z of the column-walking kernels (nc_params.elem_chunk >= 0): 0 picks 4.
 static int level0_kc(int requested) { return requested > 0 ? requested : 4; }
 
 template <typename R, bool TR, bool FIRST>

@@ -129,12 +129,13 @@ def test_double_float_outer_operators(lib, shape, alpha, seed):
     gp.close()
 
 
-# mixed path variants: the default (IEEE FP64 outer residuals and Krylov basis) and the fast one
-# (double-float outer residuals, FP32 Krylov basis)
+# mixed path variants: the default (IEEE FP64 outer residuals and Krylov basis, frozen-coefficient
+# finest multigrid level), the fast one (double-float outer residuals, FP32 Krylov basis) and the
+# exact Jacobian on the finest multigrid level
 VARIANTS = {"fp64": (1, 1e-8, {}), "mixed": (0, 1e-6, {}),
             "mixed_fp64_refinement": (0, 1e-6, {"adjoint_df64_steps": 0}),
             "mixed_fast": (0, 1e-6, {"outer_arith": 0, "krylov_basis": 1}),
-            "mixed_picard": (0, 1e-6, {"mg_op0": 1})}
+            "mixed_exact_mg": (0, 1e-6, {"mg_op0": 0})}
 
 
 @pytest.mark.parametrize("shape,alpha,seed", CASES)
