@@ -285,14 +285,18 @@ ALU_CLASSES = {"mg_op0": "fp32", "outer_op32": "fp32", "mg_setup_fine": "fp32",
 # library then counts their FP32 operations (a double-float add 11, a multiply 10 flops).
 DF64_CLASSES = ("residual", "outer_op64", "sens")
 ALU_PEAK_TFLOPS = {"fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "fp64": 152 * 2 * 2 * 2.07e9 / 1e12}
+# classes that time one kernel (with its output clear): candidates for the dominant-kernel roofline
+SINGLE_KERNEL_CLASSES = ("residual", "outer_op64", "mg_op0", "mg_op0_picard", "mg_setup_fine", "adjoint_df64",
+                         "coarse_factor", "mg_stencil_l1", "sens")
 
 
-# DRAM bytes per launch (dram__bytes read + write) of the kernel behind a class at 128^3, default
-# mixed precision, from one ncu capture of the unchanged kernel (summaries under profiles/).
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel behind a class at
+# 128^3, from one ncu capture of the current kernel in the benchmark command (summaries under
+# profiles/); a class whose kernel changes after its capture must leave this table.
 NCU_TRAFFIC_128 = {
-    "outer_op64": (172.4e6, "profiles/k_jprod_transpose_fp64_128cubed.md"),
-    "residual": (107.5e6, "profiles/k_residual_fp64_128cubed.md"),
-    "mg_op0": (69.1e6, "profiles/k_level0_apply_float_128cubed.md"),
+    "residual": (110.47e6, "profiles/k_residual_fp64_128cubed.md"),
+    "outer_op64": (171.59e6, "profiles/k_jprod_transpose_fp64_128cubed.md"),
+    "mg_op0": (69.03e6, "profiles/k_level0_apply_float_128cubed.md"),
 }
 
 
@@ -365,7 +369,10 @@ def run_gpu(args, rank, world, local):
         step(i)
     torch.cuda.synchronize(dev)
     warm_prof = pb.profile()
-    dom = max(warm_prof, key=lambda k: warm_prof[k][0])
+    # the dominant kernel: the single-kernel class with the most device time (classes that group
+    # several kernels of many small launches are left out; timing their every launch would also
+    # perturb the timed region)
+    dom = max((k for k in warm_prof if k in SINGLE_KERNEL_CLASSES), key=lambda k: warm_prof[k][0])
     if dist:
         dist.barrier()
     pb.set_profiling(classes=[dom])
@@ -408,6 +415,16 @@ def run_gpu(args, rank, world, local):
         wall = max_over_ranks(wall, dist, dev)
         e2e = {"value": whole_job_rate(world, args.steps, wall), "unit": UNIT, "h2d_bytes_per_step": 8 * E,
                "d2h_bytes_per_step": 8 * E + 8}
+
+    # the finest-level multigrid operator (the matrix-free operator of the preconditioner) timed on its
+    # own over two more steps: every launch of its class bracketed by CUDA events on the library stream
+    l0cls = "mg_op0_picard" if args.mg_op0 == "picard" else "mg_op0"
+    pb.set_profiling(classes=[l0cls])
+    for i in range(2):
+        step(args.warmup + args.steps + i)
+    torch.cuda.synchronize(dev)
+    l0prof = pb.profile()[l0cls]
+    pb.set_profiling(False)
 
     # the same workload on the all-FP64 path (the mixed-vs-FP64 comparison) and on the fast mixed
     # variant (double-float outer residuals, FP32 Krylov basis); each on its own problem
@@ -538,16 +555,16 @@ def run_gpu(args, rank, world, local):
         peaks = json.load(fh)
     df64 = pb_params["precision"] == nc.NC_PREC_MIXED and pb_params["outer_arith"] == nc.NC_ARITH_DF64
     roof = roofline_entry(dom, prof[dom], peaks, df64) if prof[dom][1] > 0 else None
-    if roof and n == 128 and not df64 and dom in NCU_TRAFFIC_128:
-        # the element kernels gained the boundary-condition and region predicates after these captures
-        # (the same loads and stores, a few more integer compares); the counters are kept beside a
-        # null traffic until a capture of the current kernels replaces them
-        b, src = NCU_TRAFFIC_128[dom]
-        roof["traffic"] = None
-        roof["traffic_last_capture"] = {"bytes": b, "source": src,
-                                        "note": "captured before the kernel's last change; same memory accesses"}
+    def add_traffic(entry, cls):
+        if entry and n == 128 and not df64 and cls in NCU_TRAFFIC_128:
+            entry["traffic"], entry["traffic_source"] = NCU_TRAFFIC_128[cls]
+    add_traffic(roof, dom)
     if roof:
         roof["timed"] = "live, CUDA events on the library stream around every launch of this class in the timed region"
+    roof_l0 = roofline_entry(l0cls, l0prof, peaks, df64) if l0prof[1] > 0 else None
+    add_traffic(roof_l0, l0cls)
+    if roof_l0:
+        roof_l0["timed"] = "CUDA events on the library stream around every launch of this class, two steps after the timed region"
     # breakdown and per-class rooflines from the profiled warm-up steps (all classes timed)
     warm_ms = sum(v[0] for v in warm_prof.values())
     rooflines = {k: roofline_entry(k, v, peaks, df64) for k, v in warm_prof.items() if v[1] > 0}
@@ -573,7 +590,7 @@ def run_gpu(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
             "config": workload_config(args), "clocks": clk, "e2e": e2e,
-            "gpu_launches": int(l1 - l0), "roofline": roof, "cpu_baseline": cpu,
+            "gpu_launches": int(l1 - l0), "roofline": roof, "roofline_level0": roof_l0, "cpu_baseline": cpu,
             "fp64_path": fp64, "mixed_fast": fast, "concurrent": concurrent, "cavity": cavity, "serving": serving,
             "solver": solver, "kernel_time_share_warmup": breakdown, "rooflines_warmup": rooflines}
     if args.detail_out:
@@ -603,6 +620,12 @@ def compact_line(line):
         roof = {k: (_r(v) if isinstance(v, float) else v) for k, v in roof.items() if k != "timed"}
         roof["timed"] = "live CUDA events on the library stream, every launch of the class in the timed region"
     out["roofline"] = roof
+    r0 = line.get("roofline_level0")
+    if r0:
+        out["roofline_level0"] = {k: (_r(v) if isinstance(v, float) else v) for k, v in r0.items()
+                                  if k in ("bound", "kernel_class", "achieved", "peak", "unit", "frac", "traffic",
+                                           "per_launch_us", "alg_bytes_per_launch", "alg_flops_per_launch",
+                                           "hbm_frac")}
     out["cpu_baseline"] = line["cpu_baseline"]
     sv = line["solver"]
     out["solver"] = {"newton_its": sv["newton_its"], "krylov_its": sv["krylov_its"],

@@ -72,6 +72,10 @@ struct MG {
   const double* in64 = nullptr;
   double* out64 = nullptr;
   bool factored = false;   // Ainv32 holds an inverse of some earlier coarsest matrix
+  // the V-cycle below the finest level (levels 1 .. L-1) captured as a CUDA graph, per direction
+  // (0: A, 1: A^T), and the counters its launches add
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  Counters graph_cnt[2];
 };
 
 }  // namespace
@@ -475,6 +479,56 @@ int tail_level(const nc_problem* pb) {
   return 0;
 }
 
+template <typename R>
+nc_status vcycle(nc_problem* pb, int l, bool tr);
+
+// Kernel classes launched by the V-cycle below the finest level.
+const int kCoarseCycleClasses = (1 << NC_PROF_SMOOTH) | (1 << NC_PROF_MG_STENCIL) | (1 << NC_PROF_MG_STENCIL_L1) |
+                                (1 << NC_PROF_COARSE_SOLVE) | (1 << NC_PROF_MG_TAIL);
+
+void drop_graphs(nc_problem* pb) {
+  for (int t = 0; t < 2; ++t) {
+    if (pb->mg32.graph[t]) cudaGraphExecDestroy(pb->mg32.graph[t]);
+    if (pb->mg64.graph[t]) cudaGraphExecDestroy(pb->mg64.graph[t]);
+    pb->mg32.graph[t] = pb->mg64.graph[t] = nullptr;
+  }
+}
+
+// The V-cycle on levels 1 .. L-1 (called from the finest level). Its launch sequence and arguments
+// are the same at every call once the hierarchy exists (set-ups change values, not buffers), and its
+// dozens of small launches are latency bound, so it is captured once per direction as a CUDA graph
+// and replayed. Replaying is equivalent when the x / xn exchanges of a cycle leave every level's
+// pointers as they were (an even number of sweeps after the first); it is skipped while one of its
+// kernel classes is being timed (nc_set_profiling), since timing events cannot be replayed.
+template <typename R>
+nc_status coarse_cycle(nc_problem* pb, bool tr) {
+  MG<R>& mg = mg_of<R>(pb);
+  const int swaps = std::max(1, pb->par.nu_pre) - 1 + std::max(0, pb->par.nu_post);
+  if ((swaps & 1) || (pb->prof_mask & kCoarseCycleClasses)) return vcycle<R>(pb, 1, tr);
+  const int t = tr ? 1 : 0;
+  if (!mg.graph[t]) {
+    const Counters before = pb->cnt;
+    CK(cudaStreamBeginCapture(pb->st, cudaStreamCaptureModeThreadLocal));
+    const nc_status s = vcycle<R>(pb, 1, tr);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(pb->st, &gr);
+    if (s != NC_OK) { if (gr) cudaGraphDestroy(gr); return s; }
+    if (e != cudaSuccess) return cuda_fail(pb, e, "capture of the coarse V-cycle");
+    const cudaError_t ei = cudaGraphInstantiate(&mg.graph[t], gr, 0);
+    cudaGraphDestroy(gr);
+    if (ei != cudaSuccess) { mg.graph[t] = nullptr; return cuda_fail(pb, ei, "graph instantiation"); }
+    mg.graph_cnt[t].launches = pb->cnt.launches - before.launches;
+    mg.graph_cnt[t].bytes = pb->cnt.bytes - before.bytes;
+    mg.graph_cnt[t].flops = pb->cnt.flops - before.flops;
+  } else {
+    pb->cnt.launches += mg.graph_cnt[t].launches;
+    pb->cnt.bytes += mg.graph_cnt[t].bytes;
+    pb->cnt.flops += mg.graph_cnt[t].flops;
+  }
+  CK(cudaGraphLaunch(mg.graph[t], pb->st));
+  return NC_OK;
+}
+
 // V-cycle on level l: solves approximately A_l x_l = b_l; the result is left in lev[l].x.
 // Level 0 applies the matrix-free Jacobian and updates separately; coarser levels fuse the
 // stencil product with the Jacobi update or the residual.
@@ -535,7 +589,7 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
         launch_stencil_apply<R>(d.g, d.S, d.x, d.b, d.dinv, om, d.xn, tr, 1, pb->st, &pb->cnt));
     PCK(NC_PROF_SMOOTH, launch_restrict<R>(d.g, c.g, d.xn, c.b, pb->st, &pb->cnt));
   }
-  CKS(vcycle<R>(pb, l + 1, tr));
+  CKS(l == 0 ? coarse_cycle<R>(pb, tr) : vcycle<R>(pb, l + 1, tr));
   PCK(NC_PROF_SMOOTH, launch_prolong_add<R>(d.g, c.g, c.x, d.x, pb->st, &pb->cnt));
   for (int it = 0; it < nu2; ++it) CKS(sweep(it == nu2 - 1));
   return NC_OK;
@@ -1221,6 +1275,7 @@ nc_status nc_destroy_problem(nc_problem* pb) {
   DeviceGuard dg(pb->device);
   if (pb->st) cudaStreamSynchronize(pb->st);
   prof_flush(pb);
+  drop_graphs(pb);
   for (cudaEvent_t e : pb->evpool) cudaEventDestroy(e);
   for (void* q : pb->allocs) cudaFree(q);
   if (pb->hres) cudaFreeHost(pb->hres);
@@ -1241,6 +1296,7 @@ nc_status nc_set_params(nc_problem* pb, const nc_params* p) {
     return fail(pb, NC_ERR_ARG, "precision, mg_levels, restart, krylov_basis and bc are fixed at creation");
   DeviceGuard dg(pb->device);
   CKS(sync(pb, "set_params"));
+  drop_graphs(pb);   // omega, sweeps and the tail choice are arguments of the captured launches
   apply_params(pb, p);
   CK(launch_helmholtz_diag(pb->g, pb->F, pb->fdinv, pb->st));   // the filter radius may have changed
   CK(launch_cast_d2f(pb->fdinvf, pb->fdinv, pb->g.nn, pb->st, nullptr));

@@ -824,96 +824,114 @@ __global__ void k_gjm_permute(const float* __restrict__ W, int nf, const int* __
   }
 }
 
-// In-place Gauss-Jordan inversion with partial pivoting, whole matrix in shared memory (FP32,
-// nf <= NC_GJ_SMEM_MAX, rows padded to ld = a multiple of 4). Step k: pick the pivot row p >= k of
-// column k and exchange rows k and p; with r'_j = (j == k ? 1 : A[k][j]) / A[k][k] and
-// c_i = A[i][k] (c_k := -1), zero row k and column k and apply the rank-1 update A -= c r'^T. This
-// leaves r' in row k and -c_i / A[k][k] in column k, as in-place Gauss-Jordan requires. The result
-// is the inverse with its columns permuted by the row exchanges, undone at the end.
-#define NC_GJ_SMEM_MAX 224
-__global__ void __launch_bounds__(1024) k_gj32_smem(const double* __restrict__ A, float* __restrict__ Ainv32,
-                                                    int nf, int* flag) {
-  extern __shared__ float sm[];
-  const int ld = (nf + 3) & ~3;
-  float* M = sm;                     // nf x ld
-  float* rp = M + nf * ld;           // ld
-  float* cf = rp + ld;               // nf
-  int* perm = (int*)(cf + nf);       // nf
-  __shared__ float s_val[32];
-  __shared__ int s_idx[32];
-  __shared__ int s_piv;
-  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
-  const int nq = ld >> 2;            // float4 per row
-  for (int i = ty; i < nf; i += 32)
-    for (int j = tx; j < ld; j += 32) M[i * ld + j] = j < nf ? (float)A[(long long)i * nf + j] : 0.f;
-  __syncthreads();
-  for (int k = 0; k < nf; ++k) {
-    float best = -1.f;
-    int bi = nf;
-    for (int r = k + t; r < nf; r += 1024) {
-      const float v = fabsf(M[r * ld + k]);
-      if (v > best) { best = v; bi = r; }
-    }
+// In-place Gauss-Jordan inversion with partial pivoting held in registers (FP32, nf <= 224): one block
+// of 16 x 32 threads; thread (ty, tx) holds M[r][c] for the rows r = ty + 16 a (a < RA) and columns
+// c = tx + 32 b (b < CB). Pivoting is implicit (no row exchange): step k takes as pivot the row p, not
+// yet used, with the largest |M[p][k]| (ties to the lower row), forms the pivot row
+// prow = M[p] / d with prow[k] = 1 / d (d = M[p][k]), sets M[i][k] = 0 and subtracts
+// M_old[i][k] prow from every other row i, and stores prow as row p. Each warp reads its rows'
+// column-k values from lane k mod 32 by a shuffle; the pivot candidates (one per warp) and the pivot
+// row pass through double-buffered shared memory, so a step needs two barriers. With p_k the pivot of
+// step k and q its inverse permutation, the result M satisfies A^-1[q[r]][p_c] = M[r][c].
+template <int RA, int CB>
+__global__ void __launch_bounds__(512) k_gj32_reg(const double* __restrict__ A, float* __restrict__ Ainv32, int nf,
+                                                  int* flag) {
+  __shared__ float s_best[2][16], s_d[2][16];
+  __shared__ int s_row[2][16];
+  __shared__ float s_prow[2][CB * 32];
+  __shared__ int s_piv[RA * 16], s_inv[RA * 16];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float M[RA][CB];
+  unsigned used = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_down_sync(0xffffffffu, best, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  for (int a = 0; a < RA; ++a) {
+    const int r = ty + 16 * a;
+    if (r >= nf) used |= 1u << a;
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      const int c = tx + 32 * b;
+      M[a][b] = (r < nf && c < nf) ? (float)A[(long long)r * nf + c] : 0.f;
     }
-    if (tx == 0) { s_val[ty] = best; s_idx[ty] = bi; }
+  }
+  bool ok = true;
+  for (int k = 0; k < nf; ++k) {
+    const int kb = k >> 5, kl = k & 31, buf = k & 1;
+    // pivot candidate of this warp's rows: column k from lane kl
+    float best = -1.f, bd = 0.f;
+    int br = nf;
+#pragma unroll
+    for (int a = 0; a < RA; ++a) {
+      float v = 0.f;
+#pragma unroll
+      for (int b = 0; b < CB; ++b) v = (b == kb) ? M[a][b] : v;
+      const float m = __shfl_sync(0xffffffffu, v, kl);
+      const float am = fabsf(m);
+      if (!((used >> a) & 1u) && am > best) { best = am; bd = m; br = ty + 16 * a; }
+    }
+    if (tx == 0) { s_best[buf][ty] = best; s_d[buf][ty] = bd; s_row[buf][ty] = br; }
     __syncthreads();
-    if (t == 0) {
-      float bb = -1.f;
-      int bidx = nf;
-      for (int w = 0; w < 32; ++w)
-        if (s_val[w] > bb || (s_val[w] == bb && s_idx[w] < bidx)) { bb = s_val[w]; bidx = s_idx[w]; }
-      s_piv = (bb > 0.f && bidx < nf) ? bidx : -1;
-      perm[k] = bidx;
+    float pb = -1.f, d = 0.f;
+    int p = nf;
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+      const float v = s_best[buf][w];
+      const int r = s_row[buf][w];
+      if (v > pb || (v == pb && r < p)) { pb = v; p = r; d = s_d[buf][w]; }
+    }
+    if (!(pb > 0.f) || !isfinite(pb) || p >= nf) { ok = false; break; }   // the same decision in every thread
+    const float inv = 1.f / d;
+    if (ty == (p & 15)) {
+      const int ap = p >> 4;
+#pragma unroll
+      for (int b = 0; b < CB; ++b) {
+        float v = 0.f;
+#pragma unroll
+        for (int a = 0; a < RA; ++a) v = (a == ap) ? M[a][b] : v;
+        const int c = tx + 32 * b;
+        s_prow[buf][c] = (c == k) ? inv : v * inv;
+      }
+      if (tx == 0) { s_piv[k] = p; s_inv[p] = k; }
     }
     __syncthreads();
-    const int p = s_piv;
-    if (p < 0) { if (t == 0) atomicExch(flag, 1); return; }
-    // exchange rows k and p; pivot row -> rp (unscaled), old row k -> row p
-    for (int j = t; j < ld; j += 1024) {
-      const float a = M[k * ld + j], b = M[p * ld + j];
-      rp[j] = b;
-      if (p != k) M[p * ld + j] = a;
-    }
-    __syncthreads();
-    const float ipiv = 1.f / rp[k];
-    for (int i = t; i < nf; i += 1024) cf[i] = (i == k) ? -1.f : M[i * ld + k];
-    __syncthreads();
-    for (int j = t; j < ld; j += 1024) {
-      rp[j] = ((j == k) ? 1.f : rp[j]) * ipiv;
-      M[k * ld + j] = 0.f;
-    }
-    for (int i = t; i < nf; i += 1024) M[i * ld + k] = 0.f;
-    __syncthreads();
-    const float4* rp4 = reinterpret_cast<const float4*>(rp);
-    for (int i = ty; i < nf; i += 32) {
-      const float c = cf[i];
-      float4* row = reinterpret_cast<float4*>(M + i * ld);
-      for (int q = tx; q < nq; q += 32) {
-        float4 m = row[q];
-        const float4 r = rp4[q];
-        m.x -= c * r.x; m.y -= c * r.y; m.z -= c * r.z; m.w -= c * r.w;
-        row[q] = m;
+    float pr[CB];
+#pragma unroll
+    for (int b = 0; b < CB; ++b) pr[b] = s_prow[buf][tx + 32 * b];
+#pragma unroll
+    for (int a = 0; a < RA; ++a) {
+      const int r = ty + 16 * a;
+      float v = 0.f;
+#pragma unroll
+      for (int b = 0; b < CB; ++b) v = (b == kb) ? M[a][b] : v;
+      const float m = __shfl_sync(0xffffffffu, v, kl);
+      if (r == p) {
+#pragma unroll
+        for (int b = 0; b < CB; ++b) M[a][b] = pr[b];
+        used |= 1u << a;
+      } else {
+#pragma unroll
+        for (int b = 0; b < CB; ++b) {
+          const float base = (b == kb && tx == kl) ? 0.f : M[a][b];
+          M[a][b] = base - m * pr[b];
+        }
       }
     }
-    __syncthreads();
   }
-  for (int k = nf - 1; k >= 0; --k) {
-    const int p = perm[k];
-    if (p != k)
-      for (int i = t; i < nf; i += 1024) {
-        const float a = M[i * ld + k];
-        M[i * ld + k] = M[i * ld + p];
-        M[i * ld + p] = a;
-      }
-    __syncthreads();
+  if (!ok) {
+    if (tx == 0 && ty == 0) atomicExch(flag, 1);
+    return;
   }
-  for (int i = ty; i < nf; i += 32)
-    for (int j = tx; j < nf; j += 32) Ainv32[i * nf + j] = M[i * ld + j];
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    const int r = ty + 16 * a;
+    if (r >= nf) continue;
+    const int row = s_inv[r];
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      const int c = tx + 32 * b;
+      if (c < nf) Ainv32[(long long)row * nf + s_piv[c]] = M[a][b];
+    }
+  }
 }
 
 // x = A^-1 b on the free DOFs of the coarsest level (or A^-T b), in three launches:
@@ -1248,24 +1266,14 @@ cudaError_t launch_dense_assemble(const Grid& g, const R* ebe, double* A, int nf
 
 cudaError_t launch_coarse_factor(const double* A, float* work, float* Ainv32, int nf, int* flag, cudaStream_t st,
                                  Counters* c) {
-  if (nf <= NC_GJ_SMEM_MAX) {
-    const int ld = (nf + 3) & ~3;
-    const size_t sm = sizeof(float) * ((size_t)nf * ld + ld + 2 * nf);
-    static std::mutex mu;
-    static bool attr_set_dev[kMaxDevices] = {false};
-    int dev = 0;
-    cudaError_t ge = cudaGetDevice(&dev);
-    if (ge != cudaSuccess) return ge;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    bool& attr_set = attr_set_dev[dev];
-    if (!attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(k_gj32_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(sizeof(float) * (NC_GJ_SMEM_MAX * NC_GJ_SMEM_MAX + 3 * NC_GJ_SMEM_MAX)));
-      if (e != cudaSuccess) return e;
-      attr_set = true;
+  if (nf <= 224) {
+    const dim3 blk(32, 16);
+#define NC_GJR(RA) case RA: k_gj32_reg<RA, (RA + 1) / 2><<<1, blk, 0, st>>>(A, Ainv32, nf, flag); break
+    switch ((nf + 15) / 16) {   // row tiles of 16
+      NC_GJR(1); NC_GJR(2); NC_GJR(3); NC_GJR(4); NC_GJR(5); NC_GJR(6); NC_GJR(7);
+      NC_GJR(8); NC_GJR(9); NC_GJR(10); NC_GJR(11); NC_GJR(12); NC_GJR(13); default: NC_GJR(14);
     }
-    k_gj32_smem<<<1, dim3(32, 32), sm, st>>>(A, Ainv32, nf, flag);
+#undef NC_GJR
     if (c) c->launches += 1;
   } else {
     // work: W (nf x 2nf floats), then piv, used (nf ints each) and the multipliers (nf floats)
