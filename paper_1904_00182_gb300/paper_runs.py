@@ -1,0 +1,92 @@
+"""State and adjoint solves on the paper's own meshes and geometries, one GPU.
+
+* The closed-cavity benchmark of Sec. 6.1 on the meshes of Sec. 6.2 (Tables 3 and 4): the quarter
+  cavity on n x n x 2n elements for n = 80, 160, 320 (2.1 M to 131 M unknowns), alpha = 1e3 and
+  1e6, from the paper's initial design gamma = 0.05 in the design box.
+* The suspended cylinder of Sec. 7 on its 160 x 160 x 320 mesh, alpha = 1e6 (kappa_f = 0.000676 as
+  the paper sets it), from a uniform design 0.25 in the design annulus (the paper's initial design,
+  four radial fins, is not reproduced).
+
+Each case creates the problem (footprint from nc_footprint_bytes), solves the state from zero to a
+relative residual of 1e-8, then the adjoint of the mean heated-region temperature and the
+sensitivities, and prints one JSON line with the times (CUDA events on the problem's stream), the
+Newton and Krylov iterations and the device memory the problem holds. The paper ran these meshes
+with MPI domain decomposition on 16 to 640 CPU cores (Table 3); here each runs on one GPU.
+
+  python -m paper_1904_00182_gb300.paper_runs [--cases cavity80,cavity160,cavity320,cylinder160]
+"""
+
+import argparse
+import json
+import time
+
+import torch
+
+from . import _abi
+from .optimize import cavity_params, cylinder_params
+from .problem import Problem
+
+CASES = {
+    "cavity80": ("cavity", 80), "cavity160": ("cavity", 160), "cavity320": ("cavity", 320),
+    "cylinder160": ("cylinder", 160), "cylinder320": ("cylinder", 320),
+}
+
+
+def run_case(kind, n, alpha, device="cuda", **overrides):
+    geom = cavity_params(n) if kind == "cavity" else cylinder_params(n)
+    geom.update(overrides)
+    nx, ny, nz = n, n, 2 * n
+    grid = _abi.Grid(nx, ny, nz, 1.0 / nz)
+    footprint = _abi.footprint_bytes(grid, _abi.default_params(alpha=alpha, **geom))
+    stream = torch.cuda.Stream(device=device)
+    free0 = torch.cuda.mem_get_info(device)[0]
+    t0 = time.perf_counter()
+    pb = Problem(nx, ny, nz, 1.0 / nz, stream=stream.cuda_stream, device=device, alpha=alpha, timeout_s=3600.0,
+                 **geom)
+    t_create = time.perf_counter() - t0
+    held = free0 - torch.cuda.mem_get_info(device)[0]
+    ne = nx * ny * nz
+    rho = torch.full((ne,), 0.05 if kind == "cavity" else 0.25, dtype=torch.float64, device=device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    pb.set_design(rho)
+    ev[1].record(stream)
+    st = pb.solve_state()
+    ev[2].record(stream)
+    f, ast = pb.solve_adjoint()
+    pb.sensitivities()
+    ev[3].record(stream)
+    ev[3].synchronize()
+    out = {"case": "%s %dx%dx%d" % (kind, nx, ny, nz), "alpha": alpha, "elements": ne,
+           "unknowns": 2 * (nx + 1) * (ny + 1) * (nz + 1), "footprint_gib": footprint / 2 ** 30,
+           "device_memory_held_gib": held / 2 ** 30, "create_s": t_create,
+           "design_ms": ev[0].elapsed_time(ev[1]), "state_ms": ev[1].elapsed_time(ev[2]),
+           "adjoint_sens_ms": ev[2].elapsed_time(ev[3]), "newton_its": st["newton_its"],
+           "krylov_its": st["krylov_its"], "krylov_per_newton": st["krylov_hist"], "rel_residual": st["rel_residual"],
+           "adjoint_krylov_its": ast["krylov_its"], "adjoint_rel_residual": ast["rel_residual"], "f": f,
+           "mg_setups": st["mg_setups"]}
+    pb.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--cases", default="cavity80,cavity160,cylinder160")
+    ap.add_argument("--alphas", default="1e3,1e6")
+    ap.add_argument("--mg-op0", default="picard", choices=["exact", "picard"])
+    a = ap.parse_args()
+    op0 = _abi.NC_MGOP_PICARD if a.mg_op0 == "picard" else _abi.NC_MGOP_EXACT
+    for name in a.cases.split(","):
+        kind, n = CASES[name]
+        alphas = [1e6] if kind == "cylinder" else [float(x) for x in a.alphas.split(",")]
+        for alpha in alphas:
+            try:
+                rec = run_case(kind, n, alpha, mg_op0=op0)
+            except _abi.NatConvError as e:
+                rec = {"case": name, "alpha": alpha, "error": str(e)}
+            rec["mg_op0"] = a.mg_op0
+            print(json.dumps(rec), flush=True)
+
+
+if __name__ == "__main__":
+    main()
