@@ -702,7 +702,7 @@ nc_status fgmres_t(nc_problem* pb, bool tr, bool fp32, T* V, T* Z, const double*
   PCK(NC_PROF_KRYLOV_VEC, launch_scale_copy(V, b, 1.0 / beta, n, pb->st, &pb->cnt));
   PCK(NC_PROF_KRYLOV_VEC, launch_zero_dirichlet(pb->g, V, pb->st, &pb->cnt));
   int total = 0;
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m), h(m + 2), h2(m + 2);
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m), h(m + 2), h2(m + 2), resh(m);
   while (true) {
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
@@ -777,6 +777,11 @@ nc_status fgmres_t(nc_problem* pb, bool tr, bool fp32, T* V, T* Z, const double*
       const double res = std::fabs(gv[j + 1]);
       *relres_out = res / bnorm;
       if (res <= rtol * bnorm || hn == 0.0) { ++j; ++total; done = true; break; }
+      // FP64 operator: an Arnoldi estimate within a factor 100 of the tolerance that has not halved
+      // over three iterations is checked against the true residual by restarting early (near a
+      // tight tolerance the estimate can stall while the true residual keeps falling)
+      resh[j] = res;
+      if (!fp32 && j >= 3 && res < 1e2 * rtol * bnorm && res > 0.5 * resh[j - 3]) { ++j; ++total; break; }
     }
     // x += Z y, y = H^-1 g (upper triangular j x j)
     for (int i = j - 1; i >= 0; --i) {

@@ -833,6 +833,87 @@ __global__ void k_gjm_permute(const float* __restrict__ W, int nf, const int* __
 // column-k values from lane k mod 32 by a shuffle; the pivot candidates (one per warp) and the pivot
 // row pass through double-buffered shared memory, so a step needs two barriers. With p_k the pivot of
 // step k and q its inverse permutation, the result M satisfies A^-1[q[r]][p_c] = M[r][c].
+// One elimination step of k_gj32_reg for column k = 32 KB + kl (KB a compile-time column block, so
+// every register access below has a constant index). Returns false if no usable pivot is left.
+template <int RA, int CB, int KB>
+__device__ __forceinline__ bool gj_step(float (&M)[RA][CB], unsigned& used, int kl, int nf, int tx, int ty,
+                                        float (*s_best)[16], float (*s_d)[16], int (*s_row)[16],
+                                        float (*s_prow)[CB * 32], int* s_piv, int* s_inv) {
+  const int k = 32 * KB + kl, buf = k & 1;
+  // pivot candidate of this warp's rows: column k from lane kl
+  float best = -1.f, bd = 0.f;
+  int br = nf;
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    const float m = __shfl_sync(0xffffffffu, M[a][KB], kl);
+    const float am = fabsf(m);
+    if (!((used >> a) & 1u) && am > best) { best = am; bd = m; br = ty + 16 * a; }
+  }
+  if (tx == 0) { s_best[buf][ty] = best; s_d[buf][ty] = bd; s_row[buf][ty] = br; }
+  __syncthreads();
+  float pb = -1.f, d = 0.f;
+  int p = nf;
+#pragma unroll
+  for (int w = 0; w < 16; ++w) {
+    const float v = s_best[buf][w];
+    const int r = s_row[buf][w];
+    if (v > pb || (v == pb && r < p)) { pb = v; p = r; d = s_d[buf][w]; }
+  }
+  if (!(pb > 0.f) || !isfinite(pb) || p >= nf) return false;   // the same decision in every thread
+  const float inv = 1.f / d;
+  if (ty == (p & 15)) {   // the warp holding row p publishes it, scaled
+    const int ap = p >> 4;
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      float v = 0.f;
+#pragma unroll
+      for (int a = 0; a < RA; ++a) v = (a == ap) ? M[a][b] : v;
+      const int c = tx + 32 * b;
+      s_prow[buf][c] = (c == k) ? inv : v * inv;
+    }
+    if (tx == 0) { s_piv[k] = p; s_inv[p] = k; }
+  }
+  __syncthreads();
+  const float* pr = s_prow[buf] + tx;   // pivot row entries of this thread's columns: pr[32 b]
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    const float m = __shfl_sync(0xffffffffu, M[a][KB], kl);
+    if (ty + 16 * a == p) {
+#pragma unroll
+      for (int b = 0; b < CB; ++b) M[a][b] = pr[32 * b];
+      used |= 1u << a;
+    } else {
+      if (tx == kl) M[a][KB] = 0.f;
+#pragma unroll
+      for (int b = 0; b < CB; ++b) M[a][b] -= m * pr[32 * b];
+    }
+  }
+  return true;
+}
+
+template <int RA, int CB, int KB>
+__device__ __forceinline__ bool gj_block(float (&M)[RA][CB], unsigned& used, int nf, int tx, int ty,
+                                         float (*s_best)[16], float (*s_d)[16], int (*s_row)[16],
+                                         float (*s_prow)[CB * 32], int* s_piv, int* s_inv) {
+  if constexpr (KB < CB) {
+    const int kend = min(32, nf - 32 * KB);
+    for (int kl = 0; kl < kend; ++kl)
+      if (!gj_step<RA, CB, KB>(M, used, kl, nf, tx, ty, s_best, s_d, s_row, s_prow, s_piv, s_inv)) return false;
+    return gj_block<RA, CB, KB + 1>(M, used, nf, tx, ty, s_best, s_d, s_row, s_prow, s_piv, s_inv);
+  }
+  return true;
+}
+
+// In-place Gauss-Jordan inversion with partial pivoting held in registers (FP32, nf <= 224): one block
+// of 16 x 32 threads; thread (ty, tx) holds M[r][c] for the rows r = ty + 16 a (a < RA) and columns
+// c = tx + 32 b (b < CB). Pivoting is implicit (no row exchange): step k takes as pivot the row p, not
+// yet used, with the largest |M[p][k]| (ties to the lower row), forms the pivot row
+// prow = M[p] / d with prow[k] = 1 / d (d = M[p][k]), sets M[i][k] = 0 and subtracts
+// M_old[i][k] prow from every other row i, and stores prow as row p. Each warp reads its rows'
+// column-k values from lane k mod 32 by a shuffle (the steps run in blocks of 32 columns, so the
+// register holding column k is known at compile time); the pivot candidates (one per warp) and the
+// pivot row pass through double-buffered shared memory, so a step needs two barriers. With p_k the
+// pivot of step k and q its inverse permutation, the result M satisfies A^-1[q[r]][p_c] = M[r][c].
 template <int RA, int CB>
 __global__ void __launch_bounds__(512) k_gj32_reg(const double* __restrict__ A, float* __restrict__ Ainv32, int nf,
                                                   int* flag) {
@@ -853,70 +934,7 @@ __global__ void __launch_bounds__(512) k_gj32_reg(const double* __restrict__ A, 
       M[a][b] = (r < nf && c < nf) ? (float)A[(long long)r * nf + c] : 0.f;
     }
   }
-  bool ok = true;
-  for (int k = 0; k < nf; ++k) {
-    const int kb = k >> 5, kl = k & 31, buf = k & 1;
-    // pivot candidate of this warp's rows: column k from lane kl
-    float best = -1.f, bd = 0.f;
-    int br = nf;
-#pragma unroll
-    for (int a = 0; a < RA; ++a) {
-      float v = 0.f;
-#pragma unroll
-      for (int b = 0; b < CB; ++b) v = (b == kb) ? M[a][b] : v;
-      const float m = __shfl_sync(0xffffffffu, v, kl);
-      const float am = fabsf(m);
-      if (!((used >> a) & 1u) && am > best) { best = am; bd = m; br = ty + 16 * a; }
-    }
-    if (tx == 0) { s_best[buf][ty] = best; s_d[buf][ty] = bd; s_row[buf][ty] = br; }
-    __syncthreads();
-    float pb = -1.f, d = 0.f;
-    int p = nf;
-#pragma unroll
-    for (int w = 0; w < 16; ++w) {
-      const float v = s_best[buf][w];
-      const int r = s_row[buf][w];
-      if (v > pb || (v == pb && r < p)) { pb = v; p = r; d = s_d[buf][w]; }
-    }
-    if (!(pb > 0.f) || !isfinite(pb) || p >= nf) { ok = false; break; }   // the same decision in every thread
-    const float inv = 1.f / d;
-    if (ty == (p & 15)) {
-      const int ap = p >> 4;
-#pragma unroll
-      for (int b = 0; b < CB; ++b) {
-        float v = 0.f;
-#pragma unroll
-        for (int a = 0; a < RA; ++a) v = (a == ap) ? M[a][b] : v;
-        const int c = tx + 32 * b;
-        s_prow[buf][c] = (c == k) ? inv : v * inv;
-      }
-      if (tx == 0) { s_piv[k] = p; s_inv[p] = k; }
-    }
-    __syncthreads();
-    float pr[CB];
-#pragma unroll
-    for (int b = 0; b < CB; ++b) pr[b] = s_prow[buf][tx + 32 * b];
-#pragma unroll
-    for (int a = 0; a < RA; ++a) {
-      const int r = ty + 16 * a;
-      float v = 0.f;
-#pragma unroll
-      for (int b = 0; b < CB; ++b) v = (b == kb) ? M[a][b] : v;
-      const float m = __shfl_sync(0xffffffffu, v, kl);
-      if (r == p) {
-#pragma unroll
-        for (int b = 0; b < CB; ++b) M[a][b] = pr[b];
-        used |= 1u << a;
-      } else {
-#pragma unroll
-        for (int b = 0; b < CB; ++b) {
-          const float base = (b == kb && tx == kl) ? 0.f : M[a][b];
-          M[a][b] = base - m * pr[b];
-        }
-      }
-    }
-  }
-  if (!ok) {
+  if (!gj_block<RA, CB, 0>(M, used, nf, tx, ty, s_best, s_d, s_row, s_prow, s_piv, s_inv)) {
     if (tx == 0 && ty == 0) atomicExch(flag, 1);
     return;
   }
