@@ -4,15 +4,16 @@
   cavity on n x n x 2n elements for n = 80, 160, 320 (2.1 M to 131 M unknowns), alpha = 1e3 and
   1e6, from the paper's initial design gamma = 0.05 in the design box.
 * The suspended cylinder of Sec. 7 on its 160 x 160 x 320 mesh, alpha = 1e6 (kappa_f = 0.000676 as
-  the paper sets it), from a uniform design 0.25 in the design annulus (the paper's initial design,
-  four radial fins, is not reproduced).
+  the paper sets it), from an initial design of the paper's kind: four regularly spaced radial fins
+  holding the volume fraction 0.15 of the design annulus (in the quarter domain one fin on its
+  diagonal, solid, with fluid elsewhere in the annulus).
 
 Each case creates the problem (footprint from nc_footprint_bytes), solves the state from zero to a
 relative residual of 1e-8, then the adjoint of the mean heated-region temperature and the
 sensitivities, and prints one JSON line with the times (CUDA events on the problem's stream), the
 Newton and Krylov iterations and the device memory the problem holds. When Newton does not converge
-from zero, the state is reached by warm starts (Sec. 5.4) up the ladder alpha = 1e3, 1e4, 1e5 and the
-last, warm-started solve is timed. The paper ran these meshes
+from zero (the cylinder at alpha = 1e6: its linear solves stall), the state is reached by warm starts
+(Sec. 5.4) up the ladder alpha = 1e5, 2e5, 4e5, 7e5 and the last, warm-started solve is timed. The paper ran these meshes
 with MPI domain decomposition on 16 to 640 CPU cores (Table 3); here each runs on one GPU.
 
   python -m paper_1904_00182_gb300.paper_runs [--cases cavity80,cavity160,cavity320,cylinder160]
@@ -20,18 +21,34 @@ with MPI domain decomposition on 16 to 640 CPU cores (Table 3); here each runs o
 
 import argparse
 import json
+import math
 import time
 
 import torch
 
 from . import _abi
-from .optimize import cavity_params, cylinder_params
+from .optimize import cavity_params, cylinder_params, region_masks
 from .problem import Problem
 
 CASES = {
     "cavity80": ("cavity", 80), "cavity160": ("cavity", 160), "cavity320": ("cavity", 320),
     "cylinder160": ("cylinder", 160), "cylinder320": ("cylinder", 320),
 }
+
+
+def fin_design(n, params, volfrac=0.15):
+    """Initial cylinder design of Sec. 7's kind: four regularly spaced radial fins holding `volfrac` of
+    the design annulus. In the quarter domain (symmetry planes x = 0, y = 0) that is one fin along the
+    diagonal x = y, of constant thickness; heated elements 1, every other element 0."""
+    nz = 2 * n
+    design, heated = region_masks(n, n, nz, params)
+    k, j, i = torch.meshgrid(torch.arange(nz), torch.arange(n), torch.arange(n), indexing="ij")
+    dist = ((i.reshape(-1) - j.reshape(-1)).abs().double()) / math.sqrt(2.0)   # centroid distance to x = y
+    r_in, r_out = params.heat_radius, params.design_radius
+    half = 0.5 * volfrac * (math.pi / 4.0) * (r_out ** 2 - r_in ** 2) / (r_out - r_in)
+    rho = heated.double()
+    rho[design & (dist < half)] = 1.0
+    return rho
 
 
 def run_case(kind, n, alpha, device="cuda", continuation=(), **overrides):
@@ -48,7 +65,10 @@ def run_case(kind, n, alpha, device="cuda", continuation=(), **overrides):
     t_create = time.perf_counter() - t0
     held = free0 - torch.cuda.mem_get_info(device)[0]
     ne = nx * ny * nz
-    rho = torch.full((ne,), 0.05 if kind == "cavity" else 0.25, dtype=torch.float64, device=device)
+    if kind == "cavity":
+        rho = torch.full((ne,), 0.05, dtype=torch.float64, device=device)
+    else:
+        rho = fin_design(n, pb.params).to(device)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     cont = []
     for a_c in continuation:
@@ -109,7 +129,7 @@ def main():
             except _abi.NatConvError as e:
                 # from zero Newton may not reach the strongly convective state; the paper warm-starts
                 # every solve from the previous one, so climb to alpha from a weakly convective state
-                ladder = [a for a in (1e3, 1e4, 1e5) if a < alpha]
+                ladder = [a for a in (1e5, 2e5, 4e5, 7e5) if a < alpha]
                 try:
                     rec = run_case(kind, n, alpha, mg_op0=op0, continuation=ladder)
                 except _abi.NatConvError as e2:
