@@ -32,7 +32,7 @@ from .problem import Problem
 
 CASES = {
     "cavity80": ("cavity", 80), "cavity160": ("cavity", 160), "cavity320": ("cavity", 320),
-    "cylinder160": ("cylinder", 160), "cylinder320": ("cylinder", 320),
+    "cylinder80": ("cylinder", 80), "cylinder160": ("cylinder", 160), "cylinder320": ("cylinder", 320),
 }
 
 
