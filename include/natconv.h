@@ -178,6 +178,7 @@ typedef struct {
                            thread per element; 1, 2, 4, 8, 16 (0: 4) elements per thread, each thread
                            walking a column of elements with the shared node plane in registers (fewer
                            loads and atomics, but more registers: measured slower on GB300) [-1] */
+  int mg_nu_coarse;     /* post-smoothing sweeps on the multigrid levels below the finest; 0: nu_post [0] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */
