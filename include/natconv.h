@@ -178,7 +178,9 @@ typedef struct {
                            thread per element; 1, 2, 4, 8, 16 (0: 4) elements per thread, each thread
                            walking a column of elements with the shared node plane in registers (fewer
                            loads and atomics, but more registers: measured slower on GB300) [-1] */
-  int mg_nu_coarse;     /* post-smoothing sweeps on the multigrid levels below the finest; 0: nu_post [0] */
+  int mg_nu_coarse;     /* post-smoothing sweeps on the multigrid levels from mg_nu_coarse_level down
+                           to the one above the coarsest; 0: nu_post [0] */
+  int mg_nu_coarse_level; /* first level that takes mg_nu_coarse sweeps (levels >= 1; 0: 1) [0] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */

@@ -67,7 +67,7 @@ class Params(ctypes.Structure):
         ("design_ny", ctypes.c_int), ("design_nz", ctypes.c_int), ("region_shape", ctypes.c_int),
         ("heat_radius", ctypes.c_double), ("design_radius", ctypes.c_double), ("heat_z0", ctypes.c_int),
         ("mg_op0", ctypes.c_int), ("mg_tail_ctas", ctypes.c_int), ("elem_chunk", ctypes.c_int),
-        ("mg_nu_coarse", ctypes.c_int),
+        ("mg_nu_coarse", ctypes.c_int), ("mg_nu_coarse_level", ctypes.c_int),
     ]
 
     def as_dict(self):

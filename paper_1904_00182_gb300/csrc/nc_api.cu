@@ -482,9 +482,10 @@ int tail_level(const nc_problem* pb) {
 template <typename R>
 nc_status vcycle(nc_problem* pb, int l, bool tr);
 
-// Post-smoothing sweeps on the levels below the finest.
-int coarse_post_sweeps(const nc_problem* pb) {
-  return pb->par.mg_nu_coarse > 0 ? pb->par.mg_nu_coarse : std::max(0, pb->par.nu_post);
+// Post-smoothing sweeps on level l >= 1: mg_nu_coarse from level mg_nu_coarse_level on, else nu_post.
+int coarse_post_sweeps(const nc_problem* pb, int l) {
+  const int from = std::max(1, pb->par.mg_nu_coarse_level);
+  return (pb->par.mg_nu_coarse > 0 && l >= from) ? pb->par.mg_nu_coarse : std::max(0, pb->par.nu_post);
 }
 
 // Kernel classes launched by the V-cycle below the finest level.
@@ -508,8 +509,9 @@ void drop_graphs(nc_problem* pb) {
 template <typename R>
 nc_status coarse_cycle(nc_problem* pb, bool tr) {
   MG<R>& mg = mg_of<R>(pb);
-  const int swaps = std::max(1, pb->par.nu_pre) - 1 + coarse_post_sweeps(pb);
-  if ((swaps & 1) || (pb->prof_mask & kCoarseCycleClasses)) return vcycle<R>(pb, 1, tr);
+  bool odd = false;
+  for (int l = 1; l < (int)mg.lev.size() - 1; ++l) odd |= ((std::max(1, pb->par.nu_pre) - 1 + coarse_post_sweeps(pb, l)) & 1) != 0;
+  if (odd || (pb->prof_mask & kCoarseCycleClasses)) return vcycle<R>(pb, 1, tr);
   const int t = tr ? 1 : 0;
   if (!mg.graph[t]) {
     const Counters before = pb->cnt;
@@ -547,7 +549,7 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
     return NC_OK;
   }
   const R om = (R)pb->par.omega;
-  const int nu1 = std::max(1, pb->par.nu_pre), nu2 = l > 0 ? coarse_post_sweeps(pb) : std::max(0, pb->par.nu_post);
+  const int nu1 = std::max(1, pb->par.nu_pre), nu2 = l > 0 ? coarse_post_sweeps(pb, l) : std::max(0, pb->par.nu_post);
   if (l > 0 && l == tail_level(pb)) {
     // levels l .. L-1 in one cluster kernel; the host pointers follow its x / xn swaps
     TailArgs<R> a;
@@ -1013,6 +1015,7 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (p->mg_op0 != NC_MGOP_EXACT && p->mg_op0 != NC_MGOP_PICARD) { *why = "unknown mg_op0"; return NC_ERR_ARG; }
   if (p->mg_tail_ctas < 0 || p->mg_tail_ctas > 16) { *why = "mg_tail_ctas must be in [0, 16]"; return NC_ERR_ARG; }
   if (p->mg_nu_coarse < 0 || p->mg_nu_coarse > 16) { *why = "mg_nu_coarse must be in [0, 16]"; return NC_ERR_ARG; }
+  if (p->mg_nu_coarse_level < 0) { *why = "mg_nu_coarse_level must be >= 0"; return NC_ERR_ARG; }
   if (p->elem_chunk != -1 && p->elem_chunk != 0 && p->elem_chunk != 1 && p->elem_chunk != 2 && p->elem_chunk != 4 &&
       p->elem_chunk != 8 && p->elem_chunk != 16) { *why = "elem_chunk must be -1, 0, 1, 2, 4, 8 or 16"; return NC_ERR_ARG; }
   if (p->coarse_refactor < 0 || p->coarse_refactor > 2) { *why = "coarse_refactor must be 0, 1 or 2"; return NC_ERR_ARG; }
