@@ -98,7 +98,10 @@ def whole_job_rate(world, steps, seconds):
 
 # ------------------------------------------------------------------------------- clocks ------
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region. Sampling starts
+    before the region (start() waits for the first sample, so the tool's start-up is not inside it),
+    every line is stamped with its arrival time, and stop(window) keeps the samples that arrived
+    within the region's host-time window."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -113,18 +116,22 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t_end = time.perf_counter() + 5.0
+        while not self.lines and time.perf_counter() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def stop(self, window=None):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -135,7 +142,12 @@ class ClockSampler:
         self.thread.join(timeout=2)
         sm, smax, util, reasons = [], [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        lines = self.lines
+        if window is not None:
+            # a sample reports the state at its arrival, up to one period late: keep one period more
+            inside = [(t, ln) for t, ln in lines if window[0] <= t <= window[1] + 0.05]
+            lines = inside or lines
+        for _, ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 10:
                 continue
@@ -384,14 +396,16 @@ def run_gpu(args, rank, world, local):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
+    th0 = time.perf_counter()
     ev0.record(stream)
     for i in range(args.steps):
         step(args.warmup + i)
     ev1.record(stream)
     ev1.synchronize()
     torch.cuda.synchronize(dev)
+    th1 = time.perf_counter()
     ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop()
+    clk = clocks.stop((th0, th1))
     l1, _ = pb.counters()
     prof = pb.profile()
     pb.set_profiling(False)
