@@ -340,6 +340,7 @@ def run_gpu(args, rank, world, local):
     import torch
     import paper_1904_00182_gb300 as nc
     from paper_1904_00182_gb300 import build as ncbuild
+    from paper_1904_00182_gb300.presets import solver_settings
 
     ncbuild.build()
     torch.cuda.set_device(local)
@@ -524,9 +525,10 @@ def run_gpu(args, rank, world, local):
         for alpha_c in (1e3, 1e6):
             pcv = nc.Problem(80, 80, 160, 1.0 / 160, stream=stream.cuda_stream, device=dev, alpha=alpha_c,
                              Q=1e4, bc=nc.NC_BC_CAVITY, heat_nx=8, heat_ny=8, heated_layers=8, design_nx=60,
-                             design_ny=60, design_nz=120, timeout_s=60.0, mg_op0=mg_op0)
+                             design_ny=60, design_nz=120, timeout_s=60.0, mg_op0=mg_op0,
+                             **solver_settings(alpha_c))
             rho_c = torch.full((80 * 80 * 160,), 0.05, dtype=torch.float64, device=dev)
-            entry = {"alpha": alpha_c, "grid": [80, 80, 160]}
+            entry = {"alpha": alpha_c, "grid": [80, 80, 160], "settings": solver_settings(alpha_c)}
             try:
                 pcv.set_design(rho_c)
                 pcv.solve_state()
@@ -663,7 +665,8 @@ def compact_line(line):
     if c:
         out["concurrent"] = {"in_flight": c["in_flight"], "value": _r(c["value"])}
     if line["cavity"]:
-        out["cavity"] = [{"alpha": e["alpha"], "ms": _r(e.get("ms_per_state_solve")),
+        out["cavity"] = [{"alpha": e["alpha"], "smoother": "zline" if e.get("settings") else "jacobi",
+                          "ms": _r(e.get("ms_per_state_solve")),
                           "newton": (e.get("newton_its") or [None])[-1], "krylov": (e.get("krylov_its") or [None])[-1],
                           "adjoint_ms": _r(e.get("ms_adjoint")), "adjoint_krylov": e.get("adjoint_krylov_its"),
                           "error": e.get("error")} for e in line["cavity"]]

@@ -94,6 +94,13 @@ enum { NC_REGION_BOX = 0, NC_REGION_CYLINDER = 1 };
  * tau, no dP coupling): about 40 % of the arithmetic of J. The Krylov operator stays exact. */
 enum { NC_MGOP_EXACT = 0, NC_MGOP_PICARD = 1 };
 
+/* Smoothers of the multigrid levels below the finest (their operators are assembled 27-point stencils of
+ * 2x2 blocks). NC_SMOOTH_BLOCK_JACOBI: damped 2x2 block Jacobi, x += omega D^-1 (b - A x).
+ * NC_SMOOTH_ZLINE: damped z-line block Jacobi, x += omega T^-1 (b - A x), with T the block-tridiagonal
+ * part of A that couples each node column (fixed i, j) in z with itself, factored once per set-up;
+ * aimed at convection along the buoyancy direction z. */
+enum { NC_SMOOTH_BLOCK_JACOBI = 0, NC_SMOOTH_ZLINE = 1 };
+
 typedef struct nc_problem nc_problem;
 
 typedef struct {
@@ -181,6 +188,9 @@ typedef struct {
   int mg_nu_coarse;     /* post-smoothing sweeps on the multigrid levels from mg_nu_coarse_level down
                            to the one above the coarsest; 0: nu_post [0] */
   int mg_nu_coarse_level; /* first level that takes mg_nu_coarse sweeps (levels >= 1; 0: 1) [0] */
+  int mg_smoother;      /* smoother of the multigrid levels below the finest (the finest level keeps 2x2
+                           block Jacobi): NC_SMOOTH_BLOCK_JACOBI or NC_SMOOTH_ZLINE. Fixed at creation;
+                           NC_SMOOTH_ZLINE needs mg_tail_nodes = 0 [NC_SMOOTH_BLOCK_JACOBI] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */

@@ -412,7 +412,9 @@ nc_status mg_alloc(nc_problem* pb) {
     d.S = nullptr;
     d.ebe = nullptr;
     d.dinv = nullptr;
+    d.lf = nullptr;
     if (l < L - 1) CKS(dalloc(pb, &d.dinv, 4 * d.g.nn));
+    if (pb->par.mg_smoother == NC_SMOOTH_ZLINE && l > 0 && l < L - 1) CKS(dalloc(pb, &d.lf, 24 * d.g.nn));
     if (l > 0) CKS(dalloc(pb, &d.ebe, 256 * d.g.ne));
     if (l > 0 && l < L - 1) CKS(dalloc(pb, &d.S, 108 * d.g.nn));
   }
@@ -449,6 +451,9 @@ nc_status mg_setup(nc_problem* pb, bool refactor) {
   if (factor)
     PCK(NC_PROF_COARSE_FACTOR, launch_coarse_factor(mg.Ac, mg.W, mg.Ainv32, mg.nf, pb->dflag, pb->st, &pb->cnt));
   for (int l = 0; l < L - 1; ++l) PCK(NC_PROF_MG_COARSE_SETUP, launch_invert_diag<R>(mg.lev[l].g, mg.lev[l].dinv, pb->dflag, pb->st, &pb->cnt));
+  for (int l = 1; l < L - 1; ++l)
+    if (mg.lev[l].lf)
+      PCK(NC_PROF_MG_COARSE_SETUP, launch_line_factor<R>(mg.lev[l].g, mg.lev[l].S, mg.lev[l].lf, pb->dflag, pb->st, &pb->cnt));
   CK(cudaMemcpyAsync(pb->hflag, pb->dflag, sizeof(int), cudaMemcpyDeviceToHost, pb->st));
   CKS(sync(pb, "multigrid set-up"));
   if (*pb->hflag) return fail(pb, NC_ERR_NAN, "singular block in the multigrid set-up");
@@ -510,7 +515,8 @@ template <typename R>
 nc_status coarse_cycle(nc_problem* pb, bool tr) {
   MG<R>& mg = mg_of<R>(pb);
   bool odd = false;
-  for (int l = 1; l < (int)mg.lev.size() - 1; ++l) odd |= ((std::max(1, pb->par.nu_pre) - 1 + coarse_post_sweeps(pb, l)) & 1) != 0;
+  for (int l = 1; l < (int)mg.lev.size() - 1; ++l)   // the z-line smoother updates x in place
+    if (!mg.lev[l].lf) odd |= ((std::max(1, pb->par.nu_pre) - 1 + coarse_post_sweeps(pb, l)) & 1) != 0;
   if (odd || (pb->prof_mask & kCoarseCycleClasses)) return vcycle<R>(pb, 1, tr);
   const int t = tr ? 1 : 0;
   if (!mg.graph[t]) {
@@ -566,6 +572,13 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
     return NC_OK;
   }
   auto sweep = [&](bool last) -> nc_status {
+    if (d.lf) {
+      // z-line smoother: residual into xn, then x += omega T^-1 r in place (no exchange of x and xn)
+      PCK(l == 1 ? NC_PROF_MG_STENCIL_L1 : NC_PROF_MG_STENCIL,
+          launch_stencil_apply<R>(d.g, d.S, d.x, d.b, d.dinv, om, d.xn, tr, 1, pb->st, &pb->cnt));
+      PCK(NC_PROF_SMOOTH, launch_line_smooth<R>(d.g, d.lf, d.xn, d.x, om, tr, false, pb->st, &pb->cnt));
+      return NC_OK;
+    }
     if (l == 0) {
       CKS(level_apply<R>(pb, l, tr, d.x, d.y));
       if (last && mg.out64)
@@ -583,6 +596,8 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
   if (l == 0 && mg.in64)
     PCK(NC_PROF_SMOOTH, launch_jacobi_io<R>(d.g, d.dinv, d.b, mg.in64, d.y, d.x, d.x, nullptr, om, tr, true, pb->st,
                                             &pb->cnt));
+  else if (d.lf)
+    PCK(NC_PROF_SMOOTH, launch_line_smooth<R>(d.g, d.lf, d.b, d.x, om, tr, true, pb->st, &pb->cnt));
   else
     PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.x, om, tr, true, pb->st, &pb->cnt));
   for (int it = 1; it < nu1; ++it) CKS(sweep(false));
@@ -1016,6 +1031,10 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (p->mg_tail_ctas < 0 || p->mg_tail_ctas > 16) { *why = "mg_tail_ctas must be in [0, 16]"; return NC_ERR_ARG; }
   if (p->mg_nu_coarse < 0 || p->mg_nu_coarse > 16) { *why = "mg_nu_coarse must be in [0, 16]"; return NC_ERR_ARG; }
   if (p->mg_nu_coarse_level < 0) { *why = "mg_nu_coarse_level must be >= 0"; return NC_ERR_ARG; }
+  if (p->mg_smoother != NC_SMOOTH_BLOCK_JACOBI && p->mg_smoother != NC_SMOOTH_ZLINE) { *why = "unknown mg_smoother"; return NC_ERR_ARG; }
+  if (p->mg_smoother == NC_SMOOTH_ZLINE && p->mg_tail_nodes > 0) {
+    *why = "the fused multigrid tail smooths with block Jacobi (NC_SMOOTH_ZLINE needs mg_tail_nodes = 0)"; return NC_ERR_ARG;
+  }
   if (p->elem_chunk != -1 && p->elem_chunk != 0 && p->elem_chunk != 1 && p->elem_chunk != 2 && p->elem_chunk != 4 &&
       p->elem_chunk != 8 && p->elem_chunk != 16) { *why = "elem_chunk must be -1, 0, 1, 2, 4, 8 or 16"; return NC_ERR_ARG; }
   if (p->coarse_refactor < 0 || p->coarse_refactor > 2) { *why = "coarse_refactor must be 0, 1 or 2"; return NC_ERR_ARG; }
@@ -1067,6 +1086,7 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
     if (l + 1 < lv.g.size()) b += al(4 * rs * lv.g[l].nn);
     if (l > 0) b += al(256 * rs * lv.g[l].ne);
     if (l > 0 && l + 1 < lv.g.size()) b += al(108 * rs * lv.g[l].nn);
+    if (p->mg_smoother == NC_SMOOTH_ZLINE && l > 0 && l + 1 < lv.g.size()) b += al(24 * rs * lv.g[l].nn);
   }
   // coarsest level: Ac (FP64), Ainv32, the Gauss-Jordan work array W and the coarse-solve scratch cw (3 nf FP64)
   b += al(8 * (size_t)lv.nf * lv.nf) + al(4 * (size_t)lv.nf * lv.nf) + al(8 * (size_t)lv.nf * lv.nf + 12 * (size_t)lv.nf);
@@ -1203,6 +1223,7 @@ nc_status nc_default_params(nc_params* p) {
   p->krylov_reorth = 0.0;
   p->mg_tail_nodes = 0;
   p->mg_op0 = NC_MGOP_PICARD;
+  p->mg_smoother = NC_SMOOTH_BLOCK_JACOBI;
   p->elem_chunk = -1;
   p->mg_reuse_below = 1e-2;
   p->adjoint_df64_steps = 1;
@@ -1306,8 +1327,8 @@ nc_status nc_set_params(nc_problem* pb, const nc_params* p) {
   nc_status vs = validate(&gr, p, &why);
   if (vs != NC_OK) return fail(pb, vs, why);
   if (p->precision != pb->par.precision || p->mg_levels != pb->par.mg_levels || p->restart != pb->par.restart ||
-      p->krylov_basis != pb->par.krylov_basis || p->bc != pb->par.bc)
-    return fail(pb, NC_ERR_ARG, "precision, mg_levels, restart, krylov_basis and bc are fixed at creation");
+      p->krylov_basis != pb->par.krylov_basis || p->bc != pb->par.bc || p->mg_smoother != pb->par.mg_smoother)
+    return fail(pb, NC_ERR_ARG, "precision, mg_levels, restart, krylov_basis, bc and mg_smoother are fixed at creation");
   DeviceGuard dg(pb->device);
   CKS(sync(pb, "set_params"));
   drop_graphs(pb);   // omega, sweeps and the tail choice are arguments of the captured launches

@@ -736,6 +736,159 @@ __global__ void __launch_bounds__(128) k_stencil_apply(Grid g, const R* __restri
   stencil_node<R, TR, MODE>(g, S, x, b, dinv, omega, out, n, i, j, k, LdPlain());
 }
 
+// ---- z-line block-Jacobi smoother (levels with an assembled stencil) -----------------------------
+// The couplings of a node column (i, j, k = 0 .. nz) with itself form a block-tridiagonal matrix
+// T = tridiag(L_k, D_k, U_k) of 2x2 blocks: D_k is the stencil's centre block, L_k its (0,0,-1) block
+// and U_k its (0,0,+1) block (transposed operator: D_k^T, L_k = U_{k-1}^T, U_k = L_{k+1}^T). The
+// smoother uses T where block Jacobi uses D, every column from the same x:
+// x <- x + omega T^-1 (b - A x). The set-up eliminates down each column, without pivoting between
+// nodes: E_0 = D_0, E_k = D_k - L_k G_{k-1}, G_k = E_k^-1 U_k. LF holds, per direction, E_k^-1, G_k
+// and M_k = E_k^-1 L_k as three planes of 2x2 blocks (12 nn values). The solve is the pair of
+// first-order recurrences y_k = E_k^-1 r_k - M_k y_{k-1} (down the column) and d_k = y_k - G_k d_{k+1}
+// (back up). Fixed components have zero rows and columns in every block, and E_k is inverted on its
+// free components only, so they stay zero.
+
+template <typename R> __device__ __forceinline__ Blk4<R> blk_mul(const Blk4<R>& a, const Blk4<R>& b) {
+  return Blk4<R>{a.a00 * b.a00 + a.a01 * b.a10, a.a00 * b.a01 + a.a01 * b.a11,
+                 a.a10 * b.a00 + a.a11 * b.a10, a.a10 * b.a01 + a.a11 * b.a11};
+}
+template <typename R> __device__ __forceinline__ Blk4<R> blk_t(const Blk4<R>& a) {
+  return Blk4<R>{a.a00, a.a10, a.a01, a.a11};
+}
+__device__ __forceinline__ void st_blk(float* P, long long idx, const Blk4<float>& b) {
+  reinterpret_cast<float4*>(P)[idx] = make_float4(b.a00, b.a01, b.a10, b.a11);
+}
+__device__ __forceinline__ void st_blk(double* P, long long idx, const Blk4<double>& b) {
+  reinterpret_cast<double2*>(P)[2 * idx] = make_double2(b.a00, b.a01);
+  reinterpret_cast<double2*>(P)[2 * idx + 1] = make_double2(b.a10, b.a11);
+}
+
+// Inverse of the free components of a 2x2 block (fb: fixed bits, bit 0 P, bit 1 T); the rows and
+// columns of fixed components are zero. False on a singular or non-finite block.
+template <typename R> __device__ __forceinline__ bool blk_inv_free(const Blk4<R>& a, int fb, Blk4<R>& o) {
+  o = Blk4<R>{R(0), R(0), R(0), R(0)};
+  if (fb == 3) return true;
+  if (fb) {
+    const R v = fb == 2 ? a.a00 : a.a11;
+    if (!(v != R(0)) || !isfinite((double)v)) return false;
+    if (fb == 2) o.a00 = R(1) / v; else o.a11 = R(1) / v;
+    return true;
+  }
+  const R det = a.a00 * a.a11 - a.a01 * a.a10;
+  if (!(det != R(0)) || !isfinite((double)det)) return false;
+  const R id = R(1) / det;
+  o = Blk4<R>{a.a11 * id, -a.a01 * id, -a.a10 * id, a.a00 * id};
+  return true;
+}
+
+// One thread per node column c = i + NX j.
+template <typename R, bool TR>
+__global__ void __launch_bounds__(32) k_line_factor(Grid g, const R* __restrict__ S, R* __restrict__ LF,
+                                                    int* __restrict__ flag) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.NXY) return;
+  const int nn = (int)g.nn, i = c % g.NX, j = c / g.NX;
+  const Blk4<R> zero{R(0), R(0), R(0), R(0)};
+  Blk4<R> G = zero;
+  bool bad = false;
+  for (int k = 0; k <= g.nz; ++k) {
+    const int n = c + g.NXY * k;
+    Blk4<R> D = ld_blk(S, 13 * nn + n);
+    if (TR) D = blk_t(D);
+    Blk4<R> L = zero;
+    if (k > 0) {
+      L = TR ? blk_t(ld_blk(S, 22 * nn + n - g.NXY)) : ld_blk(S, 4 * nn + n);
+      const Blk4<R> LG = blk_mul(L, G);
+      D = Blk4<R>{D.a00 - LG.a00, D.a01 - LG.a01, D.a10 - LG.a10, D.a11 - LG.a11};
+    }
+    Blk4<R> Ei;
+    if (!blk_inv_free(D, fixed_bits(g, i, j, k), Ei)) bad = true;
+    Blk4<R> U = zero;
+    if (k < g.nz) U = TR ? blk_t(ld_blk(S, 4 * nn + n + g.NXY)) : ld_blk(S, 22 * nn + n);
+    G = blk_mul(Ei, U);
+    st_blk(LF, n, Ei);
+    st_blk(LF, (long long)nn + n, G);
+    st_blk(LF, 2LL * nn + n, blk_mul(Ei, L));
+  }
+  if (bad) atomicExch(flag, 1);
+}
+
+// Inclusive scan over the warp's lanes of affine maps v -> a + B v (2x2 B), composed in lane order:
+// lane q ends with the composition of the maps of lanes q, q-1, ..., 0 (lane 0's applied first).
+template <typename R>
+__device__ __forceinline__ void warp_scan_affine(R& b00, R& b01, R& b10, R& b11, R& a0, R& a1, int lane) {
+  constexpr unsigned kFull = 0xffffffffu;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const R p00 = __shfl_up_sync(kFull, b00, off), p01 = __shfl_up_sync(kFull, b01, off);
+    const R p10 = __shfl_up_sync(kFull, b10, off), p11 = __shfl_up_sync(kFull, b11, off);
+    const R q0 = __shfl_up_sync(kFull, a0, off), q1 = __shfl_up_sync(kFull, a1, off);
+    if (lane >= off) {
+      const R n0 = a0 + b00 * q0 + b01 * q1, n1 = a1 + b10 * q0 + b11 * q1;
+      const R m00 = b00 * p00 + b01 * p10, m01 = b00 * p01 + b01 * p11;
+      const R m10 = b10 * p00 + b11 * p10, m11 = b10 * p01 + b11 * p11;
+      a0 = n0; a1 = n1; b00 = m00; b01 = m01; b10 = m10; b11 = m11;
+    }
+  }
+}
+
+// x <- x + omega T^-1 r (FIRST: x <- omega T^-1 r from x = 0). One warp per column, 32 nodes of it
+// at a time, one per lane: each recurrence step is an affine map of the previous value, so a chunk is
+// one warp scan of those maps, applied to the value carried in from the chunk before; the next
+// chunk's loads are issued before the current chunk's scan. The forward values y_k go to ybuf (x when
+// FIRST, otherwise r itself, which the caller no longer needs).
+template <typename R, bool FIRST>
+__global__ void __launch_bounds__(128) k_line_smooth(Grid g, const R* __restrict__ LF, const typename Vec2<R>::type* r,
+                                                     typename Vec2<R>::type* ybuf, typename Vec2<R>::type* x,
+                                                     R omega) {
+  typedef typename Vec2<R>::type V2;
+  constexpr unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= g.NXY) return;   // uniform over the warp
+  const int nn = (int)g.nn, K = g.nz + 1, P = g.NXY;
+  // down the column: lane q of the chunk at k0 takes node k0 + q (past the top: the top node, unused)
+  R c0 = R(0), c1 = R(0);
+  int n = c + P * min(lane, K - 1);
+  Blk4<R> E = ld_blk(LF, n), M = ld_blk(LF, 2 * nn + n);
+  V2 rv = r[n];
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    const int nx = c + P * min(k0 + 32 + lane, K - 1);
+    Blk4<R> En = E, Mn = M;
+    V2 rn = rv;
+    if (k0 + 32 < K) { En = ld_blk(LF, nx); Mn = ld_blk(LF, 2 * nn + nx); rn = r[nx]; }
+    R a0 = E.a00 * rv.x + E.a01 * rv.y, a1 = E.a10 * rv.x + E.a11 * rv.y;
+    R b00 = -M.a00, b01 = -M.a01, b10 = -M.a10, b11 = -M.a11;
+    warp_scan_affine(b00, b01, b10, b11, a0, a1, lane);
+    const R y0 = a0 + b00 * c0 + b01 * c1, y1 = a1 + b10 * c0 + b11 * c1;
+    if (k0 + lane < K) ybuf[n] = mk2<R>(y0, y1);
+    c0 = __shfl_sync(kFull, y0, 31);
+    c1 = __shfl_sync(kFull, y1, 31);
+    n = nx; E = En; M = Mn; rv = rn;
+  }
+  // back up the column: lane q of the chunk at k1 takes node k1 - q (below the bottom: node 0, unused)
+  c0 = R(0); c1 = R(0);
+  n = c + P * max(K - 1 - lane, 0);
+  Blk4<R> G = ld_blk(LF, nn + n);
+  V2 yv = ybuf[n], xv = yv;
+  if (!FIRST) xv = x[n];
+  for (int k1 = K - 1; k1 >= 0; k1 -= 32) {
+    const int nx = c + P * max(k1 - 32 - lane, 0);
+    Blk4<R> Gn = G;
+    V2 yn = yv, xn = yv;
+    if (k1 - 32 >= 0) { Gn = ld_blk(LF, nn + nx); yn = ybuf[nx]; if (!FIRST) xn = x[nx]; }
+    R a0 = yv.x, a1 = yv.y;
+    R b00 = -G.a00, b01 = -G.a01, b10 = -G.a10, b11 = -G.a11;
+    warp_scan_affine(b00, b01, b10, b11, a0, a1, lane);
+    const R d0 = a0 + b00 * c0 + b01 * c1, d1 = a1 + b10 * c0 + b11 * c1;
+    if (k1 - lane >= 0) x[n] = FIRST ? mk2<R>(omega * d0, omega * d1) : mk2<R>(xv.x + omega * d0, xv.y + omega * d1);
+    c0 = __shfl_sync(kFull, d0, 31);
+    c1 = __shfl_sync(kFull, d1, 31);
+    n = nx; G = Gn; yv = yn;
+    if (!FIRST) xv = xn;
+  }
+}
+
 // ---- coarsest level: FP32 Gauss-Jordan inverse with partial pivoting ----------------------------
 // Ainv32 receives the inverse of the FP64 matrix A rounded to FP32; flag = 1 on a zero pivot.
 
@@ -1424,6 +1577,32 @@ cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st
   return e;
 }
 
+template <typename R>
+cudaError_t launch_line_factor(const Grid& g, const R* S, R* LF, int* flag, cudaStream_t st, Counters* c) {
+  const unsigned nb = grid_blocks(g.NXY, 32);
+  k_line_factor<R, false><<<nb, 32, 0, st>>>(g, S, LF, flag);
+  k_line_factor<R, true><<<nb, 32, 0, st>>>(g, S, LF + 12 * g.nn, flag);
+  if (c) { c->launches += 2; c->bytes += 2.0 * sizeof(R) * 24.0 * g.nn; }   // 3 blocks read, 3 written
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_line_smooth(const Grid& g, const R* LF, const typename Vec2<R>::type* r,
+                               typename Vec2<R>::type* x, R omega, bool transpose, bool first, cudaStream_t st,
+                               Counters* c) {
+  const unsigned nb = grid_blocks(g.NXY, 4);   // 4 columns (warps) per block
+  const R* lf = LF + (transpose ? 12 * g.nn : 0);
+  typedef typename Vec2<R>::type V2;
+  if (first) k_line_smooth<R, true><<<nb, 128, 0, st>>>(g, lf, r, x, x, omega);
+  else k_line_smooth<R, false><<<nb, 128, 0, st>>>(g, lf, r, const_cast<V2*>(r), x, omega);
+  if (c) {
+    c->launches += 1;
+    // E^-1, M, r, y written; G, y, x (not first), x written
+    c->bytes += sizeof(R) * (8.0 + 2.0 + 2.0 + 4.0 + 2.0 + (first ? 0.0 : 2.0) + 2.0) * g.nn;
+  }
+  return cudaGetLastError();
+}
+
 #define NC_INSTANTIATE_MG(R)                                                                                    \
   template cudaError_t launch_galerkin_fine<R>(const Grid&, const Grid&, const Phys&, const Vec2<R>::type*,   \
                                                const Vec2<R>::type*, R*, R*, cudaStream_t, Counters*);         \
@@ -1453,7 +1632,10 @@ cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st
   template cudaError_t launch_stencil_apply<R>(const Grid&, const R*, const Vec2<R>::type*,                  \
                                                const Vec2<R>::type*, const R*, R, Vec2<R>::type*, bool, int, \
                                                cudaStream_t, Counters*);                                       \
-  template cudaError_t launch_mg_tail<R>(const TailArgs<R>&, bool, cudaStream_t, Counters*);
+  template cudaError_t launch_mg_tail<R>(const TailArgs<R>&, bool, cudaStream_t, Counters*);             \
+  template cudaError_t launch_line_factor<R>(const Grid&, const R*, R*, int*, cudaStream_t, Counters*);     \
+  template cudaError_t launch_line_smooth<R>(const Grid&, const R*, const Vec2<R>::type*, Vec2<R>::type*, R, \
+                                             bool, bool, cudaStream_t, Counters*);
 
 NC_INSTANTIATE_MG(float)
 NC_INSTANTIATE_MG(double)

@@ -212,6 +212,7 @@ template <typename R> struct MGLevelDev {
   R* ebe;       // 256 per element (levels >= 1)
   R* S;         // assembled 27-point 2x2-block stencil, 108 per node, 27 planes of 2x2 blocks (levels 1 .. L-2)
   R* dinv;      // 4 per node (2x2 block-diagonal inverse, row major), 0 on Dirichlet nodes
+  R* lf;        // z-line smoother factors, 24 per node (levels 1 .. L-2 with the z-line smoother), else null
 };
 
 // Fused multigrid tail: the part of a V-cycle on levels l0 .. L-1 (the small coarse grids) run by
@@ -314,6 +315,17 @@ cudaError_t launch_stencil_apply(const Grid& g, const R* S, const typename Vec2<
                                  const typename Vec2<R>::type* b, const R* dinv, R omega,
                                  typename Vec2<R>::type* out, bool transpose, int mode, cudaStream_t st,
                                  Counters* c);
+// z-line block-Jacobi smoother of a level with an assembled stencil. launch_line_factor eliminates
+// down every node column of S and of its transpose (LF: 24 nn values, the forward direction's 12 nn
+// first; flag = 1 on a singular pivot block); launch_line_smooth updates x <- x + omega T^-1 r with T
+// the column-tridiagonal part of the operator (transpose: of A^T), overwriting r, or with first:
+// x <- omega T^-1 r from x = 0 (r is kept).
+template <typename R>
+cudaError_t launch_line_factor(const Grid& g, const R* S, R* LF, int* flag, cudaStream_t st, Counters* c);
+template <typename R>
+cudaError_t launch_line_smooth(const Grid& g, const R* LF, const typename Vec2<R>::type* r,
+                               typename Vec2<R>::type* x, R omega, bool transpose, bool first, cudaStream_t st,
+                               Counters* c);
 // Cast a multigrid-type state vector to FP64.
 template <typename R>
 cudaError_t launch_from_mg(const typename Vec2<R>::type* x, double* z, long long nn, cudaStream_t st,

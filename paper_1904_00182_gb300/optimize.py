@@ -265,7 +265,9 @@ if __name__ == "__main__":
     ap.add_argument("--cylinder", action="store_true",
                     help="Sec. 7's suspended cylinder on the quarter cavity of n x n x 2n elements (n a multiple of 5)")
     a = ap.parse_args()
+    from .presets import solver_settings
     geom = cavity_params(a.n) if a.cavity else cylinder_params(a.n) if a.cylinder else {}
+    geom.update(solver_settings(a.alpha))
     out = optimize(a.n, a.n, 2 * a.n if (a.cavity or a.cylinder) else a.n, a.alpha, a.volfrac, a.iters, **geom,
                    callback=lambda r: print("it %3d f %.6e g %+.2e change %.3f stage %d newton %d krylov %d/%d %.3f s"
                                             % (r["it"], r["f"], r["g"], r["change"], r["stage"], r["newton_its"],

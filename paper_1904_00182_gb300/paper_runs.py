@@ -8,13 +8,14 @@
   holding the volume fraction 0.15 of the design annulus (in the quarter domain one fin on its
   diagonal, solid, with fluid elsewhere in the annulus).
 
-Each case creates the problem (footprint from nc_footprint_bytes), solves the state from zero to a
+Each case creates the problem (footprint from nc_footprint_bytes) with the solver settings of its
+alpha (presets.solver_settings: the z-line smoother at alpha = 1e6), solves the state from zero to a
 relative residual of 1e-8, then the adjoint of the mean heated-region temperature and the
 sensitivities, and prints one JSON line with the times (CUDA events on the problem's stream), the
 Newton and Krylov iterations and the device memory the problem holds. When Newton does not converge
-from zero (the cylinder at alpha = 1e6: its linear solves stall), the state is reached by warm starts
-(Sec. 5.4) up the ladder alpha = 1e5, 2e5, 4e5, 7e5 and the last, warm-started solve is timed. The paper ran these meshes
-with MPI domain decomposition on 16 to 640 CPU cores (Table 3); here each runs on one GPU.
+from zero, the state is reached by warm starts (Sec. 5.4) up the ladder alpha = 1e5, 2e5, 4e5, 7e5
+and the last, warm-started solve is timed. The paper ran these meshes with MPI domain decomposition
+on 16 to 640 CPU cores (Table 3); here each runs on one GPU.
 
   python -m paper_1904_00182_gb300.paper_runs [--cases cavity80,cavity160,cavity320,cylinder160]
 """
@@ -28,6 +29,7 @@ import torch
 
 from . import _abi
 from .optimize import cavity_params, cylinder_params, region_masks
+from .presets import solver_settings
 from .problem import Problem
 
 CASES = {
@@ -118,17 +120,15 @@ def main():
     ap.add_argument("--cases", default="cavity80,cavity160,cylinder160")
     ap.add_argument("--alphas", default="1e3,1e6")
     ap.add_argument("--mg-op0", default="picard", choices=["exact", "picard"])
-    ap.add_argument("--nu-coarse-high", type=int, default=8,
-                    help="post-smoothing sweeps of the coarse multigrid levels at alpha >= 1e6 (0: the default)")
+    ap.add_argument("--library-defaults", action="store_true",
+                    help="the library's default smoother at every alpha instead of presets.solver_settings")
     a = ap.parse_args()
     op0 = _abi.NC_MGOP_PICARD if a.mg_op0 == "picard" else _abi.NC_MGOP_EXACT
     for name in a.cases.split(","):
         kind, n = CASES[name]
         alphas = [1e6] if kind == "cylinder" else [float(x) for x in a.alphas.split(",")]
         for alpha in alphas:
-            # at alpha >= 1e6 the coarse levels take 8 post-smoothing sweeps (convection-dominated
-            # Galerkin operators; measured: fewer Krylov iterations in state and adjoint)
-            extra = {"mg_nu_coarse": a.nu_coarse_high} if alpha >= 1e6 else {}
+            extra = {} if a.library_defaults else solver_settings(alpha)
             try:
                 rec = run_case(kind, n, alpha, mg_op0=op0, **extra)
             except _abi.NatConvError as e:

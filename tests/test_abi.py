@@ -73,6 +73,17 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
     p.krylov_basis = 2
     with pytest.raises(NatConvError):
         footprint_bytes(Grid(16, 16, 16, 1 / 16), p)
+    p = default_params()
+    p.mg_smoother = 2
+    with pytest.raises(NatConvError):
+        footprint_bytes(Grid(16, 16, 16, 1 / 16), p)
+    p = default_params()
+    p.mg_smoother, p.mg_tail_nodes = 1, 4096          # the fused tail smooths with block Jacobi
+    with pytest.raises(NatConvError):
+        footprint_bytes(Grid(16, 16, 16, 1 / 16), p)
+    p.mg_tail_nodes = 0
+    # the z-line factors: 24 values per node on the levels between the finest and the coarsest
+    assert footprint_bytes(Grid(16, 16, 16, 1 / 16), p) > footprint_bytes(Grid(16, 16, 16, 1 / 16), default_params())
 
 
 def _struct_fields(name):

@@ -3,7 +3,8 @@
 * The closed cavity of Sec. 6.1 (quarter domain, heated box under a design box, passive fluid) at
   alpha = 1e3 from the initial design gamma = 0.05.
 * The suspended cylinder of Sec. 7 (heated cylinder and design annulus, kappa_f = 0.000676) at
-  alpha = 1e5 from a radial-fin initial design (volume fraction 0.15).
+  alpha = 1e5 and at the paper's alpha = 1e6 (with the z-line smoother of presets.solver_settings),
+  from a radial-fin initial design (volume fraction 0.15).
 
 The oracle cannot solve at this size (8.2 M elements), so it checks the GPU's state and adjoint on
 sampled rows, with the element materials the GPU's design pipeline produced (the filter and RAMP are
@@ -32,7 +33,7 @@ def _oracle_params(kind, alpha, geom):
                          heat_z0=geom["heat_z0"], heated_layers=geom["heated_layers"])
 
 
-@pytest.mark.parametrize("kind,alpha", [("cavity", 1e3), ("cylinder", 1e5)])
+@pytest.mark.parametrize("kind,alpha", [("cavity", 1e3), ("cylinder", 1e5), ("cylinder", 1e6)])
 def test_paper_mesh_state_and_adjoint(kind, alpha):
     import torch
     from paper_1904_00182_gb300 import build
@@ -40,10 +41,11 @@ def test_paper_mesh_state_and_adjoint(kind, alpha):
     import paper_1904_00182_gb300 as nc
     from paper_1904_00182_gb300.optimize import cavity_params, cylinder_params
     from paper_1904_00182_gb300.paper_runs import fin_design
+    from paper_1904_00182_gb300.presets import solver_settings
 
     geom = cavity_params(N) if kind == "cavity" else cylinder_params(N)
     nx, ny, nz = N, N, 2 * N
-    pb = nc.Problem(nx, ny, nz, 1.0 / nz, alpha=alpha, **geom)
+    pb = nc.Problem(nx, ny, nz, 1.0 / nz, alpha=alpha, **geom, **solver_settings(alpha))
     if kind == "cavity":
         rho = torch.full((nx * ny * nz,), 0.05, dtype=torch.float64)
     else:
