@@ -85,7 +85,8 @@ def test_design_fields_and_operators(lib):
 
 
 VARIANTS = {"fp64": (1, 1e-8, {}), "mixed": (0, 1e-6, {}),
-            "mixed_fast": (0, 1e-6, {"outer_arith": 0, "krylov_basis": 1})}
+            "mixed_fast": (0, 1e-6, {"outer_arith": 0, "krylov_basis": 1}),
+            "mixed_zline": (0, 1e-6, {"mg_smoother": 1, "omega": 0.7})}
 
 
 @pytest.mark.parametrize("alpha", [1e3, 1e5])
@@ -150,15 +151,16 @@ def test_parameters_and_errors(lib):
     gp.close()
 
 
-def test_cylinder_regions(lib):
+@pytest.mark.parametrize("smoother", [0, 1])
+def test_cylinder_regions(lib, smoother):
     """Sec. 7's suspended cylinder on the quarter cavity (12 x 12 x 24; heat radius 4, design radius 9,
     layers 8-13): filtered design, state, both objectives and sensitivities against the oracle on the
-    mixed path."""
+    mixed path, with block-Jacobi and with z-line smoothing of the coarse multigrid levels."""
     geom = dict(heat_radius=4.0, design_radius=9.0, heat_z0=8, heated_layers=6, Q=100.0)
     n, nz = 12, 24
     rho = filtered_random(n, n, nz, 2, volfrac=0.3)
     gp = lib.Problem(n, n, nz, 1.0 / nz, alpha=1e4, precision=0, newton_rtol=1e-10, bc=lib.NC_BC_CAVITY,
-                     region_shape=lib.NC_REGION_CYLINDER, **geom)
+                     region_shape=lib.NC_REGION_CYLINDER, mg_smoother=smoother, **geom)
     gp.set_design(rho)
     op = oracle.Problem(oracle.Mesh(n, n, nz, 1.0 / nz),
                         oracle.Params(alpha=1e4, newton_rtol=1e-10, bc="cavity", region_shape="cylinder", **geom))
