@@ -138,3 +138,16 @@ def test_torch_design_recipe_matches_numpy_recipe():
     assert abs(c.mean() - 0.2) < 1e-6 and c.min() >= 0.0 and c.max() <= 1.0
     d = designs.filtered_random_torch(12, 12, 12, seed=3, volfrac=0.2).numpy()
     assert np.array_equal(c, d)
+
+
+def test_solver_presets_by_alpha():
+    """The z-line smoother with omega 0.7 from alpha = 1e6 on, the library defaults below; the preset's
+    fields are nc_params fields and the combination validates (no fused tail)."""
+    from paper_1904_00182_gb300 import Grid, NC_SMOOTH_ZLINE, default_params, footprint_bytes
+    from paper_1904_00182_gb300.presets import solver_settings
+    assert solver_settings(1e3) == {} and solver_settings(9.9e5) == {}
+    s = solver_settings(1e6)
+    assert s == {"mg_smoother": NC_SMOOTH_ZLINE, "omega": 0.7}
+    p = default_params(alpha=1e6, **s)
+    assert p.mg_smoother == NC_SMOOTH_ZLINE and p.omega == 0.7 and p.mg_tail_nodes == 0
+    assert footprint_bytes(Grid(16, 16, 32, 1 / 32), p) > 0
