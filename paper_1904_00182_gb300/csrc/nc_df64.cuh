@@ -75,6 +75,13 @@ __device__ __forceinline__ df64 df_rsqrt(const df64 x) {
   return y0 + (y0 * d) * df64(0.5f, 0.0f);
 }
 
+// Reciprocal: one Newton step y0 + y0 (1 - x y0) from the FP32 reciprocal of the leading part.
+__device__ __forceinline__ df64 df_rcp(const df64 x) {
+  const df64 y0(__frcp_rn(x.hi), 0.0f);
+  const df64 d = df64(1.0f, 0.0f) - x * y0;     // formed accurately: x y0 is close to 1
+  return y0 + y0 * d;
+}
+
 // Split of FP64 values into double-float (used by the kernels that convert their inputs once).
 __device__ __forceinline__ df64 df_from_double(double d) {
   const float h = __double2float_rn(d);

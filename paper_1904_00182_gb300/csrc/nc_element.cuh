@@ -141,6 +141,26 @@ template <typename R> __device__ __forceinline__ R nc_rsqrt(R x);
 template <> __device__ __forceinline__ double nc_rsqrt<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ float nc_rsqrt<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ df64 nc_rsqrt<df64>(df64 x) { return df_rsqrt(x); }
+// Reciprocal of a positive element factor (|x| within FP32's normal range). FP64: Newton's iteration
+// for 1/x, y <- y + y (1 - x y), twice from the FP32 reciprocal (each step squares the relative
+// error: 2^-24 -> 2^-48 -> below FP64 rounding), four FMAs and no branch.
+template <typename R> __device__ __forceinline__ R nc_rcp(R x);
+template <> __device__ __forceinline__ double nc_rcp<double>(double x) {
+  double y = (double)__frcp_rn((float)x);
+  y = fma(y, fma(-x, y, 1.0), y);
+  return fma(y, fma(-x, y, 1.0), y);
+}
+template <> __device__ __forceinline__ float nc_rcp<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ df64 nc_rcp<df64>(df64 x) { return df_rcp(x); }
+
+// Whether the element routines apply the rows' constant factors (w c / h^2 of the continuity rows,
+// w k / h^2 of the energy rows) to the 8 test sums instead of the 24 Gauss-point values (the test
+// sums are linear): fewer multiplications for one reciprocal of w k / h^2 per element. Measured on
+// GB300 (128^3 whole path): faster FP32 operators and double-float adjoint residual; the FP64 kernels,
+// bound by the FP64 pipe, were not faster (the accepting adjoint product 3 % slower), so FP64 keeps
+// the factors at the Gauss points.
+template <typename R> struct ScaleSums { static constexpr bool value = true; };
+template <> struct ScaleSums<double> { static constexpr bool value = false; };
 
 // Gauss-point state of an element: V_q = h (grad P_q - beta T_q e_z) (so u_q = -(c/h) V_q, c = kappa/mu),
 // H_q = h grad T_q, S_q = rho0 c_p u_q . grad T_q - Q, centroid velocity u0 and tau (u0, S, tau in
@@ -183,22 +203,41 @@ __device__ __forceinline__ void elem_residual(const ElemConst<R>& C, const R p[8
   ElemState<R> st;
   elem_state(C, p, t, kappa, Q, st);
   const R wc = C.wih2 * st.c;    // B^P / h = -w u / h = (w c / h^2) V
-  R bx[8], by[8], bz[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) { bx[q] = wc * st.vx[q]; by[q] = wc * st.vy[q]; bz[q] = wc * st.vz[q]; }
-  q1_test<R, false>(nullptr, bx, by, bz, C.cm, RP);
-  R A[8];
+  R A[8], bx[8], by[8], bz[8];
   const R wk = C.wih2 * kc;
-  const R wt = C.wih * st.tau;
+  if constexpr (ScaleSums<R>::value) {
+    q1_test<R, false>(nullptr, st.vx, st.vy, st.vz, C.cm, RP);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    A[q] = C.w * st.S[q];
-    const R s = wt * st.S[q];
-    bx[q] = s * st.u0x + wk * st.hx[q];
-    by[q] = s * st.u0y + wk * st.hy[q];
-    bz[q] = s * st.u0z + wk * st.hz[q];
+    for (int a = 0; a < 8; ++a) RP[a] *= wc;
+    // energy rows: A_q = w S_q, B_q / h = (w tau / h) S_q u0 + (w k / h^2) H_q = wk (s_q u0 + H_q)
+    const R iwk = nc_rcp<R>(wk);
+    const R wt = C.wih * st.tau * iwk, wa = C.w * iwk;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      A[q] = wa * st.S[q];
+      const R s = wt * st.S[q];
+      bx[q] = s * st.u0x + st.hx[q];
+      by[q] = s * st.u0y + st.hy[q];
+      bz[q] = s * st.u0z + st.hz[q];
+    }
+    q1_test<R, true>(A, bx, by, bz, C.cm, RT);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) RT[a] *= wk;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { bx[q] = wc * st.vx[q]; by[q] = wc * st.vy[q]; bz[q] = wc * st.vz[q]; }
+    q1_test<R, false>(nullptr, bx, by, bz, C.cm, RP);
+    const R wt = C.wih * st.tau;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      A[q] = C.w * st.S[q];
+      const R s = wt * st.S[q];
+      bx[q] = s * st.u0x + wk * st.hx[q];
+      by[q] = s * st.u0y + wk * st.hy[q];
+      bz[q] = s * st.u0z + wk * st.hz[q];
+    }
+    q1_test<R, true>(A, bx, by, bz, C.cm, RT);
   }
-  q1_test<R, true>(A, bx, by, bz, C.cm, RT);
 }
 
 // Exact Newton Jacobian product at the element state st for a direction given at the Gauss points
@@ -216,27 +255,47 @@ __device__ __forceinline__ void elem_jv_gauss(const ElemConst<R>& C, const ElemS
   const R du0x = m * sx, du0y = m * sy, du0z = m * sz;
   const R tau = st.tau;
   const R dtau = -tau * tau * tau * C.c4he2 * (st.u0x * du0x + st.u0y * du0y + st.u0z * du0z);
-  const R wc = C.wih2 * st.c;
   const R mrc = -st.c * C.rcih2;
+  const R wc = C.wih2 * st.c;
   const R wk = C.wih2 * kc;
-  const R wt = C.wih * tau, wdt = C.wih * dtau;
+  constexpr bool kSums = ScaleSums<R>::value;
+  // with kSums the energy rows' factor w k / h^2 is applied to the 8 test sums: the Gauss-point
+  // coefficients are divided by it and the dT gradient enters unscaled
+  const R iwk = kSums ? nc_rcp<R>(wk) : R(1);
+  const R wt = kSums ? C.wih * tau * iwk : C.wih * tau;
+  const R wdt = kSums ? C.wih * dtau * iwk : C.wih * dtau;
+  const R wa = kSums ? C.w * iwk : C.w;
   R A[8], bx[8], by[8], bz[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     // dS = rho0 c_p (du . grad T + u . grad dT), u = -(c/h) V
     const R dS = mrc * (dvx[q] * st.hx[q] + dvy[q] * st.hy[q] + dvz[q] * st.hz[q]
                       + st.vx[q] * dhx[q] + st.vy[q] * dhy[q] + st.vz[q] * dhz[q]);
-    A[q] = C.w * dS;
+    A[q] = wa * dS;
     const R a = wt * dS + wdt * st.S[q];      // coefficient of u0 (divided by h)
     const R b = wt * st.S[q];                 // coefficient of du0 (divided by h)
-    bx[q] = a * st.u0x + b * du0x + wk * dhx[q];
-    by[q] = a * st.u0y + b * du0y + wk * dhy[q];
-    bz[q] = a * st.u0z + b * du0z + wk * dhz[q];
+    if constexpr (kSums) {
+      bx[q] = a * st.u0x + b * du0x + dhx[q];
+      by[q] = a * st.u0y + b * du0y + dhy[q];
+      bz[q] = a * st.u0z + b * du0z + dhz[q];
+    } else {
+      bx[q] = a * st.u0x + b * du0x + wk * dhx[q];
+      by[q] = a * st.u0y + b * du0y + wk * dhy[q];
+      bz[q] = a * st.u0z + b * du0z + wk * dhz[q];
+    }
   }
   q1_test<R, true>(A, bx, by, bz, C.cm, oT);
+  if constexpr (kSums) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) { bx[q] = wc * dvx[q]; by[q] = wc * dvy[q]; bz[q] = wc * dvz[q]; }
-  q1_test<R, false>(nullptr, bx, by, bz, C.cm, oP);
+    for (int a = 0; a < 8; ++a) oT[a] *= wk;
+    q1_test<R, false>(nullptr, dvx, dvy, dvz, C.cm, oP);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) oP[a] *= wc;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { bx[q] = wc * dvx[q]; by[q] = wc * dvy[q]; bz[q] = wc * dvz[q]; }
+    q1_test<R, false>(nullptr, bx, by, bz, C.cm, oP);
+  }
 }
 
 // Exact Newton Jacobian product J_e (dp, dt) at the element state st.
@@ -295,9 +354,14 @@ __device__ __forceinline__ void elem_jtv(const ElemConst<R>& C, const ElemState<
   R Nx[8], Ny[8], Nz[8];
   q1_forward(lt, C.cm, m, Nx, Ny, Nz);
   const R c = st.c;
+  // with ScaleSums the energy rows' factor w k / h^2 and the continuity rows' -c / h^2 are applied to
+  // the 8 test sums (linear) instead of the Gauss-point values
+  constexpr bool kSums = ScaleSums<R>::value;
   const R wk2 = C.wih2 * kc;
+  const R iwk2 = kSums ? nc_rcp<R>(wk2) : R(1);
   const R tih = st.tau * C.ih;
   const R cih2 = c * C.ih * C.ih;
+  const R acih = kSums ? -cih2 * iwk2 : -cih2;
   R gx[8], gy[8], gz[8];         // h dL/du_q (without the centroid part)
   R g0x = 0, g0y = 0, g0z = 0, sdot = 0, kdot = 0;
 #pragma unroll
@@ -313,28 +377,44 @@ __device__ __forceinline__ void elem_jtv(const ElemConst<R>& C, const ElemState<
     sdot += wS * u0M;
     if (SENS) kdot += Nx[q] * st.hx[q] + Ny[q] * st.hy[q] + Nz[q] * st.hz[q];
     // dL/dgrad T_q / h = (w W rho0 c_p u_q + w k grad lt_q) / h, u_q = -(c/h) V_q; stored in N
-    const R a = -wWrc * cih2;
-    Nx[q] = a * st.vx[q] + wk2 * Nx[q];
-    Ny[q] = a * st.vy[q] + wk2 * Ny[q];
-    Nz[q] = a * st.vz[q] + wk2 * Nz[q];
+    // (with ScaleSums divided by w k / h^2)
+    const R a = wWrc * acih;
+    if constexpr (kSums) {
+      Nx[q] = a * st.vx[q] + Nx[q];
+      Ny[q] = a * st.vy[q] + Ny[q];
+      Nz[q] = a * st.vz[q] + Nz[q];
+    } else {
+      Nx[q] = a * st.vx[q] + wk2 * Nx[q];
+      Ny[q] = a * st.vy[q] + wk2 * Ny[q];
+      Nz[q] = a * st.vz[q] + wk2 * Nz[q];
+    }
   }
   const R t3 = -st.tau * st.tau * st.tau * C.c4he2 * sdot;
   g0x = R(0.125) * (st.tau * g0x + t3 * st.u0x);
   g0y = R(0.125) * (st.tau * g0y + t3 * st.u0y);
   g0z = R(0.125) * (st.tau * g0z + t3 * st.u0z);
   R kap = 0;
-  const R cbih = c * C.beta * C.ih;
+  const R cbih = kSums ? c * C.beta * C.ih * iwk2 : c * C.beta * C.ih;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     gx[q] += g0x; gy[q] += g0y; gz[q] += g0z;
     if (SENS) kap += gx[q] * st.vx[q] + gy[q] * st.vy[q] + gz[q] * st.vz[q];
-    m[q] = cbih * gz[q];   // dL/dT_q
+    m[q] = cbih * gz[q];   // dL/dT_q (with ScaleSums divided by w k / h^2)
   }
   if (SENS) { *dL_dkappa = -C.imu * C.ih * C.ih * kap; *dL_dk = C.wih2 * kdot; }
   q1_test<R, true>(m, Nx, Ny, Nz, C.cm, oT);
+  if constexpr (kSums) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) { gx[q] *= -cih2; gy[q] *= -cih2; gz[q] *= -cih2; }
-  q1_test<R, false>(nullptr, gx, gy, gz, C.cm, oP);
+    for (int a = 0; a < 8; ++a) oT[a] *= wk2;
+    q1_test<R, false>(nullptr, gx, gy, gz, C.cm, oP);
+    const R mcih2 = -cih2;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) oP[a] *= mcih2;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { gx[q] *= -cih2; gy[q] *= -cih2; gz[q] *= -cih2; }
+    q1_test<R, false>(nullptr, gx, gy, gz, C.cm, oP);
+  }
 }
 
 // Frozen-coefficient (Picard) element operator, a cheaper stand-in for J_e on the multigrid's finest
@@ -351,28 +431,31 @@ __device__ __forceinline__ void elem_picard(const ElemConst<R>& C, const R c, co
   q1_forward(dp, C.cm, dT, vx, vy, vz);    // dT: scratch for the (unused) P values
   R hx[8], hy[8], hz[8];
   q1_forward(dt, C.cm, dT, hx, hy, hz);
-  const R wc = C.wih2 * c;
-  R bx[8], by[8], bz[8];
+  // the factors w c / h^2 (continuity rows) and w k / h^2 (energy rows) are applied to the 8 test
+  // sums (linear) instead of the Gauss-point values
+  R bz[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    bx[q] = wc * vx[q];
-    by[q] = wc * vy[q];
-    bz[q] = wc * (vz[q] - C.betah * dT[q]);
-  }
-  q1_test<R, false>(nullptr, bx, by, bz, C.cm, oP);
-  const R a = C.wih * C.rc;      // A_q = w rho0 c_p u0 . grad dT_q = (w rho0 c_p / h) u0 . H_q
-  const R th = tau * C.ih;       // B_q / h = (tau / h) A_q u0 + (w k / h^2) H_q
+  for (int q = 0; q < 8; ++q) bz[q] = vz[q] - C.betah * dT[q];
+  q1_test<R, false>(nullptr, vx, vy, bz, C.cm, oP);
+  const R wc = C.wih2 * c;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) oP[a] *= wc;
   const R wk = C.wih2 * kc;
-  R A[8];
+  const R iwk = nc_rcp<R>(wk);
+  const R a = C.wih * C.rc * iwk;  // A_q = w rho0 c_p u0 . grad dT_q = (w rho0 c_p / h) u0 . H_q, / wk
+  const R th = tau * C.ih;         // B_q / h = (tau / h) A_q u0 + (w k / h^2) H_q, / wk
+  R A[8], bx[8], by[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     A[q] = a * (u0x * hx[q] + u0y * hy[q] + u0z * hz[q]);
     const R sq = th * A[q];
-    bx[q] = sq * u0x + wk * hx[q];
-    by[q] = sq * u0y + wk * hy[q];
-    bz[q] = sq * u0z + wk * hz[q];
+    bx[q] = sq * u0x + hx[q];
+    by[q] = sq * u0y + hy[q];
+    bz[q] = sq * u0z + hz[q];
   }
   q1_test<R, true>(A, bx, by, bz, C.cm, oT);
+#pragma unroll
+  for (int a2 = 0; a2 < 8; ++a2) oT[a2] *= wk;
 }
 
 // Transpose of elem_picard: the gradient of L = lp . A^P(d) + lt . A^T(d) with respect to d = (dP, dT).
@@ -384,24 +467,28 @@ __device__ __forceinline__ void elem_picard_t(const ElemConst<R>& C, const R c, 
   q1_forward(lp, C.cm, lv, Mx, My, Mz);    // lv: scratch for the (unused) lp values
   R Nx[8], Ny[8], Nz[8];
   q1_forward(lt, C.cm, lv, Nx, Ny, Nz);
+  // the factors w c / h^2 and w k / h^2 are applied to the 8 test sums instead of the Gauss-point values
+  q1_test<R, false>(nullptr, Mx, My, Mz, C.cm, oP);
   const R wc = C.wih2 * c;
-  R bx[8], by[8], bz[8], A[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) { bx[q] = wc * Mx[q]; by[q] = wc * My[q]; bz[q] = wc * Mz[q]; }
-  q1_test<R, false>(nullptr, bx, by, bz, C.cm, oP);
-  const R ab = -C.wih * c * C.beta;   // continuity rows into dT: A_q = -(w c beta / h) h dlp/dz
-  const R a = C.wih * C.rc;           // energy rows: B_q / h = (w rho0 c_p / h) lt*_q u0 + (w k / h^2) h grad lt
-  const R th = tau * C.ih;            // lt*_q = lt_q + tau u0 . grad lt_q
+  for (int a = 0; a < 8; ++a) oP[a] *= wc;
   const R wk = C.wih2 * kc;
+  const R iwk = nc_rcp<R>(wk);
+  const R ab = -C.wih * c * C.beta * iwk;   // continuity rows into dT: A_q = -(w c beta / h) h dlp/dz, / wk
+  const R a = C.wih * C.rc * iwk;           // energy rows: B_q / h = (w rho0 c_p / h) lt*_q u0 + (w k / h^2) h grad lt, / wk
+  const R th = tau * C.ih;                  // lt*_q = lt_q + tau u0 . grad lt_q
+  R bx[8], by[8], bz[8], A[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     A[q] = ab * Mz[q];
     const R sq = a * (lv[q] + th * (u0x * Nx[q] + u0y * Ny[q] + u0z * Nz[q]));
-    bx[q] = sq * u0x + wk * Nx[q];
-    by[q] = sq * u0y + wk * Ny[q];
-    bz[q] = sq * u0z + wk * Nz[q];
+    bx[q] = sq * u0x + Nx[q];
+    by[q] = sq * u0y + Ny[q];
+    bz[q] = sq * u0z + Nz[q];
   }
   q1_test<R, true>(A, bx, by, bz, C.cm, oT);
+#pragma unroll
+  for (int a2 = 0; a2 < 8; ++a2) oT[a2] *= wk;
 }
 
 }  // namespace nc

@@ -83,7 +83,7 @@ __global__ void k_residual_bc(Grid g, const double2* __restrict__ s, double* __r
 // J v or J^T w. With DL (transpose only), the pass also stores the element derivatives
 // (dL/dkappa_e, dL/dk_e) of L = w . R_e, the design derivatives the sensitivities need at this w.
 template <typename R, typename SV, typename O, bool TRANSPOSE, bool DL = false>
-__global__ void k_jprod(Grid g, Phys ph, ElemConst<R> C, const SV* __restrict__ s,
+__global__ void __launch_bounds__(128, 3) k_jprod(Grid g, Phys ph, ElemConst<R> C, const SV* __restrict__ s,
                         const typename Vec2<R>::type* __restrict__ mat, const double2* __restrict__ v,
                         O* __restrict__ out, double2* __restrict__ dl) {
   NC_ELEM_PROLOGUE();
@@ -362,6 +362,7 @@ static cudaError_t jprod(const Grid& g, const Phys& ph, const SV* s, const typen
   if (c) {
     c->launches += 1;
     c->bytes += (2.0 * sizeof(SV) + 32.0) * g.nn + 2.0 * sizeof(R) * g.ne + (dl ? 16.0 * g.ne : 0.0);
+    static_assert(!ScaleSums<R>::value, "the FP64 flop counts assume the Gauss-point form");
     c->flops += (kFlopsState + (TR ? (dl ? kFlopsSens : kFlopsJtv) : kFlopsJv)) * g.ne;
   }
   return cudaGetLastError();

@@ -213,7 +213,7 @@ __global__ void k_invert_diag(Grid g, R* __restrict__ diag, int* flag) {
 }
 
 template <typename R, bool TR>
-__global__ void k_level0_apply(Grid g, Phys ph, ElemConst<R> C, const typename Vec2<R>::type* __restrict__ s,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 1) k_level0_apply(Grid g, Phys ph, ElemConst<R> C, const typename Vec2<R>::type* __restrict__ s,
                                const typename Vec2<R>::type* __restrict__ mat,
                                const typename Vec2<R>::type* __restrict__ x, R* __restrict__ y) {
   NC_IJK_3D();
@@ -264,7 +264,7 @@ __global__ void k_frozen(Grid g, Phys ph, ElemConst<float> C, const float2* __re
 
 // Frozen-coefficient (Picard) finest-level operator y = A x (TR: A^T x), FP32, one thread per element.
 template <bool TR>
-__global__ void k_level0_picard(Grid g, ElemConst<float> C, const float4* __restrict__ fz,
+__global__ void __launch_bounds__(128, 10) k_level0_picard(Grid g, ElemConst<float> C, const float4* __restrict__ fz,
                                 const float2* __restrict__ mat, const float2* __restrict__ x, float* __restrict__ y) {
   NC_IJK_3D();
   if (i >= g.nx || j >= g.ny) return;
@@ -1273,7 +1273,7 @@ cudaError_t launch_galerkin_fine(const Grid& gf, const Grid& gc, const Phys& ph,
   if (c) {
     c->launches += 1;
     c->bytes += sizeof(R) * (2.0 * gf.nn + 2.0 * gf.ne + 4.0 * gf.nn + 256.0 * gc.ne);
-    c->flops += (kFlopsState + 16.0 * kFlopsJacColumn) * gf.ne;   // one element state, 16 columns
+    c->flops += (kFlopsState + 16.0 * flops_jac_column<R>()) * gf.ne;   // one element state, 16 columns
   }
   return cudaGetLastError();
 }
@@ -1317,7 +1317,7 @@ cudaError_t launch_level0_apply(const Grid& g, const Phys& ph, const typename Ve
   if (c) {
     c->launches += 1;
     c->bytes += sizeof(R) * (6.0 * g.nn + 2.0 * g.ne);   // s, x, y per node; (kappa, k) per element
-    c->flops += (kFlopsState + (transpose ? kFlopsJtv : kFlopsJv)) * g.ne;
+    c->flops += (kFlopsState + (transpose ? flops_jtv<R>() : flops_jv<R>())) * g.ne;
   }
   return cudaGetLastError();
 }

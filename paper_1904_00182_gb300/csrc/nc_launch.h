@@ -68,18 +68,25 @@ struct Counters {
 // Floating-point operations per element of the element kernels (adds + multiplies, an FMA counts
 // two), counted from nc_element.cuh by instantiating it with a counting number type: residual;
 // element state; J v direction part; J^T w part; J^T w with design derivatives; one element-Jacobian
-// column (the mean of the 8 P and 8 T columns).
+// column (the mean of the 8 P and 8 T columns). FP64 form (row factors at the Gauss points), then
+// the ScaleSums form of the FP32 kernels (row factors on the test sums).
 const double kFlopsResidual = 629.0, kFlopsState = 290.0, kFlopsJv = 743.0, kFlopsJtv = 778.0,
              kFlopsSens = 878.0, kFlopsJacColumn = 608.0;
+const double kFlopsJvS = 714.0, kFlopsJtvS = 748.0, kFlopsJacColumnS = 579.0;
+template <typename R> constexpr double flops_jv() { return ScaleSums<R>::value ? kFlopsJvS : kFlopsJv; }
+template <typename R> constexpr double flops_jtv() { return ScaleSums<R>::value ? kFlopsJtvS : kFlopsJtv; }
+template <typename R> constexpr double flops_jac_column() {
+  return ScaleSums<R>::value ? kFlopsJacColumnS : kFlopsJacColumn;
+}
 // Frozen-coefficient (Picard) element operator and its transpose.
-const double kFlopsPicard = 576.0, kFlopsPicardT = 578.0;
-// The same element code in double-float arithmetic, in FP32 flops: a double-float sum is 11 FP32
-// additions, a product 1 multiplication + 3 FMAs + 3 additions (10 flops). Adds / multiplies per
-// element: residual 351 / 278, element state 167 / 123, J^T w part 399 / 379, with design
-// derivatives 447 / 431.
+const double kFlopsPicard = 545.0, kFlopsPicardT = 548.0;
+// The same element code (ScaleSums form) in double-float arithmetic, in FP32 flops: a double-float
+// sum is 11 FP32 additions, a product 1 multiplication + 3 FMAs + 3 additions (10 flops). Adds /
+// multiplies per element: residual 351 / 248, element state 167 / 123, J^T w part 399 / 349, with
+// design derivatives 447 / 401.
 const double kDfAdd = 11.0, kDfMul = 10.0;
-const double kFlopsResidualDF = 351 * kDfAdd + 278 * kDfMul, kFlopsStateDF = 167 * kDfAdd + 123 * kDfMul,
-             kFlopsJtvDF = 399 * kDfAdd + 379 * kDfMul, kFlopsSensDF = 447 * kDfAdd + 431 * kDfMul;
+const double kFlopsResidualDF = 351 * kDfAdd + 248 * kDfMul, kFlopsStateDF = 167 * kDfAdd + 123 * kDfMul,
+             kFlopsJtvDF = 399 * kDfAdd + 349 * kDfMul, kFlopsSensDF = 447 * kDfAdd + 401 * kDfMul;
 
 // ---------------- element operators (nc_kernels_elem.cu) ----------------
 // out (2N doubles) = R(s); Dirichlet rows = s. s: double2 per node; mat: (kappa, k) per element.
