@@ -491,4 +491,139 @@ __device__ __forceinline__ void elem_picard_t(const ElemConst<R>& C, const R c, 
   for (int a2 = 0; a2 < 8; ++a2) oT[a2] *= wk;
 }
 
+// ---- the frozen-coefficient operator in the modal basis of the element ---------------------------
+// Every term of the frozen-coefficient operator is, per element, a constant coefficient times an
+// integral of products of Q1 shape functions and their derivatives, and the 2x2x2 Gauss rule
+// integrates these exactly. In the basis {1, 2s - 1} of each axis (s in [0, 1] the element
+// coordinate) the 1D integrals are diagonal or have one entry: mass diag(1, 1/3), stiffness
+// diag(0, 4), phi_m phi_n' nonzero only at (0, 1) (= 2) and phi_m' phi_n only at (1, 0) (= 2). So the
+// element Laplacian and the streamline-diffusion diagonal act mode by mode, and the convection,
+// buoyancy and cross streamline terms couple a mode with one other. The operator is then applied as:
+// nodal values -> modal coefficients (three butterfly stages), the sparse modal operator, modal test
+// sums -> nodal rows (the transposed butterflies); the same values as the Gauss-point form up to
+// rounding, with about a third of its arithmetic.
+
+// Per axis (f0, f1) -> (f0 + f1, f1 - f0): 8 x the coefficients of f in the basis {1, 2s - 1}^3.
+// Mode index m = mx + 2 my + 4 mz, bit d set for the factor 2 s_d - 1.
+template <typename R>
+__device__ __forceinline__ void q1_to_modal(const R f[8], R F[8]) {
+  R a[8], b[8];
+#pragma unroll
+  for (int yz = 0; yz < 4; ++yz) { a[2 * yz] = f[2 * yz] + f[2 * yz + 1]; a[2 * yz + 1] = f[2 * yz + 1] - f[2 * yz]; }
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int z = 0; z < 2; ++z) {
+      b[x + 4 * z] = a[x + 4 * z] + a[x + 2 + 4 * z];
+      b[x + 2 + 4 * z] = a[x + 2 + 4 * z] - a[x + 4 * z];
+    }
+#pragma unroll
+  for (int xy = 0; xy < 4; ++xy) { F[xy] = b[xy] + b[xy + 4]; F[xy + 4] = b[xy + 4] - b[xy]; }
+}
+
+// Transpose of q1_to_modal: modal test sums Y -> nodal rows, per axis (Y0, Y1) -> (Y0 - Y1, Y0 + Y1).
+template <typename R>
+__device__ __forceinline__ void q1_from_modal(const R Y[8], R y[8]) {
+  R a[8], b[8];
+#pragma unroll
+  for (int xy = 0; xy < 4; ++xy) { b[xy] = Y[xy] - Y[xy + 4]; b[xy + 4] = Y[xy] + Y[xy + 4]; }
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int z = 0; z < 2; ++z) {
+      a[x + 4 * z] = b[x + 4 * z] - b[x + 2 + 4 * z];
+      a[x + 2 + 4 * z] = b[x + 4 * z] + b[x + 2 + 4 * z];
+    }
+#pragma unroll
+  for (int yz = 0; yz < 4; ++yz) { y[2 * yz] = a[2 * yz] - a[2 * yz + 1]; y[2 * yz + 1] = a[2 * yz] + a[2 * yz + 1]; }
+}
+
+// 1D modal mass of mode bit b: 1 or 1/3; the 3D mass of the axes other than d (and e) of mode m.
+__host__ __device__ constexpr double q1m_mu(int b) { return b ? 1.0 / 3.0 : 1.0; }
+__host__ __device__ constexpr double q1m_mass_but(int m, int d) {
+  return (d == 0 ? 1.0 : q1m_mu(m & 1)) * (d == 1 ? 1.0 : q1m_mu((m >> 1) & 1)) * (d == 2 ? 1.0 : q1m_mu((m >> 2) & 1));
+}
+// Stiffness along axis d of mode m (diagonal): 4 x the mass of the other axes if bit d is set.
+__host__ __device__ constexpr double q1m_stiff(int m, int d) { return ((m >> d) & 1) ? 4.0 * q1m_mass_but(m, d) : 0.0; }
+__host__ __device__ constexpr double q1m_lambda(int m) { return q1m_stiff(m, 0) + q1m_stiff(m, 1) + q1m_stiff(m, 2); }
+// k x, without the multiplication when the compile-time weight k is 1.
+template <typename R> __device__ __forceinline__ R q1m_scale(double k, R x) { return k == 1.0 ? x : R(k) * x; }
+// Mass of the third axis f (f != d, e) of mode m.
+__host__ __device__ constexpr double q1m_mass_third(int m, int d, int e) {
+  return q1m_mu((m >> (3 - d - e)) & 1);
+}
+
+// The frozen-coefficient element operator (TR: its transpose) in the modal basis: the same inputs,
+// outputs and values (up to rounding) as elem_picard / elem_picard_t. The element integrals over
+// s in [0, 1]^3 are, with the 1/64 of the two unnormalised transforms folded into the coefficients
+// (h = 8 w/h^2, h^2 = 8 w/h):
+//   continuity rows  c h (grad phi_m . grad phi_n) P_n  -  c beta h^2 (d phi_m / dz) phi_n T_n
+//   energy rows      k h (grad phi_m . grad phi_n) T_n  +  rho0 c_p h^2 phi_m (u0 . grad phi_n) T_n
+//                    + tau rho0 c_p h (u0 . grad phi_m)(u0 . grad phi_n) T_n
+template <typename R, bool TR>
+__device__ __forceinline__ void elem_picard_modal(const ElemConst<R>& C, const R c, const R kc, const R u0x,
+                                                  const R u0y, const R u0z, const R tau, const R dp[8],
+                                                  const R dt[8], R oP[8], R oT[8]) {
+  R FP[8], FT[8];
+  q1_to_modal(dp, FP);
+  q1_to_modal(dt, FT);
+  const R q = R(0.125);
+  const R cP = q * C.wih2 * c;                    // c h / 64
+  const R cB = R(-0.25) * C.wih * C.beta * c;     // -c beta h^2 / 64 x 2 (the 1D integral of phi_1' phi_0)
+  const R cT = q * C.wih2 * kc;                   // k h / 64
+  const R cC = R(0.25) * C.wih * C.rc;            // rho0 c_p h^2 / 64 x 2 (the 1D integral of phi_0 phi_1')
+  const R cS = q * C.wih2 * C.rc * tau;           // tau rho0 c_p h / 64
+  const R u[3] = {u0x, u0y, u0z};
+  R uc[3], uu[3];
+  const R cS4 = R(4) * cS;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) { uc[d] = cC * u[d]; uu[d] = cS4 * u[d] * u[d]; }
+  R ux[3][3];                                     // 4 tau rho0 c_p h / 64 u_d u_e (d != e)
+  ux[0][1] = ux[1][0] = cS4 * u[0] * u[1];
+  ux[0][2] = ux[2][0] = cS4 * u[0] * u[2];
+  ux[1][2] = ux[2][1] = cS4 * u[1] * u[2];
+  // the Laplacian's eigenvalues 4 (one bit), 8/3 (two), 4/3 (three) times c h / 64 and k h / 64
+  const R lP[3] = {R(4) * cP, R(8.0 / 3.0) * cP, R(4.0 / 3.0) * cP};
+  const R lT[3] = {R(4) * cT, R(8.0 / 3.0) * cT, R(4.0 / 3.0) * cT};
+  R YP[8], YT[8];
+  YP[0] = R(0);                                   // the constant mode: no gradient
+  YT[0] = R(0);
+#pragma unroll
+  for (int m = 1; m < 8; ++m) {
+    // mode-diagonal parts: Laplacians, streamline diffusion along each axis with bit set
+    const int nb = (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1);
+    YP[m] = lP[nb - 1] * FP[m];
+    R dT = lT[nb - 1];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if ((m >> d) & 1) dT += q1m_scale(q1m_mass_but(m, d), uu[d]);
+    YT[m] = dT * FT[m];
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    // buoyancy: continuity test mode with bit z, temperature mode without it
+    const R b = q1m_scale(q1m_mass_but(m, 2), cB);
+    if (TR) YT[m] += b * FP[m + 4];
+    else YP[m + 4] += b * FT[m];
+  }
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int bd = 1 << d;
+      // convection: test mode without bit d, trial mode with it (transposed: the other way round)
+      if (!TR && !(m & bd)) YT[m] += uc[d] * q1m_scale(q1m_mass_but(m, d), FT[m | bd]);
+      if (TR && (m & bd)) YT[m] += uc[d] * q1m_scale(q1m_mass_but(m, d), FT[m & ~bd]);
+      // cross streamline diffusion (symmetric): test bit d set and e clear, trial the reverse
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const int be = 1 << e;
+        if (e != d && (m & bd) && !(m & be)) YT[m] += q1m_scale(q1m_mass_third(m, d, e), ux[d][e]) * FT[m ^ bd ^ be];
+      }
+    }
+  }
+  q1_from_modal(YP, oP);
+  q1_from_modal(YT, oT);
+}
+
 }  // namespace nc

@@ -262,9 +262,10 @@ __global__ void k_frozen(Grid g, Phys ph, ElemConst<float> C, const float2* __re
   fz[e] = make_float4(st.u0x, st.u0y, st.u0z, st.tau);
 }
 
-// Frozen-coefficient (Picard) finest-level operator y = A x (TR: A^T x), FP32, one thread per element.
+// Frozen-coefficient (Picard) finest-level operator y = A x (TR: A^T x), FP32, one thread per element,
+// the element operator applied in its modal basis (elem_picard_modal).
 template <bool TR>
-__global__ void __launch_bounds__(128, 10) k_level0_picard(Grid g, ElemConst<float> C, const float4* __restrict__ fz,
+__global__ void __launch_bounds__(128, 12) k_level0_picard(Grid g, ElemConst<float> C, const float4* __restrict__ fz,
                                 const float2* __restrict__ mat, const float2* __restrict__ x, float* __restrict__ y) {
   NC_IJK_3D();
   if (i >= g.nx || j >= g.ny) return;
@@ -281,8 +282,7 @@ __global__ void __launch_bounds__(128, 10) k_level0_picard(Grid g, ElemConst<flo
   const float4 f = fz[e];
   const float c = m.x * C.imu;
   float oP[8], oT[8];
-  if (TR) elem_picard_t<float>(C, c, m.y, f.x, f.y, f.z, f.w, dp, dt, oP, oT);
-  else elem_picard<float>(C, c, m.y, f.x, f.y, f.z, f.w, dp, dt, oP, oT);
+  elem_picard_modal<float, TR>(C, c, m.y, f.x, f.y, f.z, f.w, dp, dt, oP, oT);
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     if (top && (a >> 2)) continue;
@@ -368,8 +368,7 @@ __global__ void __launch_bounds__(128) k_level0_z(Grid g, Phys ph, ElemConst<flo
       } else {
         const float4 f = fz[e];
         const float c = m.x * C.imu;
-        if (TR) elem_picard_t<float>(C, c, m.y, f.x, f.y, f.z, f.w, dp, dt, oP, oT);
-        else elem_picard<float>(C, c, m.y, f.x, f.y, f.z, f.w, dp, dt, oP, oT);
+        elem_picard_modal<float, TR>(C, c, m.y, f.x, f.y, f.z, f.w, dp, dt, oP, oT);
       }
     } else {
 #pragma unroll
@@ -1349,7 +1348,7 @@ cudaError_t launch_level0_picard(const Grid& g, const Phys& ph, const float4* fz
   if (c) {
     c->launches += 1;
     c->bytes += 4.0 * (4.0 * g.nn + 6.0 * g.ne);   // x, y per node; (kappa, k), (u0, tau) per element
-    c->flops += (transpose ? kFlopsPicardT : kFlopsPicard) * g.ne;
+    c->flops += (transpose ? kFlopsPicardModalT : kFlopsPicardModal) * g.ne;
   }
   return cudaGetLastError();
 }

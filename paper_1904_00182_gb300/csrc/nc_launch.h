@@ -78,8 +78,10 @@ template <typename R> constexpr double flops_jtv() { return ScaleSums<R>::value 
 template <typename R> constexpr double flops_jac_column() {
   return ScaleSums<R>::value ? kFlopsJacColumnS : kFlopsJacColumn;
 }
-// Frozen-coefficient (Picard) element operator and its transpose.
+// Frozen-coefficient (Picard) element operator and its transpose: the Gauss-point form, and the modal
+// form the kernels use.
 const double kFlopsPicard = 545.0, kFlopsPicardT = 548.0;
+const double kFlopsPicardModal = 239.0, kFlopsPicardModalT = 239.0;
 // The same element code (ScaleSums form) in double-float arithmetic, in FP32 flops: a double-float
 // sum is 11 FP32 additions, a product 1 multiplication + 3 FMAs + 3 additions (10 flops). Adds /
 // multiplies per element: residual 351 / 248, element state 167 / 123, J^T w part 399 / 349, with

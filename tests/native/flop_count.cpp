@@ -84,6 +84,10 @@ static void count_all() {
   show("picard", sums);
   elem_picard_t<T>(C, T(1e-3), T(2.0), T(0.1), T(0.2), T(0.3), T(0.01), dp, dt, oP, oT);
   show("picard_t", sums);
+  elem_picard_modal<T, false>(C, T(1e-3), T(2.0), T(0.1), T(0.2), T(0.3), T(0.01), dp, dt, oP, oT);
+  show("picard_modal", sums);
+  elem_picard_modal<T, true>(C, T(1e-3), T(2.0), T(0.1), T(0.2), T(0.3), T(0.01), dp, dt, oP, oT);
+  show("picard_modal_t", sums);
 }
 
 int main() {

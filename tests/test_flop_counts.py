@@ -51,6 +51,8 @@ def test_flop_constants_match_the_element_code(tmp_path):
     assert vals["kFlopsJacColumnS"] == tot["jac16_sums"] / 16
     assert vals["kFlopsPicard"] == tot["picard_sums"] == tot["picard"]
     assert vals["kFlopsPicardT"] == tot["picard_t_sums"] == tot["picard_t"]
+    assert vals["kFlopsPicardModal"] == tot["picard_modal"] < vals["kFlopsPicard"] / 2
+    assert vals["kFlopsPicardModalT"] == tot["picard_modal_t"]
     # double-float kernels: the ScaleSums form
     assert df["kFlopsResidualDF"] == cnt["residual_sums"]
     assert df["kFlopsStateDF"] == cnt["state_sums"]
