@@ -487,6 +487,16 @@ int tail_level(const nc_problem* pb) {
 template <typename R>
 nc_status vcycle(nc_problem* pb, int l, bool tr);
 
+// Whether level l takes its first pre-smoothing sweep (block Jacobi from zero) from the restriction
+// that produces its right-hand side: levels between the finest and the coarsest, smoothed by block
+// Jacobi, above the fused tail.
+template <typename R>
+bool first_sweep_in_restrict(nc_problem* pb, int l) {
+  const MG<R>& mg = mg_of<R>(pb);
+  const int tl = tail_level(pb);
+  return l > 0 && l < (int)mg.lev.size() - 1 && !mg.lev[l].lf && (tl == 0 || l < tl);
+}
+
 // Post-smoothing sweeps on level l >= 1: mg_nu_coarse from level mg_nu_coarse_level on, else nu_post.
 int coarse_post_sweeps(const nc_problem* pb, int l) {
   const int from = std::max(1, pb->par.mg_nu_coarse_level);
@@ -598,18 +608,22 @@ nc_status vcycle(nc_problem* pb, int l, bool tr) {
                                             &pb->cnt));
   else if (d.lf)
     PCK(NC_PROF_SMOOTH, launch_line_smooth<R>(d.g, d.lf, d.b, d.x, om, tr, true, pb->st, &pb->cnt));
-  else
+  else if (!first_sweep_in_restrict<R>(pb, l))   // otherwise the restriction into b already swept
     PCK(NC_PROF_SMOOTH, launch_jacobi_update<R>(d.g, d.dinv, d.b, d.y, d.x, d.x, om, tr, true, pb->st, &pb->cnt));
   for (int it = 1; it < nu1; ++it) CKS(sweep(false));
   MGLevelDev<R>& c = mg.lev[l + 1];
+  // the coarse level's first sweep fused into its restriction where it is block Jacobi
+  const bool fuse = first_sweep_in_restrict<R>(pb, l + 1);
   if (l == 0) {
     // residual b - A x restricted directly, without storing it
     CKS(level_apply<R>(pb, l, tr, d.x, d.y));
-    PCK(NC_PROF_SMOOTH, launch_restrict_residual<R>(d.g, c.g, d.b, d.y, c.b, pb->st, &pb->cnt));
+    PCK(NC_PROF_SMOOTH, launch_restrict_residual<R>(d.g, c.g, d.b, d.y, c.b, pb->st, &pb->cnt, c.dinv,
+                                                    fuse ? c.x : nullptr, om, tr));
   } else {
     PCK(l == 1 ? NC_PROF_MG_STENCIL_L1 : NC_PROF_MG_STENCIL,
         launch_stencil_apply<R>(d.g, d.S, d.x, d.b, d.dinv, om, d.xn, tr, 1, pb->st, &pb->cnt));
-    PCK(NC_PROF_SMOOTH, launch_restrict<R>(d.g, c.g, d.xn, c.b, pb->st, &pb->cnt));
+    PCK(NC_PROF_SMOOTH, launch_restrict<R>(d.g, c.g, d.xn, c.b, pb->st, &pb->cnt, c.dinv, fuse ? c.x : nullptr,
+                                           om, tr));
   }
   CKS(l == 0 ? coarse_cycle<R>(pb, tr) : vcycle<R>(pb, l + 1, tr));
   PCK(NC_PROF_SMOOTH, launch_prolong_add<R>(d.g, c.g, c.x, d.x, pb->st, &pb->cnt));

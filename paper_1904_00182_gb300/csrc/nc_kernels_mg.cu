@@ -515,31 +515,54 @@ __device__ __forceinline__ typename Vec2<R>::type restrict_node(const Grid& gf, 
   return restrict_node_f<R>(gf, I, J, K, top, [&](int m) { return ld(rf + m); });
 }
 
-// Full weighting of the fine residual r = b - y formed on the fly (no stored residual vector).
-template <typename R>
-__global__ void k_restrict_res(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ b,
-                               const typename Vec2<R>::type* __restrict__ y, typename Vec2<R>::type* __restrict__ bc) {
-  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pidx >= gc.NXY) return;
-  const int K = blockIdx.y;
-  const int J = pidx / gc.NX;
-  const int I = pidx - J * gc.NX;
-  bc[pidx + gc.NXY * K] = mask_fixed<R>(gc, I, J, K, restrict_node_f<R>(gf, I, J, K, gc.bc == kBcTop && K >= gc.nz, [&](int m) {
-    const typename Vec2<R>::type bb = b[m], yy = y[m];
-    return mk2<R>(bb.x - yy.x, bb.y - yy.y);
-  }));
+// Optional first pre-smoothing sweep of the coarse level, fused into the restriction that produces
+// its right-hand side: the block-Jacobi sweep from x = 0, x_c = omega D_c^-1 b_c (SW = 1), or with
+// D_c^-T for the transposed hierarchy (SW = 2); SW = 0 stores b_c only.
+template <typename R> struct FirstSweep {
+  const R* dinv;
+  typename Vec2<R>::type* x;
+  R omega;
+};
+
+template <typename R, int SW>
+__device__ __forceinline__ void store_restricted(int n, typename Vec2<R>::type v, typename Vec2<R>::type* bc,
+                                                 const FirstSweep<R>& fs) {
+  bc[n] = v;
+  if (SW) {
+    const R* d = fs.dinv + 4 * n;
+    R z0, z1;
+    if (SW == 2) { z0 = d[0] * v.x + d[2] * v.y; z1 = d[1] * v.x + d[3] * v.y; }
+    else { z0 = d[0] * v.x + d[1] * v.y; z1 = d[2] * v.x + d[3] * v.y; }
+    fs.x[n] = mk2<R>(fs.omega * z0, fs.omega * z1);
+  }
 }
 
-template <typename R>
-__global__ void k_restrict(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ rf,
-                           typename Vec2<R>::type* __restrict__ bc) {
+// Full weighting of the fine residual r = b - y formed on the fly (no stored residual vector).
+template <typename R, int SW>
+__global__ void k_restrict_res(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ b,
+                               const typename Vec2<R>::type* __restrict__ y, typename Vec2<R>::type* __restrict__ bc,
+                               FirstSweep<R> fs) {
   const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
   if (pidx >= gc.NXY) return;
   const int K = blockIdx.y;
   const int J = pidx / gc.NX;
   const int I = pidx - J * gc.NX;
-  bc[pidx + gc.NXY * K] =
-      mask_fixed<R>(gc, I, J, K, restrict_node<R>(gf, rf, I, J, K, gc.bc == kBcTop && K >= gc.nz, LdPlain()));
+  store_restricted<R, SW>(pidx + gc.NXY * K, mask_fixed<R>(gc, I, J, K, restrict_node_f<R>(gf, I, J, K, gc.bc == kBcTop && K >= gc.nz, [&](int m) {
+    const typename Vec2<R>::type bb = b[m], yy = y[m];
+    return mk2<R>(bb.x - yy.x, bb.y - yy.y);
+  })), bc, fs);
+}
+
+template <typename R, int SW>
+__global__ void k_restrict(Grid gf, Grid gc, const typename Vec2<R>::type* __restrict__ rf,
+                           typename Vec2<R>::type* __restrict__ bc, FirstSweep<R> fs) {
+  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pidx >= gc.NXY) return;
+  const int K = blockIdx.y;
+  const int J = pidx / gc.NX;
+  const int I = pidx - J * gc.NX;
+  store_restricted<R, SW>(pidx + gc.NXY * K,
+      mask_fixed<R>(gc, I, J, K, restrict_node<R>(gf, rf, I, J, K, gc.bc == kBcTop && K >= gc.nz, LdPlain())), bc, fs);
 }
 
 // Trilinear interpolation of the coarse correction at fine node (i, j, k), added to xf.
@@ -1395,20 +1418,29 @@ cudaError_t launch_jacobi_io(const Grid& g, const R* dinv, typename Vec2<R>::typ
 
 template <typename R>
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* rf,
-                            typename Vec2<R>::type* bc, cudaStream_t st, Counters* c) {
+                            typename Vec2<R>::type* bc, cudaStream_t st, Counters* c, const R* dinv_c,
+                            typename Vec2<R>::type* xc, R omega, bool transpose) {
   const Launch3 L = launch_nodes_flat(gc);
-  k_restrict<R><<<L.grid, L.block, 0, st>>>(gf, gc, rf, bc);
-  if (c) { c->launches += 1; c->bytes += sizeof(R) * 2.0 * (gf.nn + gc.nn); }
+  const FirstSweep<R> fs{dinv_c, xc, omega};
+  if (!xc) k_restrict<R, 0><<<L.grid, L.block, 0, st>>>(gf, gc, rf, bc, fs);
+  else if (transpose) k_restrict<R, 2><<<L.grid, L.block, 0, st>>>(gf, gc, rf, bc, fs);
+  else k_restrict<R, 1><<<L.grid, L.block, 0, st>>>(gf, gc, rf, bc, fs);
+  // + D_c^-1 and x_c for the fused first sweep
+  if (c) { c->launches += 1; c->bytes += sizeof(R) * (2.0 * (gf.nn + gc.nn) + (xc ? 6.0 * gc.nn : 0.0)); }
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_restrict_residual(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* b,
                                      const typename Vec2<R>::type* y, typename Vec2<R>::type* bc, cudaStream_t st,
-                                     Counters* c) {
+                                     Counters* c, const R* dinv_c, typename Vec2<R>::type* xc, R omega,
+                                     bool transpose) {
   const Launch3 L = launch_nodes_flat(gc);
-  k_restrict_res<R><<<L.grid, L.block, 0, st>>>(gf, gc, b, y, bc);
-  if (c) { c->launches += 1; c->bytes += sizeof(R) * 2.0 * (2.0 * gf.nn + gc.nn); }
+  const FirstSweep<R> fs{dinv_c, xc, omega};
+  if (!xc) k_restrict_res<R, 0><<<L.grid, L.block, 0, st>>>(gf, gc, b, y, bc, fs);
+  else if (transpose) k_restrict_res<R, 2><<<L.grid, L.block, 0, st>>>(gf, gc, b, y, bc, fs);
+  else k_restrict_res<R, 1><<<L.grid, L.block, 0, st>>>(gf, gc, b, y, bc, fs);
+  if (c) { c->launches += 1; c->bytes += sizeof(R) * (2.0 * (2.0 * gf.nn + gc.nn) + (xc ? 6.0 * gc.nn : 0.0)); }
   return cudaGetLastError();
 }
 
@@ -1618,9 +1650,10 @@ cudaError_t launch_line_smooth(const Grid& g, const R* LF, const typename Vec2<R
                                            const Vec2<R>::type*, const Vec2<R>::type*, Vec2<R>::type*, double*, \
                                            R, bool, bool, cudaStream_t, Counters*);                             \
   template cudaError_t launch_restrict<R>(const Grid&, const Grid&, const Vec2<R>::type*, Vec2<R>::type*,     \
-                                          cudaStream_t, Counters*);                                            \
+                                          cudaStream_t, Counters*, const R*, Vec2<R>::type*, R, bool);        \
   template cudaError_t launch_restrict_residual<R>(const Grid&, const Grid&, const Vec2<R>::type*,            \
-                                                   const Vec2<R>::type*, Vec2<R>::type*, cudaStream_t, Counters*); \
+                                                   const Vec2<R>::type*, Vec2<R>::type*, cudaStream_t, Counters*, \
+                                                   const R*, Vec2<R>::type*, R, bool);                          \
   template cudaError_t launch_prolong_add<R>(const Grid&, const Grid&, const Vec2<R>::type*, Vec2<R>::type*,  \
                                              cudaStream_t, Counters*);                                         \
   template cudaError_t launch_dense_assemble<R>(const Grid&, const R*, double*, int, cudaStream_t, Counters*);\

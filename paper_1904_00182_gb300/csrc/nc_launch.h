@@ -290,15 +290,20 @@ cudaError_t launch_jacobi_io(const Grid& g, const R* dinv, typename Vec2<R>::typ
                              const typename Vec2<R>::type* y, const typename Vec2<R>::type* x,
                              typename Vec2<R>::type* xn, double* z64, R omega, bool transpose, bool first,
                              cudaStream_t st, Counters* c);
-// b_c = P^T r_f (full weighting, Dirichlet coarse rows 0)
+// b_c = P^T r_f (full weighting, Dirichlet coarse rows 0). With xc, also the coarse level's first
+// block-Jacobi sweep from zero, x_c = omega D_c^-1 b_c (transpose: D_c^-T; dinv_c: the inverted
+// 2x2 blocks).
 template <typename R>
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* rf,
-                            typename Vec2<R>::type* bc, cudaStream_t st, Counters* c);
-// Restriction of the residual b - y formed on the fly (level 0: no residual vector is stored).
+                            typename Vec2<R>::type* bc, cudaStream_t st, Counters* c, const R* dinv_c = nullptr,
+                            typename Vec2<R>::type* xc = nullptr, R omega = R(0), bool transpose = false);
+// Restriction of the residual b - y formed on the fly (level 0: no residual vector is stored); the
+// optional first coarse sweep as for launch_restrict.
 template <typename R>
 cudaError_t launch_restrict_residual(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* b,
                                      const typename Vec2<R>::type* y, typename Vec2<R>::type* bc, cudaStream_t st,
-                                     Counters* c);
+                                     Counters* c, const R* dinv_c = nullptr, typename Vec2<R>::type* xc = nullptr,
+                                     R omega = R(0), bool transpose = false);
 // x_f += P x_c
 template <typename R>
 cudaError_t launch_prolong_add(const Grid& gf, const Grid& gc, const typename Vec2<R>::type* xc,
