@@ -101,6 +101,12 @@ enum { NC_MGOP_EXACT = 0, NC_MGOP_PICARD = 1 };
  * aimed at convection along the buoyancy direction z. */
 enum { NC_SMOOTH_BLOCK_JACOBI = 0, NC_SMOOTH_ZLINE = 1 };
 
+/* Inner solver of the PDE filter's Helmholtz system (Sec. 5.2), inside FP64 iterative refinement.
+ * NC_FILTER_SPECTRAL: a direct FP32 solve in the cosine basis of each axis, which diagonalises the
+ * 1D Q1 stiffness and mass matrices with Neumann ends (six dense FP32 transforms through cuBLAS and
+ * one scaling per solve). NC_FILTER_CHEBYSHEV: Jacobi-preconditioned FP32 Chebyshev iterations. */
+enum { NC_FILTER_SPECTRAL = 0, NC_FILTER_CHEBYSHEV = 1 };
+
 typedef struct nc_problem nc_problem;
 
 typedef struct {
@@ -191,6 +197,7 @@ typedef struct {
   int mg_smoother;      /* smoother of the multigrid levels below the finest (the finest level keeps 2x2
                            block Jacobi): NC_SMOOTH_BLOCK_JACOBI or NC_SMOOTH_ZLINE. Fixed at creation;
                            NC_SMOOTH_ZLINE needs mg_tail_nodes = 0 [NC_SMOOTH_BLOCK_JACOBI] */
+  int filter_method;    /* NC_FILTER_SPECTRAL or NC_FILTER_CHEBYSHEV [NC_FILTER_SPECTRAL] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */

@@ -15,7 +15,7 @@ from . import _abi
 from ._abi import (NC_ARITH_DF64, NC_ARITH_FP64, NC_BASIS_FP32, NC_BASIS_FP64,  # noqa: F401
                    NC_OBJ_MEAN_T_HEATED, NC_OBJ_SUPG_COMPLIANCE, NC_BC_TOP, NC_BC_CAVITY,
                    NC_REGION_BOX, NC_REGION_CYLINDER, NC_MGOP_EXACT, NC_MGOP_PICARD,
-                   NC_SMOOTH_BLOCK_JACOBI, NC_SMOOTH_ZLINE,
+                   NC_SMOOTH_BLOCK_JACOBI, NC_SMOOTH_ZLINE, NC_FILTER_SPECTRAL, NC_FILTER_CHEBYSHEV,
                    NC_PREC_FP64,
                    NC_PREC_MIXED, NatConvError, Grid, Params, Stats, default_params, footprint_bytes,
                    load_library)
@@ -24,7 +24,8 @@ from .problem import Problem  # noqa: F401
 __all__ = ["Problem", "Grid", "Params", "Stats", "NatConvError", "default_params", "footprint_bytes",
            "NC_PREC_MIXED", "NC_PREC_FP64", "NC_ARITH_DF64", "NC_ARITH_FP64", "NC_BASIS_FP64", "NC_BASIS_FP32",
            "NC_OBJ_MEAN_T_HEATED", "NC_OBJ_SUPG_COMPLIANCE", "NC_BC_TOP", "NC_BC_CAVITY", "NC_REGION_BOX", "NC_REGION_CYLINDER",
-           "NC_MGOP_EXACT", "NC_MGOP_PICARD", "NC_SMOOTH_BLOCK_JACOBI", "NC_SMOOTH_ZLINE",
+           "NC_MGOP_EXACT", "NC_MGOP_PICARD", "NC_SMOOTH_BLOCK_JACOBI", "NC_SMOOTH_ZLINE", "NC_FILTER_SPECTRAL",
+           "NC_FILTER_CHEBYSHEV",
            "library_path"]
 
 

@@ -23,6 +23,8 @@ NC_MGOP_EXACT = 0
 NC_MGOP_PICARD = 1
 NC_SMOOTH_BLOCK_JACOBI = 0
 NC_SMOOTH_ZLINE = 1
+NC_FILTER_SPECTRAL = 0
+NC_FILTER_CHEBYSHEV = 1
 
 STATUS_NAMES = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_OOM", 3: "NC_ERR_CUDA", 4: "NC_ERR_DIVERGED",
                 5: "NC_ERR_MAXIT", 6: "NC_ERR_NAN", 7: "NC_ERR_TIMEOUT", 8: "NC_ERR_STATE"}
@@ -70,7 +72,7 @@ class Params(ctypes.Structure):
         ("heat_radius", ctypes.c_double), ("design_radius", ctypes.c_double), ("heat_z0", ctypes.c_int),
         ("mg_op0", ctypes.c_int), ("mg_tail_ctas", ctypes.c_int), ("elem_chunk", ctypes.c_int),
         ("mg_nu_coarse", ctypes.c_int), ("mg_nu_coarse_level", ctypes.c_int),
-        ("mg_smoother", ctypes.c_int),
+        ("mg_smoother", ctypes.c_int), ("filter_method", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -73,7 +73,9 @@ def build(verbose=False, force=False):
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, _sources()))
     tmp = LIB + ".tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    # cuBLAS (the spectral filter's dense transforms), found at run time through the toolkit's library path
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcublas", "-Xlinker", "-rpath=" + cudalib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

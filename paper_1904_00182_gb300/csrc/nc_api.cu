@@ -17,6 +17,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cublas_v2.h>
+
 #include "natconv.h"
 #include "nc_launch.h"
 
@@ -25,6 +27,7 @@ using namespace nc;
 namespace {
 
 const int kMaxRestart = 64;
+const size_t kBlasWorkspace = 32u << 20;   // cuBLAS workspace of the spectral filter transforms
 
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -114,6 +117,14 @@ struct nc_problem {
   FilterConstF Ff;
   double cheb_a = 0.0, cheb_b = 0.0;   // bounds of the spectrum of D^-1 (r^2 K + M)
   int cheb_iters = 0;                  // FP32 Chebyshev steps per refinement pass
+  // spectral filter solve: per axis the cosine matrix C_ij = cos(pi i j / n) (FP32, symmetric) and
+  // the eigenvalues of the 1D stiffness and mass matrices in that basis; the cuBLAS handle of the
+  // axis transforms (dense FP32 GEMMs) and its workspace
+  float* fC[3] = {nullptr, nullptr, nullptr};
+  float* flam[3] = {nullptr, nullptr, nullptr};
+  float* fmu[3] = {nullptr, nullptr, nullptr};
+  cublasHandle_t blas = nullptr;
+  void* blas_ws = nullptr;
   // multigrid
   Levels lv;
   MG<float> mg32;
@@ -279,6 +290,87 @@ nc_status norm2_free(nc_problem* pb, const double* a, double* out) {
 // (r^2 K + M) fx = fb, FP64 result. Each refinement pass solves the correction equation for the
 // current FP64 residual with a fixed number of FP32 Chebyshev steps (Jacobi-preconditioned, bounds
 // from the stencil's Fourier symbol, no reductions), then recomputes the residual in FP64.
+// Direct FP32 solve of the filter system (r^2 K + M) x = b on the node grid (homogeneous Neumann
+// boundaries, uniform h). The 1D Q1 stiffness and consistent mass matrices with Neumann ends are
+// both diagonalised by the cosine matrix C_ij = cos(pi i j / n) (C^T K C and C^T M C are diagonal),
+// so with C3 = Cx (x) Cy (x) Cz the 3D operator r^2 (K M M + M K M + M M K) + M M M satisfies
+// C3^T A C3 = D diagonal and x = C3 D^-1 C3^T b (C symmetric: C3^T = C3). Each axis transform is one
+// dense FP32 GEMM with the axis' cosine matrix (a batch of them for the middle axis); fd0 and fd1
+// are the work vectors. The FP64 refinement of filter_solve corrects the FP32 rounding.
+cudaError_t spectral_filter(nc_problem* pb, const float* in, float* out) {
+  const Grid& g = pb->g;
+  const int NX = g.NX, NY = g.NY, NZ = g.NZ, NXY = g.NXY;
+  const float one = 1.0f, zero = 0.0f;
+  float* t1 = pb->fd0;
+  float* t2 = pb->fd1;
+  auto ok = [](cublasStatus_t e) { return e == CUBLAS_STATUS_SUCCESS; };
+  auto tx = [&](const float* a, float* b) {   // along x: b = Cx a, a as NX x (NY NZ)
+    return ok(cublasSgemm(pb->blas, CUBLAS_OP_N, CUBLAS_OP_N, NX, NY * NZ, NX, &one, pb->fC[0], NX, a, NX, &zero, b, NX));
+  };
+  auto ty = [&](const float* a, float* b) {   // along y: per z plane b_k = a_k Cy, a_k as NX x NY
+    return ok(cublasSgemmStridedBatched(pb->blas, CUBLAS_OP_N, CUBLAS_OP_N, NX, NY, NY, &one, a, NX, NXY, pb->fC[1],
+                                        NY, 0, &zero, b, NX, NXY, NZ));
+  };
+  auto tz = [&](const float* a, float* b) {   // along z: b = a Cz, a as (NX NY) x NZ
+    return ok(cublasSgemm(pb->blas, CUBLAS_OP_N, CUBLAS_OP_N, NXY, NZ, NZ, &one, a, NXY, pb->fC[2], NZ, &zero, b, NXY));
+  };
+  if (!tx(in, t1) || !ty(t1, t2) || !tz(t2, t1)) return cudaErrorUnknown;
+  const double r = pb->par.filter_radius * g.h / (2.0 * std::sqrt(3.0));
+  cudaError_t e = launch_filter_scale(g, t1, pb->flam, pb->fmu, (float)(r * r), pb->st, nullptr);
+  if (e != cudaSuccess) return e;
+  if (!tx(t1, t2) || !ty(t2, t1) || !tz(t1, out)) return cudaErrorUnknown;
+  pb->cnt.launches += 7;
+  pb->cnt.bytes += 4.0 * 13.0 * g.nn;   // six transforms read and write the vector, the scaling reads it
+  pb->cnt.flops += 4.0 * g.nn * (NX + NY + NZ) + 8.0 * g.nn;
+  return cudaGetLastError();
+}
+
+// Cosine matrices and 1D eigenvalues of the spectral filter solve (per axis, from the grid alone),
+// and the cuBLAS handle on the problem's stream with a workspace from the problem's allocations.
+nc_status spectral_setup(nc_problem* pb) {
+  const Grid& g = pb->g;
+  const int ns[3] = {g.nx, g.ny, g.nz};
+  const double h = g.h;
+  for (int d = 0; d < 3; ++d) {
+    const int n = ns[d], N = n + 1;
+    std::vector<float> C((size_t)N * N), lam(N), mu(N);
+    std::vector<double> v(N);
+    for (int j = 0; j < N; ++j) {
+      for (int i = 0; i < N; ++i) {
+        // cos(pi i j / n) with the argument reduced to [0, 2 pi) in integers
+        v[i] = std::cos(M_PI * (double)(((long long)i * j) % (2LL * n)) / n);
+        C[(size_t)j * N + i] = (float)v[i];
+      }
+      // v^T K v and v^T M v with the assembled 1D matrices: K = (1/h) tridiag(-1, 2, -1), M = (h/6)
+      // tridiag(1, 4, 1), their end rows halved on the diagonal (Neumann ends)
+      double kv = 0.0, mv = 0.0;
+      for (int i = 0; i < N; ++i) {
+        const bool end = (i == 0 || i == n);
+        double Kv = (end ? 1.0 : 2.0) * v[i], Mv = (end ? 2.0 : 4.0) * v[i];
+        if (i > 0) { Kv -= v[i - 1]; Mv += v[i - 1]; }
+        if (i < n) { Kv -= v[i + 1]; Mv += v[i + 1]; }
+        kv += v[i] * Kv / h;
+        mv += v[i] * Mv * h / 6.0;
+      }
+      lam[j] = (float)kv;
+      mu[j] = (float)mv;
+    }
+    CKS(dalloc(pb, &pb->fC[d], (size_t)N * N));
+    CKS(dalloc(pb, &pb->flam[d], (size_t)N));
+    CKS(dalloc(pb, &pb->fmu[d], (size_t)N));
+    CK(cudaMemcpy(pb->fC[d], C.data(), sizeof(float) * C.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pb->flam[d], lam.data(), sizeof(float) * N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pb->fmu[d], mu.data(), sizeof(float) * N, cudaMemcpyHostToDevice));
+  }
+  if (cublasCreate(&pb->blas) != CUBLAS_STATUS_SUCCESS) { pb->blas = nullptr; return fail(pb, NC_ERR_CUDA, "cublasCreate failed"); }
+  CKS(dalloc(pb, (char**)&pb->blas_ws, kBlasWorkspace));
+  if (cublasSetStream(pb->blas, pb->st) != CUBLAS_STATUS_SUCCESS ||
+      cublasSetMathMode(pb->blas, CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS ||
+      cublasSetWorkspace(pb->blas, pb->blas_ws, kBlasWorkspace) != CUBLAS_STATUS_SUCCESS)
+    return fail(pb, NC_ERR_CUDA, "cuBLAS set-up failed");
+  return NC_OK;
+}
+
 nc_status filter_solve(nc_problem* pb) {
   const Grid& g = pb->g;
   const long long n = g.nn;
@@ -292,16 +384,21 @@ nc_status filter_solve(nc_problem* pb) {
   const double tol2 = pb->par.filter_rtol * pb->par.filter_rtol * bb;
   for (int pass = 0; pass < 12; ++pass) {
     PCK(NC_PROF_FILTER, launch_cast_d2f(pb->frf, pb->fr, n, pb->st, &pb->cnt));
-    PCK(NC_PROF_FILTER, launch_cheb_init(n, pb->fdinvf, pb->frf, pb->fxf, pb->fd0, (float)(1.0 / theta), pb->st, &pb->cnt));
-    double rho = 1.0 / sigma;
-    float* d0 = pb->fd0;
-    float* d1 = pb->fd1;
-    for (int it = 0; it < pb->cheb_iters; ++it) {
-      const double rho1 = 1.0 / (2.0 * sigma - rho);
-      PCK(NC_PROF_FILTER, launch_cheb_step(g, pb->Ff, pb->fdinvf, d0, d1, pb->fxf, pb->frf, (float)(rho1 * rho),
-                                           (float)(2.0 * rho1 / delta), pb->st, &pb->cnt));
-      rho = rho1;
-      std::swap(d0, d1);
+    if (pb->par.filter_method == NC_FILTER_SPECTRAL) {
+      PCK(NC_PROF_FILTER, spectral_filter(pb, pb->frf, pb->fxf));
+    } else {
+      PCK(NC_PROF_FILTER, launch_cheb_init(n, pb->fdinvf, pb->frf, pb->fxf, pb->fd0, (float)(1.0 / theta), pb->st,
+                                           &pb->cnt));
+      double rho = 1.0 / sigma;
+      float* d0 = pb->fd0;
+      float* d1 = pb->fd1;
+      for (int it = 0; it < pb->cheb_iters; ++it) {
+        const double rho1 = 1.0 / (2.0 * sigma - rho);
+        PCK(NC_PROF_FILTER, launch_cheb_step(g, pb->Ff, pb->fdinvf, d0, d1, pb->fxf, pb->frf, (float)(rho1 * rho),
+                                             (float)(2.0 * rho1 / delta), pb->st, &pb->cnt));
+        rho = rho1;
+        std::swap(d0, d1);
+      }
     }
     PCK(NC_PROF_FILTER, launch_add_f2d(pb->fx, pb->fxf, n, pb->st, &pb->cnt));
     PCK(NC_PROF_FILTER, launch_helmholtz(g, pb->F, pb->fx, pb->fq, pb->st, &pb->cnt));
@@ -1046,6 +1143,7 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (p->mg_nu_coarse < 0 || p->mg_nu_coarse > 16) { *why = "mg_nu_coarse must be in [0, 16]"; return NC_ERR_ARG; }
   if (p->mg_nu_coarse_level < 0) { *why = "mg_nu_coarse_level must be >= 0"; return NC_ERR_ARG; }
   if (p->mg_smoother != NC_SMOOTH_BLOCK_JACOBI && p->mg_smoother != NC_SMOOTH_ZLINE) { *why = "unknown mg_smoother"; return NC_ERR_ARG; }
+  if (p->filter_method != NC_FILTER_SPECTRAL && p->filter_method != NC_FILTER_CHEBYSHEV) { *why = "unknown filter_method"; return NC_ERR_ARG; }
   if (p->mg_smoother == NC_SMOOTH_ZLINE && p->mg_tail_nodes > 0) {
     *why = "the fused multigrid tail smooths with block Jacobi (NC_SMOOTH_ZLINE needs mg_tail_nodes = 0)"; return NC_ERR_ARG;
   }
@@ -1094,6 +1192,9 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
   if (p->precision != NC_PREC_FP64) b += al(16 * ne) + 2 * al(16 * nn);   // mat_df, s_df, w_df
   b += al(8 * 66 * kReduceBlocksMax) + al(8 * 132);
   b += 5 * al(8 * nn) + 5 * al(4 * nn); // filter vectors
+  for (const int n1 : {gr->nx, gr->ny, gr->nz})   // spectral filter: cosine matrix and 1D eigenvalues per axis
+    b += al(4 * (size_t)(n1 + 1) * (n1 + 1)) + 2 * al(4 * (size_t)(n1 + 1));
+  b += al(kBlasWorkspace);
   const size_t rs = p->precision == NC_PREC_FP64 ? 8 : 4;
   for (size_t l = 0; l < lv.g.size(); ++l) {
     b += 4 * al(2 * rs * lv.g[l].nn);
@@ -1238,6 +1339,7 @@ nc_status nc_default_params(nc_params* p) {
   p->mg_tail_nodes = 0;
   p->mg_op0 = NC_MGOP_PICARD;
   p->mg_smoother = NC_SMOOTH_BLOCK_JACOBI;
+  p->filter_method = NC_FILTER_SPECTRAL;
   p->elem_chunk = -1;
   p->mg_reuse_below = 1e-2;
   p->adjoint_df64_steps = 1;
@@ -1297,6 +1399,7 @@ nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream,
   A(dalloc(pb, &pb->fxf, nn)); A(dalloc(pb, &pb->frf, nn)); A(dalloc(pb, &pb->fd0, nn)); A(dalloc(pb, &pb->fd1, nn));
   A(dalloc(pb, &pb->fdinvf, nn));
   A(dalloc(pb, &pb->dflag, 1));
+  if (s == NC_OK) s = spectral_setup(pb);
   if (s == NC_OK) s = p->precision == NC_PREC_FP64 ? mg_alloc<double>(pb) : mg_alloc<float>(pb);
   if (s == NC_OK) {
     cudaError_t e = cudaMallocHost(&pb->hres, sizeof(double) * 132);
@@ -1326,6 +1429,7 @@ nc_status nc_destroy_problem(nc_problem* pb) {
   prof_flush(pb);
   drop_graphs(pb);
   for (cudaEvent_t e : pb->evpool) cudaEventDestroy(e);
+  if (pb->blas) cublasDestroy(pb->blas);
   for (void* q : pb->allocs) cudaFree(q);
   if (pb->hres) cudaFreeHost(pb->hres);
   if (pb->hflag) cudaFreeHost(pb->hflag);

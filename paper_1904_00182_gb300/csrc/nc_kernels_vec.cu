@@ -670,6 +670,29 @@ cudaError_t launch_cheb_step(const Grid& g, const FilterConstF& F, const float* 
   return cudaGetLastError();
 }
 
+// Division by the eigenvalues of the filter operator in the cosine basis of each axis:
+// t /= r^2 (lx_i my_j mz_k + mx_i ly_j mz_k + mx_i my_j lz_k) + mx_i my_j mz_k, with (l, m) the 1D
+// stiffness and mass eigenvalues of the axis.
+__global__ void k_filter_scale(Grid g, float* __restrict__ t, const float* __restrict__ lx,
+                               const float* __restrict__ mx, const float* __restrict__ ly,
+                               const float* __restrict__ my, const float* __restrict__ lz,
+                               const float* __restrict__ mz, float r2) {
+  NC_NODE_FLAT(g);
+  const float ax = lx[i], bx = mx[i], ay = ly[j], by = my[j], az = lz[k], bz = mz[k];
+  const float byz = by * bz;
+  const float d = r2 * (ax * byz + bx * (ay * bz + by * az)) + bx * byz;
+  const long long n = pidx + (long long)g.NXY * k;
+  t[n] = t[n] / d;
+}
+
+cudaError_t launch_filter_scale(const Grid& g, float* t, const float* const lam[3], const float* const mu[3],
+                                float r2, cudaStream_t st, Counters* c) {
+  const Launch3 L = launch_nodes_flat(g);
+  k_filter_scale<<<L.grid, L.block, 0, st>>>(g, t, lam[0], mu[0], lam[1], mu[1], lam[2], mu[2], r2);
+  if (c) { c->launches += 1; c->bytes += 8.0 * g.nn; }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_add_f2d(double* y, const float* x, long long n, cudaStream_t st, Counters* c) {
   k_add_f2d<<<stream_blocks(n), 256, 0, st>>>(y, x, n);
   if (c) { c->launches += 1; c->bytes += 20.0 * n; }

@@ -190,6 +190,10 @@ cudaError_t launch_cheb_step(const Grid& g, const FilterConstF& F, const float* 
                              float* x, float* r, float c1, float c2, cudaStream_t st, Counters* c);
 // y += (double) x
 cudaError_t launch_add_f2d(double* y, const float* x, long long n, cudaStream_t st, Counters* c);
+// t /= the filter operator's eigenvalue of each node's mode in the per-axis cosine basis (lam: 1D
+// stiffness, mu: 1D mass eigenvalues of x, y, z; r2: the filter's r^2).
+cudaError_t launch_filter_scale(const Grid& g, float* t, const float* const lam[3], const float* const mu[3],
+                                float r2, cudaStream_t st, Counters* c);
 // b = T^T g with g = gamma on design elements, 1 on heated and 0 on fluid elements (passive=true) or
 // g = gamma everywhere (passive=false).
 cudaError_t launch_filter_rhs(const Grid& g, const Phys& ph, bool passive, const double* gamma, double scale_elem,

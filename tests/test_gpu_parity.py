@@ -66,6 +66,25 @@ def test_design_fields(lib, shape, alpha, seed):
 
 
 @pytest.mark.parametrize("shape,alpha,seed", CASES)
+def test_design_fields_both_filter_solvers(lib, shape, alpha, seed):
+    """The filtered design from the spectral inner solve and from the Chebyshev one (both inside the
+    FP64 refinement) equals the oracle's direct filter to 1e-10, and the two agree to 1e-10; the
+    filter transpose through the sensitivities agrees between them to 1e-9."""
+    out = {}
+    for method in (lib.NC_FILTER_SPECTRAL, lib.NC_FILTER_CHEBYSHEV):
+        gp, op, _ = make_pair(lib, shape, alpha, seed, filter_method=method)
+        gt = gp.design_fields()[0].cpu().numpy()
+        assert np.abs(gt - op.gamma_t).max() < 1e-10
+        gp.solve_state()
+        gp.solve_adjoint()
+        out[method] = (gt, gp.sensitivities().cpu().numpy())
+        gp.close()
+    a, b = out[lib.NC_FILTER_SPECTRAL], out[lib.NC_FILTER_CHEBYSHEV]
+    assert np.abs(a[0] - b[0]).max() < 1e-10
+    assert rel(a[1], b[1]) < 1e-9
+
+
+@pytest.mark.parametrize("shape,alpha,seed", CASES)
 def test_residual(lib, shape, alpha, seed):
     gp, op, _ = make_pair(lib, shape, alpha, seed)
     for trial in range(2):
