@@ -198,6 +198,9 @@ typedef struct {
                            block Jacobi): NC_SMOOTH_BLOCK_JACOBI or NC_SMOOTH_ZLINE. Fixed at creation;
                            NC_SMOOTH_ZLINE needs mg_tail_nodes = 0 [NC_SMOOTH_BLOCK_JACOBI] */
   int filter_method;    /* NC_FILTER_SPECTRAL or NC_FILTER_CHEBYSHEV [NC_FILTER_SPECTRAL] */
+  int mg_galerkin;      /* NC_PREC_MIXED only: the element operator whose Galerkin products form the
+                           multigrid levels below the finest (and whose block diagonal smooths the
+                           finest), NC_MGOP_EXACT (J(s)) or NC_MGOP_PICARD [NC_MGOP_PICARD] */
 } nc_params;
 
 /* Per-solve statistics (any pointer argument of this type may be NULL). */

@@ -72,7 +72,7 @@ class Params(ctypes.Structure):
         ("heat_radius", ctypes.c_double), ("design_radius", ctypes.c_double), ("heat_z0", ctypes.c_int),
         ("mg_op0", ctypes.c_int), ("mg_tail_ctas", ctypes.c_int), ("elem_chunk", ctypes.c_int),
         ("mg_nu_coarse", ctypes.c_int), ("mg_nu_coarse_level", ctypes.c_int),
-        ("mg_smoother", ctypes.c_int), ("filter_method", ctypes.c_int),
+        ("mg_smoother", ctypes.c_int), ("filter_method", ctypes.c_int), ("mg_galerkin", ctypes.c_int),
     ]
 
     def as_dict(self):

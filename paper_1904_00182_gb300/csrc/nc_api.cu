@@ -531,8 +531,10 @@ nc_status mg_setup(nc_problem* pb, bool refactor) {
   for (int l = 0; l < L - 1; ++l) CK(cudaMemsetAsync(mg.lev[l].dinv, 0, sizeof(R) * 4 * mg.lev[l].g.nn, pb->st));
   CK(cudaMemsetAsync(pb->dflag, 0, sizeof(int), pb->st));
   if (L == 1) return fail(pb, NC_ERR_ARG, "grid dimensions must be even for the multigrid hierarchy");
+  // the hierarchy of the frozen-coefficient operator (mixed precision, mg_galerkin = NC_MGOP_PICARD) or of J(s)
+  const bool gal_picard = sizeof(R) == 4 && pb->par.mg_galerkin == NC_MGOP_PICARD;
   PCK(NC_PROF_MG_SETUP, launch_galerkin_fine<R>(mg.lev[0].g, mg.lev[1].g, pb->ph, mg_state<R>(pb), mg_mat<R>(pb), mg.lev[0].dinv,
-                             mg.lev[1].ebe, pb->st, &pb->cnt));
+                             mg.lev[1].ebe, pb->st, &pb->cnt, gal_picard));
   for (int l = 1; l < L - 1; ++l)
     PCK(NC_PROF_MG_COARSE_SETUP, launch_galerkin_coarse<R>(mg.lev[l].g, mg.lev[l + 1].g, mg.lev[l].ebe, mg.lev[l].dinv, mg.lev[l + 1].ebe,
                                  pb->st, &pb->cnt));
@@ -1144,6 +1146,7 @@ nc_status validate(const nc_grid* g, const nc_params* p, std::string* why) {
   if (p->mg_nu_coarse_level < 0) { *why = "mg_nu_coarse_level must be >= 0"; return NC_ERR_ARG; }
   if (p->mg_smoother != NC_SMOOTH_BLOCK_JACOBI && p->mg_smoother != NC_SMOOTH_ZLINE) { *why = "unknown mg_smoother"; return NC_ERR_ARG; }
   if (p->filter_method != NC_FILTER_SPECTRAL && p->filter_method != NC_FILTER_CHEBYSHEV) { *why = "unknown filter_method"; return NC_ERR_ARG; }
+  if (p->mg_galerkin != NC_MGOP_EXACT && p->mg_galerkin != NC_MGOP_PICARD) { *why = "unknown mg_galerkin"; return NC_ERR_ARG; }
   if (p->mg_smoother == NC_SMOOTH_ZLINE && p->mg_tail_nodes > 0) {
     *why = "the fused multigrid tail smooths with block Jacobi (NC_SMOOTH_ZLINE needs mg_tail_nodes = 0)"; return NC_ERR_ARG;
   }
@@ -1195,6 +1198,7 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
   for (const int n1 : {gr->nx, gr->ny, gr->nz})   // spectral filter: cosine matrix and 1D eigenvalues per axis
     b += al(4 * (size_t)(n1 + 1) * (n1 + 1)) + 2 * al(4 * (size_t)(n1 + 1));
   b += al(kBlasWorkspace);
+  b += size_t(64) << 20;   // the cuBLAS handle's own device allocations (measured: about 64 MiB)
   const size_t rs = p->precision == NC_PREC_FP64 ? 8 : 4;
   for (size_t l = 0; l < lv.g.size(); ++l) {
     b += 4 * al(2 * rs * lv.g[l].nn);
@@ -1340,6 +1344,7 @@ nc_status nc_default_params(nc_params* p) {
   p->mg_op0 = NC_MGOP_PICARD;
   p->mg_smoother = NC_SMOOTH_BLOCK_JACOBI;
   p->filter_method = NC_FILTER_SPECTRAL;
+  p->mg_galerkin = NC_MGOP_PICARD;
   p->elem_chunk = -1;
   p->mg_reuse_below = 1e-2;
   p->adjoint_df64_steps = 1;

@@ -111,7 +111,9 @@ __device__ __forceinline__ void galerkin_phase2(R (*Jc)[16 * NC_LD], R (*Tc)[16 
 #define NC_GALERKIN_CPT 4
 #endif
 
-template <typename R>
+// PIC: the element matrices of the frozen-coefficient operator (its u0 and tau from the same element
+// state), columns by elem_picard_modal on unit directions; otherwise those of the exact J(s).
+template <typename R, bool PIC>
 __global__ void __launch_bounds__(128 / NC_GALERKIN_CPT) k_galerkin_fine(Grid gf, Grid gc, Phys ph, ElemConst<R> C,
                                                        const typename Vec2<R>::type* __restrict__ s,
                                                        const typename Vec2<R>::type* __restrict__ mat,
@@ -139,7 +141,14 @@ __global__ void __launch_bounds__(128 / NC_GALERKIN_CPT) k_galerkin_fine(Grid gf
   for (int cc = 0; cc < NC_GALERKIN_CPT; ++cc) {
     const int col = col0 + cc * kCols;
     R oP[8], oT[8];
-    elem_jac_column<R>(C, st, m.y, col, oP, oT);
+    if constexpr (PIC) {
+      R dp[8], dt[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { dp[q] = R(q == col ? 1 : 0); dt[q] = R(q + 8 == col ? 1 : 0); }
+      elem_picard_modal<R, false>(C, st.c, m.y, st.u0x, st.u0y, st.u0z, st.tau, dp, dt, oP, oT);
+    } else {
+      elem_jac_column<R>(C, st, m.y, col, oP, oT);
+    }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       Jc[c][r * NC_LD + col] = oP[r];
@@ -1289,13 +1298,18 @@ __global__ void __launch_bounds__(1024, 1) k_mg_tail(const TailArgs<R> A) {
 template <typename R>
 cudaError_t launch_galerkin_fine(const Grid& gf, const Grid& gc, const Phys& ph, const typename Vec2<R>::type* s,
                                  const typename Vec2<R>::type* mat, R* diag_f, R* ebe_c, cudaStream_t st,
-                                 Counters* c) {
-  k_galerkin_fine<R><<<(unsigned)gc.ne, 128 / NC_GALERKIN_CPT, 0, st>>>(gf, gc, ph, make_econst<R>(ph), s, mat, diag_f,
-                                                                      ebe_c);
+                                 Counters* c, bool picard) {
+  if (picard)
+    k_galerkin_fine<R, true><<<(unsigned)gc.ne, 128 / NC_GALERKIN_CPT, 0, st>>>(gf, gc, ph, make_econst<R>(ph), s, mat,
+                                                                              diag_f, ebe_c);
+  else
+    k_galerkin_fine<R, false><<<(unsigned)gc.ne, 128 / NC_GALERKIN_CPT, 0, st>>>(gf, gc, ph, make_econst<R>(ph), s, mat,
+                                                                               diag_f, ebe_c);
   if (c) {
     c->launches += 1;
     c->bytes += sizeof(R) * (2.0 * gf.nn + 2.0 * gf.ne + 4.0 * gf.nn + 256.0 * gc.ne);
-    c->flops += (kFlopsState + 16.0 * flops_jac_column<R>()) * gf.ne;   // one element state, 16 columns
+    // one element state, 16 columns
+    c->flops += (kFlopsState + 16.0 * (picard ? kFlopsPicardModal : flops_jac_column<R>())) * gf.ne;
   }
   return cudaGetLastError();
 }
@@ -1636,7 +1650,7 @@ cudaError_t launch_line_smooth(const Grid& g, const R* LF, const typename Vec2<R
 
 #define NC_INSTANTIATE_MG(R)                                                                                    \
   template cudaError_t launch_galerkin_fine<R>(const Grid&, const Grid&, const Phys&, const Vec2<R>::type*,   \
-                                               const Vec2<R>::type*, R*, R*, cudaStream_t, Counters*);         \
+                                               const Vec2<R>::type*, R*, R*, cudaStream_t, Counters*, bool);   \
   template cudaError_t launch_galerkin_coarse<R>(const Grid&, const Grid&, const R*, R*, R*, cudaStream_t,    \
                                                  Counters*);                                                   \
   template cudaError_t launch_invert_diag<R>(const Grid&, R*, int*, cudaStream_t, Counters*);                 \

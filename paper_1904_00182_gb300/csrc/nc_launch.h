@@ -256,12 +256,13 @@ template <typename R> struct TailArgs {
 template <typename R>
 cudaError_t launch_mg_tail(const TailArgs<R>& a, bool transpose, cudaStream_t st, Counters* c);
 
-// Level-0 set-up: element Jacobians of J(s) (R arithmetic) -> block diagonal of level 0 and
-// Galerkin element matrices of level 1 (P^T J P with trilinear P).
+// Level-0 set-up: element matrices of J(s) (picard: of the frozen-coefficient operator at s) in R
+// arithmetic -> block diagonal of level 0 and Galerkin element matrices of level 1 (P^T A P with
+// trilinear P).
 template <typename R>
 cudaError_t launch_galerkin_fine(const Grid& gf, const Grid& gc, const Phys& ph,
                                  const typename Vec2<R>::type* s, const typename Vec2<R>::type* mat,
-                                 R* diag_f, R* ebe_c, cudaStream_t st, Counters* c);
+                                 R* diag_f, R* ebe_c, cudaStream_t st, Counters* c, bool picard = false);
 // Level l -> l+1 Galerkin from stored element matrices; accumulates the block diagonal of level l.
 template <typename R>
 cudaError_t launch_galerkin_coarse(const Grid& gf, const Grid& gc, const R* ebe_f, R* diag_f, R* ebe_c,

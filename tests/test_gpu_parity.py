@@ -155,6 +155,7 @@ VARIANTS = {"fp64": (1, 1e-8, {}), "mixed": (0, 1e-6, {}),
             "mixed_fp64_refinement": (0, 1e-6, {"adjoint_df64_steps": 0}),
             "mixed_fast": (0, 1e-6, {"outer_arith": 0, "krylov_basis": 1}),
             "mixed_exact_mg": (0, 1e-6, {"mg_op0": 0}),
+            "mixed_exact_galerkin": (0, 1e-6, {"mg_galerkin": 0}),
             "mixed_coarse_sweeps": (0, 1e-6, {"mg_nu_coarse": 8, "nu_pre": 2}),
             "mixed_zline": (0, 1e-6, {"mg_smoother": 1}),
             "fp64_zline": (1, 1e-8, {"mg_smoother": 1})}
