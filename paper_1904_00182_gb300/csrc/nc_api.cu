@@ -29,6 +29,7 @@ namespace {
 const int kMaxRestart = 64;
 const size_t kBlasWorkspace = 32u << 20;   // cuBLAS workspace of the spectral filter transforms
 
+
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }

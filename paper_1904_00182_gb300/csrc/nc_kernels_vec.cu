@@ -395,13 +395,14 @@ __global__ void k_ramp(const double* __restrict__ gt, long long n, RampConst r, 
                        double2* __restrict__ dmat, float2* __restrict__ mat32) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
+    // one division per denominator (FP64 divisions dominate this kernel)
     const double x = gt[e];
-    const double dc = 1.0 + r.q_c * (1.0 - x);
-    const double k = r.k_f + x / dc * (r.k_s - r.k_f);
-    const double dk = (r.k_s - r.k_f) * (1.0 + r.q_c) / (dc * dc);
-    const double dp = 1.0 + r.q_p * x;
-    const double kap = r.kappa_s + (1.0 - x) / dp * (r.kappa_f - r.kappa_s);
-    const double dkap = -(r.kappa_f - r.kappa_s) * (1.0 + r.q_p) / (dp * dp);
+    const double idc = 1.0 / (1.0 + r.q_c * (1.0 - x));
+    const double k = r.k_f + x * idc * (r.k_s - r.k_f);
+    const double dk = (r.k_s - r.k_f) * (1.0 + r.q_c) * (idc * idc);
+    const double idp = 1.0 / (1.0 + r.q_p * x);
+    const double kap = r.kappa_s + (1.0 - x) * idp * (r.kappa_f - r.kappa_s);
+    const double dkap = -(r.kappa_f - r.kappa_s) * (1.0 + r.q_p) * (idp * idp);
     mat[e] = make_double2(kap, k);
     dmat[e] = make_double2(dkap, dk);
     mat32[e] = make_float2((float)kap, (float)k);
