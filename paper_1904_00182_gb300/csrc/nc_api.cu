@@ -116,6 +116,8 @@ struct nc_problem {
   float *fxf = nullptr, *frf = nullptr, *fd0 = nullptr, *fd1 = nullptr, *fdinvf = nullptr;
   FilterConst F;
   FilterConstF Ff;
+  FilterConstDF Fd;                   // the filter element constants in double-float
+  df64 *fxd = nullptr, *fbd = nullptr; // double-float solution and right-hand side of the refinement
   double cheb_a = 0.0, cheb_b = 0.0;   // bounds of the spectrum of D^-1 (r^2 K + M)
   int cheb_iters = 0;                  // FP32 Chebyshev steps per refinement pass
   // spectral filter solve: per axis the cosine matrix C_ij = cos(pi i j / n) (FP32, symmetric) and
@@ -372,6 +374,10 @@ nc_status spectral_setup(nc_problem* pb) {
   return NC_OK;
 }
 
+// The filter system solved to filter_rtol by iterative refinement around an FP32 inner solve
+// (spectral or Chebyshev). On the mixed-precision path, with filter_rtol >= 1e-13, the refinement
+// keeps its solution and forms its residual in double-float arithmetic (about 48 significant bits:
+// the residual's rounding stays near 1e-14 of its terms) on the FP32 pipes; otherwise in FP64.
 nc_status filter_solve(nc_problem* pb) {
   const Grid& g = pb->g;
   const long long n = g.nn;
@@ -379,12 +385,18 @@ nc_status filter_solve(nc_problem* pb) {
   CKS(dots(pb, pb->fb, 0, 1, pb->fb, n, &bb));
   PCK(NC_PROF_FILTER, cudaMemsetAsync(pb->fx, 0, sizeof(double) * n, pb->st));
   if (bb == 0.0) return NC_OK;
-  CK(cudaMemcpyAsync(pb->fr, pb->fb, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
+  const bool df = pb->par.precision != NC_PREC_FP64 && pb->par.filter_rtol >= 1e-13;
+  if (df) {
+    PCK(NC_PROF_FILTER, launch_filter_df(0, g, nullptr, pb->fb, pb->fbd, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                         pb->st, &pb->cnt));
+    PCK(NC_PROF_FILTER, cudaMemsetAsync(pb->fxd, 0, sizeof(df64) * n, pb->st));
+  }
+  PCK(NC_PROF_FILTER, launch_cast_d2f(pb->frf, pb->fb, n, pb->st, &pb->cnt));
   const double a = pb->cheb_a, b = pb->cheb_b;
   const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
   const double tol2 = pb->par.filter_rtol * pb->par.filter_rtol * bb;
   for (int pass = 0; pass < 12; ++pass) {
-    PCK(NC_PROF_FILTER, launch_cast_d2f(pb->frf, pb->fr, n, pb->st, &pb->cnt));
+    // correction fxf from the FP32 residual frf
     if (pb->par.filter_method == NC_FILTER_SPECTRAL) {
       PCK(NC_PROF_FILTER, spectral_filter(pb, pb->frf, pb->fxf));
     } else {
@@ -401,14 +413,27 @@ nc_status filter_solve(nc_problem* pb) {
         std::swap(d0, d1);
       }
     }
-    PCK(NC_PROF_FILTER, launch_add_f2d(pb->fx, pb->fxf, n, pb->st, &pb->cnt));
-    PCK(NC_PROF_FILTER, launch_helmholtz(g, pb->F, pb->fx, pb->fq, pb->st, &pb->cnt));
-    CK(cudaMemcpyAsync(pb->fr, pb->fb, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
-    PCK(NC_PROF_FILTER, launch_axpby(pb->fr, pb->fq, -1.0, 1.0, n, pb->st, &pb->cnt));
+    if (df) {
+      PCK(NC_PROF_FILTER, launch_filter_df(1, g, nullptr, nullptr, nullptr, pb->fxd, pb->fxf, nullptr, nullptr, nullptr,
+                                           pb->st, &pb->cnt));
+      PCK(NC_PROF_FILTER, launch_filter_df(2, g, &pb->Fd, nullptr, pb->fbd, pb->fxd, nullptr, pb->frf, pb->fr, nullptr,
+                                           pb->st, &pb->cnt));
+    } else {
+      PCK(NC_PROF_FILTER, launch_add_f2d(pb->fx, pb->fxf, n, pb->st, &pb->cnt));
+      PCK(NC_PROF_FILTER, launch_helmholtz(g, pb->F, pb->fx, pb->fq, pb->st, &pb->cnt));
+      CK(cudaMemcpyAsync(pb->fr, pb->fb, sizeof(double) * n, cudaMemcpyDeviceToDevice, pb->st));
+      PCK(NC_PROF_FILTER, launch_axpby(pb->fr, pb->fq, -1.0, 1.0, n, pb->st, &pb->cnt));
+      PCK(NC_PROF_FILTER, launch_cast_d2f(pb->frf, pb->fr, n, pb->st, &pb->cnt));
+    }
     double rr;
     CKS(dots(pb, pb->fr, 0, 1, pb->fr, n, &rr));
     if (!std::isfinite(rr)) return fail(pb, NC_ERR_NAN, "non-finite residual in the filter solve");
-    if (rr <= tol2) return NC_OK;
+    if (rr <= tol2) {
+      if (df)
+        PCK(NC_PROF_FILTER, launch_filter_df(3, g, nullptr, nullptr, nullptr, pb->fxd, nullptr, nullptr, nullptr, pb->fx,
+                                             pb->st, &pb->cnt));
+      return NC_OK;
+    }
   }
   return fail(pb, NC_ERR_MAXIT, "filter refinement did not converge");
 }
@@ -1195,7 +1220,7 @@ size_t footprint(const nc_grid* gr, const nc_params* p) {
   b += al(2 * ks * nn * (m + 1)) + al(2 * ks * nn * m);     // V, Z
   if (p->precision != NC_PREC_FP64) b += al(16 * ne) + 2 * al(16 * nn);   // mat_df, s_df, w_df
   b += al(8 * 66 * kReduceBlocksMax) + al(8 * 132);
-  b += 5 * al(8 * nn) + 5 * al(4 * nn); // filter vectors
+  b += 5 * al(8 * nn) + 5 * al(4 * nn) + 2 * al(8 * nn); // filter vectors (+ double-float solution, rhs)
   for (const int n1 : {gr->nx, gr->ny, gr->nz})   // spectral filter: cosine matrix and 1D eigenvalues per axis
     b += al(4 * (size_t)(n1 + 1) * (n1 + 1)) + 2 * al(4 * (size_t)(n1 + 1));
   b += al(kBlasWorkspace);
@@ -1278,6 +1303,8 @@ void apply_params(nc_problem* pb, const nc_params* p) {
     pb->F.t0 = g.h * g.h * g.h / 8.0;
     for (int q = 0; q < 64; ++q) pb->Ff.A[q] = (float)pb->F.A[q];
     for (int q = 0; q < 27; ++q) pb->Ff.C27[q] = (float)pb->F.C27[q];
+    for (int q = 0; q < 64; ++q) pb->Fd.A[q] = df64(pb->F.A[q]);
+    for (int q = 0; q < 27; ++q) pb->Fd.C27[q] = df64(pb->F.C27[q]);
     // spectrum of D^-1 A from the interior symbol sum_o C27[o] cos(theta . o) / C27[centre]
     // (Neumann boundaries do not widen it), widened by 5 % on each side
     double lmin = 1e300, lmax = -1e300;
@@ -1404,6 +1431,7 @@ nc_status nc_create_problem(const nc_grid* gr, const nc_params* p, void* stream,
   A(dalloc(pb, &pb->fq, nn)); A(dalloc(pb, &pb->fdinv, nn));
   A(dalloc(pb, &pb->fxf, nn)); A(dalloc(pb, &pb->frf, nn)); A(dalloc(pb, &pb->fd0, nn)); A(dalloc(pb, &pb->fd1, nn));
   A(dalloc(pb, &pb->fdinvf, nn));
+  A(dalloc(pb, &pb->fxd, nn)); A(dalloc(pb, &pb->fbd, nn));
   A(dalloc(pb, &pb->dflag, 1));
   if (s == NC_OK) s = spectral_setup(pb);
   if (s == NC_OK) s = p->precision == NC_PREC_FP64 ? mg_alloc<double>(pb) : mg_alloc<float>(pb);

@@ -360,6 +360,35 @@ __global__ void k_cheb_step(Grid g, FilterConstF F, const float* __restrict__ di
   dn[n] = c1 * dv + c2 * dinv[n] * rv;
 }
 
+// ---- double-float refinement of the filter solve ----
+// b (FP64) -> double-float; the FP32 correction added to the double-float solution; the residual
+// r = b - (r^2 K + M) x in double-float arithmetic (element constants in double-float), stored as
+// its FP32 leading part (the next inner solve's right-hand side) and as FP64 (for its norm); the
+// solution back to FP64.
+__global__ void k_d2df(const double* __restrict__ b, df64* __restrict__ bd, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    bd[t] = df_from_double(b[t]);
+}
+
+__global__ void k_add_df(df64* __restrict__ x, const float* __restrict__ dx, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    x[t] = x[t] + df64(dx[t], 0.0f);
+}
+
+__global__ void k_helm_res_df(Grid g, FilterConstDF F, const df64* __restrict__ b, const df64* __restrict__ x,
+                              float* __restrict__ rf, double* __restrict__ r64) {
+  NC_NODE_FLAT(g);
+  const int n = pidx + g.NXY * k;
+  const df64 r = b[n] - helm_node<df64>(g, F, x, i, j, k, n);
+  rf[n] = r.hi;
+  r64[n] = (double)r.hi + (double)r.lo;
+}
+
+__global__ void k_df2d(const df64* __restrict__ x, double* __restrict__ y, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    y[t] = (double)x[t].hi + (double)x[t].lo;
+}
+
 __global__ void k_add_f2d(double* __restrict__ y, const float* __restrict__ x, long long n) {
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
@@ -691,6 +720,24 @@ cudaError_t launch_filter_scale(const Grid& g, float* t, const float* const lam[
   const Launch3 L = launch_nodes_flat(g);
   k_filter_scale<<<L.grid, L.block, 0, st>>>(g, t, lam[0], mu[0], lam[1], mu[1], lam[2], mu[2], r2);
   if (c) { c->launches += 1; c->bytes += 8.0 * g.nn; }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filter_df(int op, const Grid& g, const FilterConstDF* F, const double* b64, df64* bd, df64* x,
+                             const float* dx, float* rf, double* r64, double* y64, cudaStream_t st, Counters* c) {
+  const long long n = g.nn;
+  switch (op) {
+    case 0: k_d2df<<<stream_blocks(n), 256, 0, st>>>(b64, bd, n); if (c) c->bytes += 16.0 * n; break;
+    case 1: k_add_df<<<stream_blocks(n), 256, 0, st>>>(x, dx, n); if (c) c->bytes += 20.0 * n; break;
+    case 2: {
+      const Launch3 L = launch_nodes_flat(g);
+      k_helm_res_df<<<L.grid, L.block, 0, st>>>(g, *F, bd, x, rf, r64);
+      if (c) c->bytes += 28.0 * n;
+      break;
+    }
+    default: k_df2d<<<stream_blocks(n), 256, 0, st>>>(x, y64, n); if (c) c->bytes += 16.0 * n; break;
+  }
+  if (c) c->launches += 1;
   return cudaGetLastError();
 }
 

@@ -181,6 +181,11 @@ cudaError_t launch_check_design(const double* rho, long long ne, int* flag, cuda
 // Filter pieces (Helmholtz (r^2 K + M) x = T^T gamma, Q1 nodal, element mean out).
 struct FilterConst { double A[64]; double C27[27]; double t0; double diag; };
 struct FilterConstF { float A[64]; float C27[27]; };
+struct FilterConstDF { df64 A[64]; df64 C27[27]; };
+// Double-float refinement steps of the filter solve (op): 0 bd = b64 in double-float; 1 x += dx;
+// 2 r = bd - (r^2 K + M) x in double-float, rf = its FP32 leading part, r64 = r in FP64; 3 y64 = x.
+cudaError_t launch_filter_df(int op, const Grid& g, const FilterConstDF* F, const double* b64, df64* bd, df64* x,
+                             const float* dx, float* rf, double* r64, double* y64, cudaStream_t st, Counters* c);
 // y = (r^2 K + M) x (FP64 residual with F; FP32 inside the Chebyshev step with Ff); Chebyshev iteration
 // in FP32 on D^-1 (r^2 K + M):
 //   init: x = 0, d = c0 dinv r;   step: x += d, r -= A d, dn = c1 d + c2 dinv r
