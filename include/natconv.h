@@ -139,7 +139,9 @@ typedef struct {
   int mg_levels;        /* 0: coarsen while every dimension is even [0] */
   int nu_pre, nu_post;  /* smoothing sweeps; the first pre-sweep starts from x = 0 [1, 2] */
   double omega;         /* damping of the block-Jacobi smoother [0.9] */
-  double filter_rtol;   /* relative residual tolerance of the filter solve [1e-12] */
+  double filter_rtol;   /* relative residual tolerance of the filter solve; on NC_PREC_MIXED with
+                           filter_rtol >= 1e-13 its refinement runs in double-float (about 48
+                           significant bits), otherwise in FP64 [1e-12] */
   double timeout_s;     /* wall-clock limit of one call [600] */
   double adjoint_rtol;  /* adjoint stops at ||df/ds - J^T lambda|| <= adjoint_rtol ||df/ds||;
                            <= 0: the state's newton_rtol [0] */
