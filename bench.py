@@ -308,8 +308,8 @@ SINGLE_KERNEL_CLASSES = ("residual", "outer_op64", "mg_op0", "mg_op0_picard", "m
 NCU_TRAFFIC_128 = {
     "residual": (110.47e6, "profiles/k_residual_fp64_128cubed.md"),
     "outer_op64": (171.59e6, "profiles/k_jprod_transpose_fp64_128cubed.md"),
-    "mg_op0": (69.03e6, "profiles/k_level0_apply_float_128cubed.md"),
-    "mg_op0_picard": (86.77e6, "profiles/k_level0_picard_float_128cubed.md"),
+    "mg_op0": (69.80e6, "profiles/k_level0_apply_float_128cubed.md"),
+    "mg_op0_picard": (86.72e6, "profiles/k_level0_picard_float_128cubed.md"),
 }
 
 
