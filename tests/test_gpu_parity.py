@@ -242,15 +242,18 @@ def test_other_parameters_and_warm_start(lib, precision):
     """Parameters off the defaults (3 heated layers, filter radius 1.5, alpha 1e5, conductivity
     ratio 10, RAMP q_c 0.881) on the ragged 12 x 10 x 6 box against the oracle, then a warm start
     (Sec. 5.4) from the solution of a neighbouring design reaching the same state as a cold start.
-    Both solves stop at a relative residual of 1e-10; at alpha = 1e5 the pressure (about -4e3,
-    mostly hydrostatic) amplifies that residual about 1e3-fold, so the states are compared at 1e-6 and
-    the FP64 path is held instead to the oracle's own residual at the GPU state (<= 1e-9 of R(0))."""
+    At alpha = 1e5 the pressure (about -4e3, mostly hydrostatic) amplifies the stopping residual about
+    1e3-fold in the state, so the FP64 path solves (GPU and oracle) to a relative residual of 1e-12 and
+    is held to the 1e-8 state tolerance, the mixed path to 1e-10 and 1e-6; both are also held to the
+    oracle's own residual at the GPU state."""
     nx, ny, nz = 12, 10, 6
     h = 1.0 / nz
     kw = dict(alpha=1e5, heated_layers=3, filter_radius=1.5, k_s=10.0, q_c=0.881)
     rho = filtered_random(nx, ny, nz, 4, volfrac=0.3)
-    gp = lib.Problem(nx, ny, nz, h, precision=precision, newton_rtol=1e-10, **kw)
-    op = oracle.Problem(oracle.Mesh(nx, ny, nz, h), oracle.Params(newton_rtol=1e-10, **kw))
+    rtol = 1e-12 if precision == 1 else 1e-10
+    tol = 1e-8 if precision == 1 else 1e-6
+    gp = lib.Problem(nx, ny, nz, h, precision=precision, newton_rtol=rtol, **kw)
+    op = oracle.Problem(oracle.Mesh(nx, ny, nz, h), oracle.Params(newton_rtol=rtol, **kw))
     gp.set_design(rho)
     op.set_design(rho)
     gt, _, _ = gp.design_fields()
@@ -259,16 +262,15 @@ def test_other_parameters_and_warm_start(lib, precision):
     op.solve_state()
     P, T, u = gp.get_fields()
     Po, To = op.fields()
-    tol = 1e-6
     assert rel(P.cpu().numpy(), Po) < tol and rel(T.cpu().numpy(), To) < tol
     s = np.empty(2 * op.mesh.n_nodes)
     s[0::2], s[1::2] = P.cpu().numpy(), T.cpu().numpy()
     R = op.residual(s)
-    assert np.linalg.norm(R[op.free]) <= 1e-9 * op.reference_norm()
+    assert np.linalg.norm(R[op.free]) <= (1e-11 if precision == 1 else 1e-9) * op.reference_norm()
     f, _ = gp.solve_adjoint()
     assert f == pytest.approx(op.objective(), rel=tol)
     op.solve_adjoint()
-    assert rel(gp.sensitivities().cpu().numpy(), op.sensitivities()) < 1e-6
+    assert rel(gp.sensitivities().cpu().numpy(), op.sensitivities()) < (1e-8 if precision == 1 else 1e-6)
     # warm start: solve a perturbed design cold, then return to rho starting from that state
     rho2 = np.clip(rho + 0.05 * np.random.default_rng(9).standard_normal(rho.size), 0.0, 1.0)
     gp.set_design(rho2)
@@ -279,5 +281,5 @@ def test_other_parameters_and_warm_start(lib, precision):
     st = gp.solve_state()
     Pw, Tw, _ = gp.get_fields(velocity=False)
     assert rel(Pw.cpu().numpy(), Po) < tol and rel(Tw.cpu().numpy(), To) < tol
-    assert st["rel_residual"] <= 1e-10
+    assert st["rel_residual"] <= rtol
     gp.close()
